@@ -1,0 +1,179 @@
+"""Seeded synthetic scenes: the inputs both the CUDA path and the oracle consume.
+
+This module only draws room geometry; it holds none of the method's arithmetic (no
+reflection coefficients, no image sampling, no synthesis).  Draws use numpy's PCG64
+generator seeded explicitly, and every array is float32 -- the precision the library takes.
+
+The workloads follow the paper's training distribution (Sec. IV-A: speaker-array distance
+at least 0.3 m, T60 in [0.1, 0.7] s, shoebox rooms from 3x3x2.5 to 10x10x4 m) and the
+benchmark workloads built on it:
+
+  single_room()  6x5x3 m, T60 0.5 s, 16 kHz, one source at (2, 3, 1.5), 4-mic linear array
+                 (5 cm spacing along +x) centred at (4, 2.5, 1.2), 2000 images, K = 40.
+  batch_256()    256 rooms U[3,10]x U[3,8]x U[2.5,4.5] m, T60 U[0.1,0.7] s, 6-mic circular
+                 array (radius 5 cm) >= 0.5 m from the walls, 1 source, round(4000*T60)
+                 images, 16 kHz, K = 40.
+  batch_1024()   as batch_256 with 1024 rooms, 8-mic circle (4 cm), 3 sources.
+  grad_64()      64 rooms, 4-mic linear array (5 cm), T60 U[0.2,0.6] s, 1500 images, K = 40.
+  large_4096()   4096 rooms U[3,15]x U[3,12]x U[2.5,6] m, T60 U[0.2,1.2] s, 16-mic circle
+                 (10 cm), 2 sources, round(6000*T60) images, 48 kHz, K = 63.
+  tiny(...)      small scenes for exhaustive CPU/GPU comparisons.
+
+Conventions: linear arrays lie along +x centred on the array point; circular arrays lie in
+the horizontal plane with mic k at angle 2*pi*k/M + psi, psi drawn per room.  A source
+closer than 0.3 m to the array centre is redrawn (up to 16 attempts, then pushed radially).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Scene:
+    name: str
+    B: int
+    S: int
+    M: int
+    fs: float
+    half_len: int
+    dims: np.ndarray     # [B,3] float32, metres
+    rt60: np.ndarray     # [B] float32, seconds
+    src: np.ndarray      # [B,S,3] float32
+    mic: np.ndarray      # [B,M,3] float32
+    n_vs: np.ndarray     # [B] int32, images per (room, source)
+    meta: dict = field(default_factory=dict)
+
+    def subset(self, rooms) -> "Scene":
+        """The scene restricted to the given room indices (same order)."""
+        rooms = np.asarray(rooms, dtype=np.int64)
+        return Scene(self.name + f"[{len(rooms)} rooms]", len(rooms), self.S, self.M, self.fs,
+                     self.half_len, self.dims[rooms].copy(), self.rt60[rooms].copy(),
+                     self.src[rooms].copy(), self.mic[rooms].copy(), self.n_vs[rooms].copy(),
+                     dict(self.meta, parent=self.name, rooms=rooms.tolist()))
+
+
+def _linear_array(centre, M, spacing):
+    off = (np.arange(M) - (M - 1) / 2.0) * spacing
+    pos = np.repeat(np.asarray(centre, np.float64)[None, :], M, axis=0)
+    pos[:, 0] += off
+    return pos
+
+
+def _circular_array(centre, M, radius, psi):
+    ang = 2.0 * np.pi * np.arange(M) / M + psi
+    pos = np.repeat(np.asarray(centre, np.float64)[None, :], M, axis=0)
+    pos[:, 0] += radius * np.cos(ang)
+    pos[:, 1] += radius * np.sin(ang)
+    return pos
+
+
+def _draw_sources(rng, dims, centre, S, min_dist=0.3, tries=16):
+    out = np.empty((S, 3))
+    for s in range(S):
+        for _ in range(tries):
+            p = rng.uniform(0.0, 1.0, 3) * dims
+            if np.linalg.norm(p - centre) >= min_dist:
+                break
+        else:
+            d = p - centre
+            n = np.linalg.norm(d)
+            d = d / n if n > 0 else np.array([1.0, 0.0, 0.0])
+            p = centre + min_dist * d
+        out[s] = p
+    return out
+
+
+def _batch(name, seed, B, S, M, geometry, radius, dims_lo, dims_hi, t60_lo, t60_hi, fs, K,
+           images_per_second=None, images_fixed=None):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dims = rng.uniform(dims_lo, dims_hi, size=(B, 3))
+    rt60 = rng.uniform(t60_lo, t60_hi, size=B).astype(np.float32)
+    mic = np.empty((B, M, 3))
+    src = np.empty((B, S, 3))
+    for b in range(B):
+        centre = rng.uniform(0.5, dims[b] - 0.5)
+        if geometry == "circular":
+            mic[b] = _circular_array(centre, M, radius, rng.uniform(0.0, 2.0 * np.pi))
+        else:
+            mic[b] = _linear_array(centre, M, radius)
+        src[b] = _draw_sources(rng, dims[b], mic[b].mean(axis=0), S)
+    if images_fixed is not None:
+        n_vs = np.full(B, images_fixed, np.int32)
+    else:
+        n_vs = np.floor(images_per_second * rt60.astype(np.float64) + 0.5).astype(np.int32)
+    return Scene(name, B, S, M, float(fs), int(K), dims.astype(np.float32), rt60,
+                 src.astype(np.float32), mic.astype(np.float32), n_vs,
+                 dict(seed=seed, geometry=geometry, radius=radius))
+
+
+def single_room() -> Scene:
+    """6x5x3 m, T60 0.5 s, one source, 4-mic linear array, 2000 images, 16 kHz, K = 40."""
+    mic = _linear_array([4.0, 2.5, 1.2], 4, 0.05)
+    return Scene("single_room", 1, 1, 4, 16000.0, 40,
+                 np.array([[6.0, 5.0, 3.0]], np.float32), np.array([0.5], np.float32),
+                 np.array([[[2.0, 3.0, 1.5]]], np.float32), mic[None].astype(np.float32),
+                 np.array([2000], np.int32), dict(seed=None, geometry="linear", radius=0.05))
+
+
+def batch_256(seed: int = 0) -> Scene:
+    return _batch("batch_256", seed, 256, 1, 6, "circular", 0.05, [3, 3, 2.5], [10, 8, 4.5],
+                  0.1, 0.7, 16000, 40, images_per_second=4000)
+
+
+def batch_1024(seed: int = 0) -> Scene:
+    return _batch("batch_1024", seed, 1024, 3, 8, "circular", 0.04, [3, 3, 2.5], [10, 8, 4.5],
+                  0.1, 0.7, 16000, 40, images_per_second=4000)
+
+
+def grad_64(seed: int = 0) -> Scene:
+    return _batch("grad_64", seed, 64, 1, 4, "linear", 0.05, [3, 3, 2.5], [10, 8, 4.5],
+                  0.2, 0.6, 16000, 40, images_fixed=1500)
+
+
+def large_4096(seed: int = 0) -> Scene:
+    return _batch("large_4096", seed, 4096, 2, 16, "circular", 0.10, [3, 3, 2.5], [15, 12, 6],
+                  0.2, 1.2, 48000, 63, images_per_second=6000)
+
+
+def tiny(seed: int = 0, B: int = 3, S: int = 2, M: int = 3, images: int = 40, fs: float = 16000.0,
+         K: int = 40, t60_lo: float = 0.05, t60_hi: float = 0.12, geometry: str = "circular",
+         radius: float = 0.05) -> Scene:
+    """Small scenes (short RIRs, few images) for exhaustive comparisons."""
+    return _batch(f"tiny{seed}", seed, B, S, M, geometry, radius, [3, 3, 2.5], [6, 5, 3.5],
+                  t60_lo, t60_hi, fs, K, images_fixed=images)
+
+
+CONFIGS = {
+    "single_room": single_room,
+    "batch_256": batch_256,
+    "batch_1024": batch_1024,
+    "grad_64": grad_64,
+    "large_4096": large_4096,
+}
+
+
+def by_name(name: str, seed: int = 0) -> Scene:
+    fn = CONFIGS[name]
+    return fn() if name == "single_room" else fn(seed)
+
+
+def synthetic_vs(seed: int, scene: Scene, max_dist: float = 60.0):
+    """Arbitrary image positions and reflection counts for the Cartesian (user-supplied)
+    input path: positions uniform in direction and in distance from the array centre in
+    [0.5, max_dist] m, g uniform in [1, 40].  Returns (pos [N,3] f32, g [N] f32).  This is a
+    stand-in for user data, not the paper's sampler."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pos, g = [], []
+    for b in range(scene.B):
+        c = scene.mic[b].astype(np.float64).mean(axis=0)
+        n = scene.S * int(scene.n_vs[b])
+        d = rng.normal(size=(n, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        lim = min(max_dist, 0.95 * 343.0 * float(scene.rt60[b]))
+        rad = rng.uniform(0.5, lim, size=(n, 1))
+        pos.append(c + rad * d)
+        g.append(rng.uniform(1.0, 40.0, size=n))
+    return (np.concatenate(pos).astype(np.float32) if pos else np.zeros((0, 3), np.float32),
+            np.concatenate(g).astype(np.float32) if g else np.zeros(0, np.float32))

@@ -1,0 +1,167 @@
+"""Pins for the oracle's room statistics and virtual-source sampler (Sec. III-A to III-C).
+
+Each check comes from a statement of the paper or from textbook physics, not from the
+oracle's own formulas:
+  * Eq. 2 inverted through Eyring's reverberation-time formula T60 = -0.16 R / ln(1 - a)
+    recovers the requested T60 (a wrong sign, constant or square fails);
+  * Eq. 3 by a Kolmogorov-Smirnov test against the CDF of the stated PDF;
+  * Eq. 4 by the text's statement that DR is a linear map of x sending alpha -> 1 and
+    beta -> c0*T60/D0;
+  * Sec. III-B: images lie at distance D_i from the array centre, azimuth uniform on
+    [0, 2pi), elevation uniform on [-pi/2, pi/2];
+  * Eq. 5 by the 60 dB statement: the farthest image (distance c0*T60, RR_max reflections)
+    is 10^-3 of the direct path amplitude 1/D0;
+  * Eq. 6 by its end points and clamp, and by the recovered perturbation being U(a, b);
+  * counter-based draws: an image depends only on (seed, room, source, index).
+"""
+import numpy as np
+import pytest
+from scipy import stats
+
+from paper_2304_08052_gb300 import scenes
+
+
+def test_single_room_layout(oracle_mod):
+    sc = scenes.single_room()
+    rir_len, rir_off, vs_off = oracle_mod.layout(sc.rt60, sc.n_vs, sc.S, sc.M, sc.fs)
+    assert rir_len.tolist() == [8000]               # 0.5 s at 16 kHz
+    assert rir_off.tolist() == [0, 4 * 8000]
+    assert vs_off.tolist() == [0, 2000]
+
+
+def test_eyring_coefficient_inverts_to_requested_t60(oracle_mod):
+    rng = np.random.default_rng(0)
+    dims = rng.uniform([3, 3, 2.5], [15, 12, 6], size=(500, 3))
+    t60 = rng.uniform(0.05, 2.0, size=500)
+    R, r = oracle_mod.room_stats(dims, t60)
+    V = dims.prod(axis=1)
+    S = 2 * (dims[:, 0] * dims[:, 1] + dims[:, 0] * dims[:, 2] + dims[:, 1] * dims[:, 2])
+    assert np.allclose(R, V / S, rtol=1e-14)
+    assert np.all((r > 0) & (r < 1))
+    # Eq. 2 reads r = sqrt(1 - a^2) with a = 1 - exp(-0.16 R/T60) the mean absorption of
+    # Eyring's formula T60 = -0.16 V / (S ln(1 - a)); invert and recover T60.
+    mean_absorption = np.sqrt(1.0 - r ** 2)
+    t60_eyring = -0.16 * R / np.log(1.0 - mean_absorption)
+    assert np.allclose(t60_eyring, t60, rtol=1e-9)
+    # Longer reverberation -> stronger reflections; r -> 1 as T60 -> infinity.
+    _, r_long = oracle_mod.room_stats(np.array([[6.0, 5.0, 3.0]] * 3), np.array([0.5, 5.0, 5e4]))
+    assert r_long[0] < r_long[1] < r_long[2] and 1 - r_long[2] < 1e-5
+
+
+@pytest.fixture(scope="module")
+def big_draw(oracle_mod):
+    sc = scenes.tiny(seed=11, B=4, S=2, M=4, images=20000, t60_lo=0.3, t60_hi=0.9)
+    p = oracle_mod.Params(fs=sc.fs, half_len=sc.half_len)
+    return sc, p, oracle_mod.sample(sc, p, seed=12345)
+
+
+def _room_slices(sc):
+    n = sc.n_vs.astype(np.int64)
+    for b in range(sc.B):
+        for s in range(sc.S):
+            start = int(sc.S * n[:b].sum() + s * n[b])
+            yield b, s, slice(start, start + int(n[b]))
+
+
+def test_distance_ratio_follows_quadratic_pdf(big_draw):
+    sc, p, out = big_draw
+    a, b = p.alpha, p.beta
+    cdf = lambda x: (np.clip(x, a, b) ** 3 - a ** 3) / (b ** 3 - a ** 3)
+    for _, _, sl in _room_slices(sc):
+        x = out.x[sl]
+        assert np.all((x > a) & (x <= b))
+        assert stats.kstest(x, cdf).pvalue > 1e-4
+    # Mean of the quadratic PDF on (a, b]: 3/4 (b^4 - a^4)/(b^3 - a^3).
+    assert abs(out.x.mean() - 0.75 * (b ** 4 - a ** 4) / (b ** 3 - a ** 3)) < 3e-3
+
+
+def test_distance_ratio_is_linear_rescale_to_stated_range(oracle_mod, big_draw):
+    sc, p, out = big_draw
+    for b, s, sl in _room_slices(sc):
+        D0 = out.d0[b, s]
+        DR = out.dist[sl] / D0
+        slope, icpt = np.polyfit(out.x[sl], DR, 1)
+        resid = DR - (slope * out.x[sl] + icpt)
+        assert np.max(np.abs(resid)) < 1e-9 * np.max(DR)
+        assert abs(slope * p.alpha + icpt - 1.0) < 1e-9
+        cT = p.c0 * float(sc.rt60[b])
+        assert abs(slope * p.beta + icpt - cT / D0) < 1e-9 * cT / D0
+        assert np.all(DR >= 1.0)
+
+
+def test_images_on_sphere_with_uniform_angles(big_draw):
+    sc, p, out = big_draw
+    for b, s, sl in _room_slices(sc):
+        c = sc.mic[b].astype(np.float64).mean(axis=0)
+        d = out.pos[sl] - c
+        rad = np.linalg.norm(d, axis=1)
+        assert np.allclose(rad, out.dist[sl], rtol=1e-13)
+        theta = np.mod(np.arctan2(d[:, 1], d[:, 0]), 2 * np.pi)
+        phi = np.arcsin(np.clip(d[:, 2] / rad, -1, 1))
+        assert stats.kstest(theta, stats.uniform(0, 2 * np.pi).cdf).pvalue > 1e-4
+        assert stats.kstest(phi, stats.uniform(-np.pi / 2, np.pi).cdf).pvalue > 1e-4
+    # D0 is the source's distance to the array centre.
+    for b in range(sc.B):
+        c = sc.mic[b].astype(np.float64).mean(axis=0)
+        for s in range(sc.S):
+            assert np.isclose(out.d0[b, s], np.linalg.norm(sc.src[b, s].astype(np.float64) - c), rtol=1e-14)
+
+
+def test_rrmax_puts_farthest_image_60db_below_direct_path(oracle_mod, big_draw):
+    sc, p, out = big_draw
+    for b in range(sc.B):
+        cT = p.c0 * float(sc.rt60[b])
+        for s in range(sc.S):
+            far = out.r[b] ** out.rrmax[b, s] / cT
+            direct = 1.0 / out.d0[b, s]
+            assert np.isclose(far / direct, 1e-3, rtol=1e-10)
+
+
+def test_reflection_count_range_trend_and_perturbation(oracle_mod, big_draw):
+    sc, p, out = big_draw
+    for b, s, sl in _room_slices(sc):
+        RR = out.rrmax[b, s]
+        g = out.g[sl]
+        assert np.all(g >= 1.0) and np.all(g <= RR)
+        cT = p.c0 * float(sc.rt60[b])
+        D = out.dist[sl]
+        DR = D / out.d0[b, s]
+        trend = 1.0 + (D / cT) ** 2 * (RR - 1.0)
+        # The trend reaches RR_max exactly at the longest propagation distance c0*T60.
+        assert np.isclose(1.0 + (cT / cT) ** 2 * (RR - 1.0), RR)
+        free = (g > 1.0) & (g < RR)
+        pert = (g[free] - trend[free]) / DR[free] ** p.tau
+        assert np.all(pert >= p.a - 1e-9) and np.all(pert <= p.b + 1e-9)
+        assert stats.kstest(pert, stats.uniform(p.a, p.b - p.a).cdf).pvalue > 1e-4 or free.sum() < 50
+        # Clamped values are those whose unclamped value left [1, RR_max].
+        assert np.all(g[~free] == np.clip(g[~free], 1.0, RR))
+
+
+def test_draws_depend_only_on_seed_room_source_index(oracle_mod):
+    sc = scenes.tiny(seed=5, B=6, S=2, M=3, images=30)
+    p = oracle_mod.Params(fs=sc.fs, half_len=sc.half_len)
+    full = oracle_mod.sample(sc, p, seed=99)
+    # The counter uses the room index, so sampling a subset with re-indexed rooms differs;
+    # the same rooms at the same indices give identical words.
+    again = oracle_mod.sample(sc, p, seed=99)
+    assert np.array_equal(full.words, again.words) and np.array_equal(full.pos, again.pos)
+    other = oracle_mod.sample(sc, p, seed=100)
+    assert not np.any(np.all(full.words == other.words, axis=1))
+    # Moving the microphones of one room changes only that room's images.
+    sc2 = scenes.tiny(seed=5, B=6, S=2, M=3, images=30)
+    sc2.mic[2] += np.float32(0.25)
+    moved = oracle_mod.sample(sc2, p, seed=99)
+    per = sc.S * 30
+    keep = np.ones(full.pos.shape[0], bool)
+    keep[2 * per:3 * per] = False
+    assert np.array_equal(full.pos[keep], moved.pos[keep])
+    assert np.array_equal(full.words, moved.words)
+
+
+def test_invalid_scene_is_rejected(oracle_mod):
+    sc = scenes.tiny(seed=1, B=1, S=1, M=2, images=5)
+    sc.rt60[:] = 0.001        # c0 * T60 = 0.34 m is shorter than some source distances
+    sc.src[0, 0] = sc.mic[0].mean(axis=0) + np.array([2.0, 0, 0], np.float32)
+    p = oracle_mod.Params(fs=sc.fs, half_len=sc.half_len)
+    with pytest.raises(ValueError):
+        oracle_mod.sample(sc, p, seed=0)
