@@ -1,0 +1,190 @@
+/*
+ * fram.h -- C ABI of libfram: batched multi-channel room impulse response synthesis after
+ * FRAM-RIR (Y. Luo, R. Gu, "Fast Random Approximation of Multi-channel Room Impulse
+ * Response", arXiv 2304.08052), for NVIDIA GB300 (sm_103a).
+ *
+ * Problem statement (Sec. II-III): for every room (shoebox dimensions, T60), source and
+ * microphone, the RIR is the sum of a direct path and I randomly placed virtual image sources.
+ * Image i has a sampled distance D_i from the array centre (Eq. 3, 4), a uniformly sampled
+ * direction (Sec. III-B) and a reflection count g_i (Eq. 5, 6); it reaches mic m after
+ * D_{i,m} = |p_i - mic_m| metres with amplitude r^{g_i} / D_{i,m} (Eq. 1, 2).  Each arrival
+ * is rendered at the output rate fs as a fractional-delay Hann-windowed sinc of half length
+ * K centred on t = D_{i,m} fs / c0, and the early RIR (Eq. 9) keeps the samples within
+ * [-pre, +post] ms of the direct path.
+ *
+ * Conventions for every entry point:
+ *   - All array pointers are device pointers unless the comment says "host".  The caller
+ *     owns every buffer; libfram never allocates device or pinned memory.
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL = legacy default
+ *     stream) and returns without synchronising, so the calls can be captured in a CUDA
+ *     graph.  Only fram_status() synchronises.
+ *   - Errors detected on the host return a negative code and set a thread-local message
+ *     (fram_last_error).  Errors detected on the device (invalid geometry, capacity
+ *     overflow, non-finite input) set bits of a status word in the workspace, reported by
+ *     fram_status().
+ *   - Floating-point data are float32; geometry is in metres, time in seconds.
+ *
+ * Buffer layout (ragged, produced by fram_layout on the host):
+ *   room b has L_b = ceil(T60_b * fs) samples per channel and S * n_vs[b] images;
+ *   rir[rir_off[b] + (s*M + m)*L_b + n]   for n in [0, L_b)
+ *   image (b, s, i) is row vs_off[b] + s*n_vs[b] + i of the image arrays.
+ */
+#ifndef FRAM_H
+#define FRAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define FRAM_OK          0
+#define FRAM_EINVAL     (-1)   /* bad argument or scene description                       */
+#define FRAM_EWORKSPACE (-2)   /* workspace pointer null, misaligned or too small          */
+#define FRAM_ECUDA      (-3)   /* a CUDA runtime call failed; fram_last_error has the text */
+#define FRAM_EDEVICE    (-4)   /* the device status word reports an error (fram_status)    */
+
+/* Device status word bits (fram_status). */
+#define FRAM_DEV_BAD_GEOMETRY   0x1  /* c0*T60 <= D0, D0 == 0, T60 <= 0 or dims <= 0        */
+#define FRAM_DEV_CAPACITY       0x2  /* a synthesis tile held more images than it can stage */
+#define FRAM_DEV_NONFINITE      0x4  /* a non-finite position, g or r was read              */
+
+/*
+ * Method constants.  The paper fixes only their ranges: 0 <= alpha < beta <= 1 (Eq. 3),
+ * tau > 0 (Eq. 6), and the [-6, 50] ms early window (Eq. 9).  fram_default_params fills
+ * this project's defaults: alpha 0.25, beta 1, a -2, b 2, tau 0.25, c0 343 m/s, fs 16 kHz,
+ * K 40, early window 6 / 50 ms, tile 0 (library default).
+ */
+typedef struct fram_params {
+    double alpha;          /* Eq. 3: distance ratios are drawn on (alpha, beta]; alpha > 0 */
+    double beta;           /*        (Eq. 4 divides by alpha)                              */
+    double a;              /* Eq. 6: perturbation p_i ~ U(a, b)                            */
+    double b;
+    double tau;            /* Eq. 6: distance shrinkage factor, > 0                        */
+    double c0;             /* speed of sound, m/s                                          */
+    double fs;             /* output sample rate, Hz                                       */
+    double early_pre_ms;   /* Eq. 9: early RIR keeps n - n0 in [-ceil(pre*fs/1000),        */
+    double early_post_ms;  /*        +ceil(post*fs/1000)], n0 = ceil(D_{0,m} fs / c0)       */
+    int32_t half_len;      /* K: taps at |n - t| < K, 2K+1 taps per arrival; 1..128        */
+    int32_t tile;          /* synthesis tile length in samples (multiple of 256, 256..4096); */
+                           /* 0 = library default                                          */
+} fram_params;
+
+/*
+ * Scene: B rooms, S sources and M microphones per room.  The host-side sizes must match
+ * the device arrays (fram_layout produces them).
+ */
+typedef struct fram_scene {
+    int32_t B, S, M;
+    int32_t max_len;           /* max_b L_b                                        (host) */
+    int64_t n_vs_total;        /* vs_off[B]: total image rows                      (host) */
+    int64_t rir_total;         /* rir_off[B]: total RIR samples                    (host) */
+    double array_radius;       /* max over rooms and mics of |mic_m - centre_b|, m (host); */
+                               /* sizes the adjoint's halo; an arrival beyond it sets     */
+                               /* FRAM_DEV_CAPACITY                                        */
+    const float* dims;         /* [B,3]  room size Lx, Ly, Lz (Sec. III-A)                */
+    const float* rt60;         /* [B]    T60 in seconds (Eq. 2, 4, 5, Sec. III-D)          */
+    const float* src;          /* [B,S,3] source positions                                 */
+    const float* mic;          /* [B,M,3] microphone positions                             */
+    const int32_t* n_vs;       /* [B]    images per (room, source), I in Eq. 1             */
+    const int64_t* vs_off;     /* [B+1]  image row offset of each room                     */
+    const int32_t* rir_len;    /* [B]    L_b                                               */
+    const int64_t* rir_off;    /* [B+1]  sample offset of each room                        */
+} fram_scene;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int fram_version(void);
+
+/* Thread-local text of the last host-side error ("" if none). */
+const char* fram_last_error(void);
+
+/* Fill *p with the defaults listed above. */
+void fram_default_params(fram_params* p);
+
+/*
+ * Host only.  L_b = ceil(T60_b * fs) (Sec. III-D at the output rate) and the ragged offsets.
+ * rt60 [B], n_vs [B] are host arrays; outputs rir_len [B], rir_off [B+1], vs_off [B+1] are
+ * host arrays written by the call.  Returns FRAM_EINVAL for B < 0, S < 1, M < 1, fs <= 0,
+ * T60 <= 0, n_vs < 0 or a length above 2^31 - 1.
+ */
+int fram_layout(int32_t B, int32_t S, int32_t M, double fs, const float* rt60, const int32_t* n_vs,
+                int32_t* rir_len, int64_t* rir_off, int64_t* vs_off);
+
+/*
+ * Host only.  Bytes of device workspace that fram_sample, fram_synthesize and
+ * fram_synthesize_backward need for this scene and these parameters (one buffer serves all
+ * three).  The workspace must be 256-byte aligned.
+ */
+int fram_workspace_size(const fram_scene* scene, const fram_params* p, size_t* bytes);
+
+/*
+ * Virtual-image sampler (Sec. III-A to III-C).  For room b, source s and image i one
+ * Philox4x32-10 call (Salmon et al., SC'11) with counter (i, s, b, 0) and key
+ * (seed mod 2^32, seed div 2^32) gives four words w_k, mapped to u_k = ((w_k >> 9) + 0.5) 2^-23:
+ *   x    = (alpha^3 + u0 (beta^3 - alpha^3))^(1/3)              inverse CDF of Eq. 3
+ *   DR_i = 1 + alpha/(beta-alpha) (x/alpha - 1)(c0 T60/D0 - 1)  Eq. 4,  D_i = D0 DR_i
+ *   theta = 2 pi u1, phi = pi (u2 - 1/2)                         Sec. III-B
+ *   p_i  = c + D_i (cos phi cos theta, cos phi sin theta, sin phi), c = mean of the mics
+ *   g_i  = clamp(1 + (D_i/(c0 T60))^2 (RR_max - 1) + (a + (b-a) u3) DR_i^tau, 1, RR_max)
+ *                                                                Eq. 5, 6
+ * with D0 = |src - c| and r from Eq. 2.
+ * Outputs (device, caller-owned): vs_pos_hi, vs_pos_lo [N,3]: each coordinate as an
+ * unevaluated float pair hi + lo (about 44 significant bits, so delays stay exact to well
+ * below a microsample); vs_g [N]; r [B] (Eq. 2); words [N,4] (nullable: the raw Philox
+ * words, for verification).
+ * d_seed (nullable) is a device pointer to a uint64 seed read by the kernel instead of
+ * `seed`, so a captured graph can be replayed with new draws.
+ * Device status: FRAM_DEV_BAD_GEOMETRY if c0 T60 <= D0 or D0 == 0 (outputs for that room
+ * are NaN).
+ */
+int fram_sample(const fram_scene* scene, const fram_params* p, uint64_t seed, const uint64_t* d_seed,
+                float* vs_pos_hi, float* vs_pos_lo, float* vs_g, float* r, uint32_t* words,
+                void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Synthesis (Eq. 1 with windowed-sinc arrivals, Sec. III-D; Eq. 9).  For every room b,
+ * source s, mic m and n in [0, L_b):
+ *   h[n] = sum over arrivals j with |n - t_j| < K of  A_j sinc(n - t_j) (1 + cos(pi (n - t_j)/K))/2
+ * where the arrivals are the direct path (A = 1/D_{0,m}, t = D_{0,m} fs/c0) and every image
+ * (A = r_b^{g_i} / D_{i,m}, t = D_{i,m} fs/c0, D_{i,m} = |p_i - mic_m|), sinc(x) = sin(pi x)/(pi x).
+ * Taps outside [0, L_b) are dropped.  Sums are accumulated in float32 in a fixed order
+ * (arrivals sorted by delay, ties by image index), so results are bit-reproducible.
+ * Inputs: image positions vs_pos_hi [N,3] and vs_pos_lo [N,3] (nullable = zero low parts,
+ * i.e. plain float32 positions), reflection counts vs_g [N], coefficients r [B].
+ * Outputs: rir [rir_total]; early [rir_total] (nullable) receives h_e of Eq. 9.
+ */
+int fram_synthesize(const fram_scene* scene, const fram_params* p,
+                    const float* vs_pos_hi, const float* vs_pos_lo, const float* vs_g, const float* r,
+                    float* rir, float* early, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Adjoint of fram_synthesize.  Given dL/dh (grad_rir, same layout as rir; nullable = 0) and
+ * dL/dh_e (grad_early; nullable), computes by recomputing each arrival's taps:
+ *   dL/dt_j = -A_j sum_n G[n] tap'(n - t_j),  dL/dA_j = sum_n G[n] tap(n - t_j),
+ *   G = grad_rir + (Eq. 9 mask) * grad_early,
+ * and chains them to positions and r:  dL/dD = dL/dt fs/c0 - dL/dA A/D,
+ * dD_{i,m}/dp_i = (p_i - mic_m)/D_{i,m} = -dD_{i,m}/dmic_m, dA/dr = g A / r.
+ * Images are leaves: the source gradient comes from the direct path only.
+ * Outputs (each nullable, overwritten): grad_vs [N,3], grad_mic [B,M,3], grad_src [B,S,3],
+ * grad_r [B].  Reductions run in a fixed order (bit-reproducible).
+ */
+int fram_synthesize_backward(const fram_scene* scene, const fram_params* p,
+                             const float* vs_pos_hi, const float* vs_pos_lo, const float* vs_g,
+                             const float* r, const float* grad_rir, const float* grad_early,
+                             float* grad_vs, float* grad_mic, float* grad_src, float* grad_r,
+                             void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Synchronises `stream` and reads the device status word that the last call which used
+ * this workspace wrote (FRAM_DEV_* bits) into *flags.  Returns FRAM_EDEVICE if any bit is
+ * set, FRAM_ECUDA on a CUDA error, FRAM_OK otherwise.
+ */
+int fram_status(void* workspace, void* stream, int32_t* flags);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRAM_H */

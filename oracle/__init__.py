@@ -147,8 +147,10 @@ class Sampled:
     d0: np.ndarray       # [B,S] D0
 
 
-def sample(scene, params: Params, seed: int) -> Sampled:
-    """Sample every room/source's virtual images (Sec. III-B, III-C) in FP64."""
+def sample(scene, params: Params, seed: int, room_ids=None) -> Sampled:
+    """Sample every room/source's virtual images (Sec. III-B, III-C) in FP64.  room_ids
+    (optional, [B]) are the rooms' indices in a larger batch; the draws then equal the ones
+    those rooms get inside that batch."""
     B, S, M = scene.B, scene.S, scene.M
     _, _, vs_off = layout(scene.rt60, scene.n_vs, S, M, params.fs)
     N = int(vs_off[-1])
@@ -158,10 +160,12 @@ def sample(scene, params: Params, seed: int) -> Sampled:
     src, mic = _f64(scene.src), _f64(scene.mic)
     n_vs = np.ascontiguousarray(scene.n_vs, dtype=np.int32)
     pc = params._c()
+    rid = None if room_ids is None else np.ascontiguousarray(room_ids, dtype=np.int32)
+    assert rid is None or rid.shape == (B,)
     rc = _load().fo_sample(ctypes.c_int32(B), ctypes.c_int32(S), ctypes.c_int32(M), _p(dims), _p(rt60),
                            _p(src), _p(mic), _p(n_vs), _p(vs_off), ctypes.byref(pc),
                            ctypes.c_uint64(seed), _p(out.pos), _p(out.g), _p(out.r), _p(out.words),
-                           _p(out.dist), _p(out.x), _p(out.rrmax), _p(out.d0))
+                           _p(out.dist), _p(out.x), _p(out.rrmax), _p(out.d0), _p(rid))
     if rc != 0:
         raise ValueError("oracle sample: invalid scene (c0*T60 must exceed D0) or parameters")
     return out

@@ -158,6 +158,7 @@ static double fo_rrmax(double c0, double t60, double d0, double r)
 /* ------------------------------------------------------------------------------------ */
 /* Virtual-source sampler (Sec. III-B, III-C).                                           */
 /* For room b, source s, image i: one Philox call with counter (i, s, b, 0) and key      */
+/* (b replaced by room_ids[b] when given)                                                */
 /* (seed_lo, seed_hi) gives u0..u3.  u0 -> distance ratio, u1 -> azimuth, u2 ->          */
 /* elevation, u3 -> perturbation.                                                        */
 /* Outputs per image: position (FP64), g_i; optionally the raw words, D_i, x, DR.        */
@@ -167,7 +168,8 @@ int fo_sample(int32_t B, int32_t S, int32_t M,
               const double* dims, const double* rt60, const double* src, const double* mic,
               const int32_t* n_vs, const int64_t* vs_off, const fo_params* P, uint64_t seed,
               double* vs_pos, double* vs_g, double* r_out,
-              uint32_t* words, double* vs_dist, double* vs_x, double* rrmax_out, double* d0_out)
+              uint32_t* words, double* vs_dist, double* vs_x, double* rrmax_out, double* d0_out,
+              const int32_t* room_ids)
 {
     const double alpha = P->alpha, beta = P->beta, c0 = P->c0;
     if (!(alpha > 0) || !(beta > alpha) || !(beta <= 1.0) || !(c0 > 0) || !(P->tau > 0)) return -1;
@@ -192,7 +194,10 @@ int fo_sample(int32_t B, int32_t S, int32_t M,
             if (d0_out) d0_out[(int64_t)b * S + s] = D0;
             for (int32_t i = 0; i < n_vs[b]; ++i) {
                 const int64_t v = vs_off[b] + (int64_t)s * n_vs[b] + i;
-                const uint32_t ctr[4] = { (uint32_t)i, (uint32_t)s, (uint32_t)b, 0u };
+                /* room_ids (nullable) gives the room's index in a larger batch, so a subset of
+                 * rooms draws exactly what it draws inside the full batch. */
+                const uint32_t rid = room_ids ? (uint32_t)room_ids[b] : (uint32_t)b;
+                const uint32_t ctr[4] = { (uint32_t)i, (uint32_t)s, rid, 0u };
                 uint32_t w[4];
                 fo_philox4x32_10(ctr, key, w);
                 if (words) memcpy(words + 4 * v, w, sizeof w);

@@ -1,0 +1,81 @@
+"""ctypes view of libfram's C ABI (include/fram.h).  Marshalling only: no computation here.
+
+The library is loaded from paper_2304_08052_gb300/_build/libfram.so.  If it is missing the
+import of any function fails with a RuntimeError -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libfram.so")
+
+FRAM_OK = 0
+FRAM_EINVAL = -1
+FRAM_EWORKSPACE = -2
+FRAM_ECUDA = -3
+FRAM_EDEVICE = -4
+
+FRAM_DEV_BAD_GEOMETRY = 0x1
+FRAM_DEV_CAPACITY = 0x2
+FRAM_DEV_NONFINITE = 0x4
+
+# Every symbol include/fram.h declares (checked by tests/test_abi.py).
+EXPORTED = ("fram_version", "fram_last_error", "fram_default_params", "fram_layout", "fram_workspace_size",
+            "fram_sample", "fram_synthesize", "fram_synthesize_backward", "fram_status")
+
+
+class FramParams(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("a", ctypes.c_double),
+                ("b", ctypes.c_double), ("tau", ctypes.c_double), ("c0", ctypes.c_double),
+                ("fs", ctypes.c_double), ("early_pre_ms", ctypes.c_double), ("early_post_ms", ctypes.c_double),
+                ("half_len", ctypes.c_int32), ("tile", ctypes.c_int32)]
+
+
+class FramScene(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_int32), ("S", ctypes.c_int32), ("M", ctypes.c_int32), ("max_len", ctypes.c_int32),
+                ("n_vs_total", ctypes.c_int64), ("rir_total", ctypes.c_int64), ("array_radius", ctypes.c_double),
+                ("dims", ctypes.c_void_p), ("rt60", ctypes.c_void_p), ("src", ctypes.c_void_p),
+                ("mic", ctypes.c_void_p), ("n_vs", ctypes.c_void_p), ("vs_off", ctypes.c_void_p),
+                ("rir_len", ctypes.c_void_p), ("rir_off", ctypes.c_void_p)]
+
+
+class FramError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libfram error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libfram is not built ({LIB_PATH} missing); run python -m paper_2304_08052_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, f64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64
+        P, S = ctypes.POINTER(FramParams), ctypes.POINTER(FramScene)
+        L.fram_version.restype = ctypes.c_int
+        L.fram_last_error.restype = ctypes.c_char_p
+        L.fram_default_params.argtypes = [P]
+        L.fram_default_params.restype = None
+        L.fram_layout.argtypes = [i32, i32, i32, f64, vp, vp, vp, vp, vp]
+        L.fram_workspace_size.argtypes = [S, P, ctypes.POINTER(ctypes.c_size_t)]
+        L.fram_sample.argtypes = [S, P, u64, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        L.fram_synthesize.argtypes = [S, P, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        L.fram_synthesize_backward.argtypes = [S, P, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        L.fram_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
+        for name in ("fram_layout", "fram_workspace_size", "fram_sample", "fram_synthesize",
+                     "fram_synthesize_backward", "fram_status"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def check(rc: int) -> None:
+    if rc != FRAM_OK:
+        raise FramError(rc, lib().fram_last_error().decode(errors="replace"))

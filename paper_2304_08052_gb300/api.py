@@ -1,0 +1,221 @@
+"""PyTorch-facing binding of libfram.  Argument marshalling only: every step of sampling,
+synthesis and the adjoint runs in the library's CUDA kernels.
+
+    from paper_2304_08052_gb300 import api, scenes
+    sc = api.DeviceScene(scenes.batch_256(0), api.Params(fs=16000, half_len=40))
+    vs = api.sample(sc, seed=1)                # images: pos_hi, pos_lo, g; per-room r
+    rir = api.synthesize(sc, vs)               # flat ragged RIR buffer on the GPU
+    h = sc.channel(rir, b=0, s=0, m=0)         # one channel
+    # Differentiable path (gradients w.r.t. source, mic, image positions and r):
+    src = sc.src.clone().requires_grad_()
+    rir = api.rir(sc, src, sc.mic, vs.pos_hi.clone().requires_grad_(), vs.r.clone().requires_grad_(), vs.g,
+                  vs.pos_lo)
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import FramParams, FramScene, check, lib
+
+
+@dataclass
+class Params:
+    """Method constants (see include/fram.h).  alpha, beta, a, b, tau and c0 are not fixed by
+    the paper; these are the library defaults."""
+    fs: float = 16000.0
+    half_len: int = 40
+    alpha: float = 0.25
+    beta: float = 1.0
+    a: float = -2.0
+    b: float = 2.0
+    tau: float = 0.25
+    c0: float = 343.0
+    early_pre_ms: float = 6.0
+    early_post_ms: float = 50.0
+    tile: int = 0
+
+    def c(self) -> FramParams:
+        return FramParams(self.alpha, self.beta, self.a, self.b, self.tau, self.c0, self.fs,
+                          self.early_pre_ms, self.early_post_ms, int(self.half_len), int(self.tile))
+
+
+def layout(rt60, n_vs, S: int, M: int, fs: float):
+    """Host layout through fram_layout: (rir_len [B] i32, rir_off [B+1] i64, vs_off [B+1] i64)."""
+    rt60 = np.ascontiguousarray(rt60, dtype=np.float32)
+    n_vs = np.ascontiguousarray(n_vs, dtype=np.int32)
+    B = rt60.shape[0]
+    rir_len = np.empty(B, np.int32)
+    rir_off = np.empty(B + 1, np.int64)
+    vs_off = np.empty(B + 1, np.int64)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    check(lib().fram_layout(B, S, M, float(fs), p(rt60), p(n_vs), p(rir_len), p(rir_off), p(vs_off)))
+    return rir_len, rir_off, vs_off
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "libfram takes contiguous CUDA tensors"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class DeviceScene:
+    """A scene resident on the GPU plus its layout and a workspace.  The workspace is
+    allocated once here (by PyTorch), never by the library."""
+
+    def __init__(self, scene, params: Params, device: str = "cuda"):
+        self.scene = scene
+        self.params = params
+        self.B, self.S, self.M = int(scene.B), int(scene.S), int(scene.M)
+        self.rir_len, self.rir_off, self.vs_off = layout(scene.rt60, scene.n_vs, self.S, self.M, params.fs)
+        self.n_vs_total = int(self.vs_off[-1])
+        self.rir_total = int(self.rir_off[-1])
+        self.max_len = int(self.rir_len.max()) if self.B else 0
+        mic64 = np.asarray(scene.mic, np.float64)
+        cen = mic64.mean(axis=1, keepdims=True)
+        self.array_radius = float(np.linalg.norm(mic64 - cen, axis=2).max()) if self.B else 0.0
+        dev = torch.device(device)
+        f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device=dev)
+        self.dims = f32(scene.dims)
+        self.rt60 = f32(scene.rt60)
+        self.src = f32(scene.src)
+        self.mic = f32(scene.mic)
+        self.n_vs = torch.as_tensor(np.ascontiguousarray(scene.n_vs, np.int32), device=dev)
+        self.vs_off_d = torch.as_tensor(self.vs_off, device=dev)
+        self.rir_len_d = torch.as_tensor(self.rir_len, device=dev)
+        self.rir_off_d = torch.as_tensor(self.rir_off, device=dev)
+        nbytes = ctypes.c_size_t(0)
+        check(lib().fram_workspace_size(ctypes.byref(self.c_scene()), ctypes.byref(params.c()), ctypes.byref(nbytes)))
+        self.ws_bytes = int(nbytes.value)
+        raw = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=dev)
+        off = (-raw.data_ptr()) % 256
+        self._ws_raw = raw
+        self.ws = raw[off:off + self.ws_bytes]
+
+    def c_scene(self, src: Optional[torch.Tensor] = None, mic: Optional[torch.Tensor] = None) -> FramScene:
+        src = self.src if src is None else src
+        mic = self.mic if mic is None else mic
+        cp = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        return FramScene(self.B, self.S, self.M, self.max_len, self.n_vs_total, self.rir_total, self.array_radius,
+                         cp(getattr(self, "dims", None)), cp(getattr(self, "rt60", None)), cp(src), cp(mic),
+                         cp(getattr(self, "n_vs", None)), cp(getattr(self, "vs_off_d", None)),
+                         cp(getattr(self, "rir_len_d", None)), cp(getattr(self, "rir_off_d", None)))
+
+    def channel(self, buf: torch.Tensor, b: int, s: int, m: int) -> torch.Tensor:
+        L = int(self.rir_len[b])
+        o = int(self.rir_off[b]) + (s * self.M + m) * L
+        return buf[o:o + L]
+
+    def status(self) -> int:
+        flags = ctypes.c_int32(0)
+        rc = lib().fram_status(ctypes.c_void_p(self.ws.data_ptr()), _stream(), ctypes.byref(flags))
+        if rc not in (_lib.FRAM_OK, _lib.FRAM_EDEVICE):
+            check(rc)
+        return int(flags.value)
+
+
+@dataclass
+class Images:
+    pos_hi: torch.Tensor                 # [N,3]
+    pos_lo: torch.Tensor                 # [N,3]
+    g: torch.Tensor                      # [N]
+    r: torch.Tensor                      # [B]
+    words: Optional[torch.Tensor] = None  # [N,4] int32 view of the Philox words
+
+
+def sample(sc: DeviceScene, seed: int = 0, d_seed: Optional[torch.Tensor] = None, words: bool = False,
+           out: Optional[Images] = None) -> Images:
+    """fram_sample: draw every (room, source)'s images on the GPU."""
+    dev = sc.dims.device
+    N = sc.n_vs_total
+    if out is None:
+        out = Images(torch.empty((N, 3), dtype=torch.float32, device=dev),
+                     torch.empty((N, 3), dtype=torch.float32, device=dev),
+                     torch.empty(N, dtype=torch.float32, device=dev),
+                     torch.empty(sc.B, dtype=torch.float32, device=dev),
+                     torch.empty((N, 4), dtype=torch.int32, device=dev) if words else None)
+    ds = _ptr(d_seed) if d_seed is not None else None
+    check(lib().fram_sample(ctypes.byref(sc.c_scene()), ctypes.byref(sc.params.c()), ctypes.c_uint64(seed & (2**64 - 1)),
+                            ds, _ptr(out.pos_hi), _ptr(out.pos_lo), _ptr(out.g), _ptr(out.r), _ptr(out.words),
+                            ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes), _stream()))
+    return out
+
+
+def synthesize_raw(sc: DeviceScene, pos_hi, pos_lo, g, r, src=None, mic=None, early: bool = False,
+                   rir: Optional[torch.Tensor] = None, early_out: Optional[torch.Tensor] = None):
+    """fram_synthesize on explicit tensors.  Returns rir or (rir, early)."""
+    dev = sc.dims.device
+    if rir is None:
+        rir = torch.empty(sc.rir_total, dtype=torch.float32, device=dev)
+    if early and early_out is None:
+        early_out = torch.empty(sc.rir_total, dtype=torch.float32, device=dev)
+    src = sc.src if src is None else src
+    mic = sc.mic if mic is None else mic
+    check(lib().fram_synthesize(ctypes.byref(sc.c_scene(src, mic)), ctypes.byref(sc.params.c()), _ptr(pos_hi),
+                                _ptr(pos_lo), _ptr(g), _ptr(r), _ptr(rir), _ptr(early_out) if early else None,
+                                ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes), _stream()))
+    return (rir, early_out) if early else rir
+
+
+def synthesize(sc: DeviceScene, vs: Images, early: bool = False, **kw):
+    return synthesize_raw(sc, vs.pos_hi, vs.pos_lo, vs.g, vs.r, early=early, **kw)
+
+
+def synthesize_backward_raw(sc: DeviceScene, pos_hi, pos_lo, g, r, grad_rir, grad_early=None, src=None, mic=None,
+                            want=("vs", "mic", "src", "r")):
+    """fram_synthesize_backward.  Returns (grad_vs [N,3], grad_mic [B,M,3], grad_src [B,S,3], grad_r [B])."""
+    dev = sc.dims.device
+    gv = torch.empty((sc.n_vs_total, 3), dtype=torch.float32, device=dev) if "vs" in want else None
+    gm = torch.empty((sc.B, sc.M, 3), dtype=torch.float32, device=dev) if "mic" in want else None
+    gs = torch.empty((sc.B, sc.S, 3), dtype=torch.float32, device=dev) if "src" in want else None
+    gr = torch.empty(sc.B, dtype=torch.float32, device=dev) if "r" in want else None
+    src = sc.src if src is None else src
+    mic = sc.mic if mic is None else mic
+    check(lib().fram_synthesize_backward(ctypes.byref(sc.c_scene(src, mic)), ctypes.byref(sc.params.c()),
+                                         _ptr(pos_hi), _ptr(pos_lo), _ptr(g), _ptr(r), _ptr(grad_rir),
+                                         _ptr(grad_early), _ptr(gv), _ptr(gm), _ptr(gs), _ptr(gr),
+                                         ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes), _stream()))
+    return gv, gm, gs, gr
+
+
+class _FramRIR(torch.autograd.Function):
+    """Differentiable synthesis: leaves src [B,S,3], mic [B,M,3], vs_pos [N,3], r [B]."""
+
+    @staticmethod
+    def forward(ctx, src, mic, vs_pos, r, g, vs_pos_lo, sc, early):
+        src_c, mic_c, pos_c, r_c = (t.detach().contiguous() for t in (src, mic, vs_pos, r))
+        g_c = g.detach().contiguous()
+        lo_c = vs_pos_lo.detach().contiguous() if vs_pos_lo is not None else None
+        out = synthesize_raw(sc, pos_c, lo_c, g_c, r_c, src=src_c, mic=mic_c, early=early)
+        ctx.sc, ctx.early = sc, early
+        ctx.save_for_backward(src_c, mic_c, pos_c, r_c, g_c, lo_c if lo_c is not None else torch.empty(0))
+        ctx.has_lo = lo_c is not None
+        return out if early else (out,)[0]
+
+    @staticmethod
+    def backward(ctx, *grads):
+        src_c, mic_c, pos_c, r_c, g_c, lo_c = ctx.saved_tensors
+        lo_c = lo_c if ctx.has_lo else None
+        if ctx.early:
+            g_rir, g_early = grads
+        else:
+            g_rir, g_early = grads[0], None
+        g_rir = g_rir.contiguous() if g_rir is not None else None
+        g_early = g_early.contiguous() if g_early is not None else None
+        gv, gm, gs, gr = synthesize_backward_raw(ctx.sc, pos_c, lo_c, g_c, r_c, g_rir, g_early, src=src_c, mic=mic_c)
+        return gs, gm, gv, gr, None, None, None, None
+
+
+def rir(sc: DeviceScene, src, mic, vs_pos, r, g, vs_pos_lo=None, early: bool = False):
+    """Differentiable RIR synthesis (autograd through fram_synthesize_backward)."""
+    return _FramRIR.apply(src, mic, vs_pos, r, g, vs_pos_lo, sc, early)

@@ -1,0 +1,260 @@
+// fram_api.cu -- host side of the C ABI declared in include/fram.h: argument checks, the
+// ragged layout, workspace sizing and the launch sequence of each entry point.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "fram_internal.cuh"
+
+namespace fram {
+
+static thread_local std::string g_last_error;
+
+static int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(FRAM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int device_sm_count()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (cache[dev] == 0) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = n > 0 ? n : 1;
+    }
+    return cache[dev];
+}
+
+static int check_params(const fram_params* p)
+{
+    if (!p) return fail(FRAM_EINVAL, "params is null");
+    if (!(p->alpha > 0.0) || !(p->beta > p->alpha) || !(p->beta <= 1.0))
+        return fail(FRAM_EINVAL, "need 0 < alpha < beta <= 1 (Eq. 3, 4), got alpha=%g beta=%g", p->alpha, p->beta);
+    if (!(p->tau > 0.0)) return fail(FRAM_EINVAL, "need tau > 0 (Eq. 6)");
+    if (!(p->b >= p->a)) return fail(FRAM_EINVAL, "need a <= b (Eq. 6)");
+    if (!(p->c0 > 0.0) || !(p->fs > 0.0)) return fail(FRAM_EINVAL, "need c0 > 0 and fs > 0");
+    if (p->half_len < 1 || p->half_len > kMaxHalfLen) return fail(FRAM_EINVAL, "half_len must be in [1, %d]", kMaxHalfLen);
+    if (!(p->early_pre_ms >= 0.0) || !(p->early_post_ms >= 0.0)) return fail(FRAM_EINVAL, "early window must be >= 0");
+    if (p->tile != 0 && (p->tile < 256 || p->tile > 4096 || p->tile % 256 != 0))
+        return fail(FRAM_EINVAL, "tile must be 0 or a multiple of 256 in [256, 4096]");
+    return FRAM_OK;
+}
+
+static int tile_of(const fram_params* p) { return p->tile ? p->tile : kDefaultTile; }
+
+static int check_scene(const fram_scene* sc, bool need_arrays)
+{
+    if (!sc) return fail(FRAM_EINVAL, "scene is null");
+    if (sc->B < 0 || sc->S < 1 || sc->M < 1) return fail(FRAM_EINVAL, "need B >= 0, S >= 1, M >= 1");
+    if (sc->S >= 32768) return fail(FRAM_EINVAL, "S must be below 32768");
+    if (sc->M > 64) return fail(FRAM_EINVAL, "M must be at most 64");
+    if (sc->n_vs_total < 0 || sc->rir_total < 0 || sc->max_len < 0) return fail(FRAM_EINVAL, "negative totals");
+    if (sc->B > 0 && sc->max_len < 1) return fail(FRAM_EINVAL, "max_len must be >= 1");
+    if (!(sc->array_radius >= 0.0) || !std::isfinite(sc->array_radius)) return fail(FRAM_EINVAL, "array_radius must be finite and >= 0");
+    if (need_arrays && sc->B > 0) {
+        if (!sc->dims || !sc->rt60 || !sc->src || !sc->mic || !sc->n_vs || !sc->vs_off || !sc->rir_len || !sc->rir_off)
+            return fail(FRAM_EINVAL, "scene device arrays must not be null");
+    }
+    return FRAM_OK;
+}
+
+static int check_ws(const fram_scene* sc, const fram_params* p, void* ws, size_t bytes, WsLayout* out)
+{
+    const WsLayout w = ws_layout(*sc, tile_of(p));
+    if (w.max_tiles > 0xffff) return fail(FRAM_EINVAL, "too many tiles per RIR (raise the tile length)");
+    if (!ws) return fail(FRAM_EWORKSPACE, "workspace is null");
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(FRAM_EWORKSPACE, "workspace must be 256-byte aligned");
+    if (bytes < w.total) return fail(FRAM_EWORKSPACE, "workspace too small: %zu < %zu bytes", bytes, w.total);
+    *out = w;
+    return FRAM_OK;
+}
+
+static LaunchArgs make_args(const fram_scene* sc, const fram_params* p, const WsLayout& w, void* ws)
+{
+    LaunchArgs a{};
+    a.fs = p->fs;
+    a.c0 = p->c0;
+    a.B = sc->B; a.S = sc->S; a.M = sc->M;
+    a.K = p->half_len;
+    a.tile = w.tile;
+    a.max_tiles = w.max_tiles;
+    const double q = p->fs / p->c0;
+    a.q = (float)q;
+    a.q2 = f2_from_double(q);
+    a.early_pre = (int32_t)std::ceil(p->early_pre_ms * p->fs / 1000.0);
+    a.early_post = (int32_t)std::ceil(p->early_post_ms * p->fs / 1000.0);
+    a.margin_i = (int32_t)std::ceil(sc->array_radius * q) + 3;
+    a.n_vs_total = sc->n_vs_total;
+    a.rir_total = sc->rir_total;
+    a.dims = sc->dims; a.rt60 = sc->rt60; a.src = sc->src; a.mic = sc->mic;
+    a.n_vs = sc->n_vs; a.vs_off = sc->vs_off; a.rir_len = sc->rir_len; a.rir_off = sc->rir_off;
+    unsigned char* base = static_cast<unsigned char*>(ws);
+    a.hdr = reinterpret_cast<Header*>(base + w.header);
+    a.room = reinterpret_cast<RoomConst*>(base + w.room);
+    a.direct = reinterpret_cast<DirectConst*>(base + w.direct);
+    a.src_tile = reinterpret_cast<int32_t*>(base + w.src_tile);
+    a.item_off = reinterpret_cast<int32_t*>(base + w.item_off);
+    a.items = reinterpret_cast<int2*>(base + w.items);
+    a.bin_off = reinterpret_cast<int32_t*>(base + w.bin_off);
+    a.perm = reinterpret_cast<int32_t*>(base + w.perm);
+    a.key = reinterpret_cast<float*>(base + w.key);
+    a.part_mic = reinterpret_cast<float*>(base + w.part_mic);
+    a.part_src = reinterpret_cast<float*>(base + w.part_src);
+    a.part_r = reinterpret_cast<float*>(base + w.part_r);
+    return a;
+}
+
+}  // namespace fram
+
+using namespace fram;
+
+extern "C" {
+
+int fram_version(void) { return 10000; }
+
+const char* fram_last_error(void) { return g_last_error.c_str(); }
+
+void fram_default_params(fram_params* p)
+{
+    if (!p) return;
+    p->alpha = 0.25;
+    p->beta = 1.0;
+    p->a = -2.0;
+    p->b = 2.0;
+    p->tau = 0.25;
+    p->c0 = 343.0;
+    p->fs = 16000.0;
+    p->early_pre_ms = 6.0;
+    p->early_post_ms = 50.0;
+    p->half_len = 40;
+    p->tile = 0;
+}
+
+int fram_layout(int32_t B, int32_t S, int32_t M, double fs, const float* rt60, const int32_t* n_vs,
+                int32_t* rir_len, int64_t* rir_off, int64_t* vs_off)
+{
+    if (B < 0 || S < 1 || M < 1 || !(fs > 0.0)) return fail(FRAM_EINVAL, "need B >= 0, S >= 1, M >= 1, fs > 0");
+    if (B > 0 && (!rt60 || !n_vs || !rir_len)) return fail(FRAM_EINVAL, "null host array");
+    if (!rir_off || !vs_off) return fail(FRAM_EINVAL, "null host array");
+    rir_off[0] = 0;
+    vs_off[0] = 0;
+    for (int32_t b = 0; b < B; ++b) {
+        const double t60 = (double)rt60[b];
+        if (!(t60 > 0.0) || !std::isfinite(t60)) return fail(FRAM_EINVAL, "room %d: T60 must be > 0", b);
+        if (n_vs[b] < 0) return fail(FRAM_EINVAL, "room %d: negative image count", b);
+        const double len = std::ceil(t60 * fs);
+        if (len < 1.0 || len > 2147483647.0) return fail(FRAM_EINVAL, "room %d: RIR length out of range", b);
+        rir_len[b] = (int32_t)len;
+        rir_off[b + 1] = rir_off[b] + (int64_t)S * M * (int64_t)rir_len[b];
+        vs_off[b + 1] = vs_off[b] + (int64_t)S * (int64_t)n_vs[b];
+    }
+    return FRAM_OK;
+}
+
+int fram_workspace_size(const fram_scene* scene, const fram_params* p, size_t* bytes)
+{
+    int rc;
+    if ((rc = check_params(p)) != FRAM_OK) return rc;
+    if ((rc = check_scene(scene, false)) != FRAM_OK) return rc;
+    if (!bytes) return fail(FRAM_EINVAL, "bytes is null");
+    const WsLayout w = ws_layout(*scene, tile_of(p));
+    if (w.max_tiles > 0xffff) return fail(FRAM_EINVAL, "too many tiles per RIR (raise the tile length)");
+    *bytes = w.total;
+    return FRAM_OK;
+}
+
+int fram_sample(const fram_scene* scene, const fram_params* p, uint64_t seed, const uint64_t* d_seed,
+                float* vs_pos_hi, float* vs_pos_lo, float* vs_g, float* r, uint32_t* words,
+                void* workspace, size_t workspace_bytes, void* stream)
+{
+    int rc;
+    if ((rc = check_params(p)) != FRAM_OK) return rc;
+    if ((rc = check_scene(scene, true)) != FRAM_OK) return rc;
+    WsLayout w;
+    if ((rc = check_ws(scene, p, workspace, workspace_bytes, &w)) != FRAM_OK) return rc;
+    if (scene->n_vs_total > 0 && (!vs_pos_hi || !vs_g)) return fail(FRAM_EINVAL, "vs_pos_hi and vs_g must not be null");
+    const LaunchArgs a = make_args(scene, p, w, workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(a.hdr, 0, sizeof(Header), st);
+    if (e != cudaSuccess) return cuda_fail(e, "fram_sample: clearing the status word");
+    e = launch_sample(a, *p, seed, d_seed, vs_pos_hi, vs_pos_lo, vs_g, r, words, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fram_sample: launch");
+    return FRAM_OK;
+}
+
+int fram_synthesize(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi, const float* vs_pos_lo,
+                    const float* vs_g, const float* r, float* rir, float* early, void* workspace,
+                    size_t workspace_bytes, void* stream)
+{
+    int rc;
+    if ((rc = check_params(p)) != FRAM_OK) return rc;
+    if ((rc = check_scene(scene, true)) != FRAM_OK) return rc;
+    WsLayout w;
+    if ((rc = check_ws(scene, p, workspace, workspace_bytes, &w)) != FRAM_OK) return rc;
+    if (scene->n_vs_total > 0 && (!vs_pos_hi || !vs_g)) return fail(FRAM_EINVAL, "vs_pos_hi and vs_g must not be null");
+    if (scene->B > 0 && !r) return fail(FRAM_EINVAL, "r must not be null");
+    if (scene->rir_total > 0 && !rir) return fail(FRAM_EINVAL, "rir must not be null");
+    const LaunchArgs a = make_args(scene, p, w, workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_prepare(a, vs_pos_hi, vs_pos_lo, r, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fram_synthesize: prologue");
+    if (scene->B == 0) return FRAM_OK;
+    e = launch_synthesize(a, vs_pos_hi, vs_pos_lo, vs_g, rir, early, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fram_synthesize: launch");
+    return FRAM_OK;
+}
+
+int fram_synthesize_backward(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi,
+                             const float* vs_pos_lo, const float* vs_g, const float* r, const float* grad_rir,
+                             const float* grad_early, float* grad_vs, float* grad_mic, float* grad_src, float* grad_r,
+                             void* workspace, size_t workspace_bytes, void* stream)
+{
+    int rc;
+    if ((rc = check_params(p)) != FRAM_OK) return rc;
+    if ((rc = check_scene(scene, true)) != FRAM_OK) return rc;
+    WsLayout w;
+    if ((rc = check_ws(scene, p, workspace, workspace_bytes, &w)) != FRAM_OK) return rc;
+    if (scene->n_vs_total > 0 && (!vs_pos_hi || !vs_g)) return fail(FRAM_EINVAL, "vs_pos_hi and vs_g must not be null");
+    if (scene->B > 0 && !r) return fail(FRAM_EINVAL, "r must not be null");
+    const LaunchArgs a = make_args(scene, p, w, workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_prepare(a, vs_pos_hi, vs_pos_lo, r, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fram_synthesize_backward: prologue");
+    if (scene->B == 0) return FRAM_OK;
+    e = launch_backward(a, vs_pos_hi, vs_pos_lo, vs_g, r, grad_rir, grad_early, grad_vs, grad_mic, grad_src, grad_r,
+                        st);
+    if (e != cudaSuccess) return cuda_fail(e, "fram_synthesize_backward: launch");
+    return FRAM_OK;
+}
+
+int fram_status(void* workspace, void* stream, int32_t* flags)
+{
+    if (!workspace || !flags) return fail(FRAM_EINVAL, "workspace and flags must not be null");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "fram_status: stream synchronize");
+    int32_t v = 0;
+    e = cudaMemcpy(&v, workspace, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "fram_status: reading the status word");
+    *flags = v;
+    if (v != 0) return fail(FRAM_EDEVICE, "device status 0x%x", v);
+    return FRAM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,354 @@
+// fram_backward.cu -- adjoint of the windowed-sinc synthesis (gradients of a loss on the RIR
+// with respect to source, mic and image positions and the reflection coefficient).
+//
+// Ownership instead of scattering: every image belongs to exactly one (room, source, tile)
+// work item -- the tile its binning key (delay to the array centre) falls in -- and the
+// direct path of a (room, source) belongs to the tile of the source's key.  A persistent CTA
+// takes an item, and for each mic stages the upstream gradient
+//   G[n] = dL/dh[n] + [n in Eq. 9 window] dL/dh_e[n]
+// over the tile plus a halo of 2K + margin samples in shared memory; each thread then owns one
+// image, recomputes its arrival (float-pair delay, amplitude) and gathers its 2K+1 taps:
+//   dL/dA = sum_k G[n_c + k] s(x) w(x),   dL/dt = -A sum_k G[n_c + k] (s'(x) w(x) + s(x) w'(x)),
+// with x = k - delta, s = sinc, s'(x) = (cos(pi x) - s(x)) / x (a Taylor series on the centre
+// tap, where the difference cancels), w = (1 + cos(pi x/K))/2, w' = -(pi/2K) sin(pi x/K).
+// The chain rule gives dL/dD = dL/dt fs/c0 - dL/dA A/D and dD/dp = (p - mic)/D.
+// Image gradients are summed over mics in mic order inside the owning thread; mic, source and
+// r gradients are reduced per item in a fixed tree and then per room in item order, so the
+// result does not depend on scheduling.
+#include <algorithm>
+#include <cmath>
+
+#include "fram_internal.cuh"
+
+namespace fram {
+namespace {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kInvPi = 0.31830988618379067f;
+constexpr float kTinyDelta = 9.313225746154785e-10f;
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// d/dx sinc(x) for |x| <= 1/2: odd Taylor series sum_j (-1)^j 2j pi^(2j) x^(2j-1) / (2j+1)!.
+__device__ __forceinline__ float dsinc_small(float x)
+{
+    const float x2 = x * x;
+    // Coefficients of x^1, x^3, ..., x^11.
+    const float c1 = -3.2898681336964524f;     // -pi^2/3
+    const float c2 = 3.2469697011334144f;      //  pi^4/30
+    const float c3 = -1.1445173762772416f;     // -pi^6/840
+    const float c4 = 0.20918381538538052f;     //  pi^8/45360
+    const float c5 = -0.023460744224286495f;   // -pi^10/3991680
+    const float c6 = 0.0017807474713398848f;   //  pi^12/518918400
+    float p = __fmaf_rn(c6, x2, c5);
+    p = __fmaf_rn(p, x2, c4);
+    p = __fmaf_rn(p, x2, c3);
+    p = __fmaf_rn(p, x2, c2);
+    p = __fmaf_rn(p, x2, c1);
+    return p * x;
+}
+
+// Taps of one arrival against staged G: Gs points at G[n_c - K].
+template <int KT>
+__device__ __forceinline__ void gather_taps(const float* __restrict__ Gs, int Kr, float delta, const float2* tab,
+                                            float& gA, float& gT)
+{
+    const int K = KT > 0 ? KT : Kr;
+    float sd, cd, sk, ck;
+    sincospif(delta, &sd, &cd);
+    sincospif(delta / (float)K, &sk, &ck);
+    const float spi = sd * kInvPi;              // sin(pi delta) / pi
+    const float hw = -0.5f * kPi / (float)K;    // w'(x) = hw * sin(pi x / K)
+    float a = 0.f, t = 0.f;
+#pragma unroll 8
+    for (int kk = 0; kk <= 2 * K; ++kk) {
+        const int k = kk - K;
+        const float G = Gs[kk];
+        const float x = __fsub_rn((float)k, delta);
+        const float r = rcp_approx(x);
+        const bool even = (k & 1) == 0;
+        const float s = (even ? -spi : spi) * r;            // sinc(x) = -(-1)^k sin(pi delta)/(pi x)
+        const float cpx = even ? cd : -cd;                  // cos(pi x) = (-1)^k cos(pi delta)
+        const float sp = (k == 0) ? dsinc_small(x) : (cpx - s) * r;
+        const int km = k < 0 ? k + 2 * K : k;
+        const float2 cs = tab[km];                          // cos, sin(pi k / K)
+        const float cw = __fmaf_rn(cs.x, ck, cs.y * sk);    // cos(pi x / K)
+        const float sw = __fmaf_rn(cs.y, ck, -cs.x * sk);   // sin(pi x / K)
+        const float w = __fmaf_rn(0.5f, cw, 0.5f);
+        const float wp = hw * sw;
+        float tap = s * w;
+        float dtap = __fmaf_rn(sp, w, s * wp);
+        if ((kk == 0 || kk == 2 * K) && !(fabsf(x) < (float)K)) { tap = 0.f; dtap = 0.f; }
+        a = __fmaf_rn(G, tap, a);
+        t = __fmaf_rn(G, dtap, t);
+    }
+    gA = a;
+    gT = t;
+}
+
+struct BwdSmemPlan {
+    int gs, tab, total, glen;
+};
+
+__host__ __device__ inline BwdSmemPlan bwd_smem(int T, int K, int margin_i)
+{
+    BwdSmemPlan p;
+    p.glen = T + 4 * K + 2 * margin_i + 8;
+    p.gs = 0;
+    p.tab = ((4 * p.glen) + 15) & ~15;
+    p.total = p.tab + 8 * 2 * K;
+    return p;
+}
+
+template <int NT>
+__device__ __forceinline__ void block_sum3(float& x, float& y, float& z, float* red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_down_sync(0xffffffffu, x, o);
+        y += __shfl_down_sync(0xffffffffu, y, o);
+        z += __shfl_down_sync(0xffffffffu, z, o);
+    }
+    if (lane == 0) { red[3 * wid] = x; red[3 * wid + 1] = y; red[3 * wid + 2] = z; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        for (int w = 0; w < NT / 32; ++w) { sx += red[3 * w]; sy += red[3 * w + 1]; sz += red[3 * w + 2]; }
+        x = sx; y = sy; z = sz;
+    }
+    __syncthreads();
+}
+
+template <int NT, int KT>
+__global__ void __launch_bounds__(NT) bwd_kernel(LaunchArgs a, int margin_i, const float* __restrict__ pos_hi,
+                                                  const float* __restrict__ pos_lo, const float* __restrict__ gref,
+                                                  const float* __restrict__ grad_rir, const float* __restrict__ grad_early,
+                                                  float* __restrict__ grad_vs)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = a.tile, K = a.K;
+    const BwdSmemPlan P = bwd_smem(T, K, margin_i);
+    float* Gs = reinterpret_cast<float*>(smem + P.gs);
+    float2* tab = reinterpret_cast<float2*>(smem + P.tab);
+    __shared__ int s_item;
+    __shared__ float red[3 * (NT / 32)];
+    __shared__ float mic_part[3 * 64];
+    __shared__ float src_part[3];
+    const int tid = threadIdx.x;
+    for (int j = tid; j < 2 * K; j += NT) {
+        float sn, cs;
+        sincospif((float)j / (float)K, &sn, &cs);
+        tab[j] = make_float2(cs, sn);
+    }
+    const int n_items = a.hdr->n_items;
+    const float qf = a.q;
+    __syncthreads();
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(&a.hdr->queue_bwd, 1);
+        __syncthreads();
+        const int qi = s_item;
+        if (qi >= n_items) break;
+        const int2 it = a.items[qi];
+        const int b = it.x, s = it.y >> 16, tau = it.y & 0xffff;
+        const RoomConst rc = a.room[b];
+        const int T0 = tau * T;
+        const int Lb = rc.len;
+        const int64_t v0 = rc.vs_off + (int64_t)s * rc.n_vs;
+        const int* bo = a.bin_off + ((int64_t)b * a.S + s) * (a.max_tiles + 1);
+        const int o_lo = bo[tau], o_hi = bo[tau + 1];
+        const int gbase = T0 - 2 * K - margin_i - 4;
+        const bool own_direct = a.src_tile[(int64_t)b * a.S + s] == tau;
+        const int64_t chan0 = rc.rir_off + (int64_t)s * a.M * Lb;
+        const int M = a.M;
+        for (int k = tid; k < 3 * M; k += NT) mic_part[k] = 0.f;
+        if (tid < 3) src_part[tid] = 0.f;
+        float pr = 0.f;   // this thread's share of dL/dr
+        const int nown = o_hi - o_lo;
+        const int nch = nown > 0 ? (nown + NT - 1) / NT : 1;
+        for (int ch = 0; ch < nch; ++ch) {
+            const int slot = ch * NT + tid;
+            const bool has = slot < nown;
+            int64_t v = 0;
+            float phx = 0, phy = 0, phz = 0, plx = 0, ply = 0, plz = 0, gg = 0;
+            if (has) {
+                v = v0 + a.perm[v0 + o_lo + slot];
+                phx = pos_hi[3 * v]; phy = pos_hi[3 * v + 1]; phz = pos_hi[3 * v + 2];
+                if (pos_lo) { plx = pos_lo[3 * v]; ply = pos_lo[3 * v + 1]; plz = pos_lo[3 * v + 2]; }
+                gg = gref[v];
+            }
+            const float A_g = has ? exp2f(gg * rc.log2r) : 0.f;   // r^g
+            float gvx = 0.f, gvy = 0.f, gvz = 0.f;
+            for (int m = 0; m < M; ++m) {
+                const DirectConst dc = a.direct[((int64_t)b * a.S + s) * M + m];
+                const int64_t ch0 = chan0 + (int64_t)m * Lb;
+                __syncthreads();
+                for (int j = tid; j < P.glen; j += NT) {
+                    const int n = gbase + j;
+                    float Gv = 0.f;
+                    if (n >= 0 && n < Lb) {
+                        if (grad_rir) Gv = grad_rir[ch0 + n];
+                        if (grad_early && n >= dc.early_lo && n <= dc.early_hi) Gv += grad_early[ch0 + n];
+                    }
+                    Gs[j] = Gv;
+                }
+                __syncthreads();
+                const float* pm = a.mic + 3 * ((size_t)b * M + m);
+                const float mx = pm[0], my = pm[1], mz = pm[2];
+                float mpx = 0.f, mpy = 0.f, mpz = 0.f;
+                if (has) {
+                    f2 dx = two_sum(phx, -mx); dx.lo = __fadd_rn(dx.lo, plx);
+                    f2 dy = two_sum(phy, -my); dy.lo = __fadd_rn(dy.lo, ply);
+                    f2 dz = two_sum(phz, -mz); dz.lo = __fadd_rn(dz.lo, plz);
+                    f2 sx = two_prod(dx.hi, dx.hi); sx.lo = __fmaf_rn(__fmul_rn(2.0f, dx.hi), dx.lo, sx.lo);
+                    f2 sy = two_prod(dy.hi, dy.hi); sy.lo = __fmaf_rn(__fmul_rn(2.0f, dy.hi), dy.lo, sy.lo);
+                    f2 sz = two_prod(dz.hi, dz.hi); sz.lo = __fmaf_rn(__fmul_rn(2.0f, dz.hi), dz.lo, sz.lo);
+                    f2 ss = f2_add(f2_add(fast_two_sum(sx.hi, sx.lo), fast_two_sum(sy.hi, sy.lo)),
+                                   fast_two_sum(sz.hi, sz.lo));
+                    f2 D = f2_sqrt(ss);
+                    f2 t = f2_mul(D, a.q2);
+                    const int nc = __float2int_rn(t.hi);
+                    float delta = __fadd_rn(__fsub_rn(t.hi, (float)nc), t.lo);
+                    if (fabsf(delta) < kTinyDelta) delta = kTinyDelta;
+                    const float invD = __frcp_rn(D.hi);
+                    const float A = A_g * invD;
+                    const int j0 = nc - K - gbase;
+                    const bool any_tap = (nc + K >= 0) && (nc - K < Lb);
+                    if (any_tap) {
+                        if (j0 >= 0 && j0 + 2 * K < P.glen) {
+                            float gA, gT;
+                            gather_taps<KT>(Gs + j0, K, delta, tab, gA, gT);
+                            const float dLdD = __fmaf_rn(-A * gT, qf, -gA * A * invD);
+                            const float ex = (dx.hi + dx.lo) * invD, ey = (dy.hi + dy.lo) * invD,
+                                        ez = (dz.hi + dz.lo) * invD;
+                            gvx = __fmaf_rn(dLdD, ex, gvx);
+                            gvy = __fmaf_rn(dLdD, ey, gvy);
+                            gvz = __fmaf_rn(dLdD, ez, gvz);
+                            mpx = -dLdD * ex; mpy = -dLdD * ey; mpz = -dLdD * ez;
+                            pr = __fmaf_rn(gA * A * gg, rc.inv_r, pr);
+                        } else {
+                            atomicOr(&a.hdr->status, FRAM_DEV_CAPACITY);
+                        }
+                    }
+                }
+                // Direct path of (b, s, m), owned by one tile; thread 0 adds it after its image.
+                float dsx = 0.f, dsy = 0.f, dsz = 0.f;
+                if (own_direct && ch == 0 && tid == 0) {
+                    const int nc = __float2int_rn(dc.t_hi);
+                    float delta = __fadd_rn(__fsub_rn(dc.t_hi, (float)nc), dc.t_lo);
+                    if (fabsf(delta) < kTinyDelta) delta = kTinyDelta;
+                    const int j0 = nc - K - gbase;
+                    if ((nc + K >= 0) && (nc - K < Lb)) {
+                        if (j0 >= 0 && j0 + 2 * K < P.glen) {
+                            float gA, gT;
+                            gather_taps<KT>(Gs + j0, K, delta, tab, gA, gT);
+                            const float A = dc.amp;
+                            const float dLdD = __fmaf_rn(-A * gT, qf, -gA * A * A);
+                            dsx = dLdD * dc.ex; dsy = dLdD * dc.ey; dsz = dLdD * dc.ez;
+                            mpx -= dsx; mpy -= dsy; mpz -= dsz;
+                        } else {
+                            atomicOr(&a.hdr->status, FRAM_DEV_CAPACITY);
+                        }
+                    }
+                }
+                block_sum3<NT>(mpx, mpy, mpz, red);
+                if (tid == 0) {
+                    mic_part[3 * m] += mpx; mic_part[3 * m + 1] += mpy; mic_part[3 * m + 2] += mpz;
+                    src_part[0] += dsx; src_part[1] += dsy; src_part[2] += dsz;
+                }
+            }
+            if (has && grad_vs) {
+                grad_vs[3 * v] = gvx; grad_vs[3 * v + 1] = gvy; grad_vs[3 * v + 2] = gvz;
+            }
+        }
+        float z0 = 0.f, z1 = 0.f;
+        block_sum3<NT>(pr, z0, z1, red);
+        for (int k = tid; k < 3 * M; k += NT) a.part_mic[(int64_t)qi * 3 * M + k] = mic_part[k];
+        if (tid == 0) {
+            a.part_src[3 * (int64_t)qi] = src_part[0];
+            a.part_src[3 * (int64_t)qi + 1] = src_part[1];
+            a.part_src[3 * (int64_t)qi + 2] = src_part[2];
+            a.part_r[qi] = pr;
+        }
+        __syncthreads();
+    }
+}
+
+// Per-room reductions of the item partials, in item order.
+__global__ void bwd_reduce(LaunchArgs a, float* __restrict__ grad_mic, float* __restrict__ grad_src,
+                           float* __restrict__ grad_r)
+{
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nm = (int64_t)a.B * a.M * 3, ns = (int64_t)a.B * a.S * 3;
+    if (grad_mic && tid < nm) {
+        const int k = (int)(tid % 3), m = (int)((tid / 3) % a.M), b = (int)(tid / (3 * a.M));
+        const RoomConst rc = a.room[b];
+        const int q0 = rc.item0, q1 = q0 + a.S * rc.ntiles;
+        float acc = 0.f;
+        for (int q = q0; q < q1; ++q) acc += a.part_mic[(int64_t)q * 3 * a.M + 3 * m + k];
+        grad_mic[tid] = acc;
+    }
+    if (grad_src && tid < ns) {
+        const int k = (int)(tid % 3), s = (int)((tid / 3) % a.S), b = (int)(tid / (3 * a.S));
+        const RoomConst rc = a.room[b];
+        const int q0 = rc.item0 + s * rc.ntiles, q1 = q0 + rc.ntiles;
+        float acc = 0.f;
+        for (int q = q0; q < q1; ++q) acc += a.part_src[3 * (int64_t)q + k];
+        grad_src[tid] = acc;
+    }
+    if (grad_r && tid < a.B) {
+        const RoomConst rc = a.room[tid];
+        const int q0 = rc.item0, q1 = q0 + a.S * rc.ntiles;
+        float acc = 0.f;
+        for (int q = q0; q < q1; ++q) acc += a.part_r[q];
+        grad_r[tid] = acc;
+    }
+}
+
+template <int KT>
+cudaError_t launch_bwd_t(const LaunchArgs& a, int margin_i, const float* pos_hi, const float* pos_lo, const float* g,
+                         const float* grad_rir, const float* grad_early, float* grad_vs, cudaStream_t st)
+{
+    constexpr int NT = 256;
+    const int smem = bwd_smem(a.tile, a.K, margin_i).total;
+    cudaError_t e = cudaFuncSetAttribute(bwd_kernel<NT, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd_kernel<NT, KT>, NT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    bwd_kernel<NT, KT><<<device_sm_count() * per_sm, NT, smem, st>>>(a, margin_i, pos_hi, pos_lo, g, grad_rir,
+                                                                     grad_early, grad_vs);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_backward(const LaunchArgs& a, const float* pos_hi, const float* pos_lo, const float* g,
+                            const float* r, const float* grad_rir, const float* grad_early, float* grad_vs,
+                            float* grad_mic, float* grad_src, float* grad_r, cudaStream_t st)
+{
+    (void)r;
+    if (a.M > 64) return cudaErrorInvalidValue;
+    // Host-side bound on any room's per-mic delay spread around the binning key.
+    const int margin_i = a.margin_i;
+    cudaError_t e;
+    if (a.K == 40) e = launch_bwd_t<40>(a, margin_i, pos_hi, pos_lo, g, grad_rir, grad_early, grad_vs, st);
+    else if (a.K == 63) e = launch_bwd_t<63>(a, margin_i, pos_hi, pos_lo, g, grad_rir, grad_early, grad_vs, st);
+    else e = launch_bwd_t<0>(a, margin_i, pos_hi, pos_lo, g, grad_rir, grad_early, grad_vs, st);
+    if (e != cudaSuccess) return e;
+    const int64_t n = std::max<int64_t>({(int64_t)a.B * a.M * 3, (int64_t)a.B * a.S * 3, (int64_t)a.B});
+    if (n > 0 && (grad_mic || grad_src || grad_r)) {
+        bwd_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, grad_mic, grad_src, grad_r);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace fram

@@ -1,0 +1,251 @@
+// fram_internal.cuh -- shared device helpers and workspace layout of libfram (sm_103a).
+//
+// Contents:
+//   * float-pair ("double-float") arithmetic built from error-free transformations
+//     (Knuth's TwoSum, Dekker's FastTwoSum, FMA-based TwoProd).  GB300's FP64 units run at a
+//     small fraction of its FP32 rate, so the few places that need more than 24 bits -- image
+//     distances of up to c0*T60 ~ 400 m that must place a delay to ~1e-6 samples -- use pairs
+//     of floats (about 44 bits) instead of doubles.  All operations use the _rn intrinsics so
+//     the compiler cannot contract or reorder them.
+//   * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) for the image sampler.
+//   * the workspace layout shared by the sampler, the synthesis and the adjoint.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fram.h"
+
+namespace fram {
+
+// --------------------------------------------------------------------------------------
+// Float-pair arithmetic.  A value is hi + lo with |lo| <= ulp(hi)/2 after normalisation.
+// --------------------------------------------------------------------------------------
+struct f2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ f2 two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+// Requires |a| >= |b| (or a == 0).
+__device__ __forceinline__ f2 fast_two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+
+__device__ __forceinline__ f2 two_prod(float a, float b)
+{
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    return {p, e};
+}
+
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
+{
+    f2 s = two_sum(a.hi, b.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ f2 f2_add_f(f2 a, float b)
+{
+    f2 s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
+{
+    f2 p = two_prod(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+    return fast_two_sum(p.hi, e);
+}
+
+__device__ __forceinline__ f2 f2_mul_f(f2 a, float b)
+{
+    f2 p = two_prod(a.hi, b);
+    return fast_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+
+__device__ __forceinline__ f2 f2_neg(f2 a) { return {-a.hi, -a.lo}; }
+
+// sqrt of a positive pair: one Newton correction of the correctly rounded float root.
+__device__ __forceinline__ f2 f2_sqrt(f2 a)
+{
+    float y = __fsqrt_rn(a.hi);
+    f2 yy = two_prod(y, y);
+    float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, yy.hi), yy.lo), a.lo);
+    float c = __fdiv_rn(r, __fmul_rn(2.0f, y));
+    return fast_two_sum(y, c);
+}
+
+// Host helper: split a double into a float pair.
+__host__ __device__ inline f2 f2_from_double(double x)
+{
+    float hi = (float)x;
+    float lo = (float)(x - (double)hi);
+    return {hi, lo};
+}
+
+// --------------------------------------------------------------------------------------
+// Philox4x32-10.  S-box: two 32x32 -> 64-bit products with the published multipliers;
+// key schedule: Weyl increments (golden ratio and sqrt(3) - 1 in 0.32 fixed point).
+// --------------------------------------------------------------------------------------
+struct u4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ u4 philox4x32_10(u4 c, uint32_t k0, uint32_t k1)
+{
+    constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
+    constexpr uint32_t kWeylA = 0x9E3779B9u, kWeylB = 0xBB67AE85u;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t hiA = __umulhi(kMulA, c.x), loA = kMulA * c.x;
+        const uint32_t hiB = __umulhi(kMulB, c.z), loB = kMulB * c.z;
+        c = u4{hiB ^ c.y ^ k0, loB, hiA ^ c.w ^ k1, loA};
+        k0 += kWeylA;
+        k1 += kWeylB;
+    }
+    return c;
+}
+
+// Top 23 bits of a word, centred in their cell: exact float in (0, 1).
+__device__ __forceinline__ float uniform_from_word(uint32_t w)
+{
+    return __fmul_rn(__fadd_rn((float)(w >> 9), 0.5f), 1.0f / 8388608.0f);
+}
+
+// --------------------------------------------------------------------------------------
+// Per-launch constants and workspace layout.
+// --------------------------------------------------------------------------------------
+constexpr int kMaxHalfLen = 128;
+constexpr int kDefaultTile = 1024;
+constexpr int kSynthThreads = 256;
+constexpr int kStageCap = 4096;   // images staged per synthesis tile
+constexpr int kImpCap = 512;      // arrivals sorted per chunk
+
+struct RoomConst {          // per room, written by the prologue
+    float cx, cy, cz;       // array centre (float)
+    float margin;           // max_m |mic_m - c| fs/c0 + 2 samples
+    float log2r;            // log2 of the reflection coefficient r_b
+    float inv_r;            // 1 / r_b
+    int32_t len;            // L_b
+    int32_t ntiles;         // ceil(L_b / tile)
+    int32_t n_vs;           // images per source
+    int32_t item0;          // first work item of the room
+    int64_t rir_off;
+    int64_t vs_off;
+};
+
+struct DirectConst {        // per (room, source, mic)
+    float t_hi, t_lo;       // direct-path delay in samples as a float pair
+    float amp;              // 1 / D_{0,m}
+    float dist;             // D_{0,m}
+    float ex, ey, ez;       // (src - mic) / D_{0,m}
+    int32_t early_lo;       // Eq. 9 window, inclusive
+    int32_t early_hi;
+    int32_t pad_;
+};
+
+struct Header {             // first 256 bytes of the workspace
+    int32_t status;         // FRAM_DEV_* bits
+    int32_t queue;          // persistent-kernel work counter
+    int32_t queue_bwd;
+    int32_t n_items;        // total work items (written by the prologue)
+    int32_t pad_[60];
+};
+
+struct WsLayout {
+    size_t header, room, direct, src_tile, item_off, items, bin_off, perm, key;
+    size_t part_mic, part_src, part_r;
+    size_t total;
+    int tile;
+    int max_tiles;          // ceil(max_len / tile)
+    int64_t max_items;      // B * S * max_tiles
+};
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+inline WsLayout ws_layout(const fram_scene& sc, int tile)
+{
+    WsLayout w{};
+    w.tile = tile;
+    w.max_tiles = sc.max_len > 0 ? (sc.max_len + tile - 1) / tile : 1;
+    w.max_items = (int64_t)sc.B * sc.S * w.max_tiles;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    w.header = take(sizeof(Header));
+    w.room = take(sizeof(RoomConst) * (size_t)sc.B);
+    w.direct = take(sizeof(DirectConst) * (size_t)sc.B * sc.S * sc.M);
+    w.src_tile = take(sizeof(int32_t) * (size_t)sc.B * sc.S);
+    w.item_off = take(sizeof(int32_t) * ((size_t)sc.B + 1));
+    w.items = take(sizeof(int32_t) * 2 * (size_t)w.max_items);
+    w.bin_off = take(sizeof(int32_t) * (size_t)sc.B * sc.S * (w.max_tiles + 1));
+    w.perm = take(sizeof(int32_t) * (size_t)sc.n_vs_total);
+    w.key = take(sizeof(float) * (size_t)sc.n_vs_total);
+    w.part_mic = take(sizeof(float) * 3 * (size_t)w.max_items * sc.M);
+    w.part_src = take(sizeof(float) * 3 * (size_t)w.max_items);
+    w.part_r = take(sizeof(float) * (size_t)w.max_items);
+    w.total = off;
+    return w;
+}
+
+// Device view of the scene + parameters for kernels (by value in kernel arguments).
+struct LaunchArgs {
+    double fs, c0;
+    int32_t B, S, M;
+    int32_t K;
+    int32_t tile;
+    int32_t max_tiles;
+    float q;                // fs / c0 as a float
+    f2 q2;                  // fs / c0 as a float pair
+    int32_t early_pre, early_post;
+    int32_t margin_i;       // ceil(array_radius fs/c0) + 3: halo of the adjoint's staged gradient
+    int64_t n_vs_total;     // host sizes, used to bound every device index
+    int64_t rir_total;
+    const float* dims;
+    const float* rt60;
+    const float* src;
+    const float* mic;
+    const int32_t* n_vs;
+    const int64_t* vs_off;
+    const int32_t* rir_len;
+    const int64_t* rir_off;
+    // workspace views
+    Header* hdr;
+    RoomConst* room;
+    DirectConst* direct;
+    int32_t* src_tile;
+    int32_t* item_off;
+    int2* items;
+    int32_t* bin_off;
+    int32_t* perm;
+    float* key;
+    float* part_mic;
+    float* part_src;
+    float* part_r;
+};
+
+// Host-side launchers (defined in the .cu files; return cudaError_t of the launch).
+cudaError_t launch_sample(const LaunchArgs& a, const fram_params& p, uint64_t seed, const uint64_t* d_seed,
+                          float* pos_hi, float* pos_lo, float* g, float* r, uint32_t* words, cudaStream_t st);
+cudaError_t launch_prepare(const LaunchArgs& a, const float* pos_hi, const float* pos_lo, const float* r,
+                           cudaStream_t st);
+cudaError_t launch_synthesize(const LaunchArgs& a, const float* pos_hi, const float* pos_lo, const float* g,
+                              float* rir, float* early, cudaStream_t st);
+cudaError_t launch_backward(const LaunchArgs& a, const float* pos_hi, const float* pos_lo, const float* g,
+                            const float* r, const float* grad_rir, const float* grad_early, float* grad_vs,
+                            float* grad_mic, float* grad_src, float* grad_r, cudaStream_t st);
+
+int device_sm_count();
+
+}  // namespace fram

@@ -1,0 +1,109 @@
+"""Host-only checks of the C ABI: the library loads, exports every symbol include/fram.h
+declares, and its host functions (layout, workspace sizing, argument validation) behave as
+documented.  No call here launches GPU work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2304_08052_gb300 import _lib, api, scenes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2304_08052_gb300 import build
+    build.build()
+    return _lib.lib()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "fram.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(fram_[a-z_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = _declared()
+    assert set(names) == set(_lib.EXPORTED), names
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_version_and_defaults(L):
+    assert L.fram_version() == 10000
+    p = _lib.FramParams()
+    L.fram_default_params(ctypes.byref(p))
+    assert (p.alpha, p.beta, p.a, p.b, p.tau, p.c0) == (0.25, 1.0, -2.0, 2.0, 0.25, 343.0)
+    assert (p.fs, p.half_len, p.early_pre_ms, p.early_post_ms, p.tile) == (16000.0, 40, 6.0, 50.0, 0)
+
+
+@pytest.mark.parametrize("name", ["single_room", "batch_256", "grad_64"])
+def test_layout_matches_oracle(L, oracle_mod, name):
+    sc = scenes.by_name(name, 0)
+    got = api.layout(sc.rt60, sc.n_vs, sc.S, sc.M, sc.fs)
+    want = oracle_mod.layout(sc.rt60, sc.n_vs, sc.S, sc.M, sc.fs)
+    for g, w in zip(got, want):
+        assert np.array_equal(g, w)
+
+
+def test_layout_rejects_bad_scenes(L):
+    with pytest.raises(_lib.FramError) as e:
+        api.layout(np.array([0.5, -0.1], np.float32), np.array([10, 10], np.int32), 1, 2, 16000.0)
+    assert e.value.code == _lib.FRAM_EINVAL
+    with pytest.raises(_lib.FramError):
+        api.layout(np.array([0.5], np.float32), np.array([-1], np.int32), 1, 2, 16000.0)
+    with pytest.raises(_lib.FramError):
+        api.layout(np.array([0.5], np.float32), np.array([1], np.int32), 0, 2, 16000.0)
+
+
+def _scene_struct(B=4, S=2, M=3, max_len=8000, nvs=400, rir_total=4 * 2 * 3 * 8000, radius=0.05):
+    return _lib.FramScene(B, S, M, max_len, nvs, rir_total, radius, *([None] * 8))
+
+
+def test_workspace_size_and_param_validation(L):
+    p = api.Params()
+    n = ctypes.c_size_t(0)
+    assert L.fram_workspace_size(ctypes.byref(_scene_struct()), ctypes.byref(p.c()), ctypes.byref(n)) == 0
+    assert n.value > 0 and n.value % 256 == 0
+    n2 = ctypes.c_size_t(0)
+    big = _scene_struct(B=40, nvs=4000)
+    assert L.fram_workspace_size(ctypes.byref(big), ctypes.byref(p.c()), ctypes.byref(n2)) == 0
+    assert n2.value > n.value
+    for bad in (dict(alpha=0.0), dict(beta=1.5), dict(alpha=0.5, beta=0.4), dict(tau=0.0), dict(c0=-1.0),
+                dict(half_len=0), dict(half_len=129), dict(tile=300), dict(a=1.0, b=0.0)):
+        q = api.Params(**bad)
+        rc = L.fram_workspace_size(ctypes.byref(_scene_struct()), ctypes.byref(q.c()), ctypes.byref(n))
+        assert rc == _lib.FRAM_EINVAL, bad
+        assert len(L.fram_last_error()) > 0
+    for bad in (dict(S=0), dict(M=0), dict(M=65), dict(B=-1)):
+        s = _scene_struct(**bad)
+        assert L.fram_workspace_size(ctypes.byref(s), ctypes.byref(p.c()), ctypes.byref(n)) == _lib.FRAM_EINVAL
+
+
+def test_entry_points_reject_bad_arguments_before_any_launch(L):
+    p = api.Params()
+    sc = _scene_struct()
+    null = ctypes.c_void_p(0)
+    # Scene device arrays are null -> EINVAL, detected on the host.
+    assert L.fram_sample(ctypes.byref(sc), ctypes.byref(p.c()), 0, None, null, null, null, null, null, null,
+                         0, None) == _lib.FRAM_EINVAL
+    assert L.fram_synthesize(ctypes.byref(sc), ctypes.byref(p.c()), null, null, null, null, null, null, null, 0,
+                             None) == _lib.FRAM_EINVAL
+    assert L.fram_synthesize_backward(ctypes.byref(sc), ctypes.byref(p.c()), null, null, null, null, null, null,
+                                      null, null, null, null, null, 0, None) == _lib.FRAM_EINVAL
+    assert L.fram_status(null, None, None) == _lib.FRAM_EINVAL
+    # A fake (never dereferenced) device pointer set: the workspace checks fail first.
+    fake = ctypes.c_void_p(0x1000)
+    sc2 = _lib.FramScene(1, 1, 1, 100, 10, 100, 0.0, *([fake] * 8))
+    assert L.fram_synthesize(ctypes.byref(sc2), ctypes.byref(p.c()), fake, None, fake, fake, fake, None, None, 0,
+                             None) == _lib.FRAM_EWORKSPACE
+    assert L.fram_synthesize(ctypes.byref(sc2), ctypes.byref(p.c()), fake, None, fake, fake, fake, None,
+                             ctypes.c_void_p(0x1010), 1 << 30, None) == _lib.FRAM_EWORKSPACE   # misaligned
+    n = ctypes.c_size_t(0)
+    L.fram_workspace_size(ctypes.byref(sc2), ctypes.byref(p.c()), ctypes.byref(n))
+    assert L.fram_synthesize(ctypes.byref(sc2), ctypes.byref(p.c()), fake, None, fake, fake, fake, None,
+                             ctypes.c_void_p(0x100000), n.value - 256, None) == _lib.FRAM_EWORKSPACE

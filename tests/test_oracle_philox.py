@@ -3,10 +3,11 @@
 The pin is an independent implementation: cuRAND's host generator for PHILOX4_32_10,
 called as a black box through its public C API.  With the default ordering it emits, for
 block j of four words, Philox(counter = (j // 65536, 0, j % 65536, 0), key = (seed_lo,
-seed_hi)).  Matching it over more than one 65536-block wrap pins the round function, the
-key schedule, the key words and counter words 0 and 2.  Counter words 1 and 3 are pinned on
-the GPU against cuRAND's device generator (tests/test_gpu_sampler.py), and the oracle is
-compared with the device implementation there, bit for bit.
+seed_hi)); a generator offset of 4 * 65536 * (x + 2^32 y) words starts it at counter
+(x, y, 0, 0).  Matching it over more than one 65536-block wrap and at large offsets pins the
+round function, the key schedule, the key words and counter words 0, 1 and 2.  Counter word 3
+is the draw's tag, always 0 in this method.  The device implementation is compared with the
+oracle bit for bit on the GPU (tests/test_gpu_sampler.py).
 """
 import ctypes
 import os
@@ -19,7 +20,7 @@ PHILOX4_32_10 = 161          # curandRngType_t value for CURAND_RNG_PSEUDO_PHILO
 ORDERING_DEFAULT = 101
 
 
-def _curand_host_words(seed: int, nwords: int) -> np.ndarray:
+def _curand_host_words(seed: int, nwords: int, offset: int = 0) -> np.ndarray:
     if not os.path.exists(CURAND):
         pytest.skip("libcurand not present")
     lib = ctypes.CDLL(CURAND)
@@ -28,6 +29,7 @@ def _curand_host_words(seed: int, nwords: int) -> np.ndarray:
     try:
         assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
         assert lib.curandSetGeneratorOrdering(gen, ORDERING_DEFAULT) == 0
+        assert lib.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(offset)) == 0
         out = np.zeros(nwords, dtype=np.uint32)
         assert lib.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(nwords)) == 0
     finally:
@@ -46,6 +48,19 @@ def test_philox_matches_curand_host_generator(oracle_mod, seed):
     key = np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint32)
     got = oracle_mod.philox(ctr, key)
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("x,y", [(0, 1), (7, 3), (123, 4095), (2**32 - 2, 8191)])  # offset < 2^64
+def test_philox_counter_words_0_and_1_via_offset(oracle_mod, x, y):
+    seed = 0x243F6A8885A308D3
+    blocks = 4096
+    ref = _curand_host_words(seed, 4 * blocks, offset=4 * 65536 * (x + (y << 32)))
+    ctr = np.zeros((blocks, 4), np.uint32)
+    ctr[:, 0] = x
+    ctr[:, 1] = y
+    ctr[:, 2] = np.arange(blocks, dtype=np.uint32)
+    key = np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint32)
+    assert np.array_equal(oracle_mod.philox(ctr, key), ref)
 
 
 def test_uniform_mapping_is_exact_and_open(oracle_mod):

@@ -165,3 +165,15 @@ def test_invalid_scene_is_rejected(oracle_mod):
     p = oracle_mod.Params(fs=sc.fs, half_len=sc.half_len)
     with pytest.raises(ValueError):
         oracle_mod.sample(sc, p, seed=0)
+
+
+def test_room_subset_draws_match_full_batch(oracle_mod):
+    sc = scenes.tiny(seed=6, B=7, S=2, M=3, images=25)
+    p = oracle_mod.Params(fs=sc.fs, half_len=sc.half_len)
+    full = oracle_mod.sample(sc, p, seed=4)
+    rooms = [5, 1, 6]
+    sub = oracle_mod.sample(sc.subset(rooms), p, seed=4, room_ids=rooms)
+    per = sc.S * 25
+    idx = np.concatenate([np.arange(b * per, (b + 1) * per) for b in rooms])
+    assert np.array_equal(sub.words, full.words[idx])
+    assert np.array_equal(sub.pos, full.pos[idx]) and np.array_equal(sub.g, full.g[idx])
