@@ -1,0 +1,427 @@
+#!/usr/bin/env python
+"""Benchmark of the FRAM-RIR hot path on one GB300 (or N, one process per GPU under torchrun).
+
+Workload (default): large_4096 -- 4096 rooms x 2 sources x 16-mic circle at 48 kHz, K = 63
+(127-tap windowed sinc), round(6000 T60) images per (room, source), T60 ~ U[0.2, 1.2] s.
+A step is one pass of the whole hot path over the batch:
+  fwd:      fram_sample (Philox images) -> fram_synthesize (prologue, delay bins, synthesis)
+  fwd+bwd:  fwd -> fram_synthesize_backward_prepared (adjoint, reusing the forward's bins)
+value = RIRs/s of the fwd step (one RIR = one 16-channel filter per room x source), whole job.
+
+Also reported: taps/s; the synthesis kernel alone against the ALU roofline; the adjoint kernel
+alone; an end-to-end number through host buffers; the graph-captured batched path against a
+plain per-room launch loop (batch_1024 with early RIRs); the FP64 oracle on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "multi-ch RIRs/s and sinc-taps/s (fwd, fwd+bwd) at 1 GB300, % of roofline"
+
+# Algorithmic work per tap (the tap arithmetic of the paper's sum, Eq. 1 with windowed sincs):
+# forward 8 FP32-pipe operations and 1 reciprocal on the MUFU (special function) pipe; adjoint
+# 14 FP32 and 1 MUFU.  Per arrival (image x mic) 40 FP32 + 6 MUFU more, spread over its 2K+1 taps.
+FWD_FP32, BWD_FP32, ARR_FP32 = 8.0, 14.0, 40.0
+TAP_MUFU, ARR_MUFU = 1.0, 6.0
+FP32_LANES_PER_SM, MUFU_LANES_PER_SM = 128, 16
+
+
+def rank_scene_seed(base: int, rank: int) -> int:
+    """Weak scaling: every rank synthesises its own full batch, drawn from its own seed."""
+    return base + 1000003 * rank
+
+
+def combine(units_per_rank, seconds_per_rank):
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    return sum(units_per_rank) / max(seconds_per_rank)
+
+
+def alu_peak_taps(sm_count: int, clock_hz: float, K: int, fp32_per_tap: float):
+    n = 2 * K + 1
+    p_fp32 = sm_count * FP32_LANES_PER_SM * clock_hz
+    p_mufu = sm_count * MUFU_LANES_PER_SM * clock_hz
+    by_fp32 = p_fp32 / (fp32_per_tap + ARR_FP32 / n)
+    by_mufu = p_mufu / (TAP_MUFU + ARR_MUFU / n)
+    return min(by_fp32, by_mufu), ("mufu" if by_mufu < by_fp32 else "fp32")
+
+
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while a region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.gpu_id], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _gpu_uuid(torch):
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except Exception:
+        return "0"
+
+
+def _time_steps(torch, fn, steps, dist_ok):
+    if dist_ok:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record()
+    for k in range(steps):
+        fn(k)
+    e.record()
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e)
+    if dist_ok:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    return ms / 1000.0
+
+
+def cpu_baseline(sc, seed, rooms, params):
+    """The FP64 oracle as it stands, on the host cores, on `rooms` of the workload."""
+    import oracle
+    op = oracle.Params(fs=params.fs, half_len=params.half_len, alpha=params.alpha, beta=params.beta, a=params.a,
+                       b=params.b, tau=params.tau, c0=params.c0)
+    sub = sc.subset(rooms)
+    t0 = time.perf_counter()
+    ref = oracle.sample(sub, op, seed, room_ids=list(rooms))
+    oracle.synthesize(sub, op, ref.pos, ref.g, ref.r)
+    dt = time.perf_counter() - t0
+    return len(rooms) * sc.S, dt, oracle.num_threads()
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on this machine's host cores, bounded samples of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2304_08052_gb300 import api, scenes
+    sc = scenes.by_name(args.workload, 0)
+    params = api.Params(fs=sc.fs, half_len=sc.half_len)
+    per_step = args.ref_rooms
+    import numpy as np
+    rng = np.random.default_rng(0)
+    for _ in range(args.warmup):
+        cpu_baseline(sc, 1, sorted(rng.choice(sc.B, 1, replace=False).tolist()), params)
+    units, secs, cores = 0, 0.0, 1
+    for k in range(args.steps):
+        rooms = sorted(rng.choice(sc.B, per_step, replace=False).tolist())
+        u, dt, cores = cpu_baseline(sc, 100 + k, rooms, params)
+        units += u
+        secs += dt
+    value = units / secs
+    sample = f"{per_step} seeded rooms of {args.workload} per step (sample + synthesize, FP64)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RIRs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload},
+            "cpu_baseline": {"value": value, "unit": "RIRs/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "RIRs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
+    ap.add_argument("--workload", default="large_4096")
+    ap.add_argument("--ref-rooms", type=int, default=8)
+    ap.add_argument("--cpu-rooms", type=int, default=64)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the per-room comparison and the CPU baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    from paper_2304_08052_gb300 import api, build, scenes
+
+    build.build()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist_ok = world > 1
+    if dist_ok:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    sc = scenes.by_name(args.workload, rank_scene_seed(0, rank))
+    params = api.Params(fs=sc.fs, half_len=sc.half_len)
+    ds = api.DeviceScene(sc, params)
+    N, T = ds.n_vs_total, ds.rir_total
+    vs = api.Images(torch.empty((N, 3), device="cuda"), torch.empty((N, 3), device="cuda"),
+                    torch.empty(N, device="cuda"), torch.empty(sc.B, device="cuda"))
+    rir = torch.empty(T, device="cuda")
+    G = torch.empty(T, device="cuda").normal_(generator=torch.Generator(device="cuda").manual_seed(7))
+    grads = (torch.empty((N, 3), device="cuda"), torch.empty((sc.B, sc.M, 3), device="cuda"),
+             torch.empty((sc.B, sc.S, 3), device="cuda"), torch.empty(sc.B, device="cuda"))
+    taps = api.algorithmic_taps(ds)
+    rirs = sc.B * sc.S
+
+    def fwd(k):
+        api.sample(ds, seed=1000 + k, out=vs)
+        api.synthesize_raw(ds, vs.pos_hi, vs.pos_lo, vs.g, vs.r, rir=rir)
+
+    def fwd_bwd(k):
+        fwd(k)
+        api.synthesize_backward_prepared(ds, vs.pos_hi, vs.pos_lo, vs.g, vs.r, G, None, out=grads)
+
+    peaks, peak_kind = _measured_peaks()
+    clock_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+
+    for k in range(args.warmup):
+        fwd_bwd(k)
+    torch.cuda.synchronize()
+    assert ds.status() == 0, "device status flags set"
+    with ClockSampler(_gpu_uuid(torch)) as clk:
+        t_fwd = _time_steps(torch, fwd, args.steps, dist_ok)
+        t_fb = _time_steps(torch, fwd_bwd, args.steps, dist_ok)
+        # Kernels alone on the same stream, after one preparation.
+        api.prepare(ds, vs.pos_hi, vs.pos_lo, vs.r)
+        t_syn = _time_steps(torch, lambda k: api.synthesize_prepared(ds, vs.pos_hi, vs.pos_lo, vs.g, vs.r, rir),
+                            args.steps, False)
+        t_bwd = _time_steps(torch, lambda k: api.synthesize_backward_prepared(ds, vs.pos_hi, vs.pos_lo, vs.g, vs.r, G,
+                                                                              None, out=grads), args.steps, False)
+    clocks = clk.summary()
+    assert ds.status() == 0, "device status flags set"
+
+    value = combine([args.steps * rirs] * world, [t_fwd] * world) if not dist_ok else world * args.steps * rirs / t_fwd
+    ms_step = 1000.0 * t_fwd / args.steps
+    K = params.half_len
+    peak_fwd, lim_fwd = alu_peak_taps(sm_count, clock_hz, K, FWD_FP32)
+    peak_bwd, lim_bwd = alu_peak_taps(sm_count, clock_hz, K, BWD_FP32)
+    syn_s = t_syn / args.steps
+    bwd_s = t_bwd / args.steps
+    ach_fwd = taps / syn_s
+    ach_bwd = taps / bwd_s
+    out_bytes = 4 * T
+    line = {
+        "metric": METRIC, "value": value, "unit": "RIRs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "rooms": sc.B, "sources": sc.S, "mics": sc.M, "fs": sc.fs,
+                   "half_len": K, "images": int(N), "rir_samples": int(T), "taps_per_step": taps,
+                   "l2": f"outputs {out_bytes / 1e9:.1f} GB per step, larger than L2 (129 MB)",
+                   "tile": params.tile or 1024},
+        "taps_per_s": taps * args.steps * world / t_fwd,
+        "fwd_bwd": {"value": world * args.steps * rirs / t_fb, "unit": "RIRs/s",
+                    "ms_per_step": 1000.0 * t_fb / args.steps, "taps_per_s": world * 2 * taps * args.steps / t_fb},
+        "roofline": {"bound": "alu", "achieved": ach_fwd / 1e9, "peak": peak_fwd / 1e9, "unit": "Gtap/s",
+                     "frac": ach_fwd / peak_fwd, "traffic": None, "kernel": "synth_kernel",
+                     "limit": lim_fwd, "kernel_ms": 1000.0 * syn_s, "hbm_gbs": out_bytes / syn_s / 1e9,
+                     "peak_basis": f"{sm_count} SMs x ({FP32_LANES_PER_SM} FP32, {MUFU_LANES_PER_SM} MUFU) lanes x "
+                                   f"{clock_hz / 1e6:.0f} MHz ({peak_kind} sm_max_mhz); per tap "
+                                   f"{FWD_FP32:.0f} FP32 + {TAP_MUFU:.0f} MUFU, per arrival {ARR_FP32:.0f} FP32 + "
+                                   f"{ARR_MUFU:.0f} MUFU"},
+        "roofline_bwd": {"bound": "alu", "achieved": ach_bwd / 1e9, "peak": peak_bwd / 1e9, "unit": "Gtap/s",
+                         "frac": ach_bwd / peak_bwd, "kernel": "bwd_kernel", "limit": lim_bwd,
+                         "kernel_ms": 1000.0 * bwd_s},
+        "gpu_launches": 5 * args.steps,
+        "clocks": clocks,
+    }
+
+    if not args.no_e2e:
+        line["e2e"] = e2e(torch, api, sc, params, ds, args, rirs, dist_ok, world)
+
+    if not args.no_extras and rank == 0:
+        line["graph_vs_per_room"] = graph_vs_per_room(torch, api, scenes)
+        u, dt, cores = cpu_baseline(sc, 1, list(range(args.cpu_rooms)), params)
+        line["cpu_baseline"] = {"value": u / dt, "unit": "RIRs/s", "cores": cores, "kind": "oracle",
+                                "sample": f"first {args.cpu_rooms} rooms of {args.workload} (sample + synthesize, "
+                                          f"FP64, {dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist_ok:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def e2e(torch, api, sc, params, ds, args, rirs, dist_ok, world):
+    """Same step through the public API from pinned host buffers: H2D of the scene arrays,
+    fram_sample + fram_synthesize, D2H of the RIR buffer."""
+    import numpy as np
+    host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
+            dict(dims=sc.dims, rt60=sc.rt60, src=sc.src, mic=sc.mic, n_vs=sc.n_vs.astype(np.int32),
+                 vs_off=ds.vs_off, rir_len=ds.rir_len, rir_off=ds.rir_off).items()}
+    dev = {"dims": ds.dims, "rt60": ds.rt60, "src": ds.src, "mic": ds.mic, "n_vs": ds.n_vs, "vs_off": ds.vs_off_d,
+           "rir_len": ds.rir_len_d, "rir_off": ds.rir_off_d}
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    out_host = torch.empty(ds.rir_total, dtype=torch.float32).pin_memory()
+    N = ds.n_vs_total
+    vs = api.Images(torch.empty((N, 3), device="cuda"), torch.empty((N, 3), device="cuda"),
+                    torch.empty(N, device="cuda"), torch.empty(sc.B, device="cuda"))
+    rir = torch.empty(ds.rir_total, device="cuda")
+
+    def step(k):
+        for name, t in host.items():
+            dev[name].copy_(t, non_blocking=True)
+        api.sample(ds, seed=2000 + k, out=vs)
+        api.synthesize_raw(ds, vs.pos_hi, vs.pos_lo, vs.g, vs.r, rir=rir)
+        out_host.copy_(rir, non_blocking=True)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    steps = max(3, min(args.steps, 5))
+    t = _time_steps(torch, step, steps, dist_ok)
+    return {"value": world * steps * rirs / t, "unit": "RIRs/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(4 * ds.rir_total), "ms_per_step": 1000.0 * t / steps}
+
+
+def graph_vs_per_room(torch, api, scenes):
+    """batch_1024 (1024 rooms x 3 sources x 8 mics, early RIRs): one CUDA-graph replay of
+    sample + synthesize with the seed read from device memory, against a loop of plain
+    per-room calls on the same GPU."""
+    sc = scenes.batch_1024(0)
+    params = api.Params(fs=sc.fs, half_len=sc.half_len)
+    ds = api.DeviceScene(sc, params)
+    N = ds.n_vs_total
+    vs = api.Images(torch.empty((N, 3), device="cuda"), torch.empty((N, 3), device="cuda"),
+                    torch.empty(N, device="cuda"), torch.empty(sc.B, device="cuda"))
+    rir = torch.empty(ds.rir_total, device="cuda")
+    early = torch.empty(ds.rir_total, device="cuda")
+    d_seed = torch.zeros(1, dtype=torch.int64, device="cuda")
+    seeds_host = torch.arange(1, 64, dtype=torch.int64).pin_memory()
+
+    def body():
+        api.sample(ds, seed=0, d_seed=d_seed, out=vs)
+        api.synthesize_raw(ds, vs.pos_hi, vs.pos_lo, vs.g, vs.r, early=True, rir=rir, early_out=early)
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            body()
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        body()
+    reps = 10
+    for k in range(3):
+        d_seed.copy_(seeds_host[k:k + 1], non_blocking=True)
+        g.replay()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for k in range(reps):
+        d_seed.copy_(seeds_host[3 + k:4 + k], non_blocking=True)
+        g.replay()
+    t1.record()
+    torch.cuda.synchronize()
+    t_graph = t0.elapsed_time(t1) / 1000.0 / reps
+    assert ds.status() == 0
+
+    rooms = [api.DeviceScene(sc.subset([b]), params) for b in range(sc.B)]
+    bufs = []
+    for d in rooms:
+        n = d.n_vs_total
+        bufs.append((api.Images(torch.empty((n, 3), device="cuda"), torch.empty((n, 3), device="cuda"),
+                                torch.empty(n, device="cuda"), torch.empty(1, device="cuda")),
+                     torch.empty(d.rir_total, device="cuda"), torch.empty(d.rir_total, device="cuda")))
+
+    def per_room():
+        for d, (v, h, he) in zip(rooms, bufs):
+            api.sample(d, seed=5, out=v)
+            api.synthesize_raw(d, v.pos_hi, v.pos_lo, v.g, v.r, early=True, rir=h, early_out=he)
+
+    per_room()
+    torch.cuda.synchronize()
+    t0.record()
+    per_room()
+    t1.record()
+    torch.cuda.synchronize()
+    t_loop = t0.elapsed_time(t1) / 1000.0
+    rirs = sc.B * sc.S
+    return {"workload": "batch_1024 (1024 rooms x 3 src x 8 mics, 16 kHz, K=40, + early RIR)",
+            "graph_batched": {"value": rirs / t_graph, "unit": "RIRs/s", "ms_per_batch": 1000.0 * t_graph},
+            "per_room_loop": {"value": rirs / t_loop, "unit": "RIRs/s", "ms_per_batch": 1000.0 * t_loop,
+                              "note": "1024 x (fram_sample + fram_synthesize) launched one room at a time"},
+            "speedup": t_loop / t_graph}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

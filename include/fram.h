@@ -177,6 +177,28 @@ int fram_synthesize_backward(const fram_scene* scene, const fram_params* p,
                              void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * The two stages of fram_synthesize / fram_synthesize_backward, for callers that reuse one
+ * preparation (for instance a forward and a backward pass over the same images, or timing the
+ * main kernel alone).  fram_prepare clears the status word and builds, in the workspace, the
+ * per-room tables (RIR length, array centre, direct paths of Eq. 1 and the Eq. 9 windows),
+ * the work-item list and each image's delay bin; it reads vs_pos_hi/lo and r only.
+ * fram_synthesize_prepared and fram_synthesize_backward_prepared then run the main kernel;
+ * they require the most recent fram_prepare on this workspace to have seen the same scene,
+ * parameters, image positions and r (otherwise results are undefined, but every index stays
+ * bounded by the host sizes).  Arguments mean what they mean for the one-shot calls.
+ */
+int fram_prepare(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi, const float* vs_pos_lo,
+                 const float* r, void* workspace, size_t workspace_bytes, void* stream);
+int fram_synthesize_prepared(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi,
+                             const float* vs_pos_lo, const float* vs_g, const float* r, float* rir, float* early,
+                             void* workspace, size_t workspace_bytes, void* stream);
+int fram_synthesize_backward_prepared(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi,
+                                      const float* vs_pos_lo, const float* vs_g, const float* r,
+                                      const float* grad_rir, const float* grad_early, float* grad_vs,
+                                      float* grad_mic, float* grad_src, float* grad_r,
+                                      void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * Synchronises `stream` and reads the device status word that the last call which used
  * this workspace wrote (FRAM_DEV_* bits) into *flags.  Returns FRAM_EDEVICE if any bit is
  * set, FRAM_ECUDA on a CUDA error, FRAM_OK otherwise.

@@ -23,7 +23,8 @@ FRAM_DEV_NONFINITE = 0x4
 
 # Every symbol include/fram.h declares (checked by tests/test_abi.py).
 EXPORTED = ("fram_version", "fram_last_error", "fram_default_params", "fram_layout", "fram_workspace_size",
-            "fram_sample", "fram_synthesize", "fram_synthesize_backward", "fram_status")
+            "fram_sample", "fram_synthesize", "fram_synthesize_backward", "fram_status", "fram_prepare",
+            "fram_synthesize_prepared", "fram_synthesize_backward_prepared")
 
 
 class FramParams(ctypes.Structure):
@@ -69,8 +70,10 @@ def lib():
         L.fram_synthesize.argtypes = [S, P, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         L.fram_synthesize_backward.argtypes = [S, P, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         L.fram_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
-        for name in ("fram_layout", "fram_workspace_size", "fram_sample", "fram_synthesize",
-                     "fram_synthesize_backward", "fram_status"):
+        L.fram_prepare.argtypes = [S, P, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        L.fram_synthesize_prepared.argtypes = L.fram_synthesize.argtypes
+        L.fram_synthesize_backward_prepared.argtypes = L.fram_synthesize_backward.argtypes
+        for name in EXPORTED[3:]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib

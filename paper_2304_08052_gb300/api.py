@@ -219,3 +219,49 @@ class _FramRIR(torch.autograd.Function):
 def rir(sc: DeviceScene, src, mic, vs_pos, r, g, vs_pos_lo=None, early: bool = False):
     """Differentiable RIR synthesis (autograd through fram_synthesize_backward)."""
     return _FramRIR.apply(src, mic, vs_pos, r, g, vs_pos_lo, sc, early)
+
+
+def prepare(sc: DeviceScene, pos_hi, pos_lo, r, src=None, mic=None):
+    """fram_prepare: per-room tables, work items and delay bins in the workspace."""
+    src = sc.src if src is None else src
+    mic = sc.mic if mic is None else mic
+    check(lib().fram_prepare(ctypes.byref(sc.c_scene(src, mic)), ctypes.byref(sc.params.c()), _ptr(pos_hi),
+                             _ptr(pos_lo), _ptr(r), ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes),
+                             _stream()))
+
+
+def synthesize_prepared(sc: DeviceScene, pos_hi, pos_lo, g, r, rir, early_out=None, src=None, mic=None):
+    """fram_synthesize_prepared: the synthesis kernel alone, after prepare() on the same inputs."""
+    src = sc.src if src is None else src
+    mic = sc.mic if mic is None else mic
+    check(lib().fram_synthesize_prepared(ctypes.byref(sc.c_scene(src, mic)), ctypes.byref(sc.params.c()),
+                                         _ptr(pos_hi), _ptr(pos_lo), _ptr(g), _ptr(r), _ptr(rir), _ptr(early_out),
+                                         ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes), _stream()))
+    return rir
+
+
+def synthesize_backward_prepared(sc: DeviceScene, pos_hi, pos_lo, g, r, grad_rir, grad_early=None, out=None,
+                                 src=None, mic=None):
+    """fram_synthesize_backward_prepared: the adjoint kernels alone, after prepare()."""
+    dev = sc.dims.device
+    if out is None:
+        out = (torch.empty((sc.n_vs_total, 3), dtype=torch.float32, device=dev),
+               torch.empty((sc.B, sc.M, 3), dtype=torch.float32, device=dev),
+               torch.empty((sc.B, sc.S, 3), dtype=torch.float32, device=dev),
+               torch.empty(sc.B, dtype=torch.float32, device=dev))
+    gv, gm, gs, gr = out
+    src = sc.src if src is None else src
+    mic = sc.mic if mic is None else mic
+    check(lib().fram_synthesize_backward_prepared(ctypes.byref(sc.c_scene(src, mic)), ctypes.byref(sc.params.c()),
+                                                  _ptr(pos_hi), _ptr(pos_lo), _ptr(g), _ptr(r), _ptr(grad_rir),
+                                                  _ptr(grad_early), _ptr(gv), _ptr(gm), _ptr(gs), _ptr(gr),
+                                                  ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes),
+                                                  _stream()))
+    return out
+
+
+def algorithmic_taps(sc) -> int:
+    """Windowed-sinc taps one synthesis performs: sum_b S M (I_b + 1)(2K + 1)."""
+    K = int(sc.params.half_len) if isinstance(sc, DeviceScene) else int(sc.half_len)
+    scene = sc.scene if isinstance(sc, DeviceScene) else sc
+    return int(scene.S * scene.M * (np.asarray(scene.n_vs, np.int64) + 1).sum() * (2 * K + 1))

@@ -4,7 +4,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "fram_internal.cuh"
 
@@ -39,6 +41,34 @@ int device_sm_count()
         cache[dev] = n > 0 ? n : 1;
     }
     return cache[dev];
+}
+
+cudaError_t kernel_residency(const void* func, int threads, int smem, int* per_sm)
+{
+    struct Entry {
+        const void* func;
+        int dev, threads, smem, per_sm;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry& c : cache)
+        if (c.func == func && c.dev == dev && c.threads == threads && c.smem == smem) {
+            *per_sm = c.per_sm;
+            return cudaSuccess;
+        }
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, func, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (n < 1) n = 1;
+    cache.push_back({func, dev, threads, smem, n});
+    *per_sm = n;
+    return cudaSuccess;
 }
 
 static int check_params(const fram_params* p)
@@ -198,25 +228,83 @@ int fram_sample(const fram_scene* scene, const fram_params* p, uint64_t seed, co
     return FRAM_OK;
 }
 
-int fram_synthesize(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi, const float* vs_pos_lo,
-                    const float* vs_g, const float* r, float* rir, float* early, void* workspace,
-                    size_t workspace_bytes, void* stream)
+static int common_checks(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi, const float* vs_g,
+                         const float* r, void* ws, size_t ws_bytes, WsLayout* w)
+{
+    int rc;
+    if ((rc = check_params(p)) != FRAM_OK) return rc;
+    if ((rc = check_scene(scene, true)) != FRAM_OK) return rc;
+    if ((rc = check_ws(scene, p, ws, ws_bytes, w)) != FRAM_OK) return rc;
+    if (scene->n_vs_total > 0 && (!vs_pos_hi || !vs_g)) return fail(FRAM_EINVAL, "vs_pos_hi and vs_g must not be null");
+    if (scene->B > 0 && !r) return fail(FRAM_EINVAL, "r must not be null");
+    return FRAM_OK;
+}
+
+int fram_prepare(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi, const float* vs_pos_lo,
+                 const float* r, void* workspace, size_t workspace_bytes, void* stream)
 {
     int rc;
     if ((rc = check_params(p)) != FRAM_OK) return rc;
     if ((rc = check_scene(scene, true)) != FRAM_OK) return rc;
     WsLayout w;
     if ((rc = check_ws(scene, p, workspace, workspace_bytes, &w)) != FRAM_OK) return rc;
-    if (scene->n_vs_total > 0 && (!vs_pos_hi || !vs_g)) return fail(FRAM_EINVAL, "vs_pos_hi and vs_g must not be null");
+    if (scene->n_vs_total > 0 && !vs_pos_hi) return fail(FRAM_EINVAL, "vs_pos_hi must not be null");
     if (scene->B > 0 && !r) return fail(FRAM_EINVAL, "r must not be null");
+    const LaunchArgs a = make_args(scene, p, w, workspace);
+    cudaError_t e = launch_prepare(a, vs_pos_hi, vs_pos_lo, r, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "fram_prepare");
+    return FRAM_OK;
+}
+
+int fram_synthesize_prepared(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi,
+                             const float* vs_pos_lo, const float* vs_g, const float* r, float* rir, float* early,
+                             void* workspace, size_t workspace_bytes, void* stream)
+{
+    WsLayout w;
+    int rc = common_checks(scene, p, vs_pos_hi, vs_g, r, workspace, workspace_bytes, &w);
+    if (rc != FRAM_OK) return rc;
     if (scene->rir_total > 0 && !rir) return fail(FRAM_EINVAL, "rir must not be null");
+    if (scene->B == 0) return FRAM_OK;
     const LaunchArgs a = make_args(scene, p, w, workspace);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_prepare(a, vs_pos_hi, vs_pos_lo, r, st);
-    if (e != cudaSuccess) return cuda_fail(e, "fram_synthesize: prologue");
-    if (scene->B == 0) return FRAM_OK;
+    cudaError_t e = cudaMemsetAsync(&a.hdr->queue, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return cuda_fail(e, "fram_synthesize: resetting the work counter");
     e = launch_synthesize(a, vs_pos_hi, vs_pos_lo, vs_g, rir, early, st);
     if (e != cudaSuccess) return cuda_fail(e, "fram_synthesize: launch");
+    return FRAM_OK;
+}
+
+int fram_synthesize(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi, const float* vs_pos_lo,
+                    const float* vs_g, const float* r, float* rir, float* early, void* workspace,
+                    size_t workspace_bytes, void* stream)
+{
+    WsLayout w;
+    int rc = common_checks(scene, p, vs_pos_hi, vs_g, r, workspace, workspace_bytes, &w);
+    if (rc != FRAM_OK) return rc;
+    if (scene->rir_total > 0 && !rir) return fail(FRAM_EINVAL, "rir must not be null");
+    if ((rc = fram_prepare(scene, p, vs_pos_hi, vs_pos_lo, r, workspace, workspace_bytes, stream)) != FRAM_OK)
+        return rc;
+    return fram_synthesize_prepared(scene, p, vs_pos_hi, vs_pos_lo, vs_g, r, rir, early, workspace, workspace_bytes,
+                                    stream);
+}
+
+int fram_synthesize_backward_prepared(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi,
+                                      const float* vs_pos_lo, const float* vs_g, const float* r,
+                                      const float* grad_rir, const float* grad_early, float* grad_vs, float* grad_mic,
+                                      float* grad_src, float* grad_r, void* workspace, size_t workspace_bytes,
+                                      void* stream)
+{
+    WsLayout w;
+    int rc = common_checks(scene, p, vs_pos_hi, vs_g, r, workspace, workspace_bytes, &w);
+    if (rc != FRAM_OK) return rc;
+    if (scene->B == 0) return FRAM_OK;
+    const LaunchArgs a = make_args(scene, p, w, workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(&a.hdr->queue_bwd, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return cuda_fail(e, "fram_synthesize_backward: resetting the work counter");
+    e = launch_backward(a, vs_pos_hi, vs_pos_lo, vs_g, r, grad_rir, grad_early, grad_vs, grad_mic, grad_src, grad_r,
+                        st);
+    if (e != cudaSuccess) return cuda_fail(e, "fram_synthesize_backward: launch");
     return FRAM_OK;
 }
 
@@ -225,22 +313,13 @@ int fram_synthesize_backward(const fram_scene* scene, const fram_params* p, cons
                              const float* grad_early, float* grad_vs, float* grad_mic, float* grad_src, float* grad_r,
                              void* workspace, size_t workspace_bytes, void* stream)
 {
-    int rc;
-    if ((rc = check_params(p)) != FRAM_OK) return rc;
-    if ((rc = check_scene(scene, true)) != FRAM_OK) return rc;
     WsLayout w;
-    if ((rc = check_ws(scene, p, workspace, workspace_bytes, &w)) != FRAM_OK) return rc;
-    if (scene->n_vs_total > 0 && (!vs_pos_hi || !vs_g)) return fail(FRAM_EINVAL, "vs_pos_hi and vs_g must not be null");
-    if (scene->B > 0 && !r) return fail(FRAM_EINVAL, "r must not be null");
-    const LaunchArgs a = make_args(scene, p, w, workspace);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_prepare(a, vs_pos_hi, vs_pos_lo, r, st);
-    if (e != cudaSuccess) return cuda_fail(e, "fram_synthesize_backward: prologue");
-    if (scene->B == 0) return FRAM_OK;
-    e = launch_backward(a, vs_pos_hi, vs_pos_lo, vs_g, r, grad_rir, grad_early, grad_vs, grad_mic, grad_src, grad_r,
-                        st);
-    if (e != cudaSuccess) return cuda_fail(e, "fram_synthesize_backward: launch");
-    return FRAM_OK;
+    int rc = common_checks(scene, p, vs_pos_hi, vs_g, r, workspace, workspace_bytes, &w);
+    if (rc != FRAM_OK) return rc;
+    if ((rc = fram_prepare(scene, p, vs_pos_hi, vs_pos_lo, r, workspace, workspace_bytes, stream)) != FRAM_OK)
+        return rc;
+    return fram_synthesize_backward_prepared(scene, p, vs_pos_hi, vs_pos_lo, vs_g, r, grad_rir, grad_early, grad_vs,
+                                             grad_mic, grad_src, grad_r, workspace, workspace_bytes, stream);
 }
 
 int fram_status(void* workspace, void* stream, int32_t* flags)

@@ -317,12 +317,9 @@ cudaError_t launch_bwd_t(const LaunchArgs& a, int margin_i, const float* pos_hi,
 {
     constexpr int NT = 256;
     const int smem = bwd_smem(a.tile, a.K, margin_i).total;
-    cudaError_t e = cudaFuncSetAttribute(bwd_kernel<NT, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd_kernel<NT, KT>, NT, smem);
+    cudaError_t e = kernel_residency((const void*)bwd_kernel<NT, KT>, NT, smem, &per_sm);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
     bwd_kernel<NT, KT><<<device_sm_count() * per_sm, NT, smem, st>>>(a, margin_i, pos_hi, pos_lo, g, grad_rir,
                                                                      grad_early, grad_vs);
     return cudaGetLastError();

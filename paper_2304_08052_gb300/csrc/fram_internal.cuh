@@ -248,4 +248,10 @@ cudaError_t launch_backward(const LaunchArgs& a, const float* pos_hi, const floa
 
 int device_sm_count();
 
+// Raises the kernel's dynamic shared-memory limit to `smem` (once per device and size) and
+// returns how many CTAs of `threads` threads fit on one SM.  Results are cached, so after the
+// first call with a configuration no CUDA API call other than the launch itself is made --
+// which keeps the entry points capturable in a CUDA graph.
+cudaError_t kernel_residency(const void* func, int threads, int smem, int* per_sm);
+
 }  // namespace fram

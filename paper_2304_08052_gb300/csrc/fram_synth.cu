@@ -602,12 +602,9 @@ cudaError_t launch_synthesize(const LaunchArgs& a, const float* pos_hi, const fl
                               float* rir, float* early, cudaStream_t st)
 {
     const int smem = synth_smem(a.tile, a.K).total;
-    cudaError_t e = cudaFuncSetAttribute(synth_kernel<kSynthThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, synth_kernel<kSynthThreads>, kSynthThreads, smem);
+    cudaError_t e = kernel_residency((const void*)synth_kernel<kSynthThreads>, kSynthThreads, smem, &per_sm);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
     const int grid = device_sm_count() * per_sm;
     synth_kernel<kSynthThreads><<<grid, kSynthThreads, smem, st>>>(a, pos_hi, pos_lo, g, rir, early);
     return cudaGetLastError();

@@ -103,16 +103,17 @@ def test_sampler_matches_oracle(oracle_mod, name, seed):
     # Reflection counts.
     g = vs.g.cpu().numpy().astype(np.float64)
     assert np.max(np.abs(g - ref.g) / ref.g) < 2e-6
-    tie = np.abs(ref.g - np.round(ref.g)) < 1e-5 * ref.g
-    assert tie.mean() < 1e-4
-    assert np.array_equal(np.floor(g)[~tie], np.floor(ref.g)[~tie])
+    # floor(g) must agree except where FP32 and FP64 sit on either side of an integer.
+    mism = np.floor(g) != np.floor(ref.g)
+    near_tie = np.abs(ref.g - np.round(ref.g)) < 1e-5 * ref.g
+    assert np.all(near_tie[mism]) and mism.mean() < 1e-4, (mism.sum(), g.size)
 
 
 def test_sampler_seed_from_device_memory(oracle_mod):
     sc = scenes.tiny(seed=2, B=3, S=2, M=2, images=50)
     ds = api.DeviceScene(sc, _params(sc))
     seed = 0x1234_5678_9ABC_DEF0
-    d_seed = torch.tensor([seed - 2**64], dtype=torch.int64, device="cuda")
+    d_seed = torch.tensor([seed], dtype=torch.int64, device="cuda")   # seed < 2^63
     a = api.sample(ds, seed=0, d_seed=d_seed, words=True)
     b = api.sample(ds, seed=seed, words=True)
     torch.cuda.synchronize()
