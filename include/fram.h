@@ -205,6 +205,24 @@ int fram_synthesize_backward_prepared(const fram_scene* scene, const fram_params
  */
 int fram_status(void* workspace, void* stream, int32_t* flags);
 
+/*
+ * fram_synthesize without a workspace argument, for callers that cannot allocate device
+ * memory (a plugin whose host application owns all device memory, a real-time thread that
+ * must not block on cudaMalloc/cudaFree, a fixed device-memory budget).  The paper has no
+ * counterpart: this is a deployment convenience around the same synthesis.
+ * Inputs, outputs and results are those of fram_synthesize.  The scratch is a static 16 MiB
+ * device array that every GPU loading libfram reserves until the process exits; a scene whose
+ * fram_workspace_size exceeds 16 MiB is rejected with FRAM_EWORKSPACE before any GPU work.
+ * The first call on a device (with that device current) looks up the array's device address
+ * with cudaGetSymbolAddress and caches it; make that first call before any stream capture.
+ * All calls on a device share the one array: calls that overlap on the GPU (different streams
+ * or threads without ordering) race and corrupt each other's results.  Device status bits of
+ * these calls are not reported (fram_status needs the caller's workspace).  Allocates nothing.
+ */
+int fram_synthesize_noalloc(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi,
+                            const float* vs_pos_lo, const float* vs_g, const float* r, float* rir,
+                            float* early, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,6 +25,8 @@ static int fail(int code, const char* fmt, ...)
     return code;
 }
 
+int record_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 static int cuda_fail(cudaError_t e, const char* what)
 {
     return fail(FRAM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
