@@ -27,13 +27,6 @@ constexpr float kPi = 3.14159265358979323846f;
 constexpr float kInvPi = 0.31830988618379067f;
 constexpr float kTinyDelta = 9.313225746154785e-10f;
 
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 // d/dx sinc(x) for |x| <= 1/2: odd Taylor series sum_j (-1)^j 2j pi^(2j) x^(2j-1) / (2j+1)!.
 __device__ __forceinline__ float dsinc_small(float x)
 {

@@ -87,6 +87,61 @@ __device__ __forceinline__ f2 f2_sqrt(f2 a)
     return fast_two_sum(y, c);
 }
 
+// Hardware approximations (MUFU): relative error about one ulp.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// sqrt of a positive pair from an approximate float root: the pair residual a - y^2 is formed
+// exactly and one Newton correction y + (a - y^2)/(2y) restores ~44-bit accuracy, so the seed
+// and the correction's reciprocal only need float accuracy.
+__device__ __forceinline__ f2 f2_sqrt_fast(f2 a)
+{
+    const float y = sqrt_approx(a.hi);
+    const f2 yy = two_prod(y, y);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, yy.hi), yy.lo), a.lo);
+    return fast_two_sum(y, __fmul_rn(r, __fmul_rn(0.5f, rcp_approx(y))));
+}
+
+// sin(pi x) and cos(pi x) for |x| <= 1/2 (arguments here are fractional delays delta and
+// delta / K): Taylor series of sin and cos truncated after x^13 and x^14, whose remainders
+// are below 7e-10 and 7e-11 on that interval; Horner evaluation in x^2.
+__device__ __forceinline__ float sinpi_poly(float x)
+{
+    const float x2 = x * x;
+    float p = 0.00046630280576761234f;
+    p = __fmaf_rn(p, x2, -0.007370430945714348f);
+    p = __fmaf_rn(p, x2, 0.08214588661112819f);
+    p = __fmaf_rn(p, x2, -0.5992645293207919f);
+    p = __fmaf_rn(p, x2, 2.550164039877345f);
+    p = __fmaf_rn(p, x2, -5.167712780049969f);
+    p = __fmaf_rn(p, x2, 3.141592653589793f);
+    return p * x;
+}
+
+__device__ __forceinline__ float cospi_poly(float x)
+{
+    const float x2 = x * x;
+    float p = -0.00010463810492484565f;
+    p = __fmaf_rn(p, x2, 0.001929574309403922f);
+    p = __fmaf_rn(p, x2, -0.02580689139001405f);
+    p = __fmaf_rn(p, x2, 0.23533063035889312f);
+    p = __fmaf_rn(p, x2, -1.3352627688545893f);
+    p = __fmaf_rn(p, x2, 4.058712126416768f);
+    p = __fmaf_rn(p, x2, -4.934802200544679f);
+    return __fmaf_rn(p, x2, 1.0f);
+}
+
 // Host helper: split a double into a float pair.
 __host__ __device__ inline f2 f2_from_double(double x)
 {
@@ -130,7 +185,7 @@ __device__ __forceinline__ float uniform_from_word(uint32_t w)
 constexpr int kMaxHalfLen = 128;
 constexpr int kDefaultTile = 1024;
 constexpr int kSynthThreads = 256;
-constexpr int kStageCap = 4096;   // images staged per synthesis tile
+constexpr int kStageCap = 2048;   // images staged per synthesis tile
 constexpr int kImpCap = 512;      // arrivals sorted per chunk
 
 struct RoomConst {          // per room, written by the prologue

@@ -37,13 +37,6 @@ namespace {
 constexpr float kTwoPiInv = 0.15915494309189535f;   // 1 / (2 pi)
 constexpr float kTinyDelta = 9.313225746154785e-10f; // 2^-30: keeps d != 0 at n = n_c
 
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 __global__ void room_prologue(LaunchArgs a, const float* __restrict__ r_in)
 {
     const double fs = a.fs, c0 = a.c0;
@@ -257,8 +250,16 @@ __global__ void __launch_bounds__(128) bin_images(LaunchArgs a, const float* __r
 }
 
 // Shared-memory plan of synth_kernel (bytes, 16-byte aligned pieces).
+//   stage  image indices staged for the tile
+//   rec4/recb  arrival constants in arrival order (n_c - T0, delta, P, a') and b'
+//   rkey   delay bin of each arrival (-1 = no tap in the tile)
+//   sidx   arrival order after the counting sort
+//   q0/q1/q2  sorted arrivals, two per 48-byte group: (n1, d1, n2, d2) (P1, a1, b1, P2) (a2, b2, -, -)
+//   start/fill  bin starts (exclusive prefix) and scatter cursors
+//   outt   the tile's output samples for the current mic
+//   tabT   cos, sin(pi m / K) for the tile's samples m = T0 - K - 1 + k
 struct SynthSmem {
-    int stage, rec0, rec1, rkey, ridx, srt0, srt1, sidx, start, fill, outt, tab, total;
+    int stage, rec4, recb, rkey, sidx, q0, q1, q2, start, fill, outt, tabT, total;
 };
 
 __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
@@ -267,19 +268,21 @@ __host__ __device__ inline SynthSmem synth_smem(int T, int K)
 {
     SynthSmem s;
     const int NB = T + 2 * K + 2;
+    const int NA = kImpCap + 1;        // arrivals per chunk (images + the direct path)
+    const int NP = (NA + 2) / 2;       // sorted pairs
     int off = 0;
     s.stage = off; off = al16(off + 4 * kStageCap);
-    s.rec0 = off; off = al16(off + 16 * (kImpCap + 1));
-    s.rec1 = off; off = al16(off + 4 * (kImpCap + 1));
-    s.rkey = off; off = al16(off + 4 * (kImpCap + 1));
-    s.ridx = off; off = al16(off + 4 * (kImpCap + 1));
-    s.srt0 = off; off = al16(off + 16 * (kImpCap + 1));
-    s.srt1 = off; off = al16(off + 4 * (kImpCap + 1));
-    s.sidx = off; off = al16(off + 4 * (kImpCap + 1));
+    s.rec4 = off; off = al16(off + 16 * NA);
+    s.recb = off; off = al16(off + 4 * NA);
+    s.rkey = off; off = al16(off + 4 * NA);
+    s.sidx = off; off = al16(off + 4 * NA);
+    s.q0 = off; off = al16(off + 16 * NP);
+    s.q1 = off; off = al16(off + 16 * NP);
+    s.q2 = off; off = al16(off + 16 * NP);
     s.start = off; off = al16(off + 4 * (NB + 1));
     s.fill = off; off = al16(off + 4 * (NB + 1));
     s.outt = off; off = al16(off + 4 * T);
-    s.tab = off; off = al16(off + 8 * 2 * K);
+    s.tabT = off; off = al16(off + 8 * NB);
     s.total = off;
     return s;
 }
@@ -297,16 +300,16 @@ __device__ __forceinline__ void image_delay(float phx, float phy, float phz, flo
     f2 sy = two_prod(dy.hi, dy.hi); sy.lo = __fmaf_rn(__fmul_rn(2.0f, dy.hi), dy.lo, sy.lo);
     f2 sz = two_prod(dz.hi, dz.hi); sz.lo = __fmaf_rn(__fmul_rn(2.0f, dz.hi), dz.lo, sz.lo);
     f2 ss = f2_add(f2_add(fast_two_sum(sx.hi, sx.lo), fast_two_sum(sy.hi, sy.lo)), fast_two_sum(sz.hi, sz.lo));
-    f2 D = f2_sqrt(ss);
+    f2 D = f2_sqrt_fast(ss);
     f2 t = f2_mul(D, q2);
     nc = __float2int_rn(t.hi);
     delta = __fadd_rn(__fsub_rn(t.hi, (float)nc), t.lo);
     dist = D.hi;
 }
 
-// Block-wide exclusive scan of cnt[0..nb) into out[0..nb] (out[nb] = total).
+// Block-wide exclusive scan of cnt[0..nb) into out[0..nb] and out2[0..nb) (out[nb] = total).
 template <int NT>
-__device__ void block_exclusive_scan(const int* cnt, int* out, int nb, int* warp_tot)
+__device__ void block_exclusive_scan(const int* cnt, int* out, int* out2, int nb, int* warp_tot)
 {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int per = (nb + NT - 1) / NT;
@@ -335,33 +338,124 @@ __device__ void block_exclusive_scan(const int* cnt, int* out, int nb, int* warp
     for (int k = lo; k < hi; ++k) {
         const int c = cnt[k];
         out[k] = run;
+        out2[k] = run;
         run += c;
     }
     if (tid == NT - 1) out[nb] = warp_tot[NT / 32 - 1];
     __syncthreads();
 }
 
+// One arrival record, read from the pair-interleaved sorted arrays.
+struct Arr {
+    float nc, d, P, a, b;
+};
+
+__device__ __forceinline__ Arr load_single(const float4* q0, const float4* q1, const float4* q2, int p)
+{
+    const int q = p >> 1;
+    const float4 A = q0[q], Bv = q1[q];
+    if ((p & 1) == 0) return {A.x, A.y, Bv.x, Bv.y, Bv.z};
+    const float4 C = q2[q];
+    return {A.z, A.w, Bv.w, C.x, C.y};
+}
+
+// Taps of arrivals [lo, hi) (sorted order) for the lane's sample; masked = check |t - n| < K.
+template <bool kMasked>
+__device__ __forceinline__ float row_taps(const float4* __restrict__ q0, const float4* __restrict__ q1,
+                                          const float4* __restrict__ q2, int lo, int hi, float nl, float cn, float sn,
+                                          float Kf)
+{
+    float acc0 = 0.0f, acc1 = 0.0f;
+    int p = lo;
+    if ((p & 1) && p < hi) {   // leading odd element
+        const Arr r = load_single(q0, q1, q2, p);
+        const float d = __fadd_rn(__fsub_rn(r.nc, nl), r.d);
+        float num = __fmaf_rn(cn, r.a, __fmaf_rn(sn, r.b, r.P));
+        if (kMasked && !(fabsf(d) < Kf)) num = 0.0f;
+        acc0 = __fmul_rn(num, rcp_approx(d));
+        ++p;
+    }
+    const int qend = (hi - p) >> 1;   // full pairs from p (even)
+    int q = p >> 1;
+    const int qstop = q + qend;
+    // Two pairs per iteration, two accumulators.
+    for (; q + 1 < qstop; q += 2) {
+        const float4 A0 = q0[q], B0 = q1[q], C0 = q2[q];
+        const float4 A1 = q0[q + 1], B1 = q1[q + 1], C1 = q2[q + 1];
+        {
+            const float d1 = __fadd_rn(__fsub_rn(A0.x, nl), A0.y);
+            const float d2 = __fadd_rn(__fsub_rn(A0.z, nl), A0.w);
+            float n1 = __fmaf_rn(cn, B0.y, __fmaf_rn(sn, B0.z, B0.x));
+            float n2 = __fmaf_rn(cn, C0.x, __fmaf_rn(sn, C0.y, B0.w));
+            if (kMasked) {
+                if (!(fabsf(d1) < Kf)) n1 = 0.0f;
+                if (!(fabsf(d2) < Kf)) n2 = 0.0f;
+            }
+            const float rp = rcp_approx(__fmul_rn(d1, d2));
+            const float t = __fmaf_rn(n1, d2, __fmul_rn(n2, d1));
+            acc0 = __fmaf_rn(t, rp, acc0);
+        }
+        {
+            const float d1 = __fadd_rn(__fsub_rn(A1.x, nl), A1.y);
+            const float d2 = __fadd_rn(__fsub_rn(A1.z, nl), A1.w);
+            float n1 = __fmaf_rn(cn, B1.y, __fmaf_rn(sn, B1.z, B1.x));
+            float n2 = __fmaf_rn(cn, C1.x, __fmaf_rn(sn, C1.y, B1.w));
+            if (kMasked) {
+                if (!(fabsf(d1) < Kf)) n1 = 0.0f;
+                if (!(fabsf(d2) < Kf)) n2 = 0.0f;
+            }
+            const float rp = rcp_approx(__fmul_rn(d1, d2));
+            const float t = __fmaf_rn(n1, d2, __fmul_rn(n2, d1));
+            acc1 = __fmaf_rn(t, rp, acc1);
+        }
+    }
+    if (q < qstop) {
+        const float4 A0 = q0[q], B0 = q1[q], C0 = q2[q];
+        const float d1 = __fadd_rn(__fsub_rn(A0.x, nl), A0.y);
+        const float d2 = __fadd_rn(__fsub_rn(A0.z, nl), A0.w);
+        float n1 = __fmaf_rn(cn, B0.y, __fmaf_rn(sn, B0.z, B0.x));
+        float n2 = __fmaf_rn(cn, C0.x, __fmaf_rn(sn, C0.y, B0.w));
+        if (kMasked) {
+            if (!(fabsf(d1) < Kf)) n1 = 0.0f;
+            if (!(fabsf(d2) < Kf)) n2 = 0.0f;
+        }
+        const float rp = rcp_approx(__fmul_rn(d1, d2));
+        const float t = __fmaf_rn(n1, d2, __fmul_rn(n2, d1));
+        acc0 = __fmaf_rn(t, rp, acc0);
+        ++q;
+    }
+    p = q << 1;
+    if (p < hi) {              // trailing element
+        const Arr r = load_single(q0, q1, q2, p);
+        const float d = __fadd_rn(__fsub_rn(r.nc, nl), r.d);
+        float num = __fmaf_rn(cn, r.a, __fmaf_rn(sn, r.b, r.P));
+        if (kMasked && !(fabsf(d) < Kf)) num = 0.0f;
+        acc1 = __fmaf_rn(num, rcp_approx(d), acc1);
+    }
+    return __fadd_rn(acc0, acc1);
+}
+
 template <int NT>
-__global__ void __launch_bounds__(NT) synth_kernel(LaunchArgs a, const float* __restrict__ pos_hi,
-                                                    const float* __restrict__ pos_lo, const float* __restrict__ gref,
-                                                    float* __restrict__ rir, float* __restrict__ early)
+__global__ void __launch_bounds__(NT, 3) synth_kernel(LaunchArgs a, const float* __restrict__ pos_hi,
+                                                       const float* __restrict__ pos_lo, const float* __restrict__ gref,
+                                                       float* __restrict__ rir, float* __restrict__ early)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int T = a.tile, K = a.K;
     const int NB = T + 2 * K + 2;
     const SynthSmem L = synth_smem(T, K);
     int* stage = reinterpret_cast<int*>(smem + L.stage);
-    float4* rec0 = reinterpret_cast<float4*>(smem + L.rec0);
-    float* rec1 = reinterpret_cast<float*>(smem + L.rec1);
+    float4* rec4 = reinterpret_cast<float4*>(smem + L.rec4);
+    float* recb = reinterpret_cast<float*>(smem + L.recb);
     int* rkey = reinterpret_cast<int*>(smem + L.rkey);
-    int* ridx = reinterpret_cast<int*>(smem + L.ridx);
-    float4* srt0 = reinterpret_cast<float4*>(smem + L.srt0);
-    float* srt1 = reinterpret_cast<float*>(smem + L.srt1);
     int* sidx = reinterpret_cast<int*>(smem + L.sidx);
+    float4* q0 = reinterpret_cast<float4*>(smem + L.q0);
+    float4* q1 = reinterpret_cast<float4*>(smem + L.q1);
+    float4* q2 = reinterpret_cast<float4*>(smem + L.q2);
     int* start = reinterpret_cast<int*>(smem + L.start);
     int* fill = reinterpret_cast<int*>(smem + L.fill);
     float* outt = reinterpret_cast<float*>(smem + L.outt);
-    float2* tab = reinterpret_cast<float2*>(smem + L.tab);
+    float2* tabT = reinterpret_cast<float2*>(smem + L.tabT);
     __shared__ int s_item, s_count;
     __shared__ int warp_tot[NT / 32];
 
@@ -369,16 +463,11 @@ __global__ void __launch_bounds__(NT) synth_kernel(LaunchArgs a, const float* __
     constexpr int NW = NT / 32;
     const float invK = 1.0f / (float)K;
     const float Kf = (float)K;
-    for (int j = tid; j < 2 * K; j += NT) {
-        float sn, cs;
-        sincospif((float)j * invK, &sn, &cs);
-        tab[j] = make_float2(cs, sn);
-    }
+    const int twoK = 2 * K;
     const int n_items = a.hdr->n_items;
-    __syncthreads();
 
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(&a.hdr->queue, 1);
+        if (tid == 0) { s_item = atomicAdd(&a.hdr->queue, 1); s_count = 0; }
         __syncthreads();
         const int qi = s_item;
         if (qi >= n_items) break;
@@ -387,22 +476,27 @@ __global__ void __launch_bounds__(NT) synth_kernel(LaunchArgs a, const float* __
         const RoomConst rc = a.room[b];
         const int T0 = tau * T;
         const int Lb = rc.len;
+        const int base = T0 - K - 1;           // sample index of delay bin 0
         const int64_t v0 = rc.vs_off + (int64_t)s * rc.n_vs;
         const int* bo = a.bin_off + ((int64_t)b * a.S + s) * (a.max_tiles + 1);
         const float kmin = (float)(T0 - K) - rc.margin - 1.0f;
         const float kmax = (float)(T0 + T + K) + rc.margin + 1.0f;
-        // Bins (tiles of the key) that can hold such images; keys past the RIR end sit in
-        // the last bin and are filtered below.
         const int bin_lo = max(0, (int)floorf(kmin / (float)T));
         const int bin_hi = min(rc.ntiles - 1, (int)floorf(kmax / (float)T));
         const int c_lo = bo[bin_lo];
         const int c_hi = bo[bin_hi + 1];
 
+        // Phase table for the tile's samples: cos, sin(pi m / K), m = base + k.
+        for (int k = tid; k < NB; k += NT) {
+            int m = (base + k) % twoK;
+            m = m < 0 ? m + twoK : m;
+            float sn_, cs_;
+            sincospif((float)m * invK, &sn_, &cs_);
+            tabT[k] = make_float2(cs_, sn_);
+        }
         // ---- stage images whose key lies within reach of the tile (stable compaction) ----
-        if (tid == 0) s_count = 0;
-        __syncthreads();
-        for (int base = c_lo; base < c_hi; base += NT) {
-            const int idx = base + tid;
+        for (int cb = c_lo; cb < c_hi; cb += NT) {
+            const int idx = cb + tid;
             int img = -1;
             if (idx < c_hi) {
                 const int i = a.perm[v0 + idx];
@@ -424,6 +518,7 @@ __global__ void __launch_bounds__(NT) synth_kernel(LaunchArgs a, const float* __
             }
             __syncthreads();
         }
+        __syncthreads();
         int nstage = s_count;
         if (nstage > kStageCap) {
             if (tid == 0) atomicOr(&a.hdr->status, FRAM_DEV_CAPACITY);
@@ -439,120 +534,96 @@ __global__ void __launch_bounds__(NT) synth_kernel(LaunchArgs a, const float* __
             const int nchunks = nstage > 0 ? (nstage + kImpCap - 1) / kImpCap : 1;
             for (int ch = 0; ch < nchunks; ++ch) {
                 const int c0 = ch * kImpCap;
-                const int n_in = min(kImpCap, nstage - c0);
-                // ---- arrival constants ----
+                const int n_in = max(0, min(kImpCap, nstage - c0));
+                // ---- arrival constants: slot 0 is the direct path (first chunk only) ----
                 for (int j = tid; j <= n_in; j += NT) {
-                    int nc;
-                    float delta, A;
-                    bool ok = true;
-                    if (j < n_in) {
-                        const int i = stage[c0 + j];
+                    int nc = 0;
+                    float delta = 0.f, A = 0.f;
+                    bool ok;
+                    if (j > 0) {
+                        const int i = stage[c0 + j - 1];
                         const int64_t v = v0 + i;
                         const float* ph = pos_hi + 3 * v;
                         float plx = 0.f, ply = 0.f, plz = 0.f;
                         if (pos_lo) { plx = pos_lo[3 * v]; ply = pos_lo[3 * v + 1]; plz = pos_lo[3 * v + 2]; }
                         float D;
                         image_delay(ph[0], ph[1], ph[2], plx, ply, plz, mx, my, mz, a.q2, nc, delta, D);
-                        const float gg = gref[v];
-                        A = exp2f(gg * log2r) * __frcp_rn(D);
+                        A = exp2f(gref[v] * log2r) * rcp_approx(D);
                         ok = (D > 0.0f) && (A == A) && (fabsf(A) < 3.0e38f);
-                    } else if (ch == 0) {
+                    } else {
+                        ok = (ch == 0);
                         nc = __float2int_rn(dc.t_hi);
                         delta = __fadd_rn(__fsub_rn(dc.t_hi, (float)nc), dc.t_lo);
                         A = dc.amp;
-                    } else {
-                        ok = false;
-                        nc = 0; delta = 0.f; A = 0.f;
                     }
                     int key = -1;
                     if (ok) {
-                        key = nc - (T0 - K - 1);
+                        key = nc - base;
                         if (key < 0 || key >= NB) key = -1;
                     }
                     if (key >= 0) {
                         if (fabsf(delta) < kTinyDelta) delta = kTinyDelta;
-                        const float P = ((nc & 1) ? -A : A) * sinpif(delta) * kTwoPiInv;
-                        float sk, ck;
-                        sincospif(delta * invK, &sk, &ck);
-                        int nm = nc % (2 * K);
-                        nm = nm < 0 ? nm + 2 * K : nm;
-                        const float2 cs = tab[nm];
+                        const float P = ((nc & 1) ? -A : A) * sinpi_poly(delta) * kTwoPiInv;
+                        const float y = delta * invK;
+                        const float sk = sinpi_poly(y), ck = cospi_poly(y);
+                        const float2 cs = tabT[key];
                         const float ca = cs.x * ck - cs.y * sk;   // cos(pi t / K)
                         const float sa = cs.y * ck + cs.x * sk;   // sin(pi t / K)
-                        rec0[j] = make_float4((float)(nc - T0), delta, P, P * ca);
-                        rec1[j] = P * sa;
-                        ridx[j] = (j < n_in) ? c0 + j : -1;
+                        rec4[j] = make_float4((float)(nc - T0), delta, P, P * ca);
+                        recb[j] = P * sa;
                     }
                     rkey[j] = key;
                 }
                 for (int k = tid; k <= NB; k += NT) fill[k] = 0;
                 __syncthreads();
-                // ---- counting sort by integer delay ----
+                // ---- counting sort by integer delay; ties keep arrival order ----
                 for (int j = tid; j <= n_in; j += NT)
                     if (rkey[j] >= 0) atomicAdd(&fill[rkey[j]], 1);
                 __syncthreads();
-                block_exclusive_scan<NT>(fill, start, NB, warp_tot);
-                for (int k = tid; k < NB; k += NT) fill[k] = start[k];
-                __syncthreads();
+                block_exclusive_scan<NT>(fill, start, fill, NB, warp_tot);
                 for (int j = tid; j <= n_in; j += NT) {
                     const int key = rkey[j];
-                    if (key >= 0) {
-                        const int p = atomicAdd(&fill[key], 1);
-                        srt0[p] = rec0[j];
-                        srt1[p] = rec1[j];
-                        sidx[p] = ridx[j];
-                    }
+                    if (key >= 0) sidx[atomicAdd(&fill[key], 1)] = j;
                 }
                 __syncthreads();
-                // Equal delays: order by staging index (insertion sort; bins hold 1-3 entries).
                 for (int k = tid; k < NB; k += NT) {
                     const int lo = start[k], hi = start[k + 1];
                     for (int x = lo + 1; x < hi; ++x) {
-                        const float4 r0 = srt0[x];
-                        const float r1 = srt1[x];
                         const int id = sidx[x];
                         int y = x - 1;
-                        while (y >= lo && sidx[y] > id) {
-                            srt0[y + 1] = srt0[y]; srt1[y + 1] = srt1[y]; sidx[y + 1] = sidx[y];
-                            --y;
-                        }
-                        srt0[y + 1] = r0; srt1[y + 1] = r1; sidx[y + 1] = id;
+                        while (y >= lo && sidx[y] > id) { sidx[y + 1] = sidx[y]; --y; }
+                        sidx[y + 1] = id;
                     }
+                }
+                __syncthreads();
+                const int total = start[NB];
+                for (int p = tid; p < total; p += NT) {
+                    const int j = sidx[p];
+                    const float4 r = rec4[j];
+                    const float bb = recb[j];
+                    const int q = p >> 1;
+                    float* f0 = reinterpret_cast<float*>(q0 + q);
+                    float* f1 = reinterpret_cast<float*>(q1 + q);
+                    float* f2p = reinterpret_cast<float*>(q2 + q);
+                    if ((p & 1) == 0) { f0[0] = r.x; f0[1] = r.y; f1[0] = r.z; f1[1] = r.w; f1[2] = bb; }
+                    else { f0[2] = r.x; f0[3] = r.y; f1[3] = r.z; f2p[0] = r.w; f2p[1] = bb; }
                 }
                 __syncthreads();
                 // ---- taps: each warp owns rows of 32 consecutive samples ----
                 for (int row = wid; row * 32 < T; row += NW) {
                     const int R0 = T0 + row * 32;
                     if (R0 >= Lb) break;
-                    const int lo = start[row * 32 + 1];
-                    const int hi = start[min(row * 32 + 2 * K + 33, NB)];
-                    const float nl = (float)(row * 32 + lane);
-                    int nm = (R0 + lane) % (2 * K);
-                    const float2 cs = tab[nm];
-                    const float cn = cs.x, sn = cs.y;
-                    float acc = 0.0f;
-                    int j = lo;
-                    for (; j + 1 < hi; j += 2) {
-                        const float4 r1 = srt0[j];
-                        const float4 r2 = srt0[j + 1];
-                        const float b1 = srt1[j], b2 = srt1[j + 1];
-                        const float d1 = __fadd_rn(__fsub_rn(r1.x, nl), r1.y);
-                        const float d2 = __fadd_rn(__fsub_rn(r2.x, nl), r2.y);
-                        const float num1 = __fmaf_rn(cn, r1.w, __fmaf_rn(sn, b1, r1.z));
-                        const float num2 = __fmaf_rn(cn, r2.w, __fmaf_rn(sn, b2, r2.z));
-                        const float rp = rcp_approx(__fmul_rn(d1, d2));
-                        const float i1 = __fmul_rn(d2, rp), i2 = __fmul_rn(d1, rp);
-                        if (fabsf(d1) < Kf) acc = __fmaf_rn(num1, i1, acc);
-                        if (fabsf(d2) < Kf) acc = __fmaf_rn(num2, i2, acc);
-                    }
-                    if (j < hi) {
-                        const float4 r1 = srt0[j];
-                        const float b1 = srt1[j];
-                        const float d1 = __fadd_rn(__fsub_rn(r1.x, nl), r1.y);
-                        const float num1 = __fmaf_rn(cn, r1.w, __fmaf_rn(sn, b1, r1.z));
-                        if (fabsf(d1) < Kf) acc = __fmaf_rn(num1, rcp_approx(d1), acc);
-                    }
-                    outt[row * 32 + lane] += ((R0 + lane) & 1) ? -acc : acc;
+                    const int k0 = row * 32;
+                    const int lo = start[k0 + 1];
+                    const int ilo = start[min(k0 + 33, k0 + twoK + 1)];
+                    const int ihi = start[k0 + twoK + 1];
+                    const int hi = start[min(k0 + twoK + 33, NB)];
+                    const float nl = (float)(k0 + lane);
+                    const float2 cs = tabT[k0 + lane + K + 1];
+                    float acc = row_taps<true>(q0, q1, q2, lo, ilo, nl, cs.x, cs.y, Kf);
+                    acc = __fadd_rn(acc, row_taps<false>(q0, q1, q2, ilo, ihi, nl, cs.x, cs.y, Kf));
+                    acc = __fadd_rn(acc, row_taps<true>(q0, q1, q2, max(ihi, ilo), hi, nl, cs.x, cs.y, Kf));
+                    outt[k0 + lane] += ((R0 + lane) & 1) ? -acc : acc;
                 }
                 __syncthreads();
             }
