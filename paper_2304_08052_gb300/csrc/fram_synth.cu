@@ -367,7 +367,8 @@ __device__ __forceinline__ float row_taps(const float4* __restrict__ q0, const f
 {
     float acc0 = 0.0f, acc1 = 0.0f;
     int p = lo;
-    if ((p & 1) && p < hi) {   // leading odd element
+    if (p >= hi) return 0.0f;  // empty range (also keeps p >> 1 from rounding below lo)
+    if (p & 1) {               // leading odd element
         const Arr r = load_single(q0, q1, q2, p);
         const float d = __fadd_rn(__fsub_rn(r.nc, nl), r.d);
         float num = __fmaf_rn(cn, r.a, __fmaf_rn(sn, r.b, r.P));
