@@ -51,8 +51,13 @@ cudaError_t kernel_residency(const void* func, int threads, int smem, int* per_s
         const void* func;
         int dev, threads, smem, per_sm;
     };
+    struct Limit {           // largest dynamic shared memory already allowed per kernel and device
+        const void* func;
+        int dev, smem;
+    };
     static std::mutex mu;
     static std::vector<Entry> cache;
+    static std::vector<Limit> limits;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -62,8 +67,16 @@ cudaError_t kernel_residency(const void* func, int threads, int smem, int* per_s
             *per_sm = c.per_sm;
             return cudaSuccess;
         }
-    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
+    // The limit only ever grows, so an earlier, larger configuration stays launchable.
+    Limit* lim = nullptr;
+    for (Limit& l : limits)
+        if (l.func == func && l.dev == dev) lim = &l;
+    if (!lim || lim->smem < smem) {
+        e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        if (lim) lim->smem = smem;
+        else limits.push_back({func, dev, smem});
+    }
     int n = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, func, threads, smem);
     if (e != cudaSuccess) return e;
@@ -146,6 +159,8 @@ static LaunchArgs make_args(const fram_scene* sc, const fram_params* p, const Ws
     a.bin_off = reinterpret_cast<int32_t*>(base + w.bin_off);
     a.perm = reinterpret_cast<int32_t*>(base + w.perm);
     a.key = reinterpret_cast<float*>(base + w.key);
+    a.skey = reinterpret_cast<int32_t*>(base + w.skey);
+    a.ptmp = reinterpret_cast<int32_t*>(base + w.ptmp);
     a.part_mic = reinterpret_cast<float*>(base + w.part_mic);
     a.part_src = reinterpret_cast<float*>(base + w.part_src);
     a.part_r = reinterpret_cast<float*>(base + w.part_r);

@@ -185,8 +185,8 @@ __device__ __forceinline__ float uniform_from_word(uint32_t w)
 constexpr int kMaxHalfLen = 128;
 constexpr int kDefaultTile = 1024;
 constexpr int kSynthThreads = 256;
-constexpr int kStageCap = 2048;   // images staged per synthesis tile
-constexpr int kImpCap = 512;      // arrivals sorted per chunk
+constexpr int kStageCap = 2048;   // candidate images staged per synthesis tile
+constexpr int kArrCap = 768;      // arrival records held at once (larger tiles run in chunks)
 
 struct RoomConst {          // per room, written by the prologue
     float cx, cy, cz;       // array centre (float)
@@ -220,7 +220,7 @@ struct Header {             // first 256 bytes of the workspace
 };
 
 struct WsLayout {
-    size_t header, room, direct, src_tile, item_off, items, bin_off, perm, key;
+    size_t header, room, direct, src_tile, item_off, items, bin_off, perm, key, skey, ptmp;
     size_t part_mic, part_src, part_r;
     size_t total;
     int tile;
@@ -247,6 +247,8 @@ inline WsLayout ws_layout(const fram_scene& sc, int tile)
     w.bin_off = take(sizeof(int32_t) * (size_t)sc.B * sc.S * (w.max_tiles + 1));
     w.perm = take(sizeof(int32_t) * (size_t)sc.n_vs_total);
     w.key = take(sizeof(float) * (size_t)sc.n_vs_total);
+    w.skey = take(sizeof(int32_t) * (size_t)sc.n_vs_total);
+    w.ptmp = take(sizeof(int32_t) * (size_t)sc.n_vs_total);
     w.part_mic = take(sizeof(float) * 3 * (size_t)w.max_items * sc.M);
     w.part_src = take(sizeof(float) * 3 * (size_t)w.max_items);
     w.part_r = take(sizeof(float) * (size_t)w.max_items);
@@ -283,8 +285,10 @@ struct LaunchArgs {
     int32_t* item_off;
     int2* items;
     int32_t* bin_off;
-    int32_t* perm;
-    float* key;
+    int32_t* perm;          // per (room, source): image indices sorted by tile, then by floor(key)
+    float* key;             // per image: delay to the array centre in samples (binning key)
+    int32_t* skey;          // per sorted position: floor(key), clamped past the last tile
+    int32_t* ptmp;          // scratch for the two-pass sort
     float* part_mic;
     float* part_src;
     float* part_r;

@@ -171,8 +171,20 @@ __global__ void __launch_bounds__(1024) item_scan(LaunchArgs a)
     }
 }
 
-// One warp per (room, source): binning keys and a stable counting sort by tile.
-__global__ void __launch_bounds__(128) bin_images(LaunchArgs a, const float* __restrict__ pos_hi)
+// One warp per (room, source): binning keys, a stable counting sort of the images by tile, then
+// a stable counting sort inside each tile by floor(key).  The result: perm (image indices) and
+// skey (a monotone integer key per position), so any delay range of a source's images is one
+// contiguous run, found by binary search.
+__host__ __device__ inline int bin_warp_ints(int max_tiles, int T) { return (max_tiles + 1) + 2 * T; }
+
+__device__ __forceinline__ int tile_of_key(float key, float invT, int nt)
+{
+    if (!(key < 3.0e9f)) return nt - 1;               // NaN or beyond any RIR: last tile
+    const int t = (int)floorf(key * invT);
+    return t > nt - 1 ? nt - 1 : t;
+}
+
+__global__ void __launch_bounds__(64) bin_images(LaunchArgs a, const float* __restrict__ pos_hi)
 {
     extern __shared__ int bin_smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -180,10 +192,12 @@ __global__ void __launch_bounds__(128) bin_images(LaunchArgs a, const float* __r
     if (seg >= (int64_t)a.B * a.S) return;
     const int b = (int)(seg / a.S), s = (int)(seg % a.S);
     const RoomConst rc = a.room[b];
-    int* hist = bin_smem + wib * (a.max_tiles + 1);
+    const int T = a.tile;
+    int* hist = bin_smem + wib * bin_warp_ints(a.max_tiles, T);
+    int* fine = hist + (a.max_tiles + 1);
     const int n = rc.n_vs, nt = rc.ntiles;
     const int64_t v0 = rc.vs_off + (int64_t)s * n;
-    const float invT = 1.0f / (float)a.tile;
+    const float invT = 1.0f / (float)T;
     int* bo = a.bin_off + seg * (a.max_tiles + 1);
     if (nt < 1) {   // a room the prologue rejected: no work items reference its bins
         if (lane == 0) bo[0] = 0;
@@ -197,17 +211,11 @@ __global__ void __launch_bounds__(128) bin_images(LaunchArgs a, const float* __r
         const float dx = p[0] - rc.cx, dy = p[1] - rc.cy, dz = p[2] - rc.cz;
         const float key = sqrtf(dx * dx + dy * dy + dz * dz) * a.q;
         a.key[v0 + i] = key;
-        int t;
-        if (!(key < 3.0e9f)) { t = nt - 1; bad = bad || !(key == key) || isinf(key); }
-        else {
-            t = (int)floorf(key * invT);
-            t = t > nt - 1 ? nt - 1 : t;
-        }
-        atomicAdd(&hist[t], 1);
+        bad = bad || !(key == key) || isinf(key);
+        atomicAdd(&hist[tile_of_key(key, invT, nt)], 1);
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&a.hdr->status, FRAM_DEV_NONFINITE);
     __syncwarp();
-    // Exclusive scan over nt bins (chunks of 32), write bin offsets, keep running fill.
     int carry = 0;
     for (int base = 0; base < nt; base += 32) {
         const int t = base + lane;
@@ -224,19 +232,11 @@ __global__ void __launch_bounds__(128) bin_images(LaunchArgs a, const float* __r
     }
     if (lane == 0) bo[nt] = carry;
     __syncwarp();
-    // Stable scatter in index order, 32 images at a time.
+    // Pass 1: stable scatter by tile into ptmp (index order within a tile).
     for (int base = 0; base < n; base += 32) {
         const int i = base + lane;
         const bool act = i < n;
-        int t = -1;
-        if (act) {
-            const float key = a.key[v0 + i];
-            if (!(key < 3.0e9f)) t = nt - 1;
-            else {
-                t = (int)floorf(key * invT);
-                t = t > nt - 1 ? nt - 1 : t;
-            }
-        }
+        const int t = act ? tile_of_key(a.key[v0 + i], invT, nt) : -1;
         const unsigned peers = __match_any_sync(0xffffffffu, t);
         const int leader = __ffs(peers) - 1;
         const int rank = __popc(peers & ((1u << lane) - 1u));
@@ -245,44 +245,92 @@ __global__ void __launch_bounds__(128) bin_images(LaunchArgs a, const float* __r
         __syncwarp();
         if (lane == leader && act) hist[t] = basepos + __popc(peers);
         __syncwarp();
-        if (act) a.perm[v0 + basepos + rank] = i;
+        if (act) a.ptmp[v0 + basepos + rank] = i;
+    }
+    __syncwarp();
+    // Pass 2: inside each tile, stable counting sort by floor(key) - tile start.  The last tile
+    // also takes every key beyond the RIR, in a doubled bucket range clamped at its end.
+    for (int t = 0; t < nt; ++t) {
+        const int b0 = bo[t], b1 = bo[t + 1];
+        if (b1 <= b0) continue;
+        const int nb = (t == nt - 1) ? 2 * T : T;
+        const int t0 = t * T;
+        for (int f = lane; f < nb; f += 32) fine[f] = 0;
+        __syncwarp();
+        for (int p = b0 + lane; p < b1; p += 32) {
+            const float key = a.key[v0 + a.ptmp[v0 + p]];
+            int f = (key < 3.0e9f) ? (int)floorf(key) - t0 : nb - 1;
+            f = f < 0 ? 0 : (f > nb - 1 ? nb - 1 : f);
+            atomicAdd(&fine[f], 1);
+        }
+        __syncwarp();
+        int run = b0;
+        for (int base = 0; base < nb; base += 32) {
+            const int f = base + lane;
+            const int v = fine[f];
+            int x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            fine[f] = run + x - v;
+            run = __shfl_sync(0xffffffffu, run + x, 31);
+        }
+        __syncwarp();
+        for (int base = b0; base < b1; base += 32) {
+            const int p = base + lane;
+            const bool act = p < b1;
+            int f = -1, i = 0;
+            if (act) {
+                i = a.ptmp[v0 + p];
+                const float key = a.key[v0 + i];
+                f = (key < 3.0e9f) ? (int)floorf(key) - t0 : nb - 1;
+                f = f < 0 ? 0 : (f > nb - 1 ? nb - 1 : f);
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, f);
+            const int leader = __ffs(peers) - 1;
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            int basepos = (lane == leader && act) ? fine[f] : 0;
+            basepos = __shfl_sync(0xffffffffu, basepos, leader);
+            __syncwarp();
+            if (lane == leader && act) fine[f] = basepos + __popc(peers);
+            __syncwarp();
+            if (act) {
+                a.perm[v0 + basepos + rank] = i;
+                a.skey[v0 + basepos + rank] = t0 + f;
+            }
+        }
+        __syncwarp();
     }
 }
 
 // Shared-memory plan of synth_kernel (bytes, 16-byte aligned pieces).
-//   stage  image indices staged for the tile
-//   rec4/recb  arrival constants in arrival order (n_c - T0, delta, P, a') and b'
-//   rkey   delay bin of each arrival (-1 = no tap in the tile)
-//   sidx   arrival order after the counting sort
-//   q0/q1/q2  sorted arrivals, two per 48-byte group: (n1, d1, n2, d2) (P1, a1, b1, P2) (a2, b2, -, -)
-//   start/fill  bin starts (exclusive prefix) and scatter cursors
-//   outt   the tile's output samples for the current mic
-//   tabT   cos, sin(pi m / K) for the tile's samples m = T0 - K - 1 + k
+//   sperm/skeys  the tile's candidate images (sorted by delay key) and their keys
+//   rowb         per 32-sample row: first and one-past-last candidate in reach
+//   q0/q1/q2     arrival records, two per 48-byte group: (n1, d1, n2, d2) (P1, a1, b1, P2) (a2, b2, -, -)
+//   outt         the tile's samples for the current mic
+//   tabT         cos, sin(pi m / K) for m = base + k, base = T0 - K - M - 1
 struct SynthSmem {
-    int stage, rec4, recb, rkey, sidx, q0, q1, q2, start, fill, outt, tabT, total;
+    int sperm, skeys, rowb, q0, q1, q2, outt, tabT, total, nbk;
 };
 
 __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
 
-__host__ __device__ inline SynthSmem synth_smem(int T, int K)
+__host__ __device__ inline SynthSmem synth_smem(int T, int K, int M)
 {
     SynthSmem s;
-    const int NB = T + 2 * K + 2;
-    const int NA = kImpCap + 1;        // arrivals per chunk (images + the direct path)
-    const int NP = (NA + 2) / 2;       // sorted pairs
+    s.nbk = T + 2 * K + 2 * M + 2;
+    const int NP = kArrCap / 2 + 1;
     int off = 0;
-    s.stage = off; off = al16(off + 4 * kStageCap);
-    s.rec4 = off; off = al16(off + 16 * NA);
-    s.recb = off; off = al16(off + 4 * NA);
-    s.rkey = off; off = al16(off + 4 * NA);
-    s.sidx = off; off = al16(off + 4 * NA);
+    s.sperm = off; off = al16(off + 4 * kStageCap);
+    s.skeys = off; off = al16(off + 4 * kStageCap);
+    s.rowb = off; off = al16(off + 4 * (2 * (T / 32) + 2));
     s.q0 = off; off = al16(off + 16 * NP);
     s.q1 = off; off = al16(off + 16 * NP);
     s.q2 = off; off = al16(off + 16 * NP);
-    s.start = off; off = al16(off + 4 * (NB + 1));
-    s.fill = off; off = al16(off + 4 * (NB + 1));
     s.outt = off; off = al16(off + 4 * T);
-    s.tabT = off; off = al16(off + 8 * NB);
+    s.tabT = off; off = al16(off + 8 * s.nbk);
     s.total = off;
     return s;
 }
@@ -307,133 +355,76 @@ __device__ __forceinline__ void image_delay(float phx, float phy, float phz, flo
     dist = D.hi;
 }
 
-// Block-wide exclusive scan of cnt[0..nb) into out[0..nb] and out2[0..nb) (out[nb] = total).
-template <int NT>
-__device__ void block_exclusive_scan(const int* cnt, int* out, int* out2, int nb, int* warp_tot)
+// Arrival constants of the tap identity: P = (-1)^n_c A sin(pi delta)/(2 pi), a' = P cos(pi t/K),
+// b' = P sin(pi t/K), from the phase table entry cs = (cos, sin)(pi n_c / K).
+__device__ __forceinline__ float3 arrival_consts(int nc, float delta, float A, float2 cs, float invK)
 {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int per = (nb + NT - 1) / NT;
-    const int lo = tid * per, hi = min(lo + per, nb);
-    int sum = 0;
-    for (int k = lo; k < hi; ++k) sum += cnt[k];
-    int x = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_tot[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        int w = lane < NT / 32 ? warp_tot[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < NT / 32) warp_tot[lane] = w;
-    }
-    __syncthreads();
-    int run = (wid > 0 ? warp_tot[wid - 1] : 0) + x - sum;
-    for (int k = lo; k < hi; ++k) {
-        const int c = cnt[k];
-        out[k] = run;
-        out2[k] = run;
-        run += c;
-    }
-    if (tid == NT - 1) out[nb] = warp_tot[NT / 32 - 1];
-    __syncthreads();
+    const float P = ((nc & 1) ? -A : A) * sinpi_poly(delta) * kTwoPiInv;
+    const float y = delta * invK;
+    const float sk = sinpi_poly(y), ck = cospi_poly(y);
+    const float ca = cs.x * ck - cs.y * sk;
+    const float sa = cs.y * ck + cs.x * sk;
+    return make_float3(P, P * ca, P * sa);
 }
 
-// One arrival record, read from the pair-interleaved sorted arrays.
-struct Arr {
-    float nc, d, P, a, b;
-};
-
-__device__ __forceinline__ Arr load_single(const float4* q0, const float4* q1, const float4* q2, int p)
+__device__ __forceinline__ void put_record(float4* q0, float4* q1, float4* q2, int p, float nc_l, float delta,
+                                           float3 c)
 {
     const int q = p >> 1;
-    const float4 A = q0[q], Bv = q1[q];
-    if ((p & 1) == 0) return {A.x, A.y, Bv.x, Bv.y, Bv.z};
-    const float4 C = q2[q];
-    return {A.z, A.w, Bv.w, C.x, C.y};
+    float* f0 = reinterpret_cast<float*>(q0 + q);
+    float* f1 = reinterpret_cast<float*>(q1 + q);
+    float* f2p = reinterpret_cast<float*>(q2 + q);
+    if ((p & 1) == 0) { f0[0] = nc_l; f0[1] = delta; f1[0] = c.x; f1[1] = c.y; f1[2] = c.z; }
+    else { f0[2] = nc_l; f0[3] = delta; f1[3] = c.x; f2p[0] = c.y; f2p[1] = c.z; }
 }
 
-// Taps of arrivals [lo, hi) (sorted order) for the lane's sample; masked = check |t - n| < K.
-template <bool kMasked>
+// Taps of the arrival pairs [q, qend) for the lane's sample.  Every arrival is masked with
+// |t - n| < K, so a pair may include one arrival outside the row's reach (it contributes zero);
+// a zero-weight record far from every sample completes an odd count.
+__device__ __forceinline__ float pair_tap(const float4 A, const float4 B, const float4 C, float nl, float cn, float sn,
+                                          float Kf, float acc)
+{
+    const float e1 = __fadd_rn(__fsub_rn(A.x, nl), A.y);
+    const float e2 = __fadd_rn(__fsub_rn(A.z, nl), A.w);
+    float n1 = __fmaf_rn(cn, B.y, __fmaf_rn(sn, B.z, B.x));
+    float n2 = __fmaf_rn(cn, C.x, __fmaf_rn(sn, C.y, B.w));
+    n1 = fabsf(e1) < Kf ? n1 : 0.0f;
+    n2 = fabsf(e2) < Kf ? n2 : 0.0f;
+    const float rp = rcp_approx(__fmul_rn(e1, e2));
+    return __fmaf_rn(__fmaf_rn(n1, e2, __fmul_rn(n2, e1)), rp, acc);
+}
+
 __device__ __forceinline__ float row_taps(const float4* __restrict__ q0, const float4* __restrict__ q1,
-                                          const float4* __restrict__ q2, int lo, int hi, float nl, float cn, float sn,
+                                          const float4* __restrict__ q2, int q, int qend, float nl, float cn, float sn,
                                           float Kf)
 {
     float acc0 = 0.0f, acc1 = 0.0f;
-    int p = lo;
-    if (p >= hi) return 0.0f;  // empty range (also keeps p >> 1 from rounding below lo)
-    if (p & 1) {               // leading odd element
-        const Arr r = load_single(q0, q1, q2, p);
-        const float d = __fadd_rn(__fsub_rn(r.nc, nl), r.d);
-        float num = __fmaf_rn(cn, r.a, __fmaf_rn(sn, r.b, r.P));
-        if (kMasked && !(fabsf(d) < Kf)) num = 0.0f;
-        acc0 = __fmul_rn(num, rcp_approx(d));
-        ++p;
+    for (; q + 1 < qend; q += 2) {
+        acc0 = pair_tap(q0[q], q1[q], q2[q], nl, cn, sn, Kf, acc0);
+        acc1 = pair_tap(q0[q + 1], q1[q + 1], q2[q + 1], nl, cn, sn, Kf, acc1);
     }
-    const int qend = (hi - p) >> 1;   // full pairs from p (even)
-    int q = p >> 1;
-    const int qstop = q + qend;
-    // Two pairs per iteration, two accumulators.
-    for (; q + 1 < qstop; q += 2) {
-        const float4 A0 = q0[q], B0 = q1[q], C0 = q2[q];
-        const float4 A1 = q0[q + 1], B1 = q1[q + 1], C1 = q2[q + 1];
-        {
-            const float d1 = __fadd_rn(__fsub_rn(A0.x, nl), A0.y);
-            const float d2 = __fadd_rn(__fsub_rn(A0.z, nl), A0.w);
-            float n1 = __fmaf_rn(cn, B0.y, __fmaf_rn(sn, B0.z, B0.x));
-            float n2 = __fmaf_rn(cn, C0.x, __fmaf_rn(sn, C0.y, B0.w));
-            if (kMasked) {
-                if (!(fabsf(d1) < Kf)) n1 = 0.0f;
-                if (!(fabsf(d2) < Kf)) n2 = 0.0f;
-            }
-            const float rp = rcp_approx(__fmul_rn(d1, d2));
-            const float t = __fmaf_rn(n1, d2, __fmul_rn(n2, d1));
-            acc0 = __fmaf_rn(t, rp, acc0);
-        }
-        {
-            const float d1 = __fadd_rn(__fsub_rn(A1.x, nl), A1.y);
-            const float d2 = __fadd_rn(__fsub_rn(A1.z, nl), A1.w);
-            float n1 = __fmaf_rn(cn, B1.y, __fmaf_rn(sn, B1.z, B1.x));
-            float n2 = __fmaf_rn(cn, C1.x, __fmaf_rn(sn, C1.y, B1.w));
-            if (kMasked) {
-                if (!(fabsf(d1) < Kf)) n1 = 0.0f;
-                if (!(fabsf(d2) < Kf)) n2 = 0.0f;
-            }
-            const float rp = rcp_approx(__fmul_rn(d1, d2));
-            const float t = __fmaf_rn(n1, d2, __fmul_rn(n2, d1));
-            acc1 = __fmaf_rn(t, rp, acc1);
-        }
-    }
-    if (q < qstop) {
-        const float4 A0 = q0[q], B0 = q1[q], C0 = q2[q];
-        const float d1 = __fadd_rn(__fsub_rn(A0.x, nl), A0.y);
-        const float d2 = __fadd_rn(__fsub_rn(A0.z, nl), A0.w);
-        float n1 = __fmaf_rn(cn, B0.y, __fmaf_rn(sn, B0.z, B0.x));
-        float n2 = __fmaf_rn(cn, C0.x, __fmaf_rn(sn, C0.y, B0.w));
-        if (kMasked) {
-            if (!(fabsf(d1) < Kf)) n1 = 0.0f;
-            if (!(fabsf(d2) < Kf)) n2 = 0.0f;
-        }
-        const float rp = rcp_approx(__fmul_rn(d1, d2));
-        const float t = __fmaf_rn(n1, d2, __fmul_rn(n2, d1));
-        acc0 = __fmaf_rn(t, rp, acc0);
-        ++q;
-    }
-    p = q << 1;
-    if (p < hi) {              // trailing element
-        const Arr r = load_single(q0, q1, q2, p);
-        const float d = __fadd_rn(__fsub_rn(r.nc, nl), r.d);
-        float num = __fmaf_rn(cn, r.a, __fmaf_rn(sn, r.b, r.P));
-        if (kMasked && !(fabsf(d) < Kf)) num = 0.0f;
-        acc1 = __fmaf_rn(num, rcp_approx(d), acc1);
-    }
+    if (q < qend) acc0 = pair_tap(q0[q], q1[q], q2[q], nl, cn, sn, Kf, acc0);
     return __fadd_rn(acc0, acc1);
+}
+
+__device__ __forceinline__ int lower_bound_s(const int* a, int n, int x)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int upper_bound_s(const int* a, int n, int x)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
 }
 
 template <int NT>
@@ -442,33 +433,30 @@ __global__ void __launch_bounds__(NT, 3) synth_kernel(LaunchArgs a, const float*
                                                        float* __restrict__ rir, float* __restrict__ early)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int T = a.tile, K = a.K;
-    const int NB = T + 2 * K + 2;
-    const SynthSmem L = synth_smem(T, K);
-    int* stage = reinterpret_cast<int*>(smem + L.stage);
-    float4* rec4 = reinterpret_cast<float4*>(smem + L.rec4);
-    float* recb = reinterpret_cast<float*>(smem + L.recb);
-    int* rkey = reinterpret_cast<int*>(smem + L.rkey);
-    int* sidx = reinterpret_cast<int*>(smem + L.sidx);
+    const int T = a.tile, K = a.K, Mg = a.margin_i;
+    const SynthSmem L = synth_smem(T, K, Mg);
+    const int NBK = L.nbk;
+    int* sperm = reinterpret_cast<int*>(smem + L.sperm);
+    int* skeys = reinterpret_cast<int*>(smem + L.skeys);
+    int* rowb = reinterpret_cast<int*>(smem + L.rowb);
     float4* q0 = reinterpret_cast<float4*>(smem + L.q0);
     float4* q1 = reinterpret_cast<float4*>(smem + L.q1);
     float4* q2 = reinterpret_cast<float4*>(smem + L.q2);
-    int* start = reinterpret_cast<int*>(smem + L.start);
-    int* fill = reinterpret_cast<int*>(smem + L.fill);
     float* outt = reinterpret_cast<float*>(smem + L.outt);
     float2* tabT = reinterpret_cast<float2*>(smem + L.tabT);
-    __shared__ int s_item, s_count;
-    __shared__ int warp_tot[NT / 32];
+    __shared__ int s_item, s_lo, s_hi;
+    __shared__ float s_dir[6];
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     constexpr int NW = NT / 32;
     const float invK = 1.0f / (float)K;
     const float Kf = (float)K;
     const int twoK = 2 * K;
+    const int nrows = T / 32;
     const int n_items = a.hdr->n_items;
 
     for (;;) {
-        if (tid == 0) { s_item = atomicAdd(&a.hdr->queue, 1); s_count = 0; }
+        if (tid == 0) s_item = atomicAdd(&a.hdr->queue, 1);
         __syncthreads();
         const int qi = s_item;
         if (qi >= n_items) break;
@@ -477,54 +465,42 @@ __global__ void __launch_bounds__(NT, 3) synth_kernel(LaunchArgs a, const float*
         const RoomConst rc = a.room[b];
         const int T0 = tau * T;
         const int Lb = rc.len;
-        const int base = T0 - K - 1;           // sample index of delay bin 0
+        const int base = T0 - K - Mg - 1;          // sample index of phase-table entry 0
         const int64_t v0 = rc.vs_off + (int64_t)s * rc.n_vs;
         const int* bo = a.bin_off + ((int64_t)b * a.S + s) * (a.max_tiles + 1);
-        const float kmin = (float)(T0 - K) - rc.margin - 1.0f;
-        const float kmax = (float)(T0 + T + K) + rc.margin + 1.0f;
-        const int bin_lo = max(0, (int)floorf(kmin / (float)T));
-        const int bin_hi = min(rc.ntiles - 1, (int)floorf(kmax / (float)T));
+        const int kmin = T0 - K - Mg, kmax = T0 + T + K + Mg;   // keys that can reach the tile
+        const int bin_lo = min(max(0, kmin >= 0 ? kmin / T : 0), rc.ntiles - 1);
+        const int bin_hi = min(rc.ntiles - 1, kmax / T);
         const int c_lo = bo[bin_lo];
-        const int c_hi = bo[bin_hi + 1];
-
-        // Phase table for the tile's samples: cos, sin(pi m / K), m = base + k.
-        for (int k = tid; k < NB; k += NT) {
+        int ncand = bo[bin_hi + 1] - c_lo;
+        if (ncand > kStageCap) {
+            if (tid == 0) atomicOr(&a.hdr->status, FRAM_DEV_CAPACITY);
+            ncand = kStageCap;
+        }
+        // ---- stage the candidate images (sorted by key) and the phase table ----
+        for (int j = tid; j < ncand; j += NT) {
+            sperm[j] = a.perm[v0 + c_lo + j];
+            skeys[j] = a.skey[v0 + c_lo + j];
+        }
+        for (int k = tid; k < NBK; k += NT) {
             int m = (base + k) % twoK;
             m = m < 0 ? m + twoK : m;
             float sn_, cs_;
             sincospif((float)m * invK, &sn_, &cs_);
             tabT[k] = make_float2(cs_, sn_);
         }
-        // ---- stage images whose key lies within reach of the tile (stable compaction) ----
-        for (int cb = c_lo; cb < c_hi; cb += NT) {
-            const int idx = cb + tid;
-            int img = -1;
-            if (idx < c_hi) {
-                const int i = a.perm[v0 + idx];
-                const float k = a.key[v0 + i];
-                if (k >= kmin && k <= kmax) img = i;
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, img >= 0);
-            if (lane == 0) warp_tot[wid] = __popc(bal);
-            __syncthreads();
-            int before = s_count;
-            for (int w = 0; w < wid; ++w) before += warp_tot[w];
-            const int pos = before + __popc(bal & ((1u << lane) - 1u));
-            if (img >= 0 && pos < kStageCap) stage[pos] = img;
-            __syncthreads();
-            if (tid == 0) {
-                int tot = 0;
-                for (int w = 0; w < NW; ++w) tot += warp_tot[w];
-                s_count += tot;
-            }
-            __syncthreads();
+        __syncthreads();
+        // ---- the tile's range and each row's range, by binary search on the keys ----
+        if (tid == 0) s_lo = lower_bound_s(skeys, ncand, kmin);
+        if (tid == 1) s_hi = upper_bound_s(skeys, ncand, kmax);
+        if (tid >= 2 && tid < 2 + 2 * nrows) {
+            const int r = (tid - 2) >> 1;
+            const int R0 = T0 + 32 * r;
+            rowb[tid - 2] = (tid & 1) ? upper_bound_s(skeys, ncand, R0 + 31 + K + Mg)
+                                      : lower_bound_s(skeys, ncand, R0 - K - Mg);
         }
         __syncthreads();
-        int nstage = s_count;
-        if (nstage > kStageCap) {
-            if (tid == 0) atomicOr(&a.hdr->status, FRAM_DEV_CAPACITY);
-            nstage = kStageCap;
-        }
+        const int slo = s_lo, nst = max(0, s_hi - s_lo);
         const float log2r = rc.log2r;
 
         for (int m = 0; m < a.M; ++m) {
@@ -532,98 +508,59 @@ __global__ void __launch_bounds__(NT, 3) synth_kernel(LaunchArgs a, const float*
             const float* pm = a.mic + 3 * ((size_t)b * a.M + m);
             const float mx = pm[0], my = pm[1], mz = pm[2];
             for (int k = tid; k < T; k += NT) outt[k] = 0.0f;
-            const int nchunks = nstage > 0 ? (nstage + kImpCap - 1) / kImpCap : 1;
+            const int nchunks = nst > 0 ? (nst + kArrCap - 1) / kArrCap : 1;
             for (int ch = 0; ch < nchunks; ++ch) {
-                const int c0 = ch * kImpCap;
-                const int n_in = max(0, min(kImpCap, nstage - c0));
-                // ---- arrival constants: slot 0 is the direct path (first chunk only) ----
-                for (int j = tid; j <= n_in; j += NT) {
-                    int nc = 0;
-                    float delta = 0.f, A = 0.f;
-                    bool ok;
-                    if (j > 0) {
-                        const int i = stage[c0 + j - 1];
-                        const int64_t v = v0 + i;
-                        const float* ph = pos_hi + 3 * v;
-                        float plx = 0.f, ply = 0.f, plz = 0.f;
-                        if (pos_lo) { plx = pos_lo[3 * v]; ply = pos_lo[3 * v + 1]; plz = pos_lo[3 * v + 2]; }
-                        float D;
-                        image_delay(ph[0], ph[1], ph[2], plx, ply, plz, mx, my, mz, a.q2, nc, delta, D);
-                        A = exp2f(gref[v] * log2r) * rcp_approx(D);
-                        ok = (D > 0.0f) && (A == A) && (fabsf(A) < 3.0e38f);
-                    } else {
-                        ok = (ch == 0);
-                        nc = __float2int_rn(dc.t_hi);
-                        delta = __fadd_rn(__fsub_rn(dc.t_hi, (float)nc), dc.t_lo);
-                        A = dc.amp;
-                    }
-                    int key = -1;
-                    if (ok) {
-                        key = nc - base;
-                        if (key < 0 || key >= NB) key = -1;
-                    }
-                    if (key >= 0) {
+                const int c0 = ch * kArrCap;
+                const int nin = max(0, min(kArrCap, nst - c0));
+                // ---- arrival records at their sorted positions ----
+                for (int p = tid; p < nin; p += NT) {
+                    const int i = sperm[slo + c0 + p];
+                    const int64_t v = v0 + i;
+                    const float* ph = pos_hi + 3 * v;
+                    float plx = 0.f, ply = 0.f, plz = 0.f;
+                    if (pos_lo) { plx = pos_lo[3 * v]; ply = pos_lo[3 * v + 1]; plz = pos_lo[3 * v + 2]; }
+                    int nc;
+                    float delta, D;
+                    image_delay(ph[0], ph[1], ph[2], plx, ply, plz, mx, my, mz, a.q2, nc, delta, D);
+                    const float A = exp2f(gref[v] * log2r) * rcp_approx(D);
+                    const int key = nc - base;
+                    float3 c = make_float3(0.f, 0.f, 0.f);
+                    float ncl = (float)(T + 4 * K + 64);              // out of reach: zero weight
+                    if (key >= 0 && key < NBK && D > 0.0f && A == A && fabsf(A) < 3.0e38f) {
                         if (fabsf(delta) < kTinyDelta) delta = kTinyDelta;
-                        const float P = ((nc & 1) ? -A : A) * sinpi_poly(delta) * kTwoPiInv;
-                        const float y = delta * invK;
-                        const float sk = sinpi_poly(y), ck = cospi_poly(y);
-                        const float2 cs = tabT[key];
-                        const float ca = cs.x * ck - cs.y * sk;   // cos(pi t / K)
-                        const float sa = cs.y * ck + cs.x * sk;   // sin(pi t / K)
-                        rec4[j] = make_float4((float)(nc - T0), delta, P, P * ca);
-                        recb[j] = P * sa;
+                        c = arrival_consts(nc, delta, A, tabT[key], invK);
+                        ncl = (float)(nc - T0);
                     }
-                    rkey[j] = key;
+                    put_record(q0, q1, q2, p, ncl, delta, c);
                 }
-                for (int k = tid; k <= NB; k += NT) fill[k] = 0;
-                __syncthreads();
-                // ---- counting sort by integer delay; ties keep arrival order ----
-                for (int j = tid; j <= n_in; j += NT)
-                    if (rkey[j] >= 0) atomicAdd(&fill[rkey[j]], 1);
-                __syncthreads();
-                block_exclusive_scan<NT>(fill, start, fill, NB, warp_tot);
-                for (int j = tid; j <= n_in; j += NT) {
-                    const int key = rkey[j];
-                    if (key >= 0) sidx[atomicAdd(&fill[key], 1)] = j;
-                }
-                __syncthreads();
-                for (int k = tid; k < NB; k += NT) {
-                    const int lo = start[k], hi = start[k + 1];
-                    for (int x = lo + 1; x < hi; ++x) {
-                        const int id = sidx[x];
-                        int y = x - 1;
-                        while (y >= lo && sidx[y] > id) { sidx[y + 1] = sidx[y]; --y; }
-                        sidx[y + 1] = id;
-                    }
-                }
-                __syncthreads();
-                const int total = start[NB];
-                for (int p = tid; p < total; p += NT) {
-                    const int j = sidx[p];
-                    const float4 r = rec4[j];
-                    const float bb = recb[j];
-                    const int q = p >> 1;
-                    float* f0 = reinterpret_cast<float*>(q0 + q);
-                    float* f1 = reinterpret_cast<float*>(q1 + q);
-                    float* f2p = reinterpret_cast<float*>(q2 + q);
-                    if ((p & 1) == 0) { f0[0] = r.x; f0[1] = r.y; f1[0] = r.z; f1[1] = r.w; f1[2] = bb; }
-                    else { f0[2] = r.x; f0[3] = r.y; f1[3] = r.z; f2p[0] = r.w; f2p[1] = bb; }
+                if (tid == 0) {
+                    if (nin & 1) put_record(q0, q1, q2, nin, (float)(T + 4 * K + 64), 0.25f, make_float3(0.f, 0.f, 0.f));
+                    // Direct path of (b, s, m): its constants for the rows within reach.
+                    const int nc = __float2int_rn(dc.t_hi);
+                    float delta = __fadd_rn(__fsub_rn(dc.t_hi, (float)nc), dc.t_lo);
+                    if (fabsf(delta) < kTinyDelta) delta = kTinyDelta;
+                    const int key = nc - base;
+                    float3 c = make_float3(0.f, 0.f, 0.f);
+                    if (ch == 0 && key >= 0 && key < NBK) c = arrival_consts(nc, delta, dc.amp, tabT[key], invK);
+                    s_dir[0] = (float)(nc - T0); s_dir[1] = delta; s_dir[2] = c.x; s_dir[3] = c.y; s_dir[4] = c.z;
                 }
                 __syncthreads();
                 // ---- taps: each warp owns rows of 32 consecutive samples ----
-                for (int row = wid; row * 32 < T; row += NW) {
+                const float dnc = s_dir[0], dd = s_dir[1], dP = s_dir[2], da = s_dir[3], db = s_dir[4];
+                for (int row = wid; row < nrows; row += NW) {
                     const int R0 = T0 + row * 32;
                     if (R0 >= Lb) break;
                     const int k0 = row * 32;
-                    const int lo = start[k0 + 1];
-                    const int ilo = start[min(k0 + 33, k0 + twoK + 1)];
-                    const int ihi = start[k0 + twoK + 1];
-                    const int hi = start[min(k0 + twoK + 33, NB)];
+                    const int lo = max(rowb[2 * row] - slo - c0, 0);
+                    const int hi = min(rowb[2 * row + 1] - slo - c0, nin);
+                    const float2 cs = tabT[k0 + lane + K + Mg + 1];
                     const float nl = (float)(k0 + lane);
-                    const float2 cs = tabT[k0 + lane + K + 1];
-                    float acc = row_taps<true>(q0, q1, q2, lo, ilo, nl, cs.x, cs.y, Kf);
-                    acc = __fadd_rn(acc, row_taps<false>(q0, q1, q2, ilo, ihi, nl, cs.x, cs.y, Kf));
-                    acc = __fadd_rn(acc, row_taps<true>(q0, q1, q2, max(ihi, ilo), hi, nl, cs.x, cs.y, Kf));
+                    float acc = lo < hi ? row_taps(q0, q1, q2, lo >> 1, (hi + 1) >> 1, nl, cs.x, cs.y, Kf) : 0.0f;
+                    if (dP != 0.0f && dnc >= (float)(k0 - K - 1) && dnc <= (float)(k0 + 32 + K)) {
+                        const float e = __fadd_rn(__fsub_rn(dnc, nl), dd);
+                        const float num = __fmaf_rn(cs.x, da, __fmaf_rn(cs.y, db, dP));
+                        if (fabsf(e) < Kf) acc = __fadd_rn(acc, __fmul_rn(num, rcp_approx(e)));
+                    }
                     outt[k0 + lane] += ((R0 + lane) & 1) ? -acc : acc;
                 }
                 __syncthreads();
@@ -639,14 +576,14 @@ __global__ void __launch_bounds__(NT, 3) synth_kernel(LaunchArgs a, const float*
                     if (dste) dste[n] = (n >= dc.early_lo && n <= dc.early_hi) ? h : 0.0f;
                 }
             }
-            __syncthreads();
         }
+        __syncthreads();
     }
 }
 
 }  // namespace
 
-int synth_smem_bytes(int T, int K) { return synth_smem(T, K).total; }
+
 
 cudaError_t launch_prepare(const LaunchArgs& a, const float* pos_hi, const float* pos_lo, const float* r,
                            cudaStream_t st)
@@ -663,8 +600,10 @@ cudaError_t launch_prepare(const LaunchArgs& a, const float* pos_hi, const float
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int64_t segs = (int64_t)a.B * a.S;
     if (segs > 0) {
-        const size_t sm = sizeof(int) * 4 * (size_t)(a.max_tiles + 1);
-        bin_images<<<(unsigned)((segs + 3) / 4), 128, sm, st>>>(a, pos_hi);
+        const int sm = (int)(sizeof(int) * 2 * (size_t)bin_warp_ints(a.max_tiles, a.tile));
+        int per_sm = 0;
+        if ((e = kernel_residency((const void*)bin_images, 64, sm, &per_sm)) != cudaSuccess) return e;
+        bin_images<<<(unsigned)((segs + 1) / 2), 64, sm, st>>>(a, pos_hi);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -673,7 +612,7 @@ cudaError_t launch_prepare(const LaunchArgs& a, const float* pos_hi, const float
 cudaError_t launch_synthesize(const LaunchArgs& a, const float* pos_hi, const float* pos_lo, const float* g,
                               float* rir, float* early, cudaStream_t st)
 {
-    const int smem = synth_smem(a.tile, a.K).total;
+    const int smem = synth_smem(a.tile, a.K, a.margin_i).total;
     int per_sm = 0;
     cudaError_t e = kernel_residency((const void*)synth_kernel<kSynthThreads>, kSynthThreads, smem, &per_sm);
     if (e != cudaSuccess) return e;
