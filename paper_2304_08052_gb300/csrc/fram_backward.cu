@@ -46,99 +46,175 @@ __device__ __forceinline__ float dsinc_small(float x)
     return p * x;
 }
 
-// Taps of one arrival against staged G: Gs points at G[n_c - K].
-template <int KT>
-__device__ __forceinline__ void gather_taps(const float* __restrict__ Gs, int Kr, float delta, const float2* tab,
-                                            float& gA, float& gT)
+// cos and sin(pi k / K) for k = -K..K, evaluated at compile time (Taylor series in double on
+// [-pi, pi]) and placed in constant memory, so the unrolled tap loop reads them as FMA operands.
+struct TrigTab {
+    float c[2 * kMaxHalfLen + 1];
+    float s[2 * kMaxHalfLen + 1];
+};
+
+constexpr double cx_pow_term(double x, int n)
 {
-    const int K = KT > 0 ? KT : Kr;
-    float sd, cd, sk, ck;
-    sincospif(delta, &sd, &cd);
-    sincospif(delta / (float)K, &sk, &ck);
-    const float spi = sd * kInvPi;              // sin(pi delta) / pi
-    const float hw = -0.5f * kPi / (float)K;    // w'(x) = hw * sin(pi x / K)
+    double t = 1.0;
+    for (int i = 1; i <= n; ++i) t *= x / i;
+    return t;
+}
+
+constexpr double cx_sin(double x)
+{
+    double acc = 0.0;
+    for (int j = 0; j < 30; ++j) acc += ((j & 1) ? -1.0 : 1.0) * cx_pow_term(x, 2 * j + 1);
+    return acc;
+}
+
+constexpr double cx_cos(double x)
+{
+    double acc = 0.0;
+    for (int j = 0; j < 30; ++j) acc += ((j & 1) ? -1.0 : 1.0) * cx_pow_term(x, 2 * j);
+    return acc;
+}
+
+template <int K>
+constexpr TrigTab make_trig_tab()
+{
+    TrigTab t{};
+    for (int i = 0; i <= 2 * K; ++i) {
+        const double x = 3.14159265358979323846 * (double)(i - K) / (double)K;
+        t.c[i] = (float)cx_cos(x);
+        t.s[i] = (float)cx_sin(x);
+    }
+    return t;
+}
+
+__constant__ TrigTab c_trig40 = make_trig_tab<40>();
+__constant__ TrigTab c_trig63 = make_trig_tab<63>();
+
+template <int KT> __device__ __forceinline__ const TrigTab& trig_tab();
+template <> __device__ __forceinline__ const TrigTab& trig_tab<40>() { return c_trig40; }
+template <> __device__ __forceinline__ const TrigTab& trig_tab<63>() { return c_trig63; }
+
+// Taps of one arrival against staged G (Gs points at G[n_c - K]): gA = sum G tap, gT = sum G tap'
+// with tap(x) = sinc(x) (1 + cos(pi x/K))/2, x = k - delta.  With W2 = 1 + cos(pi x/K):
+//   2 tap = s W2,   2 tap' = s' W2 - (pi/K) s sin(pi x/K),
+//   s = -(-1)^k sin(pi delta)/(pi x),  s' = ((-1)^k cos(pi delta) - s)/x.
+template <int KT>
+__device__ __forceinline__ void gather_taps_ct(const float* __restrict__ Gs, float delta, float& gA, float& gT)
+{
+    const TrigTab& tb = trig_tab<KT>();
+    const float sd = sinpi_poly(delta), cd = cospi_poly(delta);
+    const float y = delta * (1.0f / (float)KT);
+    const float sk = sinpi_poly(y), ck = cospi_poly(y);
+    const float spi = sd * kInvPi;                     // sin(pi delta) / pi
+    const float spic = spi * (-kPi / (float)KT);       // -(pi/K) sin(pi delta) / pi
     float a = 0.f, t = 0.f;
-#pragma unroll 8
+#pragma unroll
+    for (int kk = 0; kk <= 2 * KT; ++kk) {
+        const int k = kk - KT;
+        const float G = Gs[kk];
+        const float x = __fsub_rn((float)k, delta);
+        const float r = rcp_approx(x);
+        const bool even = (k & 1) == 0;
+        const float s = (even ? -spi : spi) * r;
+        const float sc = (even ? -spic : spic) * r;
+        const float sp = (k == 0) ? dsinc_small(x) : ((even ? cd : -cd) - s) * r;
+        const float W2 = __fmaf_rn(tb.c[kk], ck, __fmaf_rn(tb.s[kk], sk, 1.0f));
+        const float sw = __fmaf_rn(tb.s[kk], ck, -(tb.c[kk] * sk));
+        float tap2 = s * W2;
+        float dtap2 = __fmaf_rn(sp, W2, sc * sw);
+        if ((kk == 0 || kk == 2 * KT) && !(fabsf(x) < (float)KT)) { tap2 = 0.f; dtap2 = 0.f; }
+        a = __fmaf_rn(G, tap2, a);
+        t = __fmaf_rn(G, dtap2, t);
+    }
+    gA = 0.5f * a;
+    gT = 0.5f * t;
+}
+
+// Any K: the same taps with the trigonometric table in shared memory.
+__device__ __forceinline__ void gather_taps_rt(const float* __restrict__ Gs, int K, float delta, const float2* tab,
+                                               float& gA, float& gT)
+{
+    const float sd = sinpi_poly(delta), cd = cospi_poly(delta);
+    const float y = delta / (float)K;
+    const float sk = sinpi_poly(y), ck = cospi_poly(y);
+    const float spi = sd * kInvPi;
+    const float spic = spi * (-kPi / (float)K);
+    float a = 0.f, t = 0.f;
     for (int kk = 0; kk <= 2 * K; ++kk) {
         const int k = kk - K;
         const float G = Gs[kk];
         const float x = __fsub_rn((float)k, delta);
         const float r = rcp_approx(x);
         const bool even = (k & 1) == 0;
-        const float s = (even ? -spi : spi) * r;            // sinc(x) = -(-1)^k sin(pi delta)/(pi x)
-        const float cpx = even ? cd : -cd;                  // cos(pi x) = (-1)^k cos(pi delta)
-        const float sp = (k == 0) ? dsinc_small(x) : (cpx - s) * r;
-        const int km = k < 0 ? k + 2 * K : k;
-        const float2 cs = tab[km];                          // cos, sin(pi k / K)
-        const float cw = __fmaf_rn(cs.x, ck, cs.y * sk);    // cos(pi x / K)
-        const float sw = __fmaf_rn(cs.y, ck, -cs.x * sk);   // sin(pi x / K)
-        const float w = __fmaf_rn(0.5f, cw, 0.5f);
-        const float wp = hw * sw;
-        float tap = s * w;
-        float dtap = __fmaf_rn(sp, w, s * wp);
-        if ((kk == 0 || kk == 2 * K) && !(fabsf(x) < (float)K)) { tap = 0.f; dtap = 0.f; }
-        a = __fmaf_rn(G, tap, a);
-        t = __fmaf_rn(G, dtap, t);
+        const float s = (even ? -spi : spi) * r;
+        const float sc = (even ? -spic : spic) * r;
+        const float sp = (k == 0) ? dsinc_small(x) : ((even ? cd : -cd) - s) * r;
+        const float2 cs = tab[kk];
+        const float W2 = __fmaf_rn(cs.x, ck, __fmaf_rn(cs.y, sk, 1.0f));
+        const float sw = __fmaf_rn(cs.y, ck, -(cs.x * sk));
+        float tap2 = s * W2;
+        float dtap2 = __fmaf_rn(sp, W2, sc * sw);
+        if ((kk == 0 || kk == 2 * K) && !(fabsf(x) < (float)K)) { tap2 = 0.f; dtap2 = 0.f; }
+        a = __fmaf_rn(G, tap2, a);
+        t = __fmaf_rn(G, dtap2, t);
     }
-    gA = a;
-    gT = t;
+    gA = 0.5f * a;
+    gT = 0.5f * t;
+}
+
+template <int KT>
+__device__ __forceinline__ void gather_taps(const float* __restrict__ Gs, int K, float delta, const float2* tab,
+                                            float& gA, float& gT)
+{
+    if constexpr (KT > 0) gather_taps_ct<KT>(Gs, delta, gA, gT);
+    else gather_taps_rt(Gs, K, delta, tab, gA, gT);
 }
 
 struct BwdSmemPlan {
-    int gs, tab, total, glen;
+    int gs, tab, red, total, glen;
 };
 
-__host__ __device__ inline BwdSmemPlan bwd_smem(int T, int K, int margin_i)
+// Two staging buffers of the upstream gradient, the table for a run-time K, and the per-warp
+// mic partials.
+__host__ __device__ inline BwdSmemPlan bwd_smem(int T, int K, int margin_i, int M, int nwarps)
 {
     BwdSmemPlan p;
     p.glen = T + 4 * K + 2 * margin_i + 8;
     p.gs = 0;
-    p.tab = ((4 * p.glen) + 15) & ~15;
-    p.total = p.tab + 8 * 2 * K;
+    p.tab = ((8 * p.glen) + 15) & ~15;
+    p.red = p.tab + (((8 * (2 * K + 1)) + 15) & ~15);
+    p.total = p.red + 4 * 3 * M * nwarps;
     return p;
 }
 
-template <int NT>
-__device__ __forceinline__ void block_sum3(float& x, float& y, float& z, float* red)
+__device__ __forceinline__ float warp_sum(float x)
 {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        x += __shfl_down_sync(0xffffffffu, x, o);
-        y += __shfl_down_sync(0xffffffffu, y, o);
-        z += __shfl_down_sync(0xffffffffu, z, o);
-    }
-    if (lane == 0) { red[3 * wid] = x; red[3 * wid + 1] = y; red[3 * wid + 2] = z; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float sx = 0.f, sy = 0.f, sz = 0.f;
-        for (int w = 0; w < NT / 32; ++w) { sx += red[3 * w]; sy += red[3 * w + 1]; sz += red[3 * w + 2]; }
-        x = sx; y = sy; z = sz;
-    }
-    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
 }
 
 template <int NT, int KT>
-__global__ void __launch_bounds__(NT) bwd_kernel(LaunchArgs a, int margin_i, const float* __restrict__ pos_hi,
-                                                  const float* __restrict__ pos_lo, const float* __restrict__ gref,
-                                                  const float* __restrict__ grad_rir, const float* __restrict__ grad_early,
-                                                  float* __restrict__ grad_vs)
+__global__ void __launch_bounds__(NT, 4) bwd_kernel(LaunchArgs a, int margin_i, const float* __restrict__ pos_hi,
+                                                     const float* __restrict__ pos_lo, const float* __restrict__ gref,
+                                                     const float* __restrict__ grad_rir,
+                                                     const float* __restrict__ grad_early, float* __restrict__ grad_vs)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int T = a.tile, K = a.K;
-    const BwdSmemPlan P = bwd_smem(T, K, margin_i);
-    float* Gs = reinterpret_cast<float*>(smem + P.gs);
+    constexpr int NW = NT / 32;
+    const int T = a.tile, K = a.K, M = a.M;
+    const BwdSmemPlan P = bwd_smem(T, K, margin_i, M, NW);
+    float* Gs0 = reinterpret_cast<float*>(smem + P.gs);
     float2* tab = reinterpret_cast<float2*>(smem + P.tab);
+    float* red = reinterpret_cast<float*>(smem + P.red);   // [NW][M][3]
     __shared__ int s_item;
-    __shared__ float red[3 * (NT / 32)];
-    __shared__ float mic_part[3 * 64];
-    __shared__ float src_part[3];
-    const int tid = threadIdx.x;
-    for (int j = tid; j < 2 * K; j += NT) {
-        float sn, cs;
-        sincospif((float)j / (float)K, &sn, &cs);
-        tab[j] = make_float2(cs, sn);
-    }
+    __shared__ float s_r[NW];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (KT == 0)
+        for (int j = tid; j <= 2 * K; j += NT) {
+            float sn, cs;
+            sincospif((float)(j - K) / (float)K, &sn, &cs);
+            tab[j] = make_float2(cs, sn);
+        }
     const int n_items = a.hdr->n_items;
     const float qf = a.q;
     __syncthreads();
@@ -158,13 +234,14 @@ __global__ void __launch_bounds__(NT) bwd_kernel(LaunchArgs a, int margin_i, con
         const int o_lo = bo[tau], o_hi = bo[tau + 1];
         const int gbase = T0 - 2 * K - margin_i - 4;
         const bool own_direct = a.src_tile[(int64_t)b * a.S + s] == tau;
-        const int64_t chan0 = rc.rir_off + (int64_t)s * a.M * Lb;
-        const int M = a.M;
-        for (int k = tid; k < 3 * M; k += NT) mic_part[k] = 0.f;
-        if (tid < 3) src_part[tid] = 0.f;
-        float pr = 0.f;   // this thread's share of dL/dr
+        const int64_t chan0 = rc.rir_off + (int64_t)s * M * Lb;
+        for (int k = lane; k < 3 * M; k += 32) red[(wid * M) * 3 + k] = 0.f;
+        __syncwarp();
+        float pr = 0.f;                          // this thread's share of dL/dr
+        float dsx = 0.f, dsy = 0.f, dsz = 0.f;   // direct-path source gradient (thread 0)
         const int nown = o_hi - o_lo;
         const int nch = nown > 0 ? (nown + NT - 1) / NT : 1;
+        int iter = 0;
         for (int ch = 0; ch < nch; ++ch) {
             const int slot = ch * NT + tid;
             const bool has = slot < nown;
@@ -178,10 +255,10 @@ __global__ void __launch_bounds__(NT) bwd_kernel(LaunchArgs a, int margin_i, con
             }
             const float A_g = has ? exp2f(gg * rc.log2r) : 0.f;   // r^g
             float gvx = 0.f, gvy = 0.f, gvz = 0.f;
-            for (int m = 0; m < M; ++m) {
+            for (int m = 0; m < M; ++m, ++iter) {
                 const DirectConst dc = a.direct[((int64_t)b * a.S + s) * M + m];
                 const int64_t ch0 = chan0 + (int64_t)m * Lb;
-                __syncthreads();
+                float* Gs = Gs0 + (iter & 1) * P.glen;
                 for (int j = tid; j < P.glen; j += NT) {
                     const int n = gbase + j;
                     float Gv = 0.f;
@@ -204,16 +281,15 @@ __global__ void __launch_bounds__(NT) bwd_kernel(LaunchArgs a, int margin_i, con
                     f2 sz = two_prod(dz.hi, dz.hi); sz.lo = __fmaf_rn(__fmul_rn(2.0f, dz.hi), dz.lo, sz.lo);
                     f2 ss = f2_add(f2_add(fast_two_sum(sx.hi, sx.lo), fast_two_sum(sy.hi, sy.lo)),
                                    fast_two_sum(sz.hi, sz.lo));
-                    f2 D = f2_sqrt(ss);
+                    f2 D = f2_sqrt_fast(ss);
                     f2 t = f2_mul(D, a.q2);
                     const int nc = __float2int_rn(t.hi);
                     float delta = __fadd_rn(__fsub_rn(t.hi, (float)nc), t.lo);
                     if (fabsf(delta) < kTinyDelta) delta = kTinyDelta;
-                    const float invD = __frcp_rn(D.hi);
+                    const float invD = rcp_approx(D.hi);
                     const float A = A_g * invD;
                     const int j0 = nc - K - gbase;
-                    const bool any_tap = (nc + K >= 0) && (nc - K < Lb);
-                    if (any_tap) {
+                    if ((nc + K >= 0) && (nc - K < Lb)) {
                         if (j0 >= 0 && j0 + 2 * K < P.glen) {
                             float gA, gT;
                             gather_taps<KT>(Gs + j0, K, delta, tab, gA, gT);
@@ -230,8 +306,7 @@ __global__ void __launch_bounds__(NT) bwd_kernel(LaunchArgs a, int margin_i, con
                         }
                     }
                 }
-                // Direct path of (b, s, m), owned by one tile; thread 0 adds it after its image.
-                float dsx = 0.f, dsy = 0.f, dsz = 0.f;
+                // Direct path of (b, s, m): owned by one tile; thread 0 adds it after its image.
                 if (own_direct && ch == 0 && tid == 0) {
                     const int nc = __float2int_rn(dc.t_hi);
                     float delta = __fadd_rn(__fsub_rn(dc.t_hi, (float)nc), dc.t_lo);
@@ -243,31 +318,39 @@ __global__ void __launch_bounds__(NT) bwd_kernel(LaunchArgs a, int margin_i, con
                             gather_taps<KT>(Gs + j0, K, delta, tab, gA, gT);
                             const float A = dc.amp;
                             const float dLdD = __fmaf_rn(-A * gT, qf, -gA * A * A);
-                            dsx = dLdD * dc.ex; dsy = dLdD * dc.ey; dsz = dLdD * dc.ez;
-                            mpx -= dsx; mpy -= dsy; mpz -= dsz;
+                            dsx += dLdD * dc.ex; dsy += dLdD * dc.ey; dsz += dLdD * dc.ez;
+                            mpx -= dLdD * dc.ex; mpy -= dLdD * dc.ey; mpz -= dLdD * dc.ez;
                         } else {
                             atomicOr(&a.hdr->status, FRAM_DEV_CAPACITY);
                         }
                     }
                 }
-                block_sum3<NT>(mpx, mpy, mpz, red);
-                if (tid == 0) {
-                    mic_part[3 * m] += mpx; mic_part[3 * m + 1] += mpy; mic_part[3 * m + 2] += mpz;
-                    src_part[0] += dsx; src_part[1] += dsy; src_part[2] += dsz;
+                // Mic partials: a fixed-order warp sum; each warp keeps its own slot.
+                mpx = warp_sum(mpx); mpy = warp_sum(mpy); mpz = warp_sum(mpz);
+                if (lane == 0) {
+                    float* rw = red + (wid * M + m) * 3;
+                    rw[0] += mpx; rw[1] += mpy; rw[2] += mpz;
                 }
             }
             if (has && grad_vs) {
                 grad_vs[3 * v] = gvx; grad_vs[3 * v + 1] = gvy; grad_vs[3 * v + 2] = gvz;
             }
         }
-        float z0 = 0.f, z1 = 0.f;
-        block_sum3<NT>(pr, z0, z1, red);
-        for (int k = tid; k < 3 * M; k += NT) a.part_mic[(int64_t)qi * 3 * M + k] = mic_part[k];
+        pr = warp_sum(pr);
+        if (lane == 0) s_r[wid] = pr;
+        __syncthreads();
+        for (int k = tid; k < 3 * M; k += NT) {
+            float acc = 0.f;
+            for (int w = 0; w < NW; ++w) acc += red[w * M * 3 + k];
+            a.part_mic[(int64_t)qi * 3 * M + k] = acc;
+        }
         if (tid == 0) {
-            a.part_src[3 * (int64_t)qi] = src_part[0];
-            a.part_src[3 * (int64_t)qi + 1] = src_part[1];
-            a.part_src[3 * (int64_t)qi + 2] = src_part[2];
-            a.part_r[qi] = pr;
+            float acc = 0.f;
+            for (int w = 0; w < NW; ++w) acc += s_r[w];
+            a.part_r[qi] = acc;
+            a.part_src[3 * (int64_t)qi] = dsx;
+            a.part_src[3 * (int64_t)qi + 1] = dsy;
+            a.part_src[3 * (int64_t)qi + 2] = dsz;
         }
         __syncthreads();
     }
@@ -309,7 +392,7 @@ cudaError_t launch_bwd_t(const LaunchArgs& a, int margin_i, const float* pos_hi,
                          const float* grad_rir, const float* grad_early, float* grad_vs, cudaStream_t st)
 {
     constexpr int NT = 256;
-    const int smem = bwd_smem(a.tile, a.K, margin_i).total;
+    const int smem = bwd_smem(a.tile, a.K, margin_i, a.M, NT / 32).total;
     int per_sm = 0;
     cudaError_t e = kernel_residency((const void*)bwd_kernel<NT, KT>, NT, smem, &per_sm);
     if (e != cudaSuccess) return e;
