@@ -17,6 +17,7 @@
 // result does not depend on scheduling.
 #include <algorithm>
 #include <cmath>
+#include <utility>
 
 #include "fram_internal.cuh"
 
@@ -47,32 +48,32 @@ __device__ __forceinline__ float dsinc_small(float x)
 }
 
 // cos and sin(pi k / K) for k = -K..K, evaluated at compile time (Taylor series in double on
-// [-pi, pi]) and placed in constant memory, so the unrolled tap loop reads them as FMA operands.
-struct TrigTab {
-    float c[2 * kMaxHalfLen + 1];
-    float s[2 * kMaxHalfLen + 1];
-};
-
-constexpr double cx_pow_term(double x, int n)
+// [-pi, pi]) and written into the unrolled tap loop as literal FMA operands.
+__host__ __device__ constexpr double cx_term(double x, int n)
 {
     double t = 1.0;
     for (int i = 1; i <= n; ++i) t *= x / i;
     return t;
 }
 
-constexpr double cx_sin(double x)
+__host__ __device__ constexpr double cx_sin(double x)
 {
     double acc = 0.0;
-    for (int j = 0; j < 30; ++j) acc += ((j & 1) ? -1.0 : 1.0) * cx_pow_term(x, 2 * j + 1);
+    for (int j = 0; j < 30; ++j) acc += ((j & 1) ? -1.0 : 1.0) * cx_term(x, 2 * j + 1);
     return acc;
 }
 
-constexpr double cx_cos(double x)
+__host__ __device__ constexpr double cx_cos(double x)
 {
     double acc = 0.0;
-    for (int j = 0; j < 30; ++j) acc += ((j & 1) ? -1.0 : 1.0) * cx_pow_term(x, 2 * j);
+    for (int j = 0; j < 30; ++j) acc += ((j & 1) ? -1.0 : 1.0) * cx_term(x, 2 * j);
     return acc;
 }
+
+struct TrigTab {
+    float c[2 * kMaxHalfLen + 1];
+    float s[2 * kMaxHalfLen + 1];
+};
 
 template <int K>
 constexpr TrigTab make_trig_tab()
@@ -89,18 +90,15 @@ constexpr TrigTab make_trig_tab()
 __constant__ TrigTab c_trig40 = make_trig_tab<40>();
 __constant__ TrigTab c_trig63 = make_trig_tab<63>();
 
-template <int KT> __device__ __forceinline__ const TrigTab& trig_tab();
-template <> __device__ __forceinline__ const TrigTab& trig_tab<40>() { return c_trig40; }
-template <> __device__ __forceinline__ const TrigTab& trig_tab<63>() { return c_trig63; }
-
 // Taps of one arrival against staged G (Gs points at G[n_c - K]): gA = sum G tap, gT = sum G tap'
 // with tap(x) = sinc(x) (1 + cos(pi x/K))/2, x = k - delta.  With W2 = 1 + cos(pi x/K):
 //   2 tap = s W2,   2 tap' = s' W2 - (pi/K) s sin(pi x/K),
 //   s = -(-1)^k sin(pi delta)/(pi x),  s' = ((-1)^k cos(pi delta) - s)/x.
+// The loop is fully unrolled and the constant tables are named directly, so their entries are
+// read as constant-bank operands of the FMAs.
 template <int KT>
 __device__ __forceinline__ void gather_taps_ct(const float* __restrict__ Gs, float delta, float& gA, float& gT)
 {
-    const TrigTab& tb = trig_tab<KT>();
     const float sd = sinpi_poly(delta), cd = cospi_poly(delta);
     const float y = delta * (1.0f / (float)KT);
     const float sk = sinpi_poly(y), ck = cospi_poly(y);
@@ -110,6 +108,8 @@ __device__ __forceinline__ void gather_taps_ct(const float* __restrict__ Gs, flo
 #pragma unroll
     for (int kk = 0; kk <= 2 * KT; ++kk) {
         const int k = kk - KT;
+        const float Ck = (KT == 40) ? c_trig40.c[kk] : c_trig63.c[kk];
+        const float Sk = (KT == 40) ? c_trig40.s[kk] : c_trig63.s[kk];
         const float G = Gs[kk];
         const float x = __fsub_rn((float)k, delta);
         const float r = rcp_approx(x);
@@ -117,8 +117,8 @@ __device__ __forceinline__ void gather_taps_ct(const float* __restrict__ Gs, flo
         const float s = (even ? -spi : spi) * r;
         const float sc = (even ? -spic : spic) * r;
         const float sp = (k == 0) ? dsinc_small(x) : ((even ? cd : -cd) - s) * r;
-        const float W2 = __fmaf_rn(tb.c[kk], ck, __fmaf_rn(tb.s[kk], sk, 1.0f));
-        const float sw = __fmaf_rn(tb.s[kk], ck, -(tb.c[kk] * sk));
+        const float W2 = __fmaf_rn(Ck, ck, __fmaf_rn(Sk, sk, 1.0f));
+        const float sw = __fmaf_rn(Sk, ck, -(Ck * sk));
         float tap2 = s * W2;
         float dtap2 = __fmaf_rn(sp, W2, sc * sw);
         if ((kk == 0 || kk == 2 * KT) && !(fabsf(x) < (float)KT)) { tap2 = 0.f; dtap2 = 0.f; }
