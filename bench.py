@@ -247,6 +247,9 @@ def main():
         fwd(k)
         api.synthesize_backward_prepared(ds, vs.pos_hi, vs.pos_lo, vs.g, vs.r, G, None, out=grads)
 
+    api.sample(ds, seed=999, out=vs)
+    tile = api.autotune(ds, vs, rir)       # picks the tile length; tile = 0 launches use it
+
     peaks, peak_kind = _measured_peaks()
     clock_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
@@ -284,7 +287,7 @@ def main():
         "config": {"workload": args.workload, "rooms": sc.B, "sources": sc.S, "mics": sc.M, "fs": sc.fs,
                    "half_len": K, "images": int(N), "rir_samples": int(T), "taps_per_step": taps,
                    "l2": f"outputs {out_bytes / 1e9:.1f} GB per step, larger than L2 (129 MB)",
-                   "tile": params.tile or 1024},
+                   "tile": tile, "tile_choice": "fram_autotune over 256/512/1024/2048"},
         "taps_per_s": taps * args.steps * world / t_fwd,
         "fwd_bwd": {"value": world * args.steps * rirs / t_fb, "unit": "RIRs/s",
                     "ms_per_step": 1000.0 * t_fb / args.steps, "taps_per_s": world * 2 * taps * args.steps / t_fb},

@@ -69,7 +69,8 @@ typedef struct fram_params {
     double early_post_ms;  /*        +ceil(post*fs/1000)], n0 = ceil(D_{0,m} fs / c0)       */
     int32_t half_len;      /* K: taps at |n - t| < K, 2K+1 taps per arrival; 1..128        */
     int32_t tile;          /* synthesis tile length in samples (multiple of 256, 256..4096); */
-                           /* 0 = library default                                          */
+                           /* 0 = the tile fram_autotune chose for this kind of workload,  */
+                           /* else 1024; size workspaces with 0 to allow any tile          */
 } fram_params;
 
 /*
@@ -197,6 +198,21 @@ int fram_synthesize_backward_prepared(const fram_scene* scene, const fram_params
                                       const float* grad_rir, const float* grad_early, float* grad_vs,
                                       float* grad_mic, float* grad_src, float* grad_r,
                                       void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Tile-length autotuner for the synthesis kernel.  Runs fram_synthesize on the caller's own
+ * inputs with each candidate tile length (256, 512, 1024, 2048 samples; those whose workspace
+ * or shared memory does not fit are skipped), times them with CUDA events on `stream`, and
+ * records the fastest for this kind of workload (device, K, fs, S, M, RIR-length octave, image
+ * density).  Later calls with p->tile == 0 on a matching workload use it.  The tile length
+ * sets how many images and arrivals each CTA stages and sorts, so it also picks the number of
+ * impulses per CTA.  Writes the choice to *tile_out (nullable).  Overwrites `rir`.
+ * Synchronises the stream: call it before capturing a CUDA graph.  The workspace must be sized
+ * with p->tile == 0 (fram_workspace_size then covers every candidate).
+ */
+int fram_autotune(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi, const float* vs_pos_lo,
+                  const float* vs_g, const float* r, float* rir, void* workspace, size_t workspace_bytes,
+                  void* stream, int32_t* tile_out);
 
 /*
  * Synchronises `stream` and reads the device status word that the last call which used

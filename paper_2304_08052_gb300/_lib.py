@@ -24,7 +24,8 @@ FRAM_DEV_NONFINITE = 0x4
 # Every symbol include/fram.h declares (checked by tests/test_abi.py).
 EXPORTED = ("fram_version", "fram_last_error", "fram_default_params", "fram_layout", "fram_workspace_size",
             "fram_sample", "fram_synthesize", "fram_synthesize_backward", "fram_status", "fram_prepare",
-            "fram_synthesize_prepared", "fram_synthesize_backward_prepared", "fram_synthesize_noalloc")
+            "fram_synthesize_prepared", "fram_synthesize_backward_prepared", "fram_synthesize_noalloc",
+            "fram_autotune")
 
 
 class FramParams(ctypes.Structure):
@@ -74,6 +75,7 @@ def lib():
         L.fram_synthesize_prepared.argtypes = L.fram_synthesize.argtypes
         L.fram_synthesize_backward_prepared.argtypes = L.fram_synthesize_backward.argtypes
         L.fram_synthesize_noalloc.argtypes = [S, P, vp, vp, vp, vp, vp, vp, vp]
+        L.fram_autotune.argtypes = [S, P, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_int32)]
         for name in EXPORTED[3:]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L

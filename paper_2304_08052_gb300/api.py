@@ -265,3 +265,15 @@ def algorithmic_taps(sc) -> int:
     K = int(sc.params.half_len) if isinstance(sc, DeviceScene) else int(sc.half_len)
     scene = sc.scene if isinstance(sc, DeviceScene) else sc
     return int(scene.S * scene.M * (np.asarray(scene.n_vs, np.int64) + 1).sum() * (2 * K + 1))
+
+
+def autotune(sc: DeviceScene, vs: Images, rir: Optional[torch.Tensor] = None) -> int:
+    """fram_autotune: time the candidate tile lengths on these inputs; later calls with
+    params.tile == 0 on this kind of workload use the fastest.  Returns the chosen tile."""
+    if rir is None:
+        rir = torch.empty(sc.rir_total, dtype=torch.float32, device=sc.dims.device)
+    out = ctypes.c_int32(0)
+    check(lib().fram_autotune(ctypes.byref(sc.c_scene()), ctypes.byref(sc.params.c()), _ptr(vs.pos_hi),
+                              _ptr(vs.pos_lo), _ptr(vs.g), _ptr(vs.r), _ptr(rir), ctypes.c_void_p(sc.ws.data_ptr()),
+                              ctypes.c_size_t(sc.ws_bytes), _stream(), ctypes.byref(out)))
+    return int(out.value)

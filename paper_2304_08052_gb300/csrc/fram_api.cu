@@ -101,7 +101,51 @@ static int check_params(const fram_params* p)
     return FRAM_OK;
 }
 
-static int tile_of(const fram_params* p) { return p->tile ? p->tile : kDefaultTile; }
+// ---- tile length: explicit, or chosen by fram_autotune for this kind of workload ----------
+// Workloads are grouped by device, K, fs, sources, mics, the RIR-length octave and the image
+// density (images per output sample, half-octave bins); fram_autotune records the fastest tile
+// per group and launches with tile = 0 use it (the library default until a group is tuned).
+static const int kTileCandidates[] = {256, 512, 1024, 2048};
+
+struct TuneKey {
+    int dev, K, S, M, len_oct, dens_bin;
+    double fs;
+    bool operator==(const TuneKey& o) const
+    {
+        return dev == o.dev && K == o.K && S == o.S && M == o.M && len_oct == o.len_oct && dens_bin == o.dens_bin &&
+               fs == o.fs;
+    }
+};
+
+static std::mutex g_tune_mu;
+static std::vector<std::pair<TuneKey, int>> g_tune;
+
+static TuneKey tune_key(const fram_scene* sc, const fram_params* p)
+{
+    TuneKey k{};
+    if (cudaGetDevice(&k.dev) != cudaSuccess) k.dev = -1;
+    k.K = p->half_len;
+    k.S = sc->S;
+    k.M = sc->M;
+    k.fs = p->fs;
+    k.len_oct = sc->max_len > 0 ? (int)std::ceil(std::log2((double)sc->max_len)) : 0;
+    const double samples = sc->M > 0 ? (double)sc->rir_total / sc->M : 0.0;
+    const double dens = samples > 0 ? (double)sc->n_vs_total / samples : 0.0;
+    k.dens_bin = dens > 0 ? (int)std::floor(2.0 * std::log2(dens)) : -1000;
+    return k;
+}
+
+static int tile_for(const fram_scene* sc, const fram_params* p)
+{
+    if (p->tile) return p->tile;
+    const TuneKey k = tune_key(sc, p);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto& e : g_tune)
+        if (e.first == k) return e.second;
+    return kDefaultTile;
+}
+
+static int tile_of(const fram_params* p) { return p->tile ? p->tile : kTileCandidates[0]; }
 
 static int check_scene(const fram_scene* sc, bool need_arrays)
 {
@@ -121,7 +165,7 @@ static int check_scene(const fram_scene* sc, bool need_arrays)
 
 static int check_ws(const fram_scene* sc, const fram_params* p, void* ws, size_t bytes, WsLayout* out)
 {
-    const WsLayout w = ws_layout(*sc, tile_of(p));
+    const WsLayout w = ws_layout(*sc, tile_for(sc, p));
     if (w.max_tiles > 0xffff) return fail(FRAM_EINVAL, "too many tiles per RIR (raise the tile length)");
     if (!ws) return fail(FRAM_EWORKSPACE, "workspace is null");
     if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(FRAM_EWORKSPACE, "workspace must be 256-byte aligned");
@@ -337,6 +381,61 @@ int fram_synthesize_backward(const fram_scene* scene, const fram_params* p, cons
         return rc;
     return fram_synthesize_backward_prepared(scene, p, vs_pos_hi, vs_pos_lo, vs_g, r, grad_rir, grad_early, grad_vs,
                                              grad_mic, grad_src, grad_r, workspace, workspace_bytes, stream);
+}
+
+int fram_autotune(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi, const float* vs_pos_lo,
+                  const float* vs_g, const float* r, float* rir, void* workspace, size_t workspace_bytes, void* stream,
+                  int32_t* tile_out)
+{
+    WsLayout w0;
+    fram_params base = *p;
+    base.tile = 0;
+    int rc = common_checks(scene, &base, vs_pos_hi, vs_g, r, workspace, workspace_bytes, &w0);
+    if (rc != FRAM_OK) return rc;
+    if (scene->rir_total > 0 && !rir) return fail(FRAM_EINVAL, "rir must not be null");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const double q = p->fs / p->c0;
+    const int margin = (int)std::ceil(scene->array_radius * q) + 3;
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return cuda_fail(e, "fram_autotune: event");
+    e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(e, "fram_autotune: event"); }
+    int best = kDefaultTile;
+    float best_ms = 3.0e38f;
+    for (int T : kTileCandidates) {
+        fram_params cand = *p;
+        cand.tile = T;
+        const WsLayout w = ws_layout(*scene, T);
+        if (w.max_tiles > 0xffff || w.total > workspace_bytes) continue;
+        if (synth_smem_total(T, p->half_len, margin) > 227 * 1024) continue;
+        rc = fram_synthesize(scene, &cand, vs_pos_hi, vs_pos_lo, vs_g, r, rir, nullptr, workspace, workspace_bytes,
+                             stream);
+        if (rc != FRAM_OK) break;
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 2 && rc == FRAM_OK; ++rep)
+            rc = fram_synthesize(scene, &cand, vs_pos_hi, vs_pos_lo, vs_g, r, rir, nullptr, workspace,
+                                 workspace_bytes, stream);
+        cudaEventRecord(e1, st);
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { rc = cuda_fail(e, "fram_autotune: timing"); break; }
+        if (rc != FRAM_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best = T; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != FRAM_OK) return rc;
+    const TuneKey k = tune_key(scene, p);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        bool found = false;
+        for (auto& ent : g_tune)
+            if (ent.first == k) { ent.second = best; found = true; }
+        if (!found) g_tune.push_back({k, best});
+    }
+    if (tile_out) *tile_out = best;
+    return FRAM_OK;
 }
 
 int fram_status(void* workspace, void* stream, int32_t* flags)

@@ -307,6 +307,9 @@ cudaError_t launch_backward(const LaunchArgs& a, const float* pos_hi, const floa
 
 int device_sm_count();
 
+// Dynamic shared memory of the synthesis kernel for tile T, half length K and halo margin M.
+int synth_smem_total(int T, int K, int M);
+
 // Raises the kernel's dynamic shared-memory limit to `smem` (once per device and size) and
 // returns how many CTAs of `threads` threads fit on one SM.  Results are cached, so after the
 // first call with a configuration no CUDA API call other than the launch itself is made --

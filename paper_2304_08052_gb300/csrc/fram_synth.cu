@@ -585,6 +585,8 @@ __global__ void __launch_bounds__(NT, 3) synth_kernel(LaunchArgs a, const float*
 
 
 
+int synth_smem_total(int T, int K, int M) { return synth_smem(T, K, M).total; }
+
 cudaError_t launch_prepare(const LaunchArgs& a, const float* pos_hi, const float* pos_lo, const float* r,
                            cudaStream_t st)
 {

@@ -107,3 +107,15 @@ def test_entry_points_reject_bad_arguments_before_any_launch(L):
     L.fram_workspace_size(ctypes.byref(sc2), ctypes.byref(p.c()), ctypes.byref(n))
     assert L.fram_synthesize(ctypes.byref(sc2), ctypes.byref(p.c()), fake, None, fake, fake, fake, None,
                              ctypes.c_void_p(0x100000), n.value - 256, None) == _lib.FRAM_EWORKSPACE
+
+
+def test_auto_tile_workspace_covers_every_candidate(L):
+    n_auto, n_fix = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    sc = _scene_struct(B=64, max_len=20000, nvs=64 * 2 * 3000)
+    for tile, out in ((0, n_auto), (256, n_fix)):
+        assert L.fram_workspace_size(ctypes.byref(sc), ctypes.byref(api.Params(tile=tile).c()), ctypes.byref(out)) == 0
+    assert n_auto.value >= n_fix.value
+    for tile in (512, 1024, 2048):
+        n = ctypes.c_size_t(0)
+        L.fram_workspace_size(ctypes.byref(sc), ctypes.byref(api.Params(tile=tile).c()), ctypes.byref(n))
+        assert n.value <= n_auto.value
