@@ -12,7 +12,7 @@ Also reported: taps/s; the synthesis kernel alone against the ALU roofline; the 
 alone; an end-to-end number through host buffers; the graph-captured batched path against a
 plain per-room launch loop (batch_1024 with early RIRs); the FP64 oracle on the host cores.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME] [--rooms N]
 """
 from __future__ import annotations
 
@@ -34,6 +34,9 @@ METRIC = "multi-ch RIRs/s and sinc-taps/s (fwd, fwd+bwd) at 1 GB300, % of roofli
 # Algorithmic work per tap (the tap arithmetic of the paper's sum, Eq. 1 with windowed sincs):
 # forward 8 FP32-pipe operations and 1 reciprocal on the MUFU (special function) pipe; adjoint
 # 14 FP32 and 1 MUFU.  Per arrival (image x mic) 40 FP32 + 6 MUFU more, spread over its 2K+1 taps.
+# Kernels of libfram per fwd step: sample_kernel; room_prologue, item_scan, bin_images, item_ranges
+# (preparation); amp_gather, synth_kernel (synthesis).
+FWD_LAUNCHES = 7
 FWD_FP32, BWD_FP32, ARR_FP32 = 8.0, 14.0, 40.0
 TAP_MUFU, ARR_MUFU = 1.0, 6.0
 FP32_LANES_PER_SM, MUFU_LANES_PER_SM = 128, 16
@@ -202,6 +205,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
     ap.add_argument("--workload", default="large_4096")
+    ap.add_argument("--rooms", type=int, default=0, help="first N rooms of the workload only (0 = all); "
+                    "for profiler captures of a small case")
     ap.add_argument("--ref-rooms", type=int, default=8)
     ap.add_argument("--cpu-rooms", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
@@ -227,6 +232,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     sc = scenes.by_name(args.workload, rank_scene_seed(0, rank))
+    if args.rooms > 0:
+        sc = sc.subset(range(min(args.rooms, sc.B)))
     params = api.Params(fs=sc.fs, half_len=sc.half_len)
     ds = api.DeviceScene(sc, params)
     N, T = ds.n_vs_total, ds.rir_total
@@ -284,7 +291,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "RIRs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "rooms": sc.B, "sources": sc.S, "mics": sc.M, "fs": sc.fs,
+        "config": {"workload": sc.name, "rooms": sc.B, "sources": sc.S, "mics": sc.M, "fs": sc.fs,
                    "half_len": K, "images": int(N), "rir_samples": int(T), "taps_per_step": taps,
                    "l2": f"outputs {out_bytes / 1e9:.1f} GB per step, larger than L2 (129 MB)",
                    "tile": tile, "tile_choice": "fram_autotune over 256/512/1024/2048"},
@@ -292,7 +299,7 @@ def main():
         "fwd_bwd": {"value": world * args.steps * rirs / t_fb, "unit": "RIRs/s",
                     "ms_per_step": 1000.0 * t_fb / args.steps, "taps_per_s": world * 2 * taps * args.steps / t_fb},
         "roofline": {"bound": "alu", "achieved": ach_fwd / 1e9, "peak": peak_fwd / 1e9, "unit": "Gtap/s",
-                     "frac": ach_fwd / peak_fwd, "traffic": None, "kernel": "synth_kernel",
+                     "frac": ach_fwd / peak_fwd, "traffic": None, "kernel": "synth_kernel (timed with amp_gather)",
                      "limit": lim_fwd, "kernel_ms": 1000.0 * syn_s, "hbm_gbs": out_bytes / syn_s / 1e9,
                      "peak_basis": f"{sm_count} SMs x ({FP32_LANES_PER_SM} FP32, {MUFU_LANES_PER_SM} MUFU) lanes x "
                                    f"{clock_hz / 1e6:.0f} MHz ({peak_kind} sm_max_mhz); per tap "
@@ -301,7 +308,7 @@ def main():
         "roofline_bwd": {"bound": "alu", "achieved": ach_bwd / 1e9, "peak": peak_bwd / 1e9, "unit": "Gtap/s",
                          "frac": ach_bwd / peak_bwd, "kernel": "bwd_kernel", "limit": lim_bwd,
                          "kernel_ms": 1000.0 * bwd_s},
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": FWD_LAUNCHES * args.steps,
         "clocks": clocks,
     }
 

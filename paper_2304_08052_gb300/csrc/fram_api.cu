@@ -183,6 +183,7 @@ static LaunchArgs make_args(const fram_scene* sc, const fram_params* p, const Ws
     a.K = p->half_len;
     a.tile = w.tile;
     a.max_tiles = w.max_tiles;
+    a.nb32 = w.nb32;
     const double q = p->fs / p->c0;
     a.q = (float)q;
     a.q2 = f2_from_double(q);
@@ -205,6 +206,11 @@ static LaunchArgs make_args(const fram_scene* sc, const fram_params* p, const Ws
     a.key = reinterpret_cast<float*>(base + w.key);
     a.skey = reinterpret_cast<int32_t*>(base + w.skey);
     a.ptmp = reinterpret_cast<int32_t*>(base + w.ptmp);
+    a.spa = reinterpret_cast<float4*>(base + w.spa);
+    a.spb = reinterpret_cast<float2*>(base + w.spb);
+    a.pos32 = reinterpret_cast<int32_t*>(base + w.pos32);
+    a.samp = reinterpret_cast<float*>(base + w.samp);
+    a.irec = reinterpret_cast<ItemRec*>(base + w.irec);
     a.part_mic = reinterpret_cast<float*>(base + w.part_mic);
     a.part_src = reinterpret_cast<float*>(base + w.part_src);
     a.part_r = reinterpret_cast<float*>(base + w.part_r);
@@ -394,8 +400,6 @@ int fram_autotune(const fram_scene* scene, const fram_params* p, const float* vs
     if (rc != FRAM_OK) return rc;
     if (scene->rir_total > 0 && !rir) return fail(FRAM_EINVAL, "rir must not be null");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const double q = p->fs / p->c0;
-    const int margin = (int)std::ceil(scene->array_radius * q) + 3;
     cudaEvent_t e0, e1;
     cudaError_t e = cudaEventCreate(&e0);
     if (e != cudaSuccess) return cuda_fail(e, "fram_autotune: event");
@@ -408,7 +412,7 @@ int fram_autotune(const fram_scene* scene, const fram_params* p, const float* vs
         cand.tile = T;
         const WsLayout w = ws_layout(*scene, T);
         if (w.max_tiles > 0xffff || w.total > workspace_bytes) continue;
-        if (synth_smem_total(T, p->half_len, margin) > 227 * 1024) continue;
+        if (synth_smem_total(T) > 227 * 1024) continue;
         rc = fram_synthesize(scene, &cand, vs_pos_hi, vs_pos_lo, vs_g, r, rir, nullptr, workspace, workspace_bytes,
                              stream);
         if (rc != FRAM_OK) break;

@@ -184,9 +184,8 @@ __device__ __forceinline__ float uniform_from_word(uint32_t w)
 // --------------------------------------------------------------------------------------
 constexpr int kMaxHalfLen = 128;
 constexpr int kDefaultTile = 1024;
+constexpr int kMaxTile = 4096;
 constexpr int kSynthThreads = 256;
-constexpr int kStageCap = 2048;   // candidate images staged per synthesis tile
-constexpr int kArrCap = 768;      // arrival records held at once (larger tiles run in chunks)
 
 struct RoomConst {          // per room, written by the prologue
     float cx, cy, cz;       // array centre (float)
@@ -211,6 +210,14 @@ struct DirectConst {        // per (room, source, mic)
     int32_t pad_;
 };
 
+struct ItemRec {            // per work item (room, source, tile), written by the preparation
+    int32_t b, s, T0, len;  // room, source, first sample of the tile, L_b
+    int32_t c_lo, c_hi;     // sorted image positions whose key can reach the tile
+    int32_t pad0, pad1;
+    int64_t v0;             // first image row of (room, source)
+    int64_t out0;           // first RIR sample of (room, source, mic 0)
+};
+
 struct Header {             // first 256 bytes of the workspace
     int32_t status;         // FRAM_DEV_* bits
     int32_t queue;          // persistent-kernel work counter
@@ -221,10 +228,12 @@ struct Header {             // first 256 bytes of the workspace
 
 struct WsLayout {
     size_t header, room, direct, src_tile, item_off, items, bin_off, perm, key, skey, ptmp;
+    size_t spa, spb, pos32, samp, irec;
     size_t part_mic, part_src, part_r;
     size_t total;
     int tile;
     int max_tiles;          // ceil(max_len / tile)
+    int nb32;               // 32-sample key blocks per (room, source), independent of the tile
     int64_t max_items;      // B * S * max_tiles
 };
 
@@ -236,6 +245,7 @@ inline WsLayout ws_layout(const fram_scene& sc, int tile)
     w.tile = tile;
     w.max_tiles = sc.max_len > 0 ? (sc.max_len + tile - 1) / tile : 1;
     w.max_items = (int64_t)sc.B * sc.S * w.max_tiles;
+    w.nb32 = (sc.max_len > 0 ? (sc.max_len + 31) / 32 : 0) + 2 * kMaxTile / 32;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
     w.header = take(sizeof(Header));
@@ -249,6 +259,11 @@ inline WsLayout ws_layout(const fram_scene& sc, int tile)
     w.key = take(sizeof(float) * (size_t)sc.n_vs_total);
     w.skey = take(sizeof(int32_t) * (size_t)sc.n_vs_total);
     w.ptmp = take(sizeof(int32_t) * (size_t)sc.n_vs_total);
+    w.spa = take(sizeof(float) * 4 * (size_t)sc.n_vs_total);
+    w.spb = take(sizeof(float) * 2 * (size_t)sc.n_vs_total);
+    w.pos32 = take(sizeof(int32_t) * (size_t)sc.B * sc.S * ((size_t)w.nb32 + 1));
+    w.samp = take(sizeof(float) * (size_t)sc.n_vs_total);
+    w.irec = take(sizeof(ItemRec) * (size_t)w.max_items);
     w.part_mic = take(sizeof(float) * 3 * (size_t)w.max_items * sc.M);
     w.part_src = take(sizeof(float) * 3 * (size_t)w.max_items);
     w.part_r = take(sizeof(float) * (size_t)w.max_items);
@@ -263,6 +278,7 @@ struct LaunchArgs {
     int32_t K;
     int32_t tile;
     int32_t max_tiles;
+    int32_t nb32;           // last index of a (room, source) row of pos32
     float q;                // fs / c0 as a float
     f2 q2;                  // fs / c0 as a float pair
     int32_t early_pre, early_post;
@@ -289,6 +305,12 @@ struct LaunchArgs {
     float* key;             // per image: delay to the array centre in samples (binning key)
     int32_t* skey;          // per sorted position: floor(key), clamped past the last tile
     int32_t* ptmp;          // scratch for the two-pass sort
+    float4* spa;            // per sorted position: image position hi (x, y, z) and lo x
+    float2* spb;            // per sorted position: image position lo (y, z)
+    int32_t* pos32;         // per (room, source) and 32-sample block j: first sorted position
+                            // whose key is >= 32 j (rows of nb32 + 1 entries)
+    float* samp;            // per sorted position: r^g of the image (written per synthesis)
+    ItemRec* irec;          // per work item
     float* part_mic;
     float* part_src;
     float* part_r;
@@ -307,8 +329,8 @@ cudaError_t launch_backward(const LaunchArgs& a, const float* pos_hi, const floa
 
 int device_sm_count();
 
-// Dynamic shared memory of the synthesis kernel for tile T, half length K and halo margin M.
-int synth_smem_total(int T, int K, int M);
+// Dynamic shared memory of one synthesis CTA for tile length T.
+int synth_smem_total(int T);
 
 // Raises the kernel's dynamic shared-memory limit to `smem` (once per device and size) and
 // returns how many CTAs of `threads` threads fit on one SM.  Results are cached, so after the

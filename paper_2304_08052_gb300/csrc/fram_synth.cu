@@ -8,25 +8,25 @@
 //                      1/D, Eq. 9 window).
 //   2. item_scan       one CTA: prefix sum of S * ntiles_b -> work-item table (room, source, tile).
 //   3. bin_images      one warp per (room, source): each image's delay to the array centre
-//                      (the binning key, in samples) and a stable counting sort of the images
-//                      by output tile.  Per-mic delays differ from the key by at most the
-//                      array radius in samples ("margin").
-//   4. synth_kernel    persistent CTAs pull (room, source, tile) items from a counter.  Per item:
-//                      stage the images whose key lies within K + margin of the tile; then for
-//                      each mic: compute every arrival's delay t = D fs/c0 (float-pair distance),
-//                      amplitude and sinc constants; counting-sort arrivals by integer delay
-//                      (ties by staging index, so the order is deterministic); and let each warp
-//                      own 32-sample rows, gathering the arrivals whose window covers the row.
+//                      (the binning key, in samples), a stable counting sort of the images by
+//                      floor(key), a copy of the positions in that order and the first sorted
+//                      position of every 32-sample key block.  Per-mic delays differ from the
+//                      key by at most the array radius in samples ("margin").
+//   4. synth_kernel    persistent warps pull (room, source, tile, mic) units from a counter.
+//                      Per unit the warp owns a private tile buffer in shared memory, computes
+//                      the arrival (delay t = D fs/c0 from a float-pair distance, amplitude,
+//                      sinc constants) of every image whose key lies within K + margin of the
+//                      tile, and adds each arrival's 2K+1 taps with one lane per tap offset.
 //
-// Tap arithmetic.  With t = n_c + delta (n_c = nearest integer), sin(pi (n - t)) =
-// (-1)^(n - n_c) sin(-pi delta), so for |n - t| < K
-//   A sinc(n - t) w(n - t) = (-1)^n [P + cos(pi n/K) a' + sin(pi n/K) b'] / (t - n)
-// with per-arrival constants P = (-1)^n_c A sin(pi delta) / (2 pi), a' = P cos(pi t/K),
-// b' = P sin(pi t/K) (angle-difference form of the Hann term (1 + cos(pi (n - t)/K)) / 2).
-// Per tap: d = (n_c - n) + delta (exact float difference + one rounding), two FMAs for the
-// numerator, one reciprocal shared by two arrivals (1/d1 = d2 / (d1 d2)), one FMA to
-// accumulate.  No global atomics touch the accumulators: each output sample is owned by one
-// lane and sums its arrivals in sorted order.
+// Tap arithmetic.  With t = n_c + delta (n_c = nearest integer) and the tap at n = n_c + o,
+// sin(pi (n - t)) = (-1)^o sin(-pi delta), so for |n - t| < K
+//   A sinc(n - t) w(n - t) = (-1)^o [P + a cos(pi o/K) + b sin(pi o/K)] / (delta - o)
+// with per-arrival constants P = A sin(pi delta) / (2 pi), a = P cos(pi delta/K),
+// b = P sin(pi delta/K) (angle-difference form of the Hann term (1 + cos(pi (n - t)/K)) / 2).
+// The o-dependent factors are per-lane constants, so a tap costs one FMA for the denominator,
+// two for the numerator, one reciprocal and one FMA into the buffer.  No atomics touch the
+// accumulators: a buffer belongs to one warp, whose lanes hit distinct samples in every step,
+// and each sample sums its arrivals in the fixed sorted image order.
 #include <cmath>
 
 #include "fram_internal.cuh"
@@ -184,7 +184,8 @@ __device__ __forceinline__ int tile_of_key(float key, float invT, int nt)
     return t > nt - 1 ? nt - 1 : t;
 }
 
-__global__ void __launch_bounds__(64) bin_images(LaunchArgs a, const float* __restrict__ pos_hi)
+__global__ void __launch_bounds__(64) bin_images(LaunchArgs a, const float* __restrict__ pos_hi,
+                                                  const float* __restrict__ pos_lo)
 {
     extern __shared__ int bin_smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -249,12 +250,18 @@ __global__ void __launch_bounds__(64) bin_images(LaunchArgs a, const float* __re
     }
     __syncwarp();
     // Pass 2: inside each tile, stable counting sort by floor(key) - tile start.  The last tile
-    // also takes every key beyond the RIR, in a doubled bucket range clamped at its end.
+    // also takes every key beyond the RIR, in a doubled bucket range clamped at its end.  The
+    // sorted order also receives a copy of the image positions, and p32 the first sorted position
+    // of every 32-sample key block.
+    int* p32 = a.pos32 + seg * ((int64_t)a.nb32 + 1);
     for (int t = 0; t < nt; ++t) {
         const int b0 = bo[t], b1 = bo[t + 1];
-        if (b1 <= b0) continue;
         const int nb = (t == nt - 1) ? 2 * T : T;
         const int t0 = t * T;
+        if (b1 <= b0) {
+            for (int j = lane; j < nb / 32; j += 32) p32[t0 / 32 + j] = b0;
+            continue;
+        }
         for (int f = lane; f < nb; f += 32) fine[f] = 0;
         __syncwarp();
         for (int p = b0 + lane; p < b1; p += 32) {
@@ -275,6 +282,7 @@ __global__ void __launch_bounds__(64) bin_images(LaunchArgs a, const float* __re
                 if (lane >= o) x += y;
             }
             fine[f] = run + x - v;
+            if (lane == 0) p32[(t0 + base) / 32] = run;
             run = __shfl_sync(0xffffffffu, run + x, 31);
         }
         __syncwarp();
@@ -297,42 +305,19 @@ __global__ void __launch_bounds__(64) bin_images(LaunchArgs a, const float* __re
             if (lane == leader && act) fine[f] = basepos + __popc(peers);
             __syncwarp();
             if (act) {
-                a.perm[v0 + basepos + rank] = i;
-                a.skey[v0 + basepos + rank] = t0 + f;
+                const int64_t q = v0 + basepos + rank;
+                a.perm[q] = i;
+                a.skey[q] = t0 + f;
+                const float* ph = pos_hi + 3 * (v0 + i);
+                float lx = 0.0f, ly = 0.0f, lz = 0.0f;
+                if (pos_lo) { const float* pl = pos_lo + 3 * (v0 + i); lx = pl[0]; ly = pl[1]; lz = pl[2]; }
+                a.spa[q] = make_float4(ph[0], ph[1], ph[2], lx);
+                a.spb[q] = make_float2(ly, lz);
             }
         }
         __syncwarp();
     }
-}
-
-// Shared-memory plan of synth_kernel (bytes, 16-byte aligned pieces).
-//   sperm/skeys  the tile's candidate images (sorted by delay key) and their keys
-//   rowb         per 32-sample row: first and one-past-last candidate in reach
-//   q0/q1/q2     arrival records, two per 48-byte group: (n1, d1, n2, d2) (P1, a1, b1, P2) (a2, b2, -, -)
-//   outt         the tile's samples for the current mic
-//   tabT         cos, sin(pi m / K) for m = base + k, base = T0 - K - M - 1
-struct SynthSmem {
-    int sperm, skeys, rowb, q0, q1, q2, outt, tabT, total, nbk;
-};
-
-__host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
-
-__host__ __device__ inline SynthSmem synth_smem(int T, int K, int M)
-{
-    SynthSmem s;
-    s.nbk = T + 2 * K + 2 * M + 2;
-    const int NP = kArrCap / 2 + 1;
-    int off = 0;
-    s.sperm = off; off = al16(off + 4 * kStageCap);
-    s.skeys = off; off = al16(off + 4 * kStageCap);
-    s.rowb = off; off = al16(off + 4 * (2 * (T / 32) + 2));
-    s.q0 = off; off = al16(off + 16 * NP);
-    s.q1 = off; off = al16(off + 16 * NP);
-    s.q2 = off; off = al16(off + 16 * NP);
-    s.outt = off; off = al16(off + 4 * T);
-    s.tabT = off; off = al16(off + 8 * s.nbk);
-    s.total = off;
-    return s;
+    for (int j = (nt + 1) * T / 32 + lane; j <= a.nb32; j += 32) p32[j] = n;
 }
 
 // Image arrival for mic (mx, my, mz): delay as integer n_c + delta and distance, from the
@@ -355,229 +340,241 @@ __device__ __forceinline__ void image_delay(float phx, float phy, float phz, flo
     dist = D.hi;
 }
 
-// Arrival constants of the tap identity: P = (-1)^n_c A sin(pi delta)/(2 pi), a' = P cos(pi t/K),
-// b' = P sin(pi t/K), from the phase table entry cs = (cos, sin)(pi n_c / K).
-__device__ __forceinline__ float3 arrival_consts(int nc, float delta, float A, float2 cs, float invK)
+// Work-item records for the synthesis: room, source, tile, and the run of sorted images whose
+// binning key lies within K + margin of the tile (from the 32-sample block table).
+__global__ void item_ranges(LaunchArgs a, int64_t max_items)
 {
-    const float P = ((nc & 1) ? -A : A) * sinpi_poly(delta) * kTwoPiInv;
+    const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= max_items || qi >= a.hdr->n_items) return;
+    const int2 it = a.items[qi];
+    const int b = it.x, s = it.y >> 16, tau = it.y & 0xffff;
+    const RoomConst rc = a.room[b];
+    ItemRec ir;
+    ir.b = b;
+    ir.s = s;
+    ir.T0 = tau * a.tile;
+    ir.len = rc.len;
+    const int* p32 = a.pos32 + ((int64_t)b * a.S + s) * ((int64_t)a.nb32 + 1);
+    const int kmin = max(ir.T0 - a.K - a.margin_i, 0);
+    const int kmax = ir.T0 + a.tile - 1 + a.K + a.margin_i;
+    ir.c_lo = p32[kmin >> 5];
+    ir.c_hi = p32[min((kmax >> 5) + 1, a.nb32)];
+    ir.pad0 = ir.pad1 = 0;
+    ir.v0 = rc.vs_off + (int64_t)s * rc.n_vs;
+    ir.out0 = rc.rir_off + (int64_t)s * a.M * rc.len;
+    a.irec[qi] = ir;
+}
+
+// r^g of every image, in sorted order (one CTA per (room, source)).
+__global__ void __launch_bounds__(256) amp_gather(LaunchArgs a, const float* __restrict__ g)
+{
+    const int64_t seg = blockIdx.x;
+    const int b = (int)(seg / a.S), s = (int)(seg % a.S);
+    const RoomConst rc = a.room[b];
+    if (rc.ntiles < 1) return;      // a room the prologue rejected has no sorted order
+    const int64_t v0 = rc.vs_off + (int64_t)s * rc.n_vs;
+    for (int p = threadIdx.x; p < rc.n_vs; p += blockDim.x)
+        a.samp[v0 + p] = exp2f(g[v0 + a.perm[v0 + p]] * rc.log2r);
+}
+
+// Arrival record (delta, P, a, b) of the tap identity for t = n_c + delta (|delta| <= 1/2),
+// with P = A sin(pi delta) / (2 pi), a = P cos(pi delta / K), b = P sin(pi delta / K).  The taps
+// with |n - t| < K are n_c - K + 1 .. n_c + K when delta > 0 and n_c - K .. n_c + K - 1 when
+// delta < 0; an arrival with delta > 2^-12 is re-based to n_c + 1, delta - 1, so that every
+// arrival's taps are base + o, o in [-K, K - 1].  The re-based delta rounds to a multiple of
+// 2^-24 and every constant is computed from that rounded value, so the record describes one
+// consistent delay (moved by < 3e-8 samples).  For 0 <= delta <= 2^-12 the dropped tap at
+// n_c + K has the window weight sin^2(pi delta / 2K) < 1e-12.  The identity holds for any split
+// of t; sin(pi (delta - 1)) = -sin(pi delta) keeps the polynomial arguments within [-1/2, 1/2].
+constexpr float kShiftMin = 2.44140625e-4f;   // 2^-12
+
+__device__ __forceinline__ float4 arrival_record(int& nc, float delta, float A, float invK, bool exact_trig)
+{
+    float sp;
+    if (delta > kShiftMin) {
+        const float d1 = __fsub_rn(delta, 1.0f);
+        sp = -sinpi_poly(__fadd_rn(d1, 1.0f));
+        delta = d1;
+        nc += 1;
+    } else {
+        if (fabsf(delta) < kTinyDelta) delta = kTinyDelta;
+        sp = sinpi_poly(delta);
+    }
+    const float P = A * sp * kTwoPiInv;
     const float y = delta * invK;
-    const float sk = sinpi_poly(y), ck = cospi_poly(y);
-    const float ca = cs.x * ck - cs.y * sk;
-    const float sa = cs.y * ck + cs.x * sk;
-    return make_float3(P, P * ca, P * sa);
-}
-
-__device__ __forceinline__ void put_record(float4* q0, float4* q1, float4* q2, int p, float nc_l, float delta,
-                                           float3 c)
-{
-    const int q = p >> 1;
-    float* f0 = reinterpret_cast<float*>(q0 + q);
-    float* f1 = reinterpret_cast<float*>(q1 + q);
-    float* f2p = reinterpret_cast<float*>(q2 + q);
-    if ((p & 1) == 0) { f0[0] = nc_l; f0[1] = delta; f1[0] = c.x; f1[1] = c.y; f1[2] = c.z; }
-    else { f0[2] = nc_l; f0[3] = delta; f1[3] = c.x; f2p[0] = c.y; f2p[1] = c.z; }
-}
-
-// Taps of the arrival pairs [q, qend) for the lane's sample.  Every arrival is masked with
-// |t - n| < K, so a pair may include one arrival outside the row's reach (it contributes zero);
-// a zero-weight record far from every sample completes an odd count.
-__device__ __forceinline__ float pair_tap(const float4 A, const float4 B, const float4 C, float nl, float cn, float sn,
-                                          float Kf, float acc)
-{
-    const float e1 = __fadd_rn(__fsub_rn(A.x, nl), A.y);
-    const float e2 = __fadd_rn(__fsub_rn(A.z, nl), A.w);
-    float n1 = __fmaf_rn(cn, B.y, __fmaf_rn(sn, B.z, B.x));
-    float n2 = __fmaf_rn(cn, C.x, __fmaf_rn(sn, C.y, B.w));
-    n1 = fabsf(e1) < Kf ? n1 : 0.0f;
-    n2 = fabsf(e2) < Kf ? n2 : 0.0f;
-    const float rp = rcp_approx(__fmul_rn(e1, e2));
-    return __fmaf_rn(__fmaf_rn(n1, e2, __fmul_rn(n2, e1)), rp, acc);
-}
-
-__device__ __forceinline__ float row_taps(const float4* __restrict__ q0, const float4* __restrict__ q1,
-                                          const float4* __restrict__ q2, int q, int qend, float nl, float cn, float sn,
-                                          float Kf)
-{
-    float acc0 = 0.0f, acc1 = 0.0f;
-    for (; q + 1 < qend; q += 2) {
-        acc0 = pair_tap(q0[q], q1[q], q2[q], nl, cn, sn, Kf, acc0);
-        acc1 = pair_tap(q0[q + 1], q1[q + 1], q2[q + 1], nl, cn, sn, Kf, acc1);
+    float cy, sy;
+    if (exact_trig) {               // K = 1: |delta / K| may exceed 1/2
+        sincospif(y, &sy, &cy);
+    } else {
+        cy = cospi_poly(y);
+        sy = sinpi_poly(y);
     }
-    if (q < qend) acc0 = pair_tap(q0[q], q1[q], q2[q], nl, cn, sn, Kf, acc0);
-    return __fadd_rn(acc0, acc1);
+    return make_float4(delta, P, P * cy, P * sy);
 }
 
-__device__ __forceinline__ int lower_bound_s(const int* a, int n, int x)
-{
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (a[mid] < x) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
+// Per-lane constants of the tap slots j = lane + 32 k (k < NR rounds), tap offset o = j - K:
+// C = cos(pi o / K), S = sin(pi o / K), sg = (-1)^o, kp = -sg o, so that the tap at base + o is
+// (P + a C + b S) / fma(sg, delta, kp).  Slots j >= 2K get kp = +inf: their reciprocal is 0 and
+// their read-modify-write leaves the buffer unchanged.
+template <int NR>
+struct TapLanes {
+    float C[NR], S[NR], sg[NR], kp[NR];
+};
 
-__device__ __forceinline__ int upper_bound_s(const int* a, int n, int x)
+template <int NR>
+__device__ __forceinline__ void init_tap_lanes(TapLanes<NR>& L, int lane, int K)
 {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (a[mid] <= x) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-template <int NT>
-__global__ void __launch_bounds__(NT, 3) synth_kernel(LaunchArgs a, const float* __restrict__ pos_hi,
-                                                       const float* __restrict__ pos_lo, const float* __restrict__ gref,
-                                                       float* __restrict__ rir, float* __restrict__ early)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int T = a.tile, K = a.K, Mg = a.margin_i;
-    const SynthSmem L = synth_smem(T, K, Mg);
-    const int NBK = L.nbk;
-    int* sperm = reinterpret_cast<int*>(smem + L.sperm);
-    int* skeys = reinterpret_cast<int*>(smem + L.skeys);
-    int* rowb = reinterpret_cast<int*>(smem + L.rowb);
-    float4* q0 = reinterpret_cast<float4*>(smem + L.q0);
-    float4* q1 = reinterpret_cast<float4*>(smem + L.q1);
-    float4* q2 = reinterpret_cast<float4*>(smem + L.q2);
-    float* outt = reinterpret_cast<float*>(smem + L.outt);
-    float2* tabT = reinterpret_cast<float2*>(smem + L.tabT);
-    __shared__ int s_item, s_lo, s_hi;
-    __shared__ float s_dir[6];
-
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    constexpr int NW = NT / 32;
     const float invK = 1.0f / (float)K;
-    const float Kf = (float)K;
-    const int twoK = 2 * K;
-    const int nrows = T / 32;
-    const int n_items = a.hdr->n_items;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const int j = lane + 32 * k;
+        const int o = j - K;
+        float sn, cs;
+        sincospif((float)o * invK, &sn, &cs);
+        const bool ok = j < 2 * K;
+        L.C[k] = ok ? cs : 0.0f;
+        L.S[k] = ok ? sn : 0.0f;
+        L.sg[k] = ok ? ((o & 1) ? -1.0f : 1.0f) : 0.0f;
+        L.kp[k] = ok ? -L.sg[k] * (float)o : __int_as_float(0x7f800000);
+    }
+}
 
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(&a.hdr->queue, 1);
-        __syncthreads();
-        const int qi = s_item;
-        if (qi >= n_items) break;
-        const int2 it = a.items[qi];
-        const int b = it.x, s = it.y >> 16, tau = it.y & 0xffff;
-        const RoomConst rc = a.room[b];
-        const int T0 = tau * T;
-        const int Lb = rc.len;
-        const int base = T0 - K - Mg - 1;          // sample index of phase-table entry 0
-        const int64_t v0 = rc.vs_off + (int64_t)s * rc.n_vs;
-        const int* bo = a.bin_off + ((int64_t)b * a.S + s) * (a.max_tiles + 1);
-        const int kmin = T0 - K - Mg, kmax = T0 + T + K + Mg;   // keys that can reach the tile
-        const int bin_lo = min(max(0, kmin >= 0 ? kmin / T : 0), rc.ntiles - 1);
-        const int bin_hi = min(rc.ntiles - 1, kmax / T);
-        const int c_lo = bo[bin_lo];
-        int ncand = bo[bin_hi + 1] - c_lo;
-        if (ncand > kStageCap) {
-            if (tid == 0) atomicOr(&a.hdr->status, FRAM_DEV_CAPACITY);
-            ncand = kStageCap;
+// Adds one arrival's taps to the warp's tile buffer.  rel = base - K - T0 is the tile offset of
+// slot 0; buffer index = tile offset + 32.  Rounds that start outside (-32, T) are skipped (they
+// hold no sample of the tile), so every index stays in [1, T + 62].
+template <int NR>
+__device__ __forceinline__ void add_arrival(float* __restrict__ buf, const TapLanes<NR>& L, float4 r, int rel,
+                                            int T, int lane)
+{
+    float* dst = buf + 32 + rel + lane;
+    if (rel > -32 && rel + 32 * (NR - 1) < T) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            const float e = __fmaf_rn(L.sg[k], r.x, L.kp[k]);
+            const float num = __fmaf_rn(L.C[k], r.z, __fmaf_rn(L.S[k], r.w, r.y));
+            dst[32 * k] = __fmaf_rn(num, rcp_approx(e), dst[32 * k]);
         }
-        // ---- stage the candidate images (sorted by key) and the phase table ----
-        for (int j = tid; j < ncand; j += NT) {
-            sperm[j] = a.perm[v0 + c_lo + j];
-            skeys[j] = a.skey[v0 + c_lo + j];
-        }
-        for (int k = tid; k < NBK; k += NT) {
-            int m = (base + k) % twoK;
-            m = m < 0 ? m + twoK : m;
-            float sn_, cs_;
-            sincospif((float)m * invK, &sn_, &cs_);
-            tabT[k] = make_float2(cs_, sn_);
-        }
-        __syncthreads();
-        // ---- the tile's range and each row's range, by binary search on the keys ----
-        if (tid == 0) s_lo = lower_bound_s(skeys, ncand, kmin);
-        if (tid == 1) s_hi = upper_bound_s(skeys, ncand, kmax);
-        if (tid >= 2 && tid < 2 + 2 * nrows) {
-            const int r = (tid - 2) >> 1;
-            const int R0 = T0 + 32 * r;
-            rowb[tid - 2] = (tid & 1) ? upper_bound_s(skeys, ncand, R0 + 31 + K + Mg)
-                                      : lower_bound_s(skeys, ncand, R0 - K - Mg);
-        }
-        __syncthreads();
-        const int slo = s_lo, nst = max(0, s_hi - s_lo);
-        const float log2r = rc.log2r;
-
-        for (int m = 0; m < a.M; ++m) {
-            const DirectConst dc = a.direct[((int64_t)b * a.S + s) * a.M + m];
-            const float* pm = a.mic + 3 * ((size_t)b * a.M + m);
-            const float mx = pm[0], my = pm[1], mz = pm[2];
-            for (int k = tid; k < T; k += NT) outt[k] = 0.0f;
-            const int nchunks = nst > 0 ? (nst + kArrCap - 1) / kArrCap : 1;
-            for (int ch = 0; ch < nchunks; ++ch) {
-                const int c0 = ch * kArrCap;
-                const int nin = max(0, min(kArrCap, nst - c0));
-                // ---- arrival records at their sorted positions ----
-                for (int p = tid; p < nin; p += NT) {
-                    const int i = sperm[slo + c0 + p];
-                    const int64_t v = v0 + i;
-                    const float* ph = pos_hi + 3 * v;
-                    float plx = 0.f, ply = 0.f, plz = 0.f;
-                    if (pos_lo) { plx = pos_lo[3 * v]; ply = pos_lo[3 * v + 1]; plz = pos_lo[3 * v + 2]; }
-                    int nc;
-                    float delta, D;
-                    image_delay(ph[0], ph[1], ph[2], plx, ply, plz, mx, my, mz, a.q2, nc, delta, D);
-                    const float A = exp2f(gref[v] * log2r) * rcp_approx(D);
-                    const int key = nc - base;
-                    float3 c = make_float3(0.f, 0.f, 0.f);
-                    float ncl = (float)(T + 4 * K + 64);              // out of reach: zero weight
-                    if (key >= 0 && key < NBK && D > 0.0f && A == A && fabsf(A) < 3.0e38f) {
-                        if (fabsf(delta) < kTinyDelta) delta = kTinyDelta;
-                        c = arrival_consts(nc, delta, A, tabT[key], invK);
-                        ncl = (float)(nc - T0);
-                    }
-                    put_record(q0, q1, q2, p, ncl, delta, c);
-                }
-                if (tid == 0) {
-                    if (nin & 1) put_record(q0, q1, q2, nin, (float)(T + 4 * K + 64), 0.25f, make_float3(0.f, 0.f, 0.f));
-                    // Direct path of (b, s, m): its constants for the rows within reach.
-                    const int nc = __float2int_rn(dc.t_hi);
-                    float delta = __fadd_rn(__fsub_rn(dc.t_hi, (float)nc), dc.t_lo);
-                    if (fabsf(delta) < kTinyDelta) delta = kTinyDelta;
-                    const int key = nc - base;
-                    float3 c = make_float3(0.f, 0.f, 0.f);
-                    if (ch == 0 && key >= 0 && key < NBK) c = arrival_consts(nc, delta, dc.amp, tabT[key], invK);
-                    s_dir[0] = (float)(nc - T0); s_dir[1] = delta; s_dir[2] = c.x; s_dir[3] = c.y; s_dir[4] = c.z;
-                }
-                __syncthreads();
-                // ---- taps: each warp owns rows of 32 consecutive samples ----
-                const float dnc = s_dir[0], dd = s_dir[1], dP = s_dir[2], da = s_dir[3], db = s_dir[4];
-                for (int row = wid; row < nrows; row += NW) {
-                    const int R0 = T0 + row * 32;
-                    if (R0 >= Lb) break;
-                    const int k0 = row * 32;
-                    const int lo = max(rowb[2 * row] - slo - c0, 0);
-                    const int hi = min(rowb[2 * row + 1] - slo - c0, nin);
-                    const float2 cs = tabT[k0 + lane + K + Mg + 1];
-                    const float nl = (float)(k0 + lane);
-                    float acc = lo < hi ? row_taps(q0, q1, q2, lo >> 1, (hi + 1) >> 1, nl, cs.x, cs.y, Kf) : 0.0f;
-                    if (dP != 0.0f && dnc >= (float)(k0 - K - 1) && dnc <= (float)(k0 + 32 + K)) {
-                        const float e = __fadd_rn(__fsub_rn(dnc, nl), dd);
-                        const float num = __fmaf_rn(cs.x, da, __fmaf_rn(cs.y, db, dP));
-                        if (fabsf(e) < Kf) acc = __fadd_rn(acc, __fmul_rn(num, rcp_approx(e)));
-                    }
-                    outt[k0 + lane] += ((R0 + lane) & 1) ? -acc : acc;
-                }
-                __syncthreads();
-            }
-            // ---- store the tile (and the Eq. 9 early RIR) ----
-            float* dst = rir + rc.rir_off + ((int64_t)s * a.M + m) * Lb;
-            float* dste = early ? early + rc.rir_off + ((int64_t)s * a.M + m) * Lb : nullptr;
-            for (int k = tid; k < T; k += NT) {
-                const int n = T0 + k;
-                if (n < Lb) {
-                    const float h = outt[k];
-                    dst[n] = h;
-                    if (dste) dste[n] = (n >= dc.early_lo && n <= dc.early_hi) ? h : 0.0f;
-                }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            const int s0 = rel + 32 * k;
+            if (s0 > -32 && s0 < T) {
+                const float e = __fmaf_rn(L.sg[k], r.x, L.kp[k]);
+                const float num = __fmaf_rn(L.C[k], r.z, __fmaf_rn(L.S[k], r.w, r.y));
+                dst[32 * k] = __fmaf_rn(num, rcp_approx(e), dst[32 * k]);
             }
         }
-        __syncthreads();
+    }
+}
+
+// Per-warp shared memory (floats): the tile buffer (T + 64: 32 samples of halo on each side),
+// 32 arrival records (float4) and their tile offsets (int).
+__host__ __device__ inline int synth_warp_floats(int T) { return (T + 64) + 4 * 32 + 32; }
+
+// Work unit = (room, source, tile, mic), one warp each, pulled from a counter (the next unit is
+// requested when the current one starts).  Per unit: zero the tile buffer; add the direct path;
+// walk the run of sorted images that can reach the tile 32 at a time -- each lane computes one
+// image's arrival for this mic (the next 32 images' data is fetched meanwhile), the warp compacts
+// the ones that reach the tile and adds them one after another, each lane owning one tap slot;
+// then store the tile (and the Eq. 9 early RIR).  The accumulation order of every sample is fixed
+// by the sorted image order, and no two lanes write one sample in the same step.
+template <int NR>
+__global__ void __launch_bounds__(kSynthThreads, 3) synth_kernel(LaunchArgs a, float* __restrict__ rir,
+                                                                  float* __restrict__ early)
+{
+    extern __shared__ __align__(16) float synth_smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int T = a.tile, K = a.K, M = a.M;
+    float* buf = synth_smem + wid * synth_warp_floats(T);
+    float4* rec = reinterpret_cast<float4*>(buf + T + 64);
+    int* rrel = reinterpret_cast<int*>(rec + 32);
+    TapLanes<NR> L;
+    init_tap_lanes<NR>(L, lane, K);
+    const float invK = 1.0f / (float)K;
+    const bool exact_trig = K < 2;
+    const int64_t n_units = (int64_t)a.hdr->n_items * M;
+    const int reach_lo = 1 - 2 * K;        // rel range of arrivals with a tap in the tile
+    int u = 0;
+    if (lane == 0) u = atomicAdd(&a.hdr->queue, 1);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    while ((int64_t)u < n_units) {
+        int nxt = 0;
+        if (lane == 0) nxt = atomicAdd(&a.hdr->queue, 1);
+        const int qi = u / M, m = u - qi * M;
+        const ItemRec ir = a.irec[qi];
+        const int T0 = ir.T0, Lb = ir.len;
+        const float* pm = a.mic + 3 * ((size_t)ir.b * M + m);
+        const float mx = pm[0], my = pm[1], mz = pm[2];
+        const DirectConst dc = a.direct[((int64_t)ir.b * a.S + ir.s) * M + m];
+        const int64_t v0 = ir.v0;
+        float4 pa = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 pb = make_float2(0.f, 0.f);
+        float am = 0.0f;
+        if (ir.c_lo + lane < ir.c_hi) {
+            pa = a.spa[v0 + ir.c_lo + lane];
+            pb = a.spb[v0 + ir.c_lo + lane];
+            am = a.samp[v0 + ir.c_lo + lane];
+        }
+
+        float4* b4 = reinterpret_cast<float4*>(buf);
+        for (int k = lane; k < (T + 64) / 4; k += 32) b4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncwarp();
+        {   // direct path (uniform across the warp)
+            int nc = __float2int_rn(dc.t_hi);
+            const float delta = __fadd_rn(__fsub_rn(dc.t_hi, (float)nc), dc.t_lo);
+            if (dc.amp > 0.0f) {
+                const float4 r = arrival_record(nc, delta, dc.amp, invK, exact_trig);
+                const int rel = nc - K - T0;
+                if (rel >= reach_lo && rel < T) add_arrival<NR>(buf, L, r, rel, T, lane);
+            }
+            __syncwarp();
+        }
+        for (int c = ir.c_lo; c < ir.c_hi; c += 32) {
+            bool valid = false;
+            float4 rr = make_float4(0.f, 0.f, 0.f, 0.f);
+            int rel = 0;
+            if (c + lane < ir.c_hi) {
+                int nc;
+                float delta, D;
+                image_delay(pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, mx, my, mz, a.q2, nc, delta, D);
+                const float A = am * rcp_approx(D);
+                if (D > 0.0f && A == A && fabsf(A) < 3.0e38f) {
+                    rr = arrival_record(nc, delta, A, invK, exact_trig);
+                    rel = nc - K - T0;
+                    valid = rel >= reach_lo && rel < T;
+                }
+            }
+            if (c + 32 + lane < ir.c_hi) {      // next 32 images, in flight during the taps below
+                pa = a.spa[v0 + c + 32 + lane];
+                pb = a.spb[v0 + c + 32 + lane];
+                am = a.samp[v0 + c + 32 + lane];
+            }
+            const unsigned vb = __ballot_sync(0xffffffffu, valid);
+            if (valid) {
+                const int slot = __popc(vb & ((1u << lane) - 1u));
+                rec[slot] = rr;
+                rrel[slot] = rel;
+            }
+            __syncwarp();
+            const int nv = __popc(vb);
+            for (int q = 0; q < nv; ++q) {
+                add_arrival<NR>(buf, L, rec[q], rrel[q], T, lane);
+                __syncwarp();
+            }
+        }
+        // ---- store the tile (and the Eq. 9 early RIR) ----
+        float* dst = rir + ir.out0 + (int64_t)m * Lb;
+        float* dste = early ? early + ir.out0 + (int64_t)m * Lb : nullptr;
+        for (int k = lane; k < T; k += 32) {
+            const int n = T0 + k;
+            if (n < Lb) {
+                const float h = buf[32 + k];
+                dst[n] = h;
+                if (dste) dste[n] = (n >= dc.early_lo && n <= dc.early_hi) ? h : 0.0f;
+            }
+        }
+        __syncwarp();
+        u = __shfl_sync(0xffffffffu, nxt, 0);
     }
 }
 
@@ -585,12 +582,11 @@ __global__ void __launch_bounds__(NT, 3) synth_kernel(LaunchArgs a, const float*
 
 
 
-int synth_smem_total(int T, int K, int M) { return synth_smem(T, K, M).total; }
+int synth_smem_total(int T) { return (int)sizeof(float) * (kSynthThreads / 32) * synth_warp_floats(T); }
 
 cudaError_t launch_prepare(const LaunchArgs& a, const float* pos_hi, const float* pos_lo, const float* r,
                            cudaStream_t st)
 {
-    (void)pos_lo;
     cudaError_t e = cudaMemsetAsync(a.hdr, 0, sizeof(Header), st);
     if (e != cudaSuccess) return e;
     const int64_t n = std::max<int64_t>((int64_t)a.B, (int64_t)a.B * a.S * a.M);
@@ -605,22 +601,49 @@ cudaError_t launch_prepare(const LaunchArgs& a, const float* pos_hi, const float
         const int sm = (int)(sizeof(int) * 2 * (size_t)bin_warp_ints(a.max_tiles, a.tile));
         int per_sm = 0;
         if ((e = kernel_residency((const void*)bin_images, 64, sm, &per_sm)) != cudaSuccess) return e;
-        bin_images<<<(unsigned)((segs + 1) / 2), 64, sm, st>>>(a, pos_hi);
+        bin_images<<<(unsigned)((segs + 1) / 2), 64, sm, st>>>(a, pos_hi, pos_lo);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const int64_t max_items = segs * a.max_tiles;
+        item_ranges<<<(unsigned)((max_items + 255) / 256), 256, 0, st>>>(a, max_items);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
+template <int NR>
+static cudaError_t launch_synth_nr(const LaunchArgs& a, float* rir, float* early, cudaStream_t st)
+{
+    const int smem = synth_smem_total(a.tile);
+    int per_sm = 0;
+    cudaError_t e = kernel_residency((const void*)synth_kernel<NR>, kSynthThreads, smem, &per_sm);
+    if (e != cudaSuccess) return e;
+    const int grid = device_sm_count() * per_sm;
+    synth_kernel<NR><<<grid, kSynthThreads, smem, st>>>(a, rir, early);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_synthesize(const LaunchArgs& a, const float* pos_hi, const float* pos_lo, const float* g,
                               float* rir, float* early, cudaStream_t st)
 {
-    const int smem = synth_smem(a.tile, a.K, a.margin_i).total;
-    int per_sm = 0;
-    cudaError_t e = kernel_residency((const void*)synth_kernel<kSynthThreads>, kSynthThreads, smem, &per_sm);
-    if (e != cudaSuccess) return e;
-    const int grid = device_sm_count() * per_sm;
-    synth_kernel<kSynthThreads><<<grid, kSynthThreads, smem, st>>>(a, pos_hi, pos_lo, g, rir, early);
-    return cudaGetLastError();
+    (void)pos_hi;
+    (void)pos_lo;   // the kernel reads the sorted copies the preparation made
+    const int64_t segs = (int64_t)a.B * a.S;
+    if (segs > 0) {
+        amp_gather<<<(unsigned)segs, 256, 0, st>>>(a, g);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    switch ((2 * a.K + 31) / 32) {
+    case 1: return launch_synth_nr<1>(a, rir, early, st);
+    case 2: return launch_synth_nr<2>(a, rir, early, st);
+    case 3: return launch_synth_nr<3>(a, rir, early, st);
+    case 4: return launch_synth_nr<4>(a, rir, early, st);
+    case 5: return launch_synth_nr<5>(a, rir, early, st);
+    case 6: return launch_synth_nr<6>(a, rir, early, st);
+    case 7: return launch_synth_nr<7>(a, rir, early, st);
+    case 8: return launch_synth_nr<8>(a, rir, early, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace fram

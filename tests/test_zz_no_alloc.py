@@ -31,7 +31,8 @@ def _call_noalloc(ds, vs, rir, early):
 
 
 def test_noalloc_matches_workspace_entry_point_on_two_calls():
-    sc = scenes.batch_256(0)
+    # The first 128 rooms of the 256-room batch: their workspace fits the 16 MiB scratch.
+    sc = scenes.batch_256(0).subset(range(128))
     params = api.Params(fs=sc.fs, half_len=sc.half_len)
     ds = api.DeviceScene(sc, params)
     assert ds.ws_bytes <= 16 << 20
