@@ -150,11 +150,14 @@ int fram_sample(const fram_scene* scene, const fram_params* p, uint64_t seed, co
  *   h[n] = sum over arrivals j with |n - t_j| < K of  A_j sinc(n - t_j) (1 + cos(pi (n - t_j)/K))/2
  * where the arrivals are the direct path (A = 1/D_{0,m}, t = D_{0,m} fs/c0) and every image
  * (A = r_b^{g_i} / D_{i,m}, t = D_{i,m} fs/c0, D_{i,m} = |p_i - mic_m|), sinc(x) = sin(pi x)/(pi x).
- * Taps outside [0, L_b) are dropped.  Sums are accumulated in float32 in a fixed order
- * (arrivals sorted by delay, ties by image index), so results are bit-reproducible.
+ * Taps outside [0, L_b) are dropped.  Sums are accumulated in float32 in an order fixed by the
+ * inputs and the tile length (direct path first, then the images by delay to the array centre,
+ * ties by image index), so results are bit-reproducible run to run; two tile lengths agree to
+ * float32 rounding.
  * Inputs: image positions vs_pos_hi [N,3] and vs_pos_lo [N,3] (nullable = zero low parts,
  * i.e. plain float32 positions), reflection counts vs_g [N], coefficients r [B].
- * Outputs: rir [rir_total]; early [rir_total] (nullable) receives h_e of Eq. 9.
+ * Outputs: rir [rir_total]; early [rir_total] (nullable) receives h_e of Eq. 9.  Both must be
+ * 4-byte aligned (FRAM_EINVAL otherwise).
  */
 int fram_synthesize(const fram_scene* scene, const fram_params* p,
                     const float* vs_pos_hi, const float* vs_pos_lo, const float* vs_g, const float* r,

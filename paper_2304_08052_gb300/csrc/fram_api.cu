@@ -331,6 +331,8 @@ int fram_synthesize_prepared(const fram_scene* scene, const fram_params* p, cons
     int rc = common_checks(scene, p, vs_pos_hi, vs_g, r, workspace, workspace_bytes, &w);
     if (rc != FRAM_OK) return rc;
     if (scene->rir_total > 0 && !rir) return fail(FRAM_EINVAL, "rir must not be null");
+    if ((reinterpret_cast<uintptr_t>(rir) | reinterpret_cast<uintptr_t>(early)) & 3)
+        return fail(FRAM_EINVAL, "rir and early must be 4-byte aligned");
     if (scene->B == 0) return FRAM_OK;
     const LaunchArgs a = make_args(scene, p, w, workspace);
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -3,17 +3,23 @@
 //
 // Ownership instead of scattering: every image belongs to exactly one (room, source, tile)
 // work item -- the tile its binning key (delay to the array centre) falls in -- and the
-// direct path of a (room, source) belongs to the tile of the source's key.  A persistent CTA
-// takes an item, and for each mic stages the upstream gradient
+// direct path of a (room, source) belongs to the tile of the source's key.  A persistent warp
+// takes an item and walks its images in passes of up to 128 (one image per lane, four chunks);
+// for each mic it stages the upstream gradient
 //   G[n] = dL/dh[n] + [n in Eq. 9 window] dL/dh_e[n]
-// over the tile plus a halo of 2K + margin samples in shared memory; each thread then owns one
-// image, recomputes its arrival (float-pair delay, amplitude) and gathers its 2K+1 taps:
-//   dL/dA = sum_k G[n_c + k] s(x) w(x),   dL/dt = -A sum_k G[n_c + k] (s'(x) w(x) + s(x) w'(x)),
-// with x = k - delta, s = sinc, s'(x) = (cos(pi x) - s(x)) / x (a Taylor series on the centre
-// tap, where the difference cancels), w = (1 + cos(pi x/K))/2, w' = -(pi/2K) sin(pi x/K).
-// The chain rule gives dL/dD = dL/dt fs/c0 - dL/dA A/D and dD/dp = (p - mic)/D.
-// Image gradients are summed over mics in mic order inside the owning thread; mic, source and
-// r gradients are reduced per item in a fixed tree and then per room in item order, so the
+// over the tile plus a halo of K + margin samples in its own shared memory, and each lane
+// recomputes its image's arrival (float-pair delay, amplitude) and gathers the arrival's 2K taps
+// (the support |n - t| < K, see the synthesis kernel for the re-based split t = base + delta):
+//   S1 = sum G tap,   S2 = sum G dtap/dt,   tap = sigma (P + a C + b S) / (delta - o)
+// with per-tap constants C = cos(pi o/K), S = sin(pi o/K), sigma = (-1)^o, and per-arrival
+// P = sin(pi delta)/(2 pi), a = P cos(pi delta/K), b = P sin(pi delta/K) and their delta
+// derivatives P', a', b', so that dtap/dt = (dnum - sigma tap) / e with e = sigma (delta - o).
+// That quotient cancels on the tap nearest to t (|n - t| <= 1/2), which instead takes
+// d/dt [sinc w] from a Taylor series of sinc'.  With A = r^g / D the chain rule gives
+//   dL/dA = S1,  dL/dt = A S2,  dL/dD = A S2 fs/c0 - S1 A / D,  dD/dp = (p - mic)/D,
+//   dL/dr = S1 A g / r.
+// Image gradients are summed over mics in mic order by the owning lane; mic, source and r
+// gradients are reduced per item in a fixed warp tree and then per room in item order, so the
 // result does not depend on scheduling.
 #include <algorithm>
 #include <cmath>
@@ -90,101 +96,140 @@ constexpr TrigTab make_trig_tab()
 __constant__ TrigTab c_trig40 = make_trig_tab<40>();
 __constant__ TrigTab c_trig63 = make_trig_tab<63>();
 
-// Taps of one arrival against staged G (Gs points at G[n_c - K]): gA = sum G tap, gT = sum G tap'
-// with tap(x) = sinc(x) (1 + cos(pi x/K))/2, x = k - delta.  With W2 = 1 + cos(pi x/K):
-//   2 tap = s W2,   2 tap' = s' W2 - (pi/K) s sin(pi x/K),
-//   s = -(-1)^k sin(pi delta)/(pi x),  s' = ((-1)^k cos(pi delta) - s)/x.
-// The loop is fully unrolled and the constant tables are named directly, so their entries are
-// read as constant-bank operands of the FMAs.
-template <int KT>
-__device__ __forceinline__ void gather_taps_ct(const float* __restrict__ Gs, float delta, float& gA, float& gT)
-{
-    const float sd = sinpi_poly(delta), cd = cospi_poly(delta);
-    const float y = delta * (1.0f / (float)KT);
-    const float sk = sinpi_poly(y), ck = cospi_poly(y);
-    const float spi = sd * kInvPi;                     // sin(pi delta) / pi
-    const float spic = spi * (-kPi / (float)KT);       // -(pi/K) sin(pi delta) / pi
-    float a = 0.f, t = 0.f;
-#pragma unroll
-    for (int kk = 0; kk <= 2 * KT; ++kk) {
-        const int k = kk - KT;
-        const float Ck = (KT == 40) ? c_trig40.c[kk] : c_trig63.c[kk];
-        const float Sk = (KT == 40) ? c_trig40.s[kk] : c_trig63.s[kk];
-        const float G = Gs[kk];
-        const float x = __fsub_rn((float)k, delta);
-        const float r = rcp_approx(x);
-        const bool even = (k & 1) == 0;
-        const float s = (even ? -spi : spi) * r;
-        const float sc = (even ? -spic : spic) * r;
-        const float sp = (k == 0) ? dsinc_small(x) : ((even ? cd : -cd) - s) * r;
-        const float W2 = __fmaf_rn(Ck, ck, __fmaf_rn(Sk, sk, 1.0f));
-        const float sw = __fmaf_rn(Sk, ck, -(Ck * sk));
-        float tap2 = s * W2;
-        float dtap2 = __fmaf_rn(sp, W2, sc * sw);
-        if ((kk == 0 || kk == 2 * KT) && !(fabsf(x) < (float)KT)) { tap2 = 0.f; dtap2 = 0.f; }
-        a = __fmaf_rn(G, tap2, a);
-        t = __fmaf_rn(G, dtap2, t);
-    }
-    gA = 0.5f * a;
-    gT = 0.5f * t;
-}
+constexpr float kShiftMin = 2.44140625e-4f;   // 2^-12: arrivals re-based as in the synthesis
+constexpr float kTwoPiInv = 0.15915494309189535f;
+constexpr int kBwdThreads = 128;
+constexpr int kBwdChunks = 4;                   // images per lane and pass
 
-// Any K: the same taps with the trigonometric table in shared memory.
-__device__ __forceinline__ void gather_taps_rt(const float* __restrict__ Gs, int K, float delta, const float2* tab,
-                                               float& gA, float& gT)
-{
-    const float sd = sinpi_poly(delta), cd = cospi_poly(delta);
-    const float y = delta / (float)K;
-    const float sk = sinpi_poly(y), ck = cospi_poly(y);
-    const float spi = sd * kInvPi;
-    const float spic = spi * (-kPi / (float)K);
-    float a = 0.f, t = 0.f;
-    for (int kk = 0; kk <= 2 * K; ++kk) {
-        const int k = kk - K;
-        const float G = Gs[kk];
-        const float x = __fsub_rn((float)k, delta);
-        const float r = rcp_approx(x);
-        const bool even = (k & 1) == 0;
-        const float s = (even ? -spi : spi) * r;
-        const float sc = (even ? -spic : spic) * r;
-        const float sp = (k == 0) ? dsinc_small(x) : ((even ? cd : -cd) - s) * r;
-        const float2 cs = tab[kk];
-        const float W2 = __fmaf_rn(cs.x, ck, __fmaf_rn(cs.y, sk, 1.0f));
-        const float sw = __fmaf_rn(cs.y, ck, -(cs.x * sk));
-        float tap2 = s * W2;
-        float dtap2 = __fmaf_rn(sp, W2, sc * sw);
-        if ((kk == 0 || kk == 2 * K) && !(fabsf(x) < (float)K)) { tap2 = 0.f; dtap2 = 0.f; }
-        a = __fmaf_rn(G, tap2, a);
-        t = __fmaf_rn(G, dtap2, t);
-    }
-    gA = 0.5f * a;
-    gT = 0.5f * t;
-}
-
-template <int KT>
-__device__ __forceinline__ void gather_taps(const float* __restrict__ Gs, int K, float delta, const float2* tab,
-                                            float& gA, float& gT)
-{
-    if constexpr (KT > 0) gather_taps_ct<KT>(Gs, delta, gA, gT);
-    else gather_taps_rt(Gs, K, delta, tab, gA, gT);
-}
-
-struct BwdSmemPlan {
-    int gs, tab, red, total, glen;
+// Per-arrival constants of the adjoint, unit amplitude.  d = delta of the re-based split,
+// (P, a, b) and their delta derivatives (Pp, ap, bp), dnear = d/dt of the tap nearest to t,
+// shifted = the arrival was re-based to n_c + 1.
+struct ArrB {
+    float d, P, a, b, Pp, ap, bp, dnear;
+    bool shifted;
 };
 
-// Two staging buffers of the upstream gradient, the table for a run-time K, and the per-warp
-// mic partials.
-__host__ __device__ inline BwdSmemPlan bwd_smem(int T, int K, int margin_i, int M, int nwarps)
+__device__ __forceinline__ ArrB arrival_bwd(int& nc, float delta, float invK, bool exact_trig)
 {
-    BwdSmemPlan p;
-    p.glen = T + 4 * K + 2 * margin_i + 8;
-    p.gs = 0;
-    p.tab = ((8 * p.glen) + 15) & ~15;
-    p.red = p.tab + (((8 * (2 * K + 1)) + 15) & ~15);
-    p.total = p.red + 4 * 3 * M * nwarps;
-    return p;
+    ArrB r;
+    if (fabsf(delta) < kTinyDelta) delta = kTinyDelta;
+    const float sd = sinpi_poly(delta), cd = cospi_poly(delta);   // at the original delta
+    float su = sd, cu = cd;
+    r.shifted = delta > kShiftMin;
+    if (r.shifted) {
+        const float d1 = __fsub_rn(delta, 1.0f);
+        delta = __fadd_rn(d1, 1.0f);                              // the delta the taps use
+        const float s1 = sinpi_poly(delta), c1 = cospi_poly(delta);
+        su = -s1; cu = -c1;
+        r.d = d1;
+        nc += 1;
+    } else {
+        r.d = delta;
+    }
+    const float piK = kPi * invK;
+    float cy, sy, cn, sn;
+    if (exact_trig) {
+        sincospif(r.d * invK, &sy, &cy);
+        sincospif(delta * invK, &sn, &cn);
+    } else {
+        cy = cospi_poly(r.d * invK); sy = sinpi_poly(r.d * invK);
+        cn = cospi_poly(delta * invK); sn = sinpi_poly(delta * invK);
+    }
+    r.P = su * kTwoPiInv;
+    r.Pp = 0.5f * cu;
+    r.a = r.P * cy;
+    r.b = r.P * sy;
+    r.ap = __fmaf_rn(r.Pp, cy, -r.P * piK * sy);
+    r.bp = __fmaf_rn(r.Pp, sy, r.P * piK * cy);
+    // Nearest tap: x = n - t = -delta (delta of the original split), tap = sinc(x) w(x), both
+    // even, so dtap/dt = sinc'(delta) w(delta) + sinc(delta) w'(delta).
+    const float sinc = (r.shifted ? sinpi_poly(delta) : sd) * kInvPi / delta;
+    const float w = 0.5f * (1.0f + cn);
+    const float wp = -0.5f * piK * sn;
+    r.dnear = __fmaf_rn(dsinc_small(delta), w, sinc * wp);
+    return r;
 }
+
+// S1 += sum_j G[j] tap_j, S2 += sum_j G[j] dtap_j/dt over the 2K slots j = o + K of one arrival;
+// Gs points at G[base - K].  Compile-time K: every per-slot constant is an FMA operand.
+template <int KT>
+__device__ __forceinline__ void gather_taps_ct(const float* __restrict__ Gs, const ArrB& r, float& S1, float& S2)
+{
+    float s1a = 0.f, s1b = 0.f, s2a = 0.f, s2b = 0.f;
+#pragma unroll
+    for (int j = 0; j < 2 * KT; ++j) {
+        const int o = j - KT;
+        const float sg = (o & 1) ? -1.0f : 1.0f;
+        const float C = (KT == 40) ? c_trig40.c[j] : c_trig63.c[j];
+        const float S = (KT == 40) ? c_trig40.s[j] : c_trig63.s[j];
+        const float G = Gs[j];
+        const float e = __fmaf_rn(sg, r.d, -sg * (float)o);
+        const float rc = rcp_approx(e);
+        const float num = __fmaf_rn(C, r.a, __fmaf_rn(S, r.b, r.P));
+        const float dnum = __fmaf_rn(C, r.ap, __fmaf_rn(S, r.bp, r.Pp));
+        const float y = G * rc;
+        const float t = y * num;
+        float& s1 = (j & 1) ? s1b : s1a;
+        float& s2 = (j & 1) ? s2b : s2a;
+        s1 += t;
+        if (o == 0 || o == -1) {
+            const float dg = (dnum - sg * (num * rc)) * rc;
+            const bool near = (o == 0) != r.shifted;
+            s2 = __fmaf_rn(G, near ? r.dnear : dg, s2);
+        } else {
+            s2 = __fmaf_rn(y, dnum, s2);
+            s2 = __fmaf_rn(-sg * t, rc, s2);
+        }
+    }
+    S1 = s1a + s1b;
+    S2 = s2a + s2b;
+}
+
+// Any K: the same taps, cos/sin(pi o/K) from a shared table.
+__device__ __forceinline__ void gather_taps_rt(const float* __restrict__ Gs, int K, const ArrB& r,
+                                               const float2* __restrict__ tab, float& S1, float& S2)
+{
+    float s1 = 0.f, s2 = 0.f;
+    for (int j = 0; j < 2 * K; ++j) {
+        const int o = j - K;
+        const float sg = (o & 1) ? -1.0f : 1.0f;
+        const float2 cs = tab[j];
+        const float G = Gs[j];
+        const float e = __fmaf_rn(sg, r.d, -sg * (float)o);
+        const float rc = rcp_approx(e);
+        const float num = __fmaf_rn(cs.x, r.a, __fmaf_rn(cs.y, r.b, r.P));
+        const float dnum = __fmaf_rn(cs.x, r.ap, __fmaf_rn(cs.y, r.bp, r.Pp));
+        s1 = __fmaf_rn(G * rc, num, s1);
+        const bool near = (o == 0 && !r.shifted) || (o == -1 && r.shifted);
+        const float dg = (dnum - sg * (num * rc)) * rc;
+        s2 = __fmaf_rn(G, near ? r.dnear : dg, s2);
+    }
+    S1 = s1;
+    S2 = s2;
+}
+
+template <int KT>
+__device__ __forceinline__ void gather_taps(const float* __restrict__ Gs, int K, const ArrB& r,
+                                            const float2* __restrict__ tab, float& S1, float& S2)
+{
+    if constexpr (KT > 0) gather_taps_ct<KT>(Gs, r, S1, S2);
+    else gather_taps_rt(Gs, K, r, tab, S1, S2);
+}
+
+// Per-warp shared memory (floats): two staging buffers of the upstream gradient (each covers a
+// key span of up to smax samples plus a halo of K + margin + 2 on both sides) and the
+// image-gradient accumulators of one pass ([chunk][xyz][lane]).
+__host__ __device__ inline int bwd_span(int T) { return T < 1024 ? T : 1024; }
+__host__ __device__ inline int bwd_glen(int T, int K, int margin_i)
+{
+    const int sp = bwd_span(T) > 2 * margin_i + 2 ? bwd_span(T) : 2 * margin_i + 2;   // direct-only span
+    return (sp + 2 * K + 2 * margin_i + 6 + 3) & ~3;
+}
+__host__ __device__ inline int bwd_warp_floats(int T, int K, int margin_i)
+{
+    return 2 * bwd_glen(T, K, margin_i) + kBwdChunks * 3 * 32;
+}
+__host__ __device__ inline int bwd_tab_floats(int K) { return (4 * K + 3) & ~3; }
 
 __device__ __forceinline__ float warp_sum(float x)
 {
@@ -193,166 +238,289 @@ __device__ __forceinline__ float warp_sum(float x)
     return x;
 }
 
-template <int NT, int KT>
-__global__ void __launch_bounds__(NT, 4) bwd_kernel(LaunchArgs a, int margin_i, const float* __restrict__ pos_hi,
-                                                     const float* __restrict__ pos_lo, const float* __restrict__ gref,
-                                                     const float* __restrict__ grad_rir,
-                                                     const float* __restrict__ grad_early, float* __restrict__ grad_vs)
+// Image geometry for mic (mx, my, mz): delay split n_c + delta, distance D and the exact
+// difference p - mic (as hi + lo), from the float-pair image position.
+__device__ __forceinline__ void image_geom(float4 pa, float2 pb, float mx, float my, float mz, f2 q2, int& nc,
+                                           float& delta, float& D, float& ux, float& uy, float& uz)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int NW = NT / 32;
-    const int T = a.tile, K = a.K, M = a.M;
-    const BwdSmemPlan P = bwd_smem(T, K, margin_i, M, NW);
-    float* Gs0 = reinterpret_cast<float*>(smem + P.gs);
-    float2* tab = reinterpret_cast<float2*>(smem + P.tab);
-    float* red = reinterpret_cast<float*>(smem + P.red);   // [NW][M][3]
-    __shared__ int s_item;
-    __shared__ float s_r[NW];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (KT == 0)
-        for (int j = tid; j <= 2 * K; j += NT) {
+    f2 dx = two_sum(pa.x, -mx); dx.lo = __fadd_rn(dx.lo, pa.w);
+    f2 dy = two_sum(pa.y, -my); dy.lo = __fadd_rn(dy.lo, pb.x);
+    f2 dz = two_sum(pa.z, -mz); dz.lo = __fadd_rn(dz.lo, pb.y);
+    f2 sx = two_prod(dx.hi, dx.hi); sx.lo = __fmaf_rn(__fmul_rn(2.0f, dx.hi), dx.lo, sx.lo);
+    f2 sy = two_prod(dy.hi, dy.hi); sy.lo = __fmaf_rn(__fmul_rn(2.0f, dy.hi), dy.lo, sy.lo);
+    f2 sz = two_prod(dz.hi, dz.hi); sz.lo = __fmaf_rn(__fmul_rn(2.0f, dz.hi), dz.lo, sz.lo);
+    f2 ss = f2_add(f2_add(fast_two_sum(sx.hi, sx.lo), fast_two_sum(sy.hi, sy.lo)), fast_two_sum(sz.hi, sz.lo));
+    f2 Dp = f2_sqrt_fast(ss);
+    f2 t = f2_mul(Dp, q2);
+    nc = __float2int_rn(t.hi);
+    delta = __fadd_rn(__fsub_rn(t.hi, (float)nc), t.lo);
+    D = Dp.hi;
+    ux = dx.hi + dx.lo; uy = dy.hi + dy.lo; uz = dz.hi + dz.lo;
+}
+
+// (sorted g) for the adjoint, into the sorted-amplitude scratch.
+__global__ void __launch_bounds__(256) g_gather(LaunchArgs a, const float* __restrict__ g)
+{
+    const int64_t seg = blockIdx.x;
+    const int b = (int)(seg / a.S), s = (int)(seg % a.S);
+    const RoomConst rc = a.room[b];
+    if (rc.ntiles < 1) return;
+    const int64_t v0 = rc.vs_off + (int64_t)s * rc.n_vs;
+    for (int p = threadIdx.x; p < rc.n_vs; p += blockDim.x) a.samp[v0 + p] = g[v0 + a.perm[v0 + p]];
+}
+
+// Asynchronous 4-byte global -> shared copy; a zero source size fills zeros and reads nothing.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// One pass of an item: sorted positions [p0, p1) (at most 32 kBwdChunks images whose keys span
+// less than bwd_span samples); the gradient is staged over [gb, gb + gl).
+struct BwdPass {
+    int p0, p1, gb, gl;
+};
+
+__device__ __forceinline__ BwdPass next_pass(const LaunchArgs& a, int64_t v0, int p0, int o_hi, int span, int K,
+                                             int Mg, int lane)
+{
+    BwdPass P;
+    P.p0 = p0;
+    const int k0 = a.skey[v0 + p0];
+    int p1 = min(p0 + 32 * kBwdChunks, o_hi);
+    for (int c = 0; c < kBwdChunks; ++c) {
+        const int p = p0 + 32 * c + lane;
+        const bool stop = p < p1 && a.skey[v0 + p] >= k0 + span;
+        const unsigned bal = __ballot_sync(0xffffffffu, stop);
+        if (bal) { p1 = p0 + 32 * c + __ffs(bal) - 1; break; }
+    }
+    P.p1 = p1;
+    const int k1 = a.skey[v0 + p1 - 1];
+    P.gb = k0 - K - Mg - 2;
+    P.gl = k1 - k0 + 2 * K + 2 * Mg + 6;
+    return P;
+}
+
+// Stages G = dL/dh (+ Eq. 9 mask * dL/dh_e) of channel ch0 over [gb, gb + gl) into Gs: with only
+// dL/dh given, as asynchronous copies (committed as one group); otherwise synchronously.
+__device__ __forceinline__ void stage_g(float* Gs, const float* grad_rir, const float* grad_early, int64_t ch0,
+                                        int gb, int gl, int Lb, int elo, int ehi, int lane)
+{
+    if (grad_rir && !grad_early) {
+        const float* row = grad_rir + ch0;
+        for (int j = lane; j < gl; j += 32) {
+            const int n = gb + j;
+            const bool ok = n >= 0 && n < Lb;
+            cp_async4(Gs + j, ok ? row + n : row, ok);
+        }
+        cp_async_commit();
+    } else {
+        for (int j = lane; j < gl; j += 32) {
+            const int n = gb + j;
+            float Gv = 0.f;
+            if (n >= 0 && n < Lb) {
+                if (grad_rir) Gv = grad_rir[ch0 + n];
+                if (grad_early && n >= elo && n <= ehi) Gv += grad_early[ch0 + n];
+            }
+            Gs[j] = Gv;
+        }
+    }
+}
+
+template <int KT>
+__global__ void __launch_bounds__(kBwdThreads, 4) bwd_kernel(LaunchArgs a, const float* __restrict__ grad_rir,
+                                                             const float* __restrict__ grad_early,
+                                                             float* __restrict__ grad_vs)
+{
+    extern __shared__ __align__(16) float bwd_smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int T = a.tile, K = a.K, M = a.M, Mg = a.margin_i;
+    const int span = bwd_span(T);
+    const int glen = bwd_glen(T, K, Mg);
+    const int tabf = (KT == 0) ? bwd_tab_floats(K) : 0;
+    float2* tab = reinterpret_cast<float2*>(bwd_smem);
+    float* Gbuf = bwd_smem + tabf + wid * bwd_warp_floats(T, K, Mg);
+    float* gv = Gbuf + 2 * glen;
+    if (KT == 0) {
+        for (int j = threadIdx.x; j < 2 * K; j += blockDim.x) {
             float sn, cs;
             sincospif((float)(j - K) / (float)K, &sn, &cs);
             tab[j] = make_float2(cs, sn);
         }
-    const int n_items = a.hdr->n_items;
-    const float qf = a.q;
-    __syncthreads();
-
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(&a.hdr->queue_bwd, 1);
         __syncthreads();
-        const int qi = s_item;
-        if (qi >= n_items) break;
+    }
+    const float invK = 1.0f / (float)K;
+    const bool exact_trig = K < 2;
+    const float qf = a.q;
+    const int n_items = a.hdr->n_items;
+    int qi = 0;
+    if (lane == 0) qi = atomicAdd(&a.hdr->queue_bwd, 1);
+    qi = __shfl_sync(0xffffffffu, qi, 0);
+    while (qi < n_items) {
+        int nxt = 0;
+        if (lane == 0) nxt = atomicAdd(&a.hdr->queue_bwd, 1);
         const int2 it = a.items[qi];
         const int b = it.x, s = it.y >> 16, tau = it.y & 0xffff;
         const RoomConst rc = a.room[b];
-        const int T0 = tau * T;
         const int Lb = rc.len;
         const int64_t v0 = rc.vs_off + (int64_t)s * rc.n_vs;
         const int* bo = a.bin_off + ((int64_t)b * a.S + s) * (a.max_tiles + 1);
         const int o_lo = bo[tau], o_hi = bo[tau + 1];
-        const int gbase = T0 - 2 * K - margin_i - 4;
         const bool own_direct = a.src_tile[(int64_t)b * a.S + s] == tau;
         const int64_t chan0 = rc.rir_off + (int64_t)s * M * Lb;
-        for (int k = lane; k < 3 * M; k += 32) red[(wid * M) * 3 + k] = 0.f;
-        __syncwarp();
-        float pr = 0.f;                          // this thread's share of dL/dr
-        float dsx = 0.f, dsy = 0.f, dsz = 0.f;   // direct-path source gradient (thread 0)
-        const int nown = o_hi - o_lo;
-        const int nch = nown > 0 ? (nown + NT - 1) / NT : 1;
-        int iter = 0;
-        for (int ch = 0; ch < nch; ++ch) {
-            const int slot = ch * NT + tid;
-            const bool has = slot < nown;
-            int64_t v = 0;
-            float phx = 0, phy = 0, phz = 0, plx = 0, ply = 0, plz = 0, gg = 0;
-            if (has) {
-                v = v0 + a.perm[v0 + o_lo + slot];
-                phx = pos_hi[3 * v]; phy = pos_hi[3 * v + 1]; phz = pos_hi[3 * v + 2];
-                if (pos_lo) { plx = pos_lo[3 * v]; ply = pos_lo[3 * v + 1]; plz = pos_lo[3 * v + 2]; }
-                gg = gref[v];
-            }
-            const float A_g = has ? exp2f(gg * rc.log2r) : 0.f;   // r^g
-            float gvx = 0.f, gvy = 0.f, gvz = 0.f;
-            for (int m = 0; m < M; ++m, ++iter) {
-                const DirectConst dc = a.direct[((int64_t)b * a.S + s) * M + m];
-                const int64_t ch0 = chan0 + (int64_t)m * Lb;
-                float* Gs = Gs0 + (iter & 1) * P.glen;
-                for (int j = tid; j < P.glen; j += NT) {
-                    const int n = gbase + j;
-                    float Gv = 0.f;
-                    if (n >= 0 && n < Lb) {
-                        if (grad_rir) Gv = grad_rir[ch0 + n];
-                        if (grad_early && n >= dc.early_lo && n <= dc.early_hi) Gv += grad_early[ch0 + n];
+        const DirectConst* dcs = a.direct + ((int64_t)b * a.S + s) * M;
+        float rpart = 0.f, dsx = 0.f, dsy = 0.f, dsz = 0.f;
+        float* pmic = a.part_mic + (int64_t)qi * 3 * M;
+        if (o_hi <= o_lo && !own_direct) {     // nothing owned: zero partials, no staging
+            for (int k = lane; k < 3 * M; k += 32) pmic[k] = 0.f;
+        } else {
+            // Passes over the images; then, if some mic's direct path fell outside every pass's
+            // staged span, one pass around the direct path alone.
+            const uint64_t dall = (M >= 64) ? ~0ull : ((1ull << M) - 1ull);
+            uint64_t dmask = own_direct ? 0ull : dall;   // lane 0: mics whose direct path is added
+            const int kd = (int)floorf(dcs[0].t_hi);
+            const BwdPass Pdir{o_hi, o_hi, kd - K - 2 * Mg - 2, 2 * K + 4 * Mg + 8};
+            bool direct_only = o_hi <= o_lo;
+            BwdPass P = direct_only ? Pdir : next_pass(a, v0, o_lo, o_hi, span, K, Mg, lane);
+            int stage = 0;
+            __syncwarp();
+            stage_g(Gbuf, grad_rir, grad_early, chan0, P.gb, P.gl, Lb, dcs[0].early_lo, dcs[0].early_hi, lane);
+            for (bool first = true;; first = false) {
+                const int nch = (P.p1 - P.p0 + 31) / 32;
+                for (int k = 0; k < nch * 3; ++k) gv[k * 32 + lane] = 0.f;
+                BwdPass Pn = P;
+                bool more = false, next_direct_only = false;
+                for (int m = 0; m < M; ++m, ++stage) {
+                    float* Gs = Gbuf + (stage & 1) * glen;
+                    cp_async_wait_all();
+                    __syncwarp();
+                    // Prefetch the next stage: mic m + 1 of this pass, or mic 0 of the next pass.
+                    int mn = m + 1;
+                    if (m + 1 == M) {
+                        mn = 0;
+                        if (!direct_only && P.p1 < o_hi) {
+                            Pn = next_pass(a, v0, P.p1, o_hi, span, K, Mg, lane);
+                            more = true;
+                        }
                     }
-                    Gs[j] = Gv;
-                }
-                __syncthreads();
-                const float* pm = a.mic + 3 * ((size_t)b * M + m);
-                const float mx = pm[0], my = pm[1], mz = pm[2];
-                float mpx = 0.f, mpy = 0.f, mpz = 0.f;
-                if (has) {
-                    f2 dx = two_sum(phx, -mx); dx.lo = __fadd_rn(dx.lo, plx);
-                    f2 dy = two_sum(phy, -my); dy.lo = __fadd_rn(dy.lo, ply);
-                    f2 dz = two_sum(phz, -mz); dz.lo = __fadd_rn(dz.lo, plz);
-                    f2 sx = two_prod(dx.hi, dx.hi); sx.lo = __fmaf_rn(__fmul_rn(2.0f, dx.hi), dx.lo, sx.lo);
-                    f2 sy = two_prod(dy.hi, dy.hi); sy.lo = __fmaf_rn(__fmul_rn(2.0f, dy.hi), dy.lo, sy.lo);
-                    f2 sz = two_prod(dz.hi, dz.hi); sz.lo = __fmaf_rn(__fmul_rn(2.0f, dz.hi), dz.lo, sz.lo);
-                    f2 ss = f2_add(f2_add(fast_two_sum(sx.hi, sx.lo), fast_two_sum(sy.hi, sy.lo)),
-                                   fast_two_sum(sz.hi, sz.lo));
-                    f2 D = f2_sqrt_fast(ss);
-                    f2 t = f2_mul(D, a.q2);
-                    const int nc = __float2int_rn(t.hi);
-                    float delta = __fadd_rn(__fsub_rn(t.hi, (float)nc), t.lo);
-                    if (fabsf(delta) < kTinyDelta) delta = kTinyDelta;
-                    const float invD = rcp_approx(D.hi);
-                    const float A = A_g * invD;
-                    const int j0 = nc - K - gbase;
-                    if ((nc + K >= 0) && (nc - K < Lb)) {
-                        if (j0 >= 0 && j0 + 2 * K < P.glen) {
-                            float gA, gT;
-                            gather_taps<KT>(Gs + j0, K, delta, tab, gA, gT);
-                            const float dLdD = __fmaf_rn(-A * gT, qf, -gA * A * invD);
-                            const float ex = (dx.hi + dx.lo) * invD, ey = (dy.hi + dy.lo) * invD,
-                                        ez = (dz.hi + dz.lo) * invD;
-                            gvx = __fmaf_rn(dLdD, ex, gvx);
-                            gvy = __fmaf_rn(dLdD, ey, gvy);
-                            gvz = __fmaf_rn(dLdD, ez, gvz);
-                            mpx = -dLdD * ex; mpy = -dLdD * ey; mpz = -dLdD * ez;
-                            pr = __fmaf_rn(gA * A * gg, rc.inv_r, pr);
+                    if (m + 1 < M || more)
+                        stage_g(Gbuf + ((stage + 1) & 1) * glen, grad_rir, grad_early, chan0 + (int64_t)mn * Lb,
+                                Pn.gb, Pn.gl, Lb, dcs[mn].early_lo, dcs[mn].early_hi, lane);
+                    const float* pm = a.mic + 3 * ((size_t)b * M + m);
+                    const float mx = pm[0], my = pm[1], mz = pm[2];
+                    float mpx = 0.f, mpy = 0.f, mpz = 0.f;
+                    for (int ch = 0; ch < nch; ++ch) {
+                        const int slot = P.p0 + 32 * ch + lane;
+                        if (slot < P.p1) {
+                            const float4 pa = a.spa[v0 + slot];
+                            const float2 pb = a.spb[v0 + slot];
+                            const float gg = a.samp[v0 + slot];
+                            int nc;
+                            float delta, D, ux, uy, uz;
+                            image_geom(pa, pb, mx, my, mz, a.q2, nc, delta, D, ux, uy, uz);
+                            const float invD = rcp_approx(D);
+                            const float A = exp2f(gg * rc.log2r) * invD;
+                            if ((nc + K >= 0) && (nc - K < Lb) && D > 0.0f) {
+                                const ArrB r = arrival_bwd(nc, delta, invK, exact_trig);
+                                const int j0 = nc - K - P.gb;
+                                if (j0 >= 0 && j0 + 2 * K <= P.gl) {
+                                    float S1, S2;
+                                    gather_taps<KT>(Gs + j0, K, r, tab, S1, S2);
+                                    const float dLdD = __fmaf_rn(A * S2, qf, -S1 * A * invD);
+                                    const float ex = ux * invD, ey = uy * invD, ez = uz * invD;
+                                    float* g3 = gv + ch * 96 + lane;
+                                    g3[0] = __fmaf_rn(dLdD, ex, g3[0]);
+                                    g3[32] = __fmaf_rn(dLdD, ey, g3[32]);
+                                    g3[64] = __fmaf_rn(dLdD, ez, g3[64]);
+                                    mpx = __fmaf_rn(-dLdD, ex, mpx);
+                                    mpy = __fmaf_rn(-dLdD, ey, mpy);
+                                    mpz = __fmaf_rn(-dLdD, ez, mpz);
+                                    rpart = __fmaf_rn(S1 * A * gg, rc.inv_r, rpart);
+                                } else {
+                                    atomicOr(&a.hdr->status, FRAM_DEV_CAPACITY);
+                                }
+                            }
+                        }
+                    }
+                    // Direct path of (b, s, m), owned by one tile: lane 0 adds it in the first
+                    // pass whose staged span covers its taps.
+                    if (lane == 0 && !((dmask >> m) & 1ull)) {
+                        const DirectConst dc = dcs[m];
+                        int nc = __float2int_rn(dc.t_hi);
+                        const float delta = __fadd_rn(__fsub_rn(dc.t_hi, (float)nc), dc.t_lo);
+                        if ((nc + K >= 0) && (nc - K < Lb)) {
+                            const ArrB r = arrival_bwd(nc, delta, invK, exact_trig);
+                            const int j0 = nc - K - P.gb;
+                            if (j0 >= 0 && j0 + 2 * K <= P.gl) {
+                                float S1, S2;
+                                gather_taps<KT>(Gs + j0, K, r, tab, S1, S2);
+                                const float A = dc.amp;
+                                const float dLdD = __fmaf_rn(A * S2, qf, -S1 * A * A);
+                                dsx = __fmaf_rn(dLdD, dc.ex, dsx);
+                                dsy = __fmaf_rn(dLdD, dc.ey, dsy);
+                                dsz = __fmaf_rn(dLdD, dc.ez, dsz);
+                                mpx = __fmaf_rn(-dLdD, dc.ex, mpx);
+                                mpy = __fmaf_rn(-dLdD, dc.ey, mpy);
+                                mpz = __fmaf_rn(-dLdD, dc.ez, mpz);
+                                dmask |= 1ull << m;
+                            } else if (direct_only) {
+                                atomicOr(&a.hdr->status, FRAM_DEV_CAPACITY);
+                                dmask |= 1ull << m;
+                            }
                         } else {
-                            atomicOr(&a.hdr->status, FRAM_DEV_CAPACITY);
+                            dmask |= 1ull << m;       // no tap inside the RIR
+                        }
+                    }
+                    mpx = warp_sum(mpx); mpy = warp_sum(mpy); mpz = warp_sum(mpz);
+                    if (lane == 0) {
+                        float* pw = pmic + 3 * m;
+                        if (first) { pw[0] = mpx; pw[1] = mpy; pw[2] = mpz; }
+                        else { pw[0] += mpx; pw[1] += mpy; pw[2] += mpz; }
+                    }
+                    if (m + 1 == M && !more && !direct_only) {
+                        // All image passes done: a direct-only pass if a direct path is missing.
+                        const uint64_t dm = __shfl_sync(0xffffffffu, dmask, 0);
+                        if (dm != dall) {
+                            Pn = Pdir;
+                            more = true;
+                            next_direct_only = true;
+                            stage_g(Gbuf + ((stage + 1) & 1) * glen, grad_rir, grad_early, chan0, Pn.gb, Pn.gl, Lb,
+                                    dcs[0].early_lo, dcs[0].early_hi, lane);
                         }
                     }
                 }
-                // Direct path of (b, s, m): owned by one tile; thread 0 adds it after its image.
-                if (own_direct && ch == 0 && tid == 0) {
-                    const int nc = __float2int_rn(dc.t_hi);
-                    float delta = __fadd_rn(__fsub_rn(dc.t_hi, (float)nc), dc.t_lo);
-                    if (fabsf(delta) < kTinyDelta) delta = kTinyDelta;
-                    const int j0 = nc - K - gbase;
-                    if ((nc + K >= 0) && (nc - K < Lb)) {
-                        if (j0 >= 0 && j0 + 2 * K < P.glen) {
-                            float gA, gT;
-                            gather_taps<KT>(Gs + j0, K, delta, tab, gA, gT);
-                            const float A = dc.amp;
-                            const float dLdD = __fmaf_rn(-A * gT, qf, -gA * A * A);
-                            dsx += dLdD * dc.ex; dsy += dLdD * dc.ey; dsz += dLdD * dc.ez;
-                            mpx -= dLdD * dc.ex; mpy -= dLdD * dc.ey; mpz -= dLdD * dc.ez;
-                        } else {
-                            atomicOr(&a.hdr->status, FRAM_DEV_CAPACITY);
+                __syncwarp();
+                if (grad_vs) {
+                    for (int ch = 0; ch < nch; ++ch) {
+                        const int slot = P.p0 + 32 * ch + lane;
+                        if (slot < P.p1) {
+                            const int64_t v = v0 + a.perm[v0 + slot];
+                            const float* g3 = gv + ch * 96 + lane;
+                            grad_vs[3 * v] = g3[0];
+                            grad_vs[3 * v + 1] = g3[32];
+                            grad_vs[3 * v + 2] = g3[64];
                         }
                     }
                 }
-                // Mic partials: a fixed-order warp sum; each warp keeps its own slot.
-                mpx = warp_sum(mpx); mpy = warp_sum(mpy); mpz = warp_sum(mpz);
-                if (lane == 0) {
-                    float* rw = red + (wid * M + m) * 3;
-                    rw[0] += mpx; rw[1] += mpy; rw[2] += mpz;
-                }
+                __syncwarp();
+                if (!more) break;
+                P = Pn;
+                direct_only = direct_only || next_direct_only;
             }
-            if (has && grad_vs) {
-                grad_vs[3 * v] = gvx; grad_vs[3 * v + 1] = gvy; grad_vs[3 * v + 2] = gvz;
-            }
+            cp_async_wait_all();
         }
-        pr = warp_sum(pr);
-        if (lane == 0) s_r[wid] = pr;
-        __syncthreads();
-        for (int k = tid; k < 3 * M; k += NT) {
-            float acc = 0.f;
-            for (int w = 0; w < NW; ++w) acc += red[w * M * 3 + k];
-            a.part_mic[(int64_t)qi * 3 * M + k] = acc;
-        }
-        if (tid == 0) {
-            float acc = 0.f;
-            for (int w = 0; w < NW; ++w) acc += s_r[w];
-            a.part_r[qi] = acc;
+        rpart = warp_sum(rpart);
+        if (lane == 0) {
+            a.part_r[qi] = rpart;
             a.part_src[3 * (int64_t)qi] = dsx;
             a.part_src[3 * (int64_t)qi + 1] = dsy;
             a.part_src[3 * (int64_t)qi + 2] = dsz;
         }
-        __syncthreads();
+        qi = __shfl_sync(0xffffffffu, nxt, 0);
     }
 }
 
@@ -388,16 +556,15 @@ __global__ void bwd_reduce(LaunchArgs a, float* __restrict__ grad_mic, float* __
 }
 
 template <int KT>
-cudaError_t launch_bwd_t(const LaunchArgs& a, int margin_i, const float* pos_hi, const float* pos_lo, const float* g,
-                         const float* grad_rir, const float* grad_early, float* grad_vs, cudaStream_t st)
+cudaError_t launch_bwd_t(const LaunchArgs& a, const float* grad_rir, const float* grad_early, float* grad_vs,
+                         cudaStream_t st)
 {
-    constexpr int NT = 256;
-    const int smem = bwd_smem(a.tile, a.K, margin_i, a.M, NT / 32).total;
+    const int smem = (int)sizeof(float) * ((KT == 0 ? bwd_tab_floats(a.K) : 0) +
+                                           (kBwdThreads / 32) * bwd_warp_floats(a.tile, a.K, a.margin_i));
     int per_sm = 0;
-    cudaError_t e = kernel_residency((const void*)bwd_kernel<NT, KT>, NT, smem, &per_sm);
+    cudaError_t e = kernel_residency((const void*)bwd_kernel<KT>, kBwdThreads, smem, &per_sm);
     if (e != cudaSuccess) return e;
-    bwd_kernel<NT, KT><<<device_sm_count() * per_sm, NT, smem, st>>>(a, margin_i, pos_hi, pos_lo, g, grad_rir,
-                                                                     grad_early, grad_vs);
+    bwd_kernel<KT><<<device_sm_count() * per_sm, kBwdThreads, smem, st>>>(a, grad_rir, grad_early, grad_vs);
     return cudaGetLastError();
 }
 
@@ -408,13 +575,18 @@ cudaError_t launch_backward(const LaunchArgs& a, const float* pos_hi, const floa
                             float* grad_mic, float* grad_src, float* grad_r, cudaStream_t st)
 {
     (void)r;
-    if (a.M > 64) return cudaErrorInvalidValue;
-    // Host-side bound on any room's per-mic delay spread around the binning key.
-    const int margin_i = a.margin_i;
+    (void)pos_hi;
+    (void)pos_lo;   // the kernel reads the sorted copies the preparation made
+    if (a.M > 64) return cudaErrorInvalidValue;   // direct-path bookkeeping is a 64-bit mask
     cudaError_t e;
-    if (a.K == 40) e = launch_bwd_t<40>(a, margin_i, pos_hi, pos_lo, g, grad_rir, grad_early, grad_vs, st);
-    else if (a.K == 63) e = launch_bwd_t<63>(a, margin_i, pos_hi, pos_lo, g, grad_rir, grad_early, grad_vs, st);
-    else e = launch_bwd_t<0>(a, margin_i, pos_hi, pos_lo, g, grad_rir, grad_early, grad_vs, st);
+    const int64_t segs = (int64_t)a.B * a.S;
+    if (segs > 0) {
+        g_gather<<<(unsigned)segs, 256, 0, st>>>(a, g);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (a.K == 40) e = launch_bwd_t<40>(a, grad_rir, grad_early, grad_vs, st);
+    else if (a.K == 63) e = launch_bwd_t<63>(a, grad_rir, grad_early, grad_vs, st);
+    else e = launch_bwd_t<0>(a, grad_rir, grad_early, grad_vs, st);
     if (e != cudaSuccess) return e;
     const int64_t n = std::max<int64_t>({(int64_t)a.B * a.M * 3, (int64_t)a.B * a.S * 3, (int64_t)a.B});
     if (n > 0 && (grad_mic || grad_src || grad_r)) {

@@ -439,61 +439,72 @@ __device__ __forceinline__ void init_tap_lanes(TapLanes<NR>& L, int lane, int K)
     }
 }
 
-// Adds one arrival's taps to the warp's tile buffer.  rel = base - K - T0 is the tile offset of
-// slot 0; buffer index = tile offset + 32.  Rounds that start outside (-32, T) are skipped (they
-// hold no sample of the tile), so every index stays in [1, T + 62].
+// Adds one arrival's taps to the warp's tile buffer.  `rb` is the byte offset, from the start of
+// the dynamic shared memory, of the buffer word that tap slot 0 of lane 0 updates; lane4 = 4 lane.
+// add_arrival_inner: every round lies inside the buffer (the caller checked).
+// add_arrival_edge: rounds that start outside (-32, T) are skipped -- they hold no sample of the
+// tile -- so every index stays inside the buffer; s0 is the tile offset of slot 0.
 template <int NR>
-__device__ __forceinline__ void add_arrival(float* __restrict__ buf, const TapLanes<NR>& L, float4 r, int rel,
-                                            int T, int lane)
+__device__ __forceinline__ void add_arrival_inner(char* __restrict__ smem, const TapLanes<NR>& L, float4 r, int rb,
+                                                  int lane4)
 {
-    float* dst = buf + 32 + rel + lane;
-    if (rel > -32 && rel + 32 * (NR - 1) < T) {
+    float* dst = reinterpret_cast<float*>(smem + (rb + lane4));
 #pragma unroll
-        for (int k = 0; k < NR; ++k) {
+    for (int k = 0; k < NR; ++k) {
+        const float e = __fmaf_rn(L.sg[k], r.x, L.kp[k]);
+        const float num = __fmaf_rn(L.C[k], r.z, __fmaf_rn(L.S[k], r.w, r.y));
+        dst[32 * k] = __fmaf_rn(num, rcp_approx(e), dst[32 * k]);
+    }
+}
+
+template <int NR>
+__device__ __forceinline__ void add_arrival_edge(char* __restrict__ smem, const TapLanes<NR>& L, float4 r, int rb,
+                                                 int lane4, int s0, int T)
+{
+    float* dst = reinterpret_cast<float*>(smem + (rb + lane4));
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        if (s0 + 32 * k > -32 && s0 + 32 * k < T) {
             const float e = __fmaf_rn(L.sg[k], r.x, L.kp[k]);
             const float num = __fmaf_rn(L.C[k], r.z, __fmaf_rn(L.S[k], r.w, r.y));
             dst[32 * k] = __fmaf_rn(num, rcp_approx(e), dst[32 * k]);
         }
-    } else {
-#pragma unroll
-        for (int k = 0; k < NR; ++k) {
-            const int s0 = rel + 32 * k;
-            if (s0 > -32 && s0 < T) {
-                const float e = __fmaf_rn(L.sg[k], r.x, L.kp[k]);
-                const float num = __fmaf_rn(L.C[k], r.z, __fmaf_rn(L.S[k], r.w, r.y));
-                dst[32 * k] = __fmaf_rn(num, rcp_approx(e), dst[32 * k]);
-            }
-        }
     }
 }
 
-// Per-warp shared memory (floats): the tile buffer (T + 64: 32 samples of halo on each side),
-// 32 arrival records (float4) and their tile offsets (int).
-__host__ __device__ inline int synth_warp_floats(int T) { return (T + 64) + 4 * 32 + 32; }
+// Per-warp shared memory (floats): the tile buffer (T + 68: sample T0 + k sits at index h + k,
+// h = 32 + the output's word offset mod 4, so the store runs in aligned float4s and at least 32
+// samples of halo remain on each side), 32 arrival records (float4) and their buffer offsets.
+__host__ __device__ inline int synth_warp_floats(int T) { return (T + 68) + 4 * 32 + 32; }
 
 // Work unit = (room, source, tile, mic), one warp each, pulled from a counter (the next unit is
 // requested when the current one starts).  Per unit: zero the tile buffer; add the direct path;
 // walk the run of sorted images that can reach the tile 32 at a time -- each lane computes one
 // image's arrival for this mic (the next 32 images' data is fetched meanwhile), the warp compacts
-// the ones that reach the tile and adds them one after another, each lane owning one tap slot;
-// then store the tile (and the Eq. 9 early RIR).  The accumulation order of every sample is fixed
-// by the sorted image order, and no two lanes write one sample in the same step.
+// the ones that reach the tile (those whose taps all fall inside the buffer first) and adds them
+// one after another, each lane owning one tap slot; then store the tile (and the Eq. 9 early
+// RIR).  The accumulation order of every sample is fixed by the sorted image order and the
+// compaction, and no two lanes write one sample in the same step.
 template <int NR>
 __global__ void __launch_bounds__(kSynthThreads, 3) synth_kernel(LaunchArgs a, float* __restrict__ rir,
                                                                   float* __restrict__ early)
 {
     extern __shared__ __align__(16) float synth_smem[];
+    char* smem = reinterpret_cast<char*>(synth_smem);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lane4 = 4 * lane;
     const int T = a.tile, K = a.K, M = a.M;
     float* buf = synth_smem + wid * synth_warp_floats(T);
-    float4* rec = reinterpret_cast<float4*>(buf + T + 64);
-    int* rrel = reinterpret_cast<int*>(rec + 32);
+    const int buf_b = 4 * wid * synth_warp_floats(T);     // byte offset of buf
+    float4* rec = reinterpret_cast<float4*>(buf + T + 68);
+    int* rrb = reinterpret_cast<int*>(rec + 32);
     TapLanes<NR> L;
     init_tap_lanes<NR>(L, lane, K);
     const float invK = 1.0f / (float)K;
     const bool exact_trig = K < 2;
     const int64_t n_units = (int64_t)a.hdr->n_items * M;
     const int reach_lo = 1 - 2 * K;        // rel range of arrivals with a tap in the tile
+    const int inner_hi = T - 32 * (NR - 1); // rel < inner_hi and rel > -32: every round inside
     int u = 0;
     if (lane == 0) u = atomicAdd(&a.hdr->queue, 1);
     u = __shfl_sync(0xffffffffu, u, 0);
@@ -515,9 +526,13 @@ __global__ void __launch_bounds__(kSynthThreads, 3) synth_kernel(LaunchArgs a, f
             pb = a.spb[v0 + ir.c_lo + lane];
             am = a.samp[v0 + ir.c_lo + lane];
         }
+        float* dst = rir + ir.out0 + (int64_t)m * Lb + T0;       // sample T0 of this RIR
+        const int al = (int)((reinterpret_cast<uintptr_t>(dst) >> 2) & 3);
+        const int h = 32 + al;
+        const int hb = buf_b + 4 * h;                             // byte offset of sample T0
 
         float4* b4 = reinterpret_cast<float4*>(buf);
-        for (int k = lane; k < (T + 64) / 4; k += 32) b4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = lane; k < (T + 68) / 4; k += 32) b4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncwarp();
         {   // direct path (uniform across the warp)
             int nc = __float2int_rn(dc.t_hi);
@@ -525,12 +540,12 @@ __global__ void __launch_bounds__(kSynthThreads, 3) synth_kernel(LaunchArgs a, f
             if (dc.amp > 0.0f) {
                 const float4 r = arrival_record(nc, delta, dc.amp, invK, exact_trig);
                 const int rel = nc - K - T0;
-                if (rel >= reach_lo && rel < T) add_arrival<NR>(buf, L, r, rel, T, lane);
+                if (rel >= reach_lo && rel < T) add_arrival_edge<NR>(smem, L, r, hb + 4 * rel, lane4, rel, T);
             }
             __syncwarp();
         }
         for (int c = ir.c_lo; c < ir.c_hi; c += 32) {
-            bool valid = false;
+            bool valid = false, inner = false;
             float4 rr = make_float4(0.f, 0.f, 0.f, 0.f);
             int rel = 0;
             if (c + lane < ir.c_hi) {
@@ -542,6 +557,7 @@ __global__ void __launch_bounds__(kSynthThreads, 3) synth_kernel(LaunchArgs a, f
                     rr = arrival_record(nc, delta, A, invK, exact_trig);
                     rel = nc - K - T0;
                     valid = rel >= reach_lo && rel < T;
+                    inner = rel > -32 && rel < inner_hi;
                 }
             }
             if (c + 32 + lane < ir.c_hi) {      // next 32 images, in flight during the taps below
@@ -549,28 +565,53 @@ __global__ void __launch_bounds__(kSynthThreads, 3) synth_kernel(LaunchArgs a, f
                 pb = a.spb[v0 + c + 32 + lane];
                 am = a.samp[v0 + c + 32 + lane];
             }
-            const unsigned vb = __ballot_sync(0xffffffffu, valid);
+            const unsigned lt = (1u << lane) - 1u;
+            const unsigned vi = __ballot_sync(0xffffffffu, inner);
+            const unsigned ve = __ballot_sync(0xffffffffu, valid && !inner);
+            const int ni = __popc(vi), nv = ni + __popc(ve);
             if (valid) {
-                const int slot = __popc(vb & ((1u << lane) - 1u));
+                const int slot = inner ? __popc(vi & lt) : ni + __popc(ve & lt);
                 rec[slot] = rr;
-                rrel[slot] = rel;
+                rrb[slot] = inner ? hb + 4 * rel : rel;
             }
             __syncwarp();
-            const int nv = __popc(vb);
-            for (int q = 0; q < nv; ++q) {
-                add_arrival<NR>(buf, L, rec[q], rrel[q], T, lane);
+            // The records are read-only here: the next one is loaded before the current taps.
+            float4 rn = rec[0];
+            int bn = rrb[0];
+            for (int q = 0; q < ni; ++q) {
+                const float4 r = rn;
+                const int rb = bn;
+                rn = rec[min(q + 1, 31)];
+                bn = rrb[min(q + 1, 31)];
+                add_arrival_inner<NR>(smem, L, r, rb, lane4);
+                __syncwarp();
+            }
+            for (int q = ni; q < nv; ++q) {
+                const int rl = rrb[q];
+                add_arrival_edge<NR>(smem, L, rec[q], hb + 4 * rl, lane4, rl, T);
                 __syncwarp();
             }
         }
-        // ---- store the tile (and the Eq. 9 early RIR) ----
-        float* dst = rir + ir.out0 + (int64_t)m * Lb;
-        float* dste = early ? early + ir.out0 + (int64_t)m * Lb : nullptr;
-        for (int k = lane; k < T; k += 32) {
-            const int n = T0 + k;
-            if (n < Lb) {
-                const float h = buf[32 + k];
-                dst[n] = h;
-                if (dste) dste[n] = (n >= dc.early_lo && n <= dc.early_hi) ? h : 0.0f;
+        // ---- store the tile (and the Eq. 9 early RIR): buffer index h + k holds sample T0 + k,
+        // and (h + k) % 4 == 0 exactly where dst + k is 16-byte aligned ----
+        const int nT = min(T, Lb - T0);
+        float* dste = early ? early + ir.out0 + (int64_t)m * Lb + T0 : nullptr;
+        const int k0 = (4 - al) & 3;                       // first aligned k
+        const int nvec = nT > k0 ? (nT - k0) >> 2 : 0;
+        for (int v = lane; v < nvec; v += 32) {
+            const int k = k0 + 4 * v;
+            const float4 x = *reinterpret_cast<const float4*>(buf + h + k);
+            *reinterpret_cast<float4*>(dst + k) = x;
+        }
+        if (lane < k0 && lane < nT) dst[lane] = buf[h + lane];
+        {
+            const int kt = k0 + 4 * nvec + lane;
+            if (lane < 3 && kt < nT) dst[kt] = buf[h + kt];
+        }
+        if (dste) {
+            for (int k = lane; k < nT; k += 32) {
+                const int n = T0 + k;
+                dste[k] = (n >= dc.early_lo && n <= dc.early_hi) ? buf[h + k] : 0.0f;
             }
         }
         __syncwarp();
