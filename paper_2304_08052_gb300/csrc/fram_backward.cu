@@ -93,8 +93,9 @@ constexpr TrigTab make_trig_tab()
     return t;
 }
 
-__constant__ TrigTab c_trig40 = make_trig_tab<40>();
-__constant__ TrigTab c_trig63 = make_trig_tab<63>();
+// Compile-time copies: the unrolled tap loops read them as literal FMA operands.
+template <int K>
+inline constexpr TrigTab kTrig = make_trig_tab<K>();
 
 constexpr float kShiftMin = 2.44140625e-4f;   // 2^-12: arrivals re-based as in the synthesis
 constexpr float kTwoPiInv = 0.15915494309189535f;
@@ -151,38 +152,53 @@ __device__ __forceinline__ ArrB arrival_bwd(int& nc, float delta, float invK, bo
 }
 
 // S1 += sum_j G[j] tap_j, S2 += sum_j G[j] dtap_j/dt over the 2K slots j = o + K of one arrival;
-// Gs points at G[base - K].  Compile-time K: every per-slot constant is an FMA operand.
+// Gs points at G[base - K].  Compile-time K: every per-slot constant is a literal FMA operand.
+struct TapAcc {
+    float s1a, s1b, s2a, s2b;
+};
+
+template <int KT, int J>
+__device__ __forceinline__ void tap_slot(const float* __restrict__ Gs, const ArrB& r, TapAcc& q)
+{
+    constexpr int o = J - KT;
+    constexpr float sg = (o & 1) ? -1.0f : 1.0f;
+    constexpr float C = kTrig<KT>.c[J];
+    constexpr float S = kTrig<KT>.s[J];
+    constexpr float kp = -sg * (float)o;
+    const float G = Gs[J];
+    const float e = __fmaf_rn(sg, r.d, kp);
+    const float rc = rcp_approx(e);
+    const float num = __fmaf_rn(C, r.a, __fmaf_rn(S, r.b, r.P));
+    const float dnum = __fmaf_rn(C, r.ap, __fmaf_rn(S, r.bp, r.Pp));
+    const float y = G * rc;
+    const float t = y * num;
+    float& s1 = (J & 1) ? q.s1b : q.s1a;
+    float& s2 = (J & 1) ? q.s2b : q.s2a;
+    s1 += t;
+    if constexpr (o == 0 || o == -1) {
+        const float dg = (dnum - sg * (num * rc)) * rc;
+        const bool near = (o == 0) != r.shifted;
+        s2 = __fmaf_rn(G, near ? r.dnear : dg, s2);
+    } else {
+        s2 = __fmaf_rn(y, dnum, s2);
+        s2 = __fmaf_rn(-sg * t, rc, s2);
+    }
+}
+
+template <int KT, int... J>
+__device__ __forceinline__ void tap_slots(const float* __restrict__ Gs, const ArrB& r, TapAcc& q,
+                                          std::integer_sequence<int, J...>)
+{
+    (tap_slot<KT, J>(Gs, r, q), ...);
+}
+
 template <int KT>
 __device__ __forceinline__ void gather_taps_ct(const float* __restrict__ Gs, const ArrB& r, float& S1, float& S2)
 {
-    float s1a = 0.f, s1b = 0.f, s2a = 0.f, s2b = 0.f;
-#pragma unroll
-    for (int j = 0; j < 2 * KT; ++j) {
-        const int o = j - KT;
-        const float sg = (o & 1) ? -1.0f : 1.0f;
-        const float C = (KT == 40) ? c_trig40.c[j] : c_trig63.c[j];
-        const float S = (KT == 40) ? c_trig40.s[j] : c_trig63.s[j];
-        const float G = Gs[j];
-        const float e = __fmaf_rn(sg, r.d, -sg * (float)o);
-        const float rc = rcp_approx(e);
-        const float num = __fmaf_rn(C, r.a, __fmaf_rn(S, r.b, r.P));
-        const float dnum = __fmaf_rn(C, r.ap, __fmaf_rn(S, r.bp, r.Pp));
-        const float y = G * rc;
-        const float t = y * num;
-        float& s1 = (j & 1) ? s1b : s1a;
-        float& s2 = (j & 1) ? s2b : s2a;
-        s1 += t;
-        if (o == 0 || o == -1) {
-            const float dg = (dnum - sg * (num * rc)) * rc;
-            const bool near = (o == 0) != r.shifted;
-            s2 = __fmaf_rn(G, near ? r.dnear : dg, s2);
-        } else {
-            s2 = __fmaf_rn(y, dnum, s2);
-            s2 = __fmaf_rn(-sg * t, rc, s2);
-        }
-    }
-    S1 = s1a + s1b;
-    S2 = s2a + s2b;
+    TapAcc q{0.f, 0.f, 0.f, 0.f};
+    tap_slots<KT>(Gs, r, q, std::make_integer_sequence<int, 2 * KT>{});
+    S1 = q.s1a + q.s1b;
+    S2 = q.s2a + q.s2b;
 }
 
 // Any K: the same taps, cos/sin(pi o/K) from a shared table.
@@ -296,7 +312,11 @@ __device__ __forceinline__ BwdPass next_pass(const LaunchArgs& a, int64_t v0, in
         const int p = p0 + 32 * c + lane;
         const bool stop = p < p1 && a.skey[v0 + p] >= k0 + span;
         const unsigned bal = __ballot_sync(0xffffffffu, stop);
-        if (bal) { p1 = p0 + 32 * c + __ffs(bal) - 1; break; }
+        if (bal) {
+            p1 = p0 + 32 * c + __ffs(bal) - 1;
+            if (p1 - p0 > 32) p1 = p0 + ((p1 - p0) & ~31);   // whole chunks: no idle lanes
+            break;
+        }
     }
     P.p1 = p1;
     const int k1 = a.skey[v0 + p1 - 1];
@@ -413,66 +433,71 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_kernel(LaunchArgs a, const
                     const float* pm = a.mic + 3 * ((size_t)b * M + m);
                     const float mx = pm[0], my = pm[1], mz = pm[2];
                     float mpx = 0.f, mpy = 0.f, mpz = 0.f;
-                    for (int ch = 0; ch < nch; ++ch) {
-                        const int slot = P.p0 + 32 * ch + lane;
-                        if (slot < P.p1) {
-                            const float4 pa = a.spa[v0 + slot];
-                            const float2 pb = a.spb[v0 + slot];
-                            const float gg = a.samp[v0 + slot];
-                            int nc;
-                            float delta, D, ux, uy, uz;
-                            image_geom(pa, pb, mx, my, mz, a.q2, nc, delta, D, ux, uy, uz);
-                            const float invD = rcp_approx(D);
-                            const float A = exp2f(gg * rc.log2r) * invD;
-                            if ((nc + K >= 0) && (nc - K < Lb) && D > 0.0f) {
-                                const ArrB r = arrival_bwd(nc, delta, invK, exact_trig);
-                                const int j0 = nc - K - P.gb;
-                                if (j0 >= 0 && j0 + 2 * K <= P.gl) {
-                                    float S1, S2;
-                                    gather_taps<KT>(Gs + j0, K, r, tab, S1, S2);
-                                    const float dLdD = __fmaf_rn(A * S2, qf, -S1 * A * invD);
-                                    const float ex = ux * invD, ey = uy * invD, ez = uz * invD;
-                                    float* g3 = gv + ch * 96 + lane;
-                                    g3[0] = __fmaf_rn(dLdD, ex, g3[0]);
-                                    g3[32] = __fmaf_rn(dLdD, ey, g3[32]);
-                                    g3[64] = __fmaf_rn(dLdD, ez, g3[64]);
-                                    mpx = __fmaf_rn(-dLdD, ex, mpx);
-                                    mpy = __fmaf_rn(-dLdD, ey, mpy);
-                                    mpz = __fmaf_rn(-dLdD, ez, mpz);
-                                    rpart = __fmaf_rn(S1 * A * gg, rc.inv_r, rpart);
-                                } else {
-                                    atomicOr(&a.hdr->status, FRAM_DEV_CAPACITY);
-                                }
+                    // Chunks of images (one per lane), then one round for the direct path of
+                    // (b, s, m) on lane 0, owned by one tile and added in the first pass whose
+                    // staged span covers its taps.  One call site of the tap loop serves both.
+                    const bool want_direct = lane == 0 && !((dmask >> m) & 1ull);
+                    const int nround = nch + (__any_sync(0xffffffffu, want_direct) ? 1 : 0);
+                    for (int ch = 0; ch < nround; ++ch) {
+                        const bool is_dir = ch == nch;
+                        bool act;
+                        int nc = 0;
+                        float delta = 0.f, A = 0.f, invD = 0.f, ex = 0.f, ey = 0.f, ez = 0.f, gg = 0.f;
+                        if (!is_dir) {
+                            const int slot = P.p0 + 32 * ch + lane;
+                            act = slot < P.p1;
+                            if (act) {
+                                const float4 pa = a.spa[v0 + slot];
+                                const float2 pb = a.spb[v0 + slot];
+                                gg = a.samp[v0 + slot];
+                                float D, ux, uy, uz;
+                                image_geom(pa, pb, mx, my, mz, a.q2, nc, delta, D, ux, uy, uz);
+                                invD = rcp_approx(D);
+                                A = exp2f(gg * rc.log2r) * invD;
+                                ex = ux * invD; ey = uy * invD; ez = uz * invD;
+                                act = D > 0.0f;
+                            }
+                        } else {
+                            act = want_direct;
+                            if (act) {
+                                const DirectConst dc = dcs[m];
+                                nc = __float2int_rn(dc.t_hi);
+                                delta = __fadd_rn(__fsub_rn(dc.t_hi, (float)nc), dc.t_lo);
+                                A = dc.amp;
+                                invD = dc.amp;
+                                ex = dc.ex; ey = dc.ey; ez = dc.ez;
                             }
                         }
-                    }
-                    // Direct path of (b, s, m), owned by one tile: lane 0 adds it in the first
-                    // pass whose staged span covers its taps.
-                    if (lane == 0 && !((dmask >> m) & 1ull)) {
-                        const DirectConst dc = dcs[m];
-                        int nc = __float2int_rn(dc.t_hi);
-                        const float delta = __fadd_rn(__fsub_rn(dc.t_hi, (float)nc), dc.t_lo);
-                        if ((nc + K >= 0) && (nc - K < Lb)) {
+                        if (act && (nc + K < 0 || nc - K >= Lb)) {      // no tap inside the RIR
+                            act = false;
+                            if (is_dir) dmask |= 1ull << m;
+                        }
+                        if (act) {
                             const ArrB r = arrival_bwd(nc, delta, invK, exact_trig);
                             const int j0 = nc - K - P.gb;
                             if (j0 >= 0 && j0 + 2 * K <= P.gl) {
                                 float S1, S2;
                                 gather_taps<KT>(Gs + j0, K, r, tab, S1, S2);
-                                const float A = dc.amp;
-                                const float dLdD = __fmaf_rn(A * S2, qf, -S1 * A * A);
-                                dsx = __fmaf_rn(dLdD, dc.ex, dsx);
-                                dsy = __fmaf_rn(dLdD, dc.ey, dsy);
-                                dsz = __fmaf_rn(dLdD, dc.ez, dsz);
-                                mpx = __fmaf_rn(-dLdD, dc.ex, mpx);
-                                mpy = __fmaf_rn(-dLdD, dc.ey, mpy);
-                                mpz = __fmaf_rn(-dLdD, dc.ez, mpz);
-                                dmask |= 1ull << m;
-                            } else if (direct_only) {
+                                const float dLdD = __fmaf_rn(A * S2, qf, -S1 * A * invD);
+                                mpx = __fmaf_rn(-dLdD, ex, mpx);
+                                mpy = __fmaf_rn(-dLdD, ey, mpy);
+                                mpz = __fmaf_rn(-dLdD, ez, mpz);
+                                if (!is_dir) {
+                                    float* g3 = gv + ch * 96 + lane;
+                                    g3[0] = __fmaf_rn(dLdD, ex, g3[0]);
+                                    g3[32] = __fmaf_rn(dLdD, ey, g3[32]);
+                                    g3[64] = __fmaf_rn(dLdD, ez, g3[64]);
+                                    rpart = __fmaf_rn(S1 * A * gg, rc.inv_r, rpart);
+                                } else {
+                                    dsx = __fmaf_rn(dLdD, ex, dsx);
+                                    dsy = __fmaf_rn(dLdD, ey, dsy);
+                                    dsz = __fmaf_rn(dLdD, ez, dsz);
+                                    dmask |= 1ull << m;
+                                }
+                            } else if (!is_dir || direct_only) {
                                 atomicOr(&a.hdr->status, FRAM_DEV_CAPACITY);
-                                dmask |= 1ull << m;
+                                if (is_dir) dmask |= 1ull << m;
                             }
-                        } else {
-                            dmask |= 1ull << m;       // no tap inside the RIR
                         }
                     }
                     mpx = warp_sum(mpx); mpy = warp_sum(mpy); mpz = warp_sum(mpz);
