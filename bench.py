@@ -34,9 +34,9 @@ METRIC = "multi-ch RIRs/s and sinc-taps/s (fwd, fwd+bwd) at 1 GB300, % of roofli
 # Algorithmic work per tap (the tap arithmetic of the paper's sum, Eq. 1 with windowed sincs):
 # forward 8 FP32-pipe operations and 1 reciprocal on the MUFU (special function) pipe; adjoint
 # 14 FP32 and 1 MUFU.  Per arrival (image x mic) 40 FP32 + 6 MUFU more, spread over its 2K+1 taps.
-# Kernels of libfram per fwd step: sample_kernel; room_prologue, item_scan, bin_images, item_ranges
-# (preparation); amp_gather, synth_kernel (synthesis).
-FWD_LAUNCHES = 7
+# Kernels of libfram per fwd step: sample_kernel; room_prologue, item_scan, bin_images,
+# sort_positions, item_ranges (preparation); amp_gather, synth_kernel (synthesis).
+FWD_LAUNCHES = 8
 FWD_FP32, BWD_FP32, ARR_FP32 = 8.0, 14.0, 40.0
 TAP_MUFU, ARR_MUFU = 1.0, 6.0
 FP32_LANES_PER_SM, MUFU_LANES_PER_SM = 128, 16
@@ -208,7 +208,7 @@ def main():
     ap.add_argument("--rooms", type=int, default=0, help="first N rooms of the workload only (0 = all); "
                     "for profiler captures of a small case")
     ap.add_argument("--ref-rooms", type=int, default=8)
-    ap.add_argument("--cpu-rooms", type=int, default=64)
+    ap.add_argument("--cpu-rooms", type=int, default=512)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-room comparison and the CPU baseline")
     args = ap.parse_args()

@@ -9,9 +9,10 @@
 //   2. item_scan       one CTA: prefix sum of S * ntiles_b -> work-item table (room, source, tile).
 //   3. bin_images      one warp per (room, source): each image's delay to the array centre
 //                      (the binning key, in samples), a stable counting sort of the images by
-//                      floor(key), a copy of the positions in that order and the first sorted
-//                      position of every 32-sample key block.  Per-mic delays differ from the
-//                      key by at most the array radius in samples ("margin").
+//                      floor(key) and the first sorted position of every 32-sample key block.
+//                      Per-mic delays differ from the key by at most the array radius in
+//                      samples ("margin").  sort_positions copies the positions into that
+//                      order; item_ranges writes the per-item records.
 //   4. synth_kernel    persistent warps pull (room, source, tile, mic) units from a counter.
 //                      Per unit the warp owns a private tile buffer in shared memory, computes
 //                      the arrival (delay t = D fs/c0 from a float-pair distance, amplitude,
@@ -184,8 +185,7 @@ __device__ __forceinline__ int tile_of_key(float key, float invT, int nt)
     return t > nt - 1 ? nt - 1 : t;
 }
 
-__global__ void __launch_bounds__(64) bin_images(LaunchArgs a, const float* __restrict__ pos_hi,
-                                                  const float* __restrict__ pos_lo)
+__global__ void __launch_bounds__(64) bin_images(LaunchArgs a, const float* __restrict__ pos_hi)
 {
     extern __shared__ int bin_smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -250,9 +250,8 @@ __global__ void __launch_bounds__(64) bin_images(LaunchArgs a, const float* __re
     }
     __syncwarp();
     // Pass 2: inside each tile, stable counting sort by floor(key) - tile start.  The last tile
-    // also takes every key beyond the RIR, in a doubled bucket range clamped at its end.  The
-    // sorted order also receives a copy of the image positions, and p32 the first sorted position
-    // of every 32-sample key block.
+    // also takes every key beyond the RIR, in a doubled bucket range clamped at its end.  p32
+    // receives the first sorted position of every 32-sample key block.
     int* p32 = a.pos32 + seg * ((int64_t)a.nb32 + 1);
     for (int t = 0; t < nt; ++t) {
         const int b0 = bo[t], b1 = bo[t + 1];
@@ -305,19 +304,32 @@ __global__ void __launch_bounds__(64) bin_images(LaunchArgs a, const float* __re
             if (lane == leader && act) fine[f] = basepos + __popc(peers);
             __syncwarp();
             if (act) {
-                const int64_t q = v0 + basepos + rank;
-                a.perm[q] = i;
-                a.skey[q] = t0 + f;
-                const float* ph = pos_hi + 3 * (v0 + i);
-                float lx = 0.0f, ly = 0.0f, lz = 0.0f;
-                if (pos_lo) { const float* pl = pos_lo + 3 * (v0 + i); lx = pl[0]; ly = pl[1]; lz = pl[2]; }
-                a.spa[q] = make_float4(ph[0], ph[1], ph[2], lx);
-                a.spb[q] = make_float2(ly, lz);
+                a.perm[v0 + basepos + rank] = i;
+                a.skey[v0 + basepos + rank] = t0 + f;
             }
         }
         __syncwarp();
     }
     for (int j = (nt + 1) * T / 32 + lane; j <= a.nb32; j += 32) p32[j] = n;
+}
+
+// Image positions in sorted order (one CTA per (room, source), coalesced over sorted positions).
+__global__ void __launch_bounds__(256) sort_positions(LaunchArgs a, const float* __restrict__ pos_hi,
+                                                      const float* __restrict__ pos_lo)
+{
+    const int64_t seg = blockIdx.x;
+    const int b = (int)(seg / a.S), s = (int)(seg % a.S);
+    const RoomConst rc = a.room[b];
+    if (rc.ntiles < 1) return;      // a room the prologue rejected has no sorted order
+    const int64_t v0 = rc.vs_off + (int64_t)s * rc.n_vs;
+    for (int p = threadIdx.x; p < rc.n_vs; p += blockDim.x) {
+        const int64_t i = v0 + a.perm[v0 + p];
+        const float* ph = pos_hi + 3 * i;
+        float lx = 0.0f, ly = 0.0f, lz = 0.0f;
+        if (pos_lo) { const float* pl = pos_lo + 3 * i; lx = pl[0]; ly = pl[1]; lz = pl[2]; }
+        a.spa[v0 + p] = make_float4(ph[0], ph[1], ph[2], lx);
+        a.spb[v0 + p] = make_float2(ly, lz);
+    }
 }
 
 // Image arrival for mic (mx, my, mz): delay as integer n_c + delta and distance, from the
@@ -642,7 +654,9 @@ cudaError_t launch_prepare(const LaunchArgs& a, const float* pos_hi, const float
         const int sm = (int)(sizeof(int) * 2 * (size_t)bin_warp_ints(a.max_tiles, a.tile));
         int per_sm = 0;
         if ((e = kernel_residency((const void*)bin_images, 64, sm, &per_sm)) != cudaSuccess) return e;
-        bin_images<<<(unsigned)((segs + 1) / 2), 64, sm, st>>>(a, pos_hi, pos_lo);
+        bin_images<<<(unsigned)((segs + 1) / 2), 64, sm, st>>>(a, pos_hi);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        sort_positions<<<(unsigned)segs, 256, 0, st>>>(a, pos_hi, pos_lo);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int64_t max_items = segs * a.max_tiles;
         item_ranges<<<(unsigned)((max_items + 255) / 256), 256, 0, st>>>(a, max_items);
