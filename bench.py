@@ -34,6 +34,11 @@ METRIC = "multi-ch RIRs/s and sinc-taps/s (fwd, fwd+bwd) at 1 GB300, % of roofli
 # Algorithmic work per tap (the tap arithmetic of the paper's sum, Eq. 1 with windowed sincs):
 # forward 8 FP32-pipe operations and 1 reciprocal on the MUFU (special function) pipe; adjoint
 # 14 FP32 and 1 MUFU.  Per arrival (image x mic) 40 FP32 + 6 MUFU more, spread over its 2K+1 taps.
+# DRAM bytes (read + write) of one synth_kernel launch per output sample, from one ncu capture
+# (large_4096, first 256 rooms, 283357184 output samples: 0.0819 GB read + 1.0746 GB written);
+# reported only while the synthesis source is the one that was measured (its SHA-256 prefix).
+SYNTH_TRAFFIC = {"source_sha256": "91c882def67a3177", "bytes_per_sample": (0.0819e9 + 1.0746e9) / 283357184}
+
 # Kernels of libfram per fwd step: sample_kernel; room_prologue, item_scan, bin_images,
 # sort_positions, item_ranges (preparation); amp_gather, synth_kernel (synthesis).
 FWD_LAUNCHES = 8
@@ -198,6 +203,16 @@ def run_reference(args):
     return 0
 
 
+def _synth_traffic(rir_samples):
+    """DRAM bytes of one synthesis launch from the recorded capture, or None if the kernel changed."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2304_08052_gb300", "csrc", "fram_synth.cu")
+    with open(src, "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest()[:16] != SYNTH_TRAFFIC["source_sha256"]:
+            return None
+    return SYNTH_TRAFFIC["bytes_per_sample"] * rir_samples
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -299,7 +314,8 @@ def main():
         "fwd_bwd": {"value": world * args.steps * rirs / t_fb, "unit": "RIRs/s",
                     "ms_per_step": 1000.0 * t_fb / args.steps, "taps_per_s": world * 2 * taps * args.steps / t_fb},
         "roofline": {"bound": "alu", "achieved": ach_fwd / 1e9, "peak": peak_fwd / 1e9, "unit": "Gtap/s",
-                     "frac": ach_fwd / peak_fwd, "traffic": None, "kernel": "synth_kernel (timed with amp_gather)",
+                     "frac": ach_fwd / peak_fwd, "traffic": _synth_traffic(T),
+                     "kernel": "synth_kernel (timed with amp_gather)",
                      "limit": lim_fwd, "kernel_ms": 1000.0 * syn_s, "hbm_gbs": out_bytes / syn_s / 1e9,
                      "peak_basis": f"{sm_count} SMs x ({FP32_LANES_PER_SM} FP32, {MUFU_LANES_PER_SM} MUFU) lanes x "
                                    f"{clock_hz / 1e6:.0f} MHz ({peak_kind} sm_max_mhz); per tap "
