@@ -152,11 +152,17 @@ def _time_steps(torch, fn, steps, dist_ok):
     ms = s.elapsed_time(e)
     if dist_ok:
         import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(torch, ms, "cuda")
         dist.barrier()
     return ms / 1000.0
+
+
+def max_over_ranks(torch, x: float, device) -> float:
+    """The largest of every rank's x (the job's time is its slowest rank's time)."""
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def cpu_baseline(sc, seed, rooms, params):
@@ -224,6 +230,7 @@ def main():
                     "for profiler captures of a small case")
     ap.add_argument("--ref-rooms", type=int, default=8)
     ap.add_argument("--cpu-rooms", type=int, default=512)
+    ap.add_argument("--cpu-rooms-1core", type=int, default=32)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-room comparison and the CPU baseline")
     args = ap.parse_args()
@@ -333,10 +340,21 @@ def main():
 
     if not args.no_extras and rank == 0:
         line["graph_vs_per_room"] = graph_vs_per_room(torch, api, scenes)
+        line["single_room_latency"] = single_room_latency(torch, api, scenes)
         u, dt, cores = cpu_baseline(sc, 1, list(range(args.cpu_rooms)), params)
         line["cpu_baseline"] = {"value": u / dt, "unit": "RIRs/s", "cores": cores, "kind": "oracle",
                                 "sample": f"first {args.cpu_rooms} rooms of {args.workload} (sample + synthesize, "
                                           f"FP64, {dt:.1f} s)"}
+        import oracle
+        threads = oracle.num_threads()
+        oracle.set_num_threads(1)
+        try:
+            u1, dt1, _ = cpu_baseline(sc, 1, list(range(args.cpu_rooms_1core)), params)
+        finally:
+            oracle.set_num_threads(threads)
+        line["cpu_baseline"]["single_core"] = {
+            "value": u1 / dt1, "unit": "RIRs/s", "cores": 1,
+            "sample": f"first {args.cpu_rooms_1core} rooms of {args.workload} (FP64, {dt1:.1f} s)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist_ok:
@@ -375,6 +393,33 @@ def e2e(torch, api, sc, params, ds, args, rirs, dist_ok, world):
     t = _time_steps(torch, step, steps, dist_ok)
     return {"value": world * steps * rirs / t, "unit": "RIRs/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(4 * ds.rir_total), "ms_per_step": 1000.0 * t / steps}
+
+
+def single_room_latency(torch, api, scenes):
+    """The single-room scene (6x5x3 m, 4 mics, 2000 images, 16 kHz) is latency-bound: time one
+    fram_sample + fram_synthesize call at a time, each call timed on its own."""
+    sc = scenes.single_room()
+    params = api.Params(fs=sc.fs, half_len=sc.half_len)
+    ds = api.DeviceScene(sc, params)
+    N = ds.n_vs_total
+    vs = api.Images(torch.empty((N, 3), device="cuda"), torch.empty((N, 3), device="cuda"),
+                    torch.empty(N, device="cuda"), torch.empty(sc.B, device="cuda"))
+    rir = torch.empty(ds.rir_total, device="cuda")
+    for k in range(5):
+        api.sample(ds, seed=k, out=vs)
+        api.synthesize_raw(ds, vs.pos_hi, vs.pos_lo, vs.g, vs.r, rir=rir)
+    torch.cuda.synchronize()
+    ms = []
+    for k in range(20):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        api.sample(ds, seed=100 + k, out=vs)
+        api.synthesize_raw(ds, vs.pos_hi, vs.pos_lo, vs.g, vs.r, rir=rir)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return {"workload": "single_room (1 room x 1 source x 4 mics, 2000 images, 16 kHz, K=40)",
+            "ms_median": statistics.median(ms), "ms_min": min(ms), "calls": len(ms)}
 
 
 def graph_vs_per_room(torch, api, scenes):
