@@ -205,7 +205,6 @@ static LaunchArgs make_args(const fram_scene* sc, const fram_params* p, const Ws
     a.perm = reinterpret_cast<int32_t*>(base + w.perm);
     a.key = reinterpret_cast<float*>(base + w.key);
     a.skey = reinterpret_cast<int32_t*>(base + w.skey);
-    a.ptmp = reinterpret_cast<int32_t*>(base + w.ptmp);
     a.spa = reinterpret_cast<float4*>(base + w.spa);
     a.spb = reinterpret_cast<float2*>(base + w.spb);
     a.pos32 = reinterpret_cast<int32_t*>(base + w.pos32);

@@ -238,7 +238,8 @@ __device__ __forceinline__ void gather_taps(const float* __restrict__ Gs, int K,
 __host__ __device__ inline int bwd_span(int T) { return T < 1024 ? T : 1024; }
 __host__ __device__ inline int bwd_glen(int T, int K, int margin_i)
 {
-    const int sp = bwd_span(T) > 2 * margin_i + 2 ? bwd_span(T) : 2 * margin_i + 2;   // direct-only span
+    // an image pass needs at most span + 2K + 2 margin + 6; a direct-only pass 2K + 4 margin + 8
+    const int sp = bwd_span(T) > 2 * margin_i + 2 ? bwd_span(T) : 2 * margin_i + 2;
     return (sp + 2 * K + 2 * margin_i + 6 + 3) & ~3;
 }
 __host__ __device__ inline int bwd_warp_floats(int T, int K, int margin_i)
@@ -295,8 +296,8 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool val
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// One pass of an item: sorted positions [p0, p1) (at most 32 kBwdChunks images whose keys span
-// less than bwd_span samples); the gradient is staged over [gb, gb + gl).
+// One pass of an item: sorted positions [p0, p1) (at most 32 kBwdChunks images whose key blocks
+// start less than bwd_span samples apart); the gradient is staged over [gb, gb + gl).
 struct BwdPass {
     int p0, p1, gb, gl;
 };
@@ -319,9 +320,11 @@ __device__ __forceinline__ BwdPass next_pass(const LaunchArgs& a, int64_t v0, in
         }
     }
     P.p1 = p1;
+    // skey is the first sample of a 32-sample key block: keys of block k1 reach k1 + 31, and
+    // k1 - k0 <= span - 32 because both are block starts.
     const int k1 = a.skey[v0 + p1 - 1];
     P.gb = k0 - K - Mg - 2;
-    P.gl = k1 - k0 + 2 * K + 2 * Mg + 6;
+    P.gl = k1 - k0 + 32 + 2 * K + 2 * Mg + 6;
     return P;
 }
 

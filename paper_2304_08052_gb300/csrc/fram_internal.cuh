@@ -227,7 +227,7 @@ struct Header {             // first 256 bytes of the workspace
 };
 
 struct WsLayout {
-    size_t header, room, direct, src_tile, item_off, items, bin_off, perm, key, skey, ptmp;
+    size_t header, room, direct, src_tile, item_off, items, bin_off, perm, key, skey;
     size_t spa, spb, pos32, samp, irec;
     size_t part_mic, part_src, part_r;
     size_t total;
@@ -258,7 +258,6 @@ inline WsLayout ws_layout(const fram_scene& sc, int tile)
     w.perm = take(sizeof(int32_t) * (size_t)sc.n_vs_total);
     w.key = take(sizeof(float) * (size_t)sc.n_vs_total);
     w.skey = take(sizeof(int32_t) * (size_t)sc.n_vs_total);
-    w.ptmp = take(sizeof(int32_t) * (size_t)sc.n_vs_total);
     w.spa = take(sizeof(float) * 4 * (size_t)sc.n_vs_total);
     w.spb = take(sizeof(float) * 2 * (size_t)sc.n_vs_total);
     w.pos32 = take(sizeof(int32_t) * (size_t)sc.B * sc.S * ((size_t)w.nb32 + 1));
@@ -301,10 +300,9 @@ struct LaunchArgs {
     int32_t* item_off;
     int2* items;
     int32_t* bin_off;
-    int32_t* perm;          // per (room, source): image indices sorted by tile, then by floor(key)
+    int32_t* perm;          // per (room, source): image indices sorted by 32-sample key block
     float* key;             // per image: delay to the array centre in samples (binning key)
-    int32_t* skey;          // per sorted position: floor(key), clamped past the last tile
-    int32_t* ptmp;          // scratch for the two-pass sort
+    int32_t* skey;          // per sorted position: first sample of the image's key block
     float4* spa;            // per sorted position: image position hi (x, y, z) and lo x
     float2* spb;            // per sorted position: image position lo (y, z)
     int32_t* pos32;         // per (room, source) and 32-sample block j: first sorted position

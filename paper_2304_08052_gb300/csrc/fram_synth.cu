@@ -9,7 +9,7 @@
 //   2. item_scan       one CTA: prefix sum of S * ntiles_b -> work-item table (room, source, tile).
 //   3. bin_images      one warp per (room, source): each image's delay to the array centre
 //                      (the binning key, in samples), a stable counting sort of the images by
-//                      floor(key) and the first sorted position of every 32-sample key block.
+//                      32-sample key block and the first sorted position of every block.
 //                      Per-mic delays differ from the key by at most the array radius in
 //                      samples ("margin").  sort_positions copies the positions into that
 //                      order; item_ranges writes the per-item records.
@@ -172,17 +172,16 @@ __global__ void __launch_bounds__(1024) item_scan(LaunchArgs a)
     }
 }
 
-// One warp per (room, source): binning keys, a stable counting sort of the images by tile, then
-// a stable counting sort inside each tile by floor(key).  The result: perm (image indices) and
-// skey (a monotone integer key per position), so any delay range of a source's images is one
-// contiguous run, found by binary search.
-__host__ __device__ inline int bin_warp_ints(int max_tiles, int T) { return (max_tiles + 1) + 2 * T; }
-
-__device__ __forceinline__ int tile_of_key(float key, float invT, int nt)
+// One warp per (room, source): binning keys and a stable counting sort of the images by 32-sample
+// key block (ties by image index).  The result: perm (image indices in sorted order), skey (the
+// first sample of each sorted image's block), p32 (the first sorted position of every block) and
+// bin_off (the first sorted position of every tile; the last tile also owns every image keyed
+// beyond the RIR).  Any delay range of a source's images is then one contiguous run.
+__device__ __forceinline__ int block_of_key(float key, int nb)
 {
-    if (!(key < 3.0e9f)) return nt - 1;               // NaN or beyond any RIR: last tile
-    const int t = (int)floorf(key * invT);
-    return t > nt - 1 ? nt - 1 : t;
+    if (!(key < 3.0e9f)) return nb - 1;               // NaN or beyond any RIR: last block
+    const int j = (int)floorf(key) >> 5;
+    return j < 0 ? 0 : (j > nb - 1 ? nb - 1 : j);
 }
 
 __global__ void __launch_bounds__(64) bin_images(LaunchArgs a, const float* __restrict__ pos_hi)
@@ -193,18 +192,17 @@ __global__ void __launch_bounds__(64) bin_images(LaunchArgs a, const float* __re
     if (seg >= (int64_t)a.B * a.S) return;
     const int b = (int)(seg / a.S), s = (int)(seg % a.S);
     const RoomConst rc = a.room[b];
-    const int T = a.tile;
-    int* hist = bin_smem + wib * bin_warp_ints(a.max_tiles, T);
-    int* fine = hist + (a.max_tiles + 1);
+    const int T = a.tile, NB = a.nb32;
+    int* hist = bin_smem + wib * (NB + 1);
     const int n = rc.n_vs, nt = rc.ntiles;
     const int64_t v0 = rc.vs_off + (int64_t)s * n;
-    const float invT = 1.0f / (float)T;
     int* bo = a.bin_off + seg * (a.max_tiles + 1);
+    int* p32 = a.pos32 + seg * ((int64_t)NB + 1);
     if (nt < 1) {   // a room the prologue rejected: no work items reference its bins
         if (lane == 0) bo[0] = 0;
         return;
     }
-    for (int t = lane; t <= nt; t += 32) hist[t] = 0;
+    for (int j = lane; j <= NB; j += 32) hist[j] = 0;
     __syncwarp();
     bool bad = false;
     for (int i = lane; i < n; i += 32) {
@@ -213,14 +211,15 @@ __global__ void __launch_bounds__(64) bin_images(LaunchArgs a, const float* __re
         const float key = sqrtf(dx * dx + dy * dy + dz * dz) * a.q;
         a.key[v0 + i] = key;
         bad = bad || !(key == key) || isinf(key);
-        atomicAdd(&hist[tile_of_key(key, invT, nt)], 1);
+        atomicAdd(&hist[block_of_key(key, NB)], 1);
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&a.hdr->status, FRAM_DEV_NONFINITE);
     __syncwarp();
+    // Exclusive prefix over the blocks -> p32 and the running offsets.
     int carry = 0;
-    for (int base = 0; base < nt; base += 32) {
-        const int t = base + lane;
-        const int v = t < nt ? hist[t] : 0;
+    for (int base = 0; base < NB; base += 32) {
+        const int j = base + lane;
+        const int v = j < NB ? hist[j] : 0;
         int x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -228,89 +227,32 @@ __global__ void __launch_bounds__(64) bin_images(LaunchArgs a, const float* __re
             if (lane >= o) x += y;
         }
         const int excl = carry + x - v;
-        if (t < nt) { bo[t] = excl; hist[t] = excl; }
+        if (j < NB) { p32[j] = excl; hist[j] = excl; }
         carry = __shfl_sync(0xffffffffu, carry + x, 31);
     }
-    if (lane == 0) bo[nt] = carry;
+    if (lane == 0) p32[NB] = n;
+    const int bpt = T >> 5;
+    for (int t = lane; t < nt; t += 32) bo[t] = hist[t * bpt];
+    if (lane == 0) bo[nt] = n;
     __syncwarp();
-    // Pass 1: stable scatter by tile into ptmp (index order within a tile).
+    // Stable scatter by block (index order inside a block).
     for (int base = 0; base < n; base += 32) {
         const int i = base + lane;
         const bool act = i < n;
-        const int t = act ? tile_of_key(a.key[v0 + i], invT, nt) : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, t);
+        const int j = act ? block_of_key(a.key[v0 + i], NB) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, j);
         const int leader = __ffs(peers) - 1;
         const int rank = __popc(peers & ((1u << lane) - 1u));
-        int basepos = (lane == leader && act) ? hist[t] : 0;
+        int basepos = (lane == leader && act) ? hist[j] : 0;
         basepos = __shfl_sync(0xffffffffu, basepos, leader);
         __syncwarp();
-        if (lane == leader && act) hist[t] = basepos + __popc(peers);
+        if (lane == leader && act) hist[j] = basepos + __popc(peers);
         __syncwarp();
-        if (act) a.ptmp[v0 + basepos + rank] = i;
+        if (act) {
+            a.perm[v0 + basepos + rank] = i;
+            a.skey[v0 + basepos + rank] = j << 5;
+        }
     }
-    __syncwarp();
-    // Pass 2: inside each tile, stable counting sort by floor(key) - tile start.  The last tile
-    // also takes every key beyond the RIR, in a doubled bucket range clamped at its end.  p32
-    // receives the first sorted position of every 32-sample key block.
-    int* p32 = a.pos32 + seg * ((int64_t)a.nb32 + 1);
-    for (int t = 0; t < nt; ++t) {
-        const int b0 = bo[t], b1 = bo[t + 1];
-        const int nb = (t == nt - 1) ? 2 * T : T;
-        const int t0 = t * T;
-        if (b1 <= b0) {
-            for (int j = lane; j < nb / 32; j += 32) p32[t0 / 32 + j] = b0;
-            continue;
-        }
-        for (int f = lane; f < nb; f += 32) fine[f] = 0;
-        __syncwarp();
-        for (int p = b0 + lane; p < b1; p += 32) {
-            const float key = a.key[v0 + a.ptmp[v0 + p]];
-            int f = (key < 3.0e9f) ? (int)floorf(key) - t0 : nb - 1;
-            f = f < 0 ? 0 : (f > nb - 1 ? nb - 1 : f);
-            atomicAdd(&fine[f], 1);
-        }
-        __syncwarp();
-        int run = b0;
-        for (int base = 0; base < nb; base += 32) {
-            const int f = base + lane;
-            const int v = fine[f];
-            int x = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            fine[f] = run + x - v;
-            if (lane == 0) p32[(t0 + base) / 32] = run;
-            run = __shfl_sync(0xffffffffu, run + x, 31);
-        }
-        __syncwarp();
-        for (int base = b0; base < b1; base += 32) {
-            const int p = base + lane;
-            const bool act = p < b1;
-            int f = -1, i = 0;
-            if (act) {
-                i = a.ptmp[v0 + p];
-                const float key = a.key[v0 + i];
-                f = (key < 3.0e9f) ? (int)floorf(key) - t0 : nb - 1;
-                f = f < 0 ? 0 : (f > nb - 1 ? nb - 1 : f);
-            }
-            const unsigned peers = __match_any_sync(0xffffffffu, f);
-            const int leader = __ffs(peers) - 1;
-            const int rank = __popc(peers & ((1u << lane) - 1u));
-            int basepos = (lane == leader && act) ? fine[f] : 0;
-            basepos = __shfl_sync(0xffffffffu, basepos, leader);
-            __syncwarp();
-            if (lane == leader && act) fine[f] = basepos + __popc(peers);
-            __syncwarp();
-            if (act) {
-                a.perm[v0 + basepos + rank] = i;
-                a.skey[v0 + basepos + rank] = t0 + f;
-            }
-        }
-        __syncwarp();
-    }
-    for (int j = (nt + 1) * T / 32 + lane; j <= a.nb32; j += 32) p32[j] = n;
 }
 
 // Image positions in sorted order (one CTA per (room, source), coalesced over sorted positions).
@@ -651,7 +593,7 @@ cudaError_t launch_prepare(const LaunchArgs& a, const float* pos_hi, const float
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int64_t segs = (int64_t)a.B * a.S;
     if (segs > 0) {
-        const int sm = (int)(sizeof(int) * 2 * (size_t)bin_warp_ints(a.max_tiles, a.tile));
+        const int sm = (int)(sizeof(int) * 2 * ((size_t)a.nb32 + 1));
         int per_sm = 0;
         if ((e = kernel_residency((const void*)bin_images, 64, sm, &per_sm)) != cudaSuccess) return e;
         bin_images<<<(unsigned)((segs + 1) / 2), 64, sm, st>>>(a, pos_hi);
