@@ -151,54 +151,73 @@ __device__ __forceinline__ ArrB arrival_bwd(int& nc, float delta, float invK, bo
     return r;
 }
 
-// S1 += sum_j G[j] tap_j, S2 += sum_j G[j] dtap_j/dt over the 2K slots j = o + K of one arrival;
-// Gs points at G[base - K].  Compile-time K: every per-slot constant is a literal FMA operand.
+// S1 = sum_j G[j] tap_j, S2 = sum_j G[j] dtap_j/dt over the 2K slots j = o + K of one arrival;
+// Gs points at G[base - K].  With r_j = 1/e_j the per-arrival constants factor out:
+//   S1 = P U0 + a U1 + b U2,   S2 = P' U0 + a' U1 + b' U2 - (P V0 + a V1 + b V2),
+//   U = sum G r (1, C, S),  V = sum G sigma r^2 (1, C, S),
+// so a slot costs one reciprocal, two multiplies and six accumulations.  The two central slots
+// (o = -1, 0), one of which holds the tap nearest to t, stay out of U and V and are added
+// directly (the nearest one with its Taylor-series derivative).  Compile-time K: every per-slot
+// constant is a literal operand.
 struct TapAcc {
-    float s1a, s1b, s2a, s2b;
+    float u0, u1, u2, v0, v1, v2;
 };
 
 template <int KT, int J>
-__device__ __forceinline__ void tap_slot(const float* __restrict__ Gs, const ArrB& r, TapAcc& q)
+__device__ __forceinline__ void tap_slot(const float* __restrict__ Gs, float d, TapAcc& q)
 {
     constexpr int o = J - KT;
-    constexpr float sg = (o & 1) ? -1.0f : 1.0f;
-    constexpr float C = kTrig<KT>.c[J];
-    constexpr float S = kTrig<KT>.s[J];
-    constexpr float kp = -sg * (float)o;
-    const float G = Gs[J];
-    const float e = __fmaf_rn(sg, r.d, kp);
-    const float rc = rcp_approx(e);
-    const float num = __fmaf_rn(C, r.a, __fmaf_rn(S, r.b, r.P));
-    const float dnum = __fmaf_rn(C, r.ap, __fmaf_rn(S, r.bp, r.Pp));
-    const float y = G * rc;
-    const float t = y * num;
-    float& s1 = (J & 1) ? q.s1b : q.s1a;
-    float& s2 = (J & 1) ? q.s2b : q.s2a;
-    s1 += t;
-    if constexpr (o == 0 || o == -1) {
-        const float dg = (dnum - sg * (num * rc)) * rc;
-        const bool near = (o == 0) != r.shifted;
-        s2 = __fmaf_rn(G, near ? r.dnear : dg, s2);
-    } else {
-        s2 = __fmaf_rn(y, dnum, s2);
-        s2 = __fmaf_rn(-sg * t, rc, s2);
+    if constexpr (o != 0 && o != -1) {
+        constexpr float sg = (o & 1) ? -1.0f : 1.0f;
+        constexpr float C = kTrig<KT>.c[J];
+        constexpr float S = kTrig<KT>.s[J];
+        constexpr float kp = -sg * (float)o;
+        const float e = __fmaf_rn(sg, d, kp);
+        const float rc = rcp_approx(e);
+        const float y = Gs[J] * rc;
+        q.u0 += y;
+        q.u1 = __fmaf_rn(C, y, q.u1);
+        q.u2 = __fmaf_rn(S, y, q.u2);
+        const float z = y * rc;
+        q.v0 = __fmaf_rn(sg, z, q.v0);
+        q.v1 = __fmaf_rn(sg * C, z, q.v1);
+        q.v2 = __fmaf_rn(sg * S, z, q.v2);
     }
 }
 
 template <int KT, int... J>
-__device__ __forceinline__ void tap_slots(const float* __restrict__ Gs, const ArrB& r, TapAcc& q,
+__device__ __forceinline__ void tap_slots(const float* __restrict__ Gs, float d, TapAcc& q,
                                           std::integer_sequence<int, J...>)
 {
-    (tap_slot<KT, J>(Gs, r, q), ...);
+    (tap_slot<KT, J>(Gs, d, q), ...);
+}
+
+// One central slot o in {-1, 0}: value and derivative added directly.
+__device__ __forceinline__ void central_slot(float G, int o, float C, float S, const ArrB& r, float& S1, float& S2)
+{
+    const float sg = (o & 1) ? -1.0f : 1.0f;
+    const float e = __fmaf_rn(sg, r.d, -sg * (float)o);
+    const float rc = rcp_approx(e);
+    const float num = __fmaf_rn(C, r.a, __fmaf_rn(S, r.b, r.P));
+    const float dnum = __fmaf_rn(C, r.ap, __fmaf_rn(S, r.bp, r.Pp));
+    const float tap = num * rc;
+    const bool near = (o == 0) != r.shifted;
+    const float dtap = near ? r.dnear : (dnum - sg * tap) * rc;
+    S1 = __fmaf_rn(G, tap, S1);
+    S2 = __fmaf_rn(G, dtap, S2);
 }
 
 template <int KT>
 __device__ __forceinline__ void gather_taps_ct(const float* __restrict__ Gs, const ArrB& r, float& S1, float& S2)
 {
-    TapAcc q{0.f, 0.f, 0.f, 0.f};
-    tap_slots<KT>(Gs, r, q, std::make_integer_sequence<int, 2 * KT>{});
-    S1 = q.s1a + q.s1b;
-    S2 = q.s2a + q.s2b;
+    TapAcc q{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    tap_slots<KT>(Gs, r.d, q, std::make_integer_sequence<int, 2 * KT>{});
+    S1 = __fmaf_rn(r.P, q.u0, __fmaf_rn(r.a, q.u1, r.b * q.u2));
+    S2 = __fmaf_rn(r.Pp, q.u0, __fmaf_rn(r.ap, q.u1, r.bp * q.u2))
+         - __fmaf_rn(r.P, q.v0, __fmaf_rn(r.a, q.v1, r.b * q.v2));
+    constexpr float Cm = kTrig<KT>.c[KT - 1], Sm = kTrig<KT>.s[KT - 1];
+    central_slot(Gs[KT - 1], -1, Cm, Sm, r, S1, S2);
+    central_slot(Gs[KT], 0, 1.0f, 0.0f, r, S1, S2);
 }
 
 // Any K: the same taps, cos/sin(pi o/K) from a shared table.
@@ -355,7 +374,7 @@ __device__ __forceinline__ void stage_g(float* Gs, const float* grad_rir, const 
 }
 
 template <int KT>
-__global__ void __launch_bounds__(kBwdThreads, 4) bwd_kernel(LaunchArgs a, const float* __restrict__ grad_rir,
+__global__ void __launch_bounds__(kBwdThreads, 5) bwd_kernel(LaunchArgs a, const float* __restrict__ grad_rir,
                                                              const float* __restrict__ grad_early,
                                                              float* __restrict__ grad_vs)
 {
