@@ -35,9 +35,9 @@ METRIC = "multi-ch RIRs/s and sinc-taps/s (fwd, fwd+bwd) at 1 GB300, % of roofli
 # forward 8 FP32-pipe operations and 1 reciprocal on the MUFU (special function) pipe; adjoint
 # 14 FP32 and 1 MUFU.  Per arrival (image x mic) 40 FP32 + 6 MUFU more, spread over its 2K+1 taps.
 # DRAM bytes (read + write) of one synth_kernel launch per output sample, from one ncu capture
-# (large_4096, first 256 rooms, 283357184 output samples: 0.0819 GB read + 1.0746 GB written);
+# (large_4096, first 256 rooms, 283357184 output samples: 0.0825 GB read + 1.0746 GB written);
 # reported only while the synthesis source is the one that was measured (its SHA-256 prefix).
-SYNTH_TRAFFIC = {"source_sha256": "91c882def67a3177", "bytes_per_sample": (0.0819e9 + 1.0746e9) / 283357184}
+SYNTH_TRAFFIC = {"source_sha256": "493a3c033a1bdeac", "bytes_per_sample": (0.0825e9 + 1.0746e9) / 283357184}
 
 # Kernels of libfram per fwd step: sample_kernel; room_prologue, item_scan, bin_images,
 # sort_positions, item_ranges (preparation); amp_gather, synth_kernel (synthesis).
