@@ -108,6 +108,15 @@ def _batch(name, seed, B, S, M, geometry, radius, dims_lo, dims_hi, t60_lo, t60_
                  dict(seed=seed, geometry=geometry, radius=radius))
 
 
+def make_batch(name, seed, B, S, M, geometry, radius, dims_lo, dims_hi, t60_lo, t60_hi, fs, K,
+               images_per_second=None, images_fixed=None) -> Scene:
+    """A seeded batch of rooms: dims uniform in [dims_lo, dims_hi], T60 uniform in [t60_lo, t60_hi],
+    a linear or circular array of M mics at a random position >= 0.5 m from the walls, S sources
+    uniform in the room, round(images_per_second * T60) (or images_fixed) images per source."""
+    return _batch(name, seed, B, S, M, geometry, radius, dims_lo, dims_hi, t60_lo, t60_hi, fs, K,
+                  images_per_second=images_per_second, images_fixed=images_fixed)
+
+
 def single_room() -> Scene:
     """6x5x3 m, T60 0.5 s, one source, 4-mic linear array, 2000 images, 16 kHz, K = 40."""
     mic = _linear_array([4.0, 2.5, 1.2], 4, 0.05)
