@@ -13,6 +13,9 @@ Functions and the passages they follow:
   sample(scene, params, seed) Eq. 3-6 and Sec. III-B: image positions and reflection counts
   synthesize(...)             Eq. 1 with windowed-sinc fractional delays; Eq. 9 early RIR
   backward(...)               analytic gradient of a loss on h (and h_e)
+  synthesize_mr(...)          the paper's multi-rate output path (Sec. II-B, Eq. 7-9): impulses
+                              on the r_h fs grid, down to r_l fs, 80 Hz high-pass, down to fs
+  mr_rates, resample_filter, hpf_coeffs   its rates and filters (readings: see fram_oracle.c)
 
 Every function is pinned by tests that do not reuse its own arithmetic (see the module
 docstrings of tests/test_oracle_*.py).  No function here is "parity unpinned".
@@ -212,3 +215,44 @@ def backward(scene, params: Params, vs_pos, vs_g, r, grad_rir, grad_early=None):
     if rc != 0:
         raise ValueError("oracle backward: invalid parameters")
     return gv, gm, gs, gr
+
+
+def mr_rates(fs: float):
+    """(r_h, r_l) = (floor(1e6 / fs), floor(sqrt(r_h))) (Sec. II-B)."""
+    rh, rl = ctypes.c_int32(), ctypes.c_int32()
+    _load().fo_mr_rates(ctypes.c_double(fs), ctypes.byref(rh), ctypes.byref(rl))
+    return rh.value, rl.value
+
+
+def resample_filter(up: int, down: int) -> np.ndarray:
+    """The resampling FIR for a reduced ratio up/down, centred: F[m + HL], |m| <= HL."""
+    L = _load()
+    L.fo_resample_filter.restype = ctypes.c_int32
+    hl = L.fo_resample_filter(ctypes.c_int32(up), ctypes.c_int32(down), None)
+    F = np.empty(2 * hl + 1)
+    L.fo_resample_filter(ctypes.c_int32(up), ctypes.c_int32(down), _p(F))
+    return F
+
+
+def hpf_coeffs(fc: float, fsr: float):
+    """(b, a) of the 2nd-order Butterworth high-pass (bilinear transform, pre-warped)."""
+    b, a = np.empty(3), np.empty(3)
+    _load().fo_hpf_coeffs(ctypes.c_double(fc), ctypes.c_double(fsr), _p(b), _p(a))
+    return b, a
+
+
+def synthesize_mr(scene, params: Params, vs_pos, vs_g, r, early: bool = False):
+    """FP64 RIRs of the paper's multi-rate path, in the layout of synthesize()."""
+    rir_len, rir_off, vs_off, src, mic, n_vs = _scene_arrays(scene, params)
+    vs_pos, vs_g, r = _f64(vs_pos).reshape(-1, 3), _f64(vs_g).reshape(-1), _f64(r).reshape(-1)
+    assert vs_pos.shape[0] == vs_off[-1] and vs_g.shape[0] == vs_off[-1] and r.shape[0] == scene.B
+    rt60 = _f64(np.asarray(scene.rt60, dtype=np.float32))
+    rir = np.empty(int(rir_off[-1]))
+    he = np.empty(int(rir_off[-1])) if early else None
+    pc = params._c()
+    rc = _load().fo_synthesize_mr(ctypes.c_int32(scene.B), ctypes.c_int32(scene.S), ctypes.c_int32(scene.M),
+                                  _p(src), _p(mic), _p(rt60), _p(n_vs), _p(vs_off), _p(rir_len), _p(rir_off),
+                                  _p(vs_pos), _p(vs_g), _p(r), ctypes.byref(pc), _p(rir), _p(he))
+    if rc != 0:
+        raise ValueError("oracle synthesize_mr: invalid parameters or out of memory")
+    return (rir, he) if early else rir

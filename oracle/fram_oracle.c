@@ -27,6 +27,9 @@
  *                     Eq. 9 as a mask on h.
  *   fo_backward       analytic gradient of a loss on h (and h_e) with respect to source, mic
  *                     and virtual-source positions and the reflection coefficient.
+ *   fo_synthesize_mr  the paper's own multi-rate output path (Sec. II-B, Eq. 7-9): impulses
+ *                     quantised to the r_h fs grid, resampled to r_l fs, high-passed at 80 Hz,
+ *                     resampled to fs (filter readings stated with the function).
  *
  * Parity pins (what fixes each function independently of itself) live in the tests:
  *   Philox against the curand host generator; Eq. 2 against Eyring's reverberation formula;
@@ -384,6 +387,195 @@ int fo_backward(int32_t B, int32_t S, int32_t M, const double* src, const double
         free(G);
     }
     return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Multi-rate output path as the paper prints it (Sec. II-B, Eq. 7-9): impulses on a grid  */
+/* at the high rate r_h fs, q = min(ceil(D r_h fs / c0), L_h - 1), L_h = ceil(T60 r_h fs),  */
+/* h[q] += r^g / D; then down to r_l fs, an 80 Hz high-pass, and down to fs, with          */
+/* r_h = floor(1e6 / fs), r_l = floor(sqrt(r_h)).  The paper does not specify the filters;  */
+/* the readings used here:                                                                 */
+/*   resampling by up/down (reduced): y[k] = sum_n x[n] F(k down - n up), F centred (zero   */
+/*     phase), F(m) = lowpass with cutoff pi / max(up, down) times a Kaiser window (beta 5) */
+/*     on |m| <= HL = 10 max(up, down), scaled so that sum_m F(m) = up;                     */
+/*   the high-pass: 2nd-order Butterworth at 80 Hz, bilinear transform with the cutoff     */
+/*     pre-warped, run forward from a zero state over the intermediate signal;             */
+/*   signal lengths: intermediate L_m = ceil(L_h up / down) (zero outside), output L =      */
+/*     ceil(T60 fs) as in the continuous path.                                              */
+/* ------------------------------------------------------------------------------------ */
+
+void fo_mr_rates(double fs, int32_t* rh, int32_t* rl)
+{
+    *rh = (int32_t)floor(1.0e6 / fs);
+    *rl = (int32_t)floor(sqrt((double)*rh));
+}
+
+static int32_t fo_gcd(int32_t a, int32_t b)
+{
+    while (b) { int32_t t = a % b; a = b; b = t; }
+    return a;
+}
+
+/* Modified Bessel function I0 by its power series sum_k ((x/2)^k / k!)^2. */
+static double fo_bessel_i0(double x)
+{
+    double sum = 1.0, term = 1.0;
+    for (int k = 1; k < 500; ++k) {
+        term *= (x / (2.0 * k)) * (x / (2.0 * k));
+        sum += term;
+        if (term < 1e-18 * sum) break;
+    }
+    return sum;
+}
+
+/* The resampling filter for a reduced ratio up/down: F[m + HL] for |m| <= HL.  Returns HL. */
+int32_t fo_resample_filter(int32_t up, int32_t down, double* F /* [2 HL + 1], may be NULL */)
+{
+    const int32_t mx = up > down ? up : down;
+    const int32_t HL = 10 * mx;
+    if (!F) return HL;
+    const double beta = 5.0, i0b = fo_bessel_i0(beta);
+    double sum = 0.0;
+    for (int32_t m = -HL; m <= HL; ++m) {
+        const double x = (double)m / (double)mx;                   /* lowpass, cutoff pi / mx */
+        const double lp = fo_sinc(x) / (double)mx;
+        const double rr = (double)m / (double)HL;
+        const double w = fo_bessel_i0(beta * sqrt(fmax(0.0, 1.0 - rr * rr))) / i0b;
+        F[m + HL] = lp * w;
+        sum += F[m + HL];
+    }
+    for (int32_t m = 0; m <= 2 * HL; ++m) F[m] *= (double)up / sum;
+    return HL;
+}
+
+/* 2nd-order Butterworth high-pass at fc for sample rate fsr (bilinear, pre-warped):
+ * H(z) = (b0 + b1 z^-1 + b2 z^-2) / (1 + a1 z^-1 + a2 z^-2). */
+void fo_hpf_coeffs(double fc, double fsr, double b[3], double a[3])
+{
+    const double k = tan(FO_PI * fc / fsr);
+    const double s2 = sqrt(2.0);
+    const double den = 1.0 + s2 * k + k * k;
+    b[0] = 1.0 / den;
+    b[1] = -2.0 / den;
+    b[2] = 1.0 / den;
+    a[0] = 1.0;
+    a[1] = 2.0 * (k * k - 1.0) / den;
+    a[2] = (1.0 - s2 * k + k * k) / den;
+}
+
+/* One channel: the high-rate impulses (q_j, A_j) -> y[0, L) at fs. */
+static void fo_mr_channel(int64_t nimp, const int64_t* q, const double* A, int64_t Lh, int32_t upA, int32_t downA,
+                          const double* FA, int32_t HLA, int32_t rl, const double* FC, int32_t HLC,
+                          const double hb[3], const double ha[3], int32_t L, double* y, double* z /* [Lm] */)
+{
+    const int64_t Lm = (Lh * upA + downA - 1) / downA;
+    for (int64_t k = 0; k < Lm; ++k) z[k] = 0.0;
+    /* stage A: y1[k] = sum_j A_j F_A(k downA - q_j upA) */
+    for (int64_t j = 0; j < nimp; ++j) {
+        const int64_t c = q[j] * upA;
+        int64_t k0 = (c - HLA + downA - 1) / downA;     /* ceil for c - HLA >= 0 */
+        if (c - HLA < 0) k0 = -((HLA - c) / downA);      /* ceil of a negative ratio */
+        for (int64_t k = k0; k * downA - c <= HLA; ++k) {
+            if (k < 0 || k >= Lm) continue;
+            const int64_t m = k * downA - c;
+            if (m >= -HLA) z[k] += A[j] * FA[m + HLA];
+        }
+    }
+    /* the high-pass, in place */
+    double x1 = 0.0, x2 = 0.0, y1 = 0.0, y2 = 0.0;
+    for (int64_t k = 0; k < Lm; ++k) {
+        const double x0 = z[k];
+        const double y0 = hb[0] * x0 + hb[1] * x1 + hb[2] * x2 - ha[1] * y1 - ha[2] * y2;
+        x2 = x1; x1 = x0; y2 = y1; y1 = y0;
+        z[k] = y0;
+    }
+    /* stage C: y[n] = sum_k z[k] F_C(n rl - k) */
+    for (int32_t n = 0; n < L; ++n) {
+        double acc = 0.0;
+        for (int64_t k = (int64_t)n * rl - HLC; k <= (int64_t)n * rl + HLC; ++k)
+            if (k >= 0 && k < Lm) acc += z[k] * FC[(int64_t)n * rl - k + HLC];
+        y[n] = acc;
+    }
+}
+
+/*
+ * The multi-rate RIRs (and early RIRs, Eq. 9 applied on the high-rate grid around
+ * n0 = ceil(D_{0,m} r_h fs / c0)) in the layout of fo_synthesize.  Returns -1 on bad
+ * parameters, -2 when out of memory.
+ */
+int fo_synthesize_mr(int32_t B, int32_t S, int32_t M, const double* src, const double* mic, const double* rt60,
+                     const int32_t* n_vs, const int64_t* vs_off, const int32_t* rir_len, const int64_t* rir_off,
+                     const double* vs_pos, const double* vs_g, const double* r, const fo_params* P,
+                     double* rir, double* early)
+{
+    int32_t rh, rl;
+    fo_mr_rates(P->fs, &rh, &rl);
+    if (rh < 1 || rl < 1) return -1;
+    const int32_t g = fo_gcd(rh, rl), upA = rl / g, downA = rh / g;
+    const int32_t HLA = fo_resample_filter(upA, downA, NULL), HLC = fo_resample_filter(1, rl, NULL);
+    double* FA = (double*)malloc(sizeof(double) * (size_t)(2 * HLA + 1));
+    double* FC = (double*)malloc(sizeof(double) * (size_t)(2 * HLC + 1));
+    if (!FA || !FC) { free(FA); free(FC); return -2; }
+    fo_resample_filter(upA, downA, FA);
+    fo_resample_filter(1, rl, FC);
+    double hb[3], ha[3];
+    fo_hpf_coeffs(80.0, (double)rl * P->fs, hb, ha);
+    const double fh = (double)rh * P->fs;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t b = 0; b < B; ++b) {
+        const int32_t L = rir_len[b];
+        const int64_t Lh = (int64_t)ceil(rt60[b] * fh);
+        const int64_t Lm = (Lh * upA + downA - 1) / downA;
+        const int64_t n = n_vs[b] + 1;
+        int64_t* q = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+        int64_t* qe = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+        double* A = (double*)malloc(sizeof(double) * (size_t)n);
+        double* Ae = (double*)malloc(sizeof(double) * (size_t)n);
+        double* z = (double*)malloc(sizeof(double) * (size_t)(Lm > 0 ? Lm : 1));
+        if (!q || !qe || !A || !Ae || !z) {
+#pragma omp atomic write
+            err = 1;
+        } else {
+            for (int32_t s = 0; s < S; ++s) {
+                const double* ps = src + 3 * ((int64_t)b * S + s);
+                for (int32_t m = 0; m < M; ++m) {
+                    const double* pm = mic + 3 * ((int64_t)b * M + m);
+                    /* Eq. 7-8: the direct path (g = 0), then the images in ascending i */
+                    const double D0m = fo_dist(ps, pm);
+                    int64_t cnt = 0;
+                    q[cnt] = (int64_t)ceil(D0m / P->c0 * fh);
+                    if (q[cnt] > Lh - 1) q[cnt] = Lh - 1;
+                    A[cnt++] = 1.0 / D0m;
+                    for (int32_t i = 0; i < n_vs[b]; ++i) {
+                        const int64_t v = vs_off[b] + (int64_t)s * n_vs[b] + i;
+                        const double D = fo_dist(vs_pos + 3 * v, pm);
+                        int64_t qi = (int64_t)ceil(D / P->c0 * fh);
+                        if (qi > Lh - 1) qi = Lh - 1;
+                        q[cnt] = qi;
+                        A[cnt++] = pow(r[b], vs_g[v]) / D;
+                    }
+                    double* h = rir + rir_off[b] + ((int64_t)s * M + m) * L;
+                    fo_mr_channel(cnt, q, A, Lh, upA, downA, FA, HLA, rl, FC, HLC, hb, ha, L, h, z);
+                    if (early) {
+                        /* Eq. 9 on the high-rate grid */
+                        const int64_t n0 = (int64_t)ceil(D0m / P->c0 * fh);
+                        const int64_t lo = n0 - (int64_t)ceil(P->early_pre_ms * fh / 1000.0);
+                        const int64_t hi = n0 + (int64_t)ceil(P->early_post_ms * fh / 1000.0);
+                        int64_t ce = 0;
+                        for (int64_t j = 0; j < cnt; ++j)
+                            if (q[j] >= lo && q[j] <= hi) { qe[ce] = q[j]; Ae[ce++] = A[j]; }
+                        double* he = early + rir_off[b] + ((int64_t)s * M + m) * L;
+                        fo_mr_channel(ce, qe, Ae, Lh, upA, downA, FA, HLA, rl, FC, HLC, hb, ha, L, he, z);
+                    }
+                }
+            }
+        }
+        free(q); free(qe); free(A); free(Ae); free(z);
+    }
+    free(FA);
+    free(FC);
+    return err ? -2 : 0;
 }
 
 int fo_num_threads(void)
