@@ -55,7 +55,7 @@ extern "C" {
  * Method constants.  The paper fixes only their ranges: 0 <= alpha < beta <= 1 (Eq. 3),
  * tau > 0 (Eq. 6), and the [-6, 50] ms early window (Eq. 9).  fram_default_params fills
  * this project's defaults: alpha 0.25, beta 1, a -2, b 2, tau 0.25, c0 343 m/s, fs 16 kHz,
- * K 40, early window 6 / 50 ms, tile 0 (library default).
+ * K 40, early window 6 / 50 ms, tile 0 (library default), delay_mode 0.
  */
 typedef struct fram_params {
     double alpha;          /* Eq. 3: distance ratios are drawn on (alpha, beta]; alpha > 0 */
@@ -71,6 +71,18 @@ typedef struct fram_params {
     int32_t tile;          /* synthesis tile length in samples (multiple of 256, 256..4096); */
                            /* 0 = the tile fram_autotune chose for this kind of workload,  */
                            /* else 1024; size workspaces with 0 to allow any tile          */
+    int32_t delay_mode;    /* 0: continuous delay t = D fs/c0, windowed sinc at fs (default; */
+                           /*    differentiable).                                            */
+                           /* 1: the paper's multi-rate path (Sec. II-B, Eq. 7-9 as printed): */
+                           /*    impulses at q = min(ceil(D r_h fs/c0), L_h - 1) on the r_h fs */
+                           /*    grid (r_h = floor(1e6/fs), L_h = ceil(T60 r_h fs)), resampled */
+                           /*    to r_l fs (r_l = floor(sqrt(r_h)), must be 2..11), 80 Hz      */
+                           /*    high-pass, resampled to fs; the same output layout.  Filters */
+                           /*    (not given in the paper): Kaiser (beta 5) windowed-sinc       */
+                           /*    polyphase resamplers of half length 10 max(up, down), DC gain */
+                           /*    up; 2nd-order Butterworth high-pass (bilinear, pre-warped).   */
+                           /*    Forward only: fram_synthesize_backward returns FRAM_EINVAL.  */
+    int32_t reserved;      /* must be 0                                                     */
 } fram_params;
 
 /*

@@ -32,7 +32,8 @@ class FramParams(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("a", ctypes.c_double),
                 ("b", ctypes.c_double), ("tau", ctypes.c_double), ("c0", ctypes.c_double),
                 ("fs", ctypes.c_double), ("early_pre_ms", ctypes.c_double), ("early_post_ms", ctypes.c_double),
-                ("half_len", ctypes.c_int32), ("tile", ctypes.c_int32)]
+                ("half_len", ctypes.c_int32), ("tile", ctypes.c_int32), ("delay_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class FramScene(ctypes.Structure):

@@ -39,10 +39,12 @@ class Params:
     early_pre_ms: float = 6.0
     early_post_ms: float = 50.0
     tile: int = 0
+    delay_mode: int = 0          # 1 = the paper's multi-rate output path (forward only)
 
     def c(self) -> FramParams:
         return FramParams(self.alpha, self.beta, self.a, self.b, self.tau, self.c0, self.fs,
-                          self.early_pre_ms, self.early_post_ms, int(self.half_len), int(self.tile))
+                          self.early_pre_ms, self.early_post_ms, int(self.half_len), int(self.tile),
+                          int(self.delay_mode), 0)
 
 
 def layout(rt60, n_vs, S: int, M: int, fs: float):

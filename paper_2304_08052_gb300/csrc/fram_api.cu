@@ -98,6 +98,12 @@ static int check_params(const fram_params* p)
     if (!(p->early_pre_ms >= 0.0) || !(p->early_post_ms >= 0.0)) return fail(FRAM_EINVAL, "early window must be >= 0");
     if (p->tile != 0 && (p->tile < 256 || p->tile > 4096 || p->tile % 256 != 0))
         return fail(FRAM_EINVAL, "tile must be 0 or a multiple of 256 in [256, 4096]");
+    if (p->delay_mode != 0 && p->delay_mode != 1) return fail(FRAM_EINVAL, "delay_mode must be 0 or 1");
+    if (p->delay_mode == 1) {
+        const int rh = (int)std::floor(1.0e6 / p->fs), rl = (int)std::floor(std::sqrt((double)rh));
+        if (rl < 2 || rl > 11)
+            return fail(FRAM_EINVAL, "delay_mode 1 needs r_l = floor(sqrt(floor(1e6/fs))) in [2, 11] (fs = %g)", p->fs);
+    }
     return FRAM_OK;
 }
 
@@ -165,7 +171,7 @@ static int check_scene(const fram_scene* sc, bool need_arrays)
 
 static int check_ws(const fram_scene* sc, const fram_params* p, void* ws, size_t bytes, WsLayout* out)
 {
-    const WsLayout w = ws_layout(*sc, tile_for(sc, p));
+    const WsLayout w = ws_layout(*sc, tile_for(sc, p), p->delay_mode, p->fs);
     if (w.max_tiles > 0xffff) return fail(FRAM_EINVAL, "too many tiles per RIR (raise the tile length)");
     if (!ws) return fail(FRAM_EWORKSPACE, "workspace is null");
     if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(FRAM_EWORKSPACE, "workspace must be 256-byte aligned");
@@ -213,6 +219,18 @@ static LaunchArgs make_args(const fram_scene* sc, const fram_params* p, const Ws
     a.part_mic = reinterpret_cast<float*>(base + w.part_mic);
     a.part_src = reinterpret_cast<float*>(base + w.part_src);
     a.part_r = reinterpret_cast<float*>(base + w.part_r);
+    a.mode = p->delay_mode;
+    a.early_pre_ms = p->early_pre_ms;
+    a.early_post_ms = p->early_post_ms;
+    if (p->delay_mode == 1) {
+        const MrRates mr = mr_rates(p->fs);
+        a.rh = mr.rh; a.rl = mr.rl; a.up = mr.up; a.down = mr.down;
+        a.HLA = 10 * (mr.up > mr.down ? mr.up : mr.down);
+        a.fh = (double)mr.rh * p->fs;
+        a.mr_y = reinterpret_cast<float*>(base + w.mr_y);
+        a.mr_ye = reinterpret_cast<float*>(base + w.mr_ye);
+        a.mr_tab = reinterpret_cast<float*>(base + w.mr_tab);
+    }
     return a;
 }
 
@@ -240,6 +258,8 @@ void fram_default_params(fram_params* p)
     p->early_post_ms = 50.0;
     p->half_len = 40;
     p->tile = 0;
+    p->delay_mode = 0;
+    p->reserved = 0;
 }
 
 int fram_layout(int32_t B, int32_t S, int32_t M, double fs, const float* rt60, const int32_t* n_vs,
@@ -269,7 +289,7 @@ int fram_workspace_size(const fram_scene* scene, const fram_params* p, size_t* b
     if ((rc = check_params(p)) != FRAM_OK) return rc;
     if ((rc = check_scene(scene, false)) != FRAM_OK) return rc;
     if (!bytes) return fail(FRAM_EINVAL, "bytes is null");
-    const WsLayout w = ws_layout(*scene, tile_of(p));
+    const WsLayout w = ws_layout(*scene, tile_of(p), p->delay_mode, p->fs);
     if (w.max_tiles > 0xffff) return fail(FRAM_EINVAL, "too many tiles per RIR (raise the tile length)");
     *bytes = w.total;
     return FRAM_OK;
@@ -337,7 +357,12 @@ int fram_synthesize_prepared(const fram_scene* scene, const fram_params* p, cons
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(&a.hdr->queue, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return cuda_fail(e, "fram_synthesize: resetting the work counter");
-    e = launch_synthesize(a, vs_pos_hi, vs_pos_lo, vs_g, rir, early, st);
+    if (p->delay_mode == 1) {
+        e = launch_amp_gather(a, vs_g, st);     // r^g in sorted order
+        if (e == cudaSuccess) e = launch_synthesize_mr(a, vs_pos_hi, vs_pos_lo, rir, early, st);
+    } else {
+        e = launch_synthesize(a, vs_pos_hi, vs_pos_lo, vs_g, rir, early, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "fram_synthesize: launch");
     return FRAM_OK;
 }
@@ -365,6 +390,8 @@ int fram_synthesize_backward_prepared(const fram_scene* scene, const fram_params
     WsLayout w;
     int rc = common_checks(scene, p, vs_pos_hi, vs_g, r, workspace, workspace_bytes, &w);
     if (rc != FRAM_OK) return rc;
+    if (p->delay_mode != 0)
+        return fail(FRAM_EINVAL, "the multi-rate path (delay_mode 1) quantises delays and has no adjoint; use delay_mode 0");
     if (scene->B == 0) return FRAM_OK;
     const LaunchArgs a = make_args(scene, p, w, workspace);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -384,6 +411,8 @@ int fram_synthesize_backward(const fram_scene* scene, const fram_params* p, cons
     WsLayout w;
     int rc = common_checks(scene, p, vs_pos_hi, vs_g, r, workspace, workspace_bytes, &w);
     if (rc != FRAM_OK) return rc;
+    if (p->delay_mode != 0)
+        return fail(FRAM_EINVAL, "the multi-rate path (delay_mode 1) quantises delays and has no adjoint; use delay_mode 0");
     if ((rc = fram_prepare(scene, p, vs_pos_hi, vs_pos_lo, r, workspace, workspace_bytes, stream)) != FRAM_OK)
         return rc;
     return fram_synthesize_backward_prepared(scene, p, vs_pos_hi, vs_pos_lo, vs_g, r, grad_rir, grad_early, grad_vs,
@@ -411,7 +440,7 @@ int fram_autotune(const fram_scene* scene, const fram_params* p, const float* vs
     for (int T : kTileCandidates) {
         fram_params cand = *p;
         cand.tile = T;
-        const WsLayout w = ws_layout(*scene, T);
+        const WsLayout w = ws_layout(*scene, T, p->delay_mode, p->fs);
         if (w.max_tiles > 0xffff || w.total > workspace_bytes) continue;
         if (synth_smem_total(T) > 227 * 1024) continue;
         rc = fram_synthesize(scene, &cand, vs_pos_hi, vs_pos_lo, vs_g, r, rir, nullptr, workspace, workspace_bytes,

@@ -11,6 +11,7 @@
 //   * the workspace layout shared by the sampler, the synthesis and the adjoint.
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -207,6 +208,9 @@ struct DirectConst {        // per (room, source, mic)
     float ex, ey, ez;       // (src - mic) / D_{0,m}
     int32_t early_lo;       // Eq. 9 window, inclusive
     int32_t early_hi;
+    int32_t q_h;            // multi-rate mode: ceil(D_{0,m} / c0 * r_h fs) (before the clamp)
+    int32_t early_lo_h;     // multi-rate mode: Eq. 9 window on the high-rate grid, inclusive
+    int32_t early_hi_h;
     int32_t pad_;
 };
 
@@ -229,6 +233,7 @@ struct Header {             // first 256 bytes of the workspace
 struct WsLayout {
     size_t header, room, direct, src_tile, item_off, items, bin_off, perm, key, skey;
     size_t spa, spb, pos32, samp, irec;
+    size_t mr_y, mr_ye, mr_tab;     // multi-rate mode: intermediate signals, resampling table
     size_t part_mic, part_src, part_r;
     size_t total;
     int tile;
@@ -239,7 +244,25 @@ struct WsLayout {
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-inline WsLayout ws_layout(const fram_scene& sc, int tile)
+// Multi-rate mode rates: r_h = floor(1e6 / fs), r_l = floor(sqrt(r_h)); the first resampling
+// ratio up/down = r_l/r_h reduced.
+struct MrRates {
+    int rh, rl, up, down;
+};
+
+inline MrRates mr_rates(double fs)
+{
+    MrRates r;
+    r.rh = (int)floor(1.0e6 / fs);
+    r.rl = (int)floor(sqrt((double)r.rh));
+    int a = r.rh, b = r.rl;
+    while (b) { const int t = a % b; a = b; b = t; }
+    r.up = r.rl / a;
+    r.down = r.rh / a;
+    return r;
+}
+
+inline WsLayout ws_layout(const fram_scene& sc, int tile, int delay_mode = 0, double fs = 16000.0)
 {
     WsLayout w{};
     w.tile = tile;
@@ -263,6 +286,15 @@ inline WsLayout ws_layout(const fram_scene& sc, int tile)
     w.pos32 = take(sizeof(int32_t) * (size_t)sc.B * sc.S * ((size_t)w.nb32 + 1));
     w.samp = take(sizeof(float) * (size_t)sc.n_vs_total);
     w.irec = take(sizeof(ItemRec) * (size_t)w.max_items);
+    if (delay_mode == 1) {
+        // per channel (room, source, mic): r_l L_b + 8 intermediate samples, and the same for
+        // the early RIR; the polyphase table is down x 32 floats.
+        const MrRates mr = mr_rates(fs);
+        const size_t inter = (size_t)mr.rl * (size_t)sc.rir_total + 8 * (size_t)sc.B * sc.S * sc.M;
+        w.mr_y = take(sizeof(float) * inter);
+        w.mr_ye = take(sizeof(float) * inter);
+        w.mr_tab = take(sizeof(float) * 32 * (size_t)mr.down);
+    }
     w.part_mic = take(sizeof(float) * 3 * (size_t)w.max_items * sc.M);
     w.part_src = take(sizeof(float) * 3 * (size_t)w.max_items);
     w.part_r = take(sizeof(float) * (size_t)w.max_items);
@@ -309,6 +341,14 @@ struct LaunchArgs {
                             // whose key is >= 32 j (rows of nb32 + 1 entries)
     float* samp;            // per sorted position: r^g of the image (written per synthesis)
     ItemRec* irec;          // per work item
+    // multi-rate mode (delay_mode 1)
+    int32_t mode;
+    int32_t rh, rl, up, down, HLA;   // rates, first resampling ratio, its filter's half length
+    double fh;                       // r_h fs
+    double early_pre_ms, early_post_ms;
+    float* mr_y;                     // intermediate signals at r_l fs, per channel
+    float* mr_ye;                    // the same for the early RIR
+    float* mr_tab;                   // first resampling filter, polyphase rows of 32
     float* part_mic;
     float* part_src;
     float* part_r;
@@ -321,6 +361,9 @@ cudaError_t launch_prepare(const LaunchArgs& a, const float* pos_hi, const float
                            cudaStream_t st);
 cudaError_t launch_synthesize(const LaunchArgs& a, const float* pos_hi, const float* pos_lo, const float* g,
                               float* rir, float* early, cudaStream_t st);
+cudaError_t launch_amp_gather(const LaunchArgs& a, const float* g, cudaStream_t st);
+cudaError_t launch_synthesize_mr(const LaunchArgs& a, const float* pos_hi, const float* pos_lo, float* rir,
+                                 float* early, cudaStream_t st);
 cudaError_t launch_backward(const LaunchArgs& a, const float* pos_hi, const float* pos_lo, const float* g,
                             const float* r, const float* grad_rir, const float* grad_early, float* grad_vs,
                             float* grad_mic, float* grad_src, float* grad_r, cudaStream_t st);

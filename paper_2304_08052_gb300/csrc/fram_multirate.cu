@@ -1,0 +1,426 @@
+// fram_multirate.cu -- the paper's own multi-rate output path (delay_mode 1; Sec. II-B and
+// Eq. 7-9 as printed).
+//
+// Every arrival (direct path with g = 0, then the images) is an impulse r^g / D at
+//   q = min(ceil(D / c0 * r_h fs), L_h - 1),   L_h = ceil(T60 r_h fs),
+// on a grid at the high rate r_h fs (r_h = floor(1e6 / fs), about 1 MHz).  That impulse train is
+// resampled to r_l fs (r_l = floor(sqrt(r_h))), high-passed at 80 Hz and resampled to fs.  The
+// paper does not give the filters; this library uses a Kaiser (beta 5) windowed-sinc polyphase
+// resampler of half length 10 max(up, down) with DC gain `up`, and a 2nd-order Butterworth
+// high-pass (bilinear transform, cutoff pre-warped), run forward from a zero state.
+//
+// The ~1 MHz train is never built.  With the first ratio up/down (reduced r_l/r_h), the
+// intermediate signal is y1[k] = sum_j A_j F(k down - q_j up): each impulse touches at most 21
+// consecutive intermediate samples (|m| <= 10 down).
+//   mr_table        the first filter F in polyphase rows: row p holds F(p - HL + i down),
+//                   i = 0..31, so the 21 taps of one impulse are one row read by 32 lanes.
+//   mr_stage_a      persistent warps over (room, source, tile, mic, sub-tile of 256 r_l
+//                   intermediate samples); the images that can reach the sub-tile come from the
+//                   32-sample key blocks; each lane evaluates one image's q in FP64 (the grid
+//                   decides an integer: the same operations in the same order as an FP64
+//                   reference, no fused multiply-add), then each impulse is added with one lane
+//                   per tap into the warp's shared buffer (and into the early buffer when q lies
+//                   in the Eq. 9 window on the high-rate grid).  Tiles go to y1 in global memory.
+//   mr_hpf_down     one thread per channel: the high-pass recursion with its state as float
+//                   pairs (poles near z = 1 at 80 Hz make a float32 recursion lose ~1e-5 of the
+//                   peak), and the second resampler (ratio 1/r_l, compile-time taps) as 21
+//                   running output accumulators, streaming y1 once.
+#include <cmath>
+#include <utility>
+
+#include "fram_internal.cuh"
+
+namespace fram {
+namespace {
+
+constexpr int kMrThreads = 256;
+constexpr int kMrNJ = 32;        // polyphase row length (>= 21 taps per impulse)
+
+// ---- the second resampler (ratio 1/RL): compile-time Kaiser windowed sinc --------------------
+constexpr double cx_pi = 3.14159265358979323846;
+
+constexpr double cx_i0(double x)
+{
+    double sum = 1.0, term = 1.0;
+    for (int k = 1; k < 200; ++k) {
+        term *= (x / (2.0 * k)) * (x / (2.0 * k));
+        sum += term;
+        if (term < 1e-18 * sum) break;
+    }
+    return sum;
+}
+
+// sin(pi n / d) for integers, after an exact reduction of n modulo 2d (argument in [-pi, pi]).
+constexpr double cx_sinpi_ratio(int n, int d)
+{
+    int r = n % (2 * d);
+    if (r > d) r -= 2 * d;
+    if (r < -d) r += 2 * d;
+    const double x = cx_pi * (double)r / (double)d;
+    double term = x, acc = x;
+    for (int j = 1; j < 40; ++j) {
+        term *= -x * x / ((2.0 * j) * (2.0 * j + 1.0));
+        acc += term;
+    }
+    return acc;
+}
+
+constexpr double cx_sqrt(double v)
+{
+    if (v <= 0.0) return 0.0;
+    double g = v > 1.0 ? v : 1.0;
+    for (int i = 0; i < 200; ++i) g = 0.5 * (g + v / g);
+    return g;
+}
+
+template <int RL>
+struct FcTab {
+    float v[20 * RL + 1];
+};
+
+template <int RL>
+constexpr FcTab<RL> make_fc()
+{
+    constexpr int HL = 10 * RL;
+    double w[2 * HL + 1] = {};
+    double sum = 0.0;
+    const double i0b = cx_i0(5.0);
+    for (int m = -HL; m <= HL; ++m) {
+        const double lp = (m == 0) ? 1.0 / RL : cx_sinpi_ratio(m, RL) / (cx_pi * (double)m);
+        const double rr = (double)m / (double)HL;
+        const double win = cx_i0(5.0 * cx_sqrt(1.0 - rr * rr)) / i0b;
+        w[m + HL] = lp * win;
+        sum += w[m + HL];
+    }
+    FcTab<RL> t{};
+    for (int i = 0; i <= 2 * HL; ++i) t.v[i] = (float)(w[i] / sum);
+    return t;
+}
+
+template <int RL>
+inline constexpr FcTab<RL> kFc = make_fc<RL>();
+
+// ---- the first resampler's table, built on the device in FP64 --------------------------------
+__device__ double dev_i0(double x)
+{
+    double sum = 1.0, term = 1.0;
+    for (int k = 1; k < 200; ++k) {
+        term *= (x / (2.0 * k)) * (x / (2.0 * k));
+        sum += term;
+        if (term < 1e-18 * sum) break;
+    }
+    return sum;
+}
+
+// F(m), |m| <= HL = 10 max(up, down): lowpass with cutoff pi / max(up, down), Kaiser window,
+// scaled to sum to `up`; stored as tab[p * 32 + i] = F(p - HL + i down) (zero past the end).
+__global__ void __launch_bounds__(256) mr_table(LaunchArgs a)
+{
+    __shared__ double part[256];
+    const int up = a.up, down = a.down, HL = a.HLA;
+    const int mx = up > down ? up : down;
+    const double i0b = dev_i0(5.0);
+    double local = 0.0;
+    for (int m = -HL + (int)threadIdx.x; m <= HL; m += blockDim.x) {
+        const double lp = (m == 0) ? 1.0 / mx : sinpi((double)m / mx) / (3.14159265358979323846 * m);
+        const double rr = (double)m / HL;
+        local += lp * dev_i0(5.0 * sqrt(fmax(0.0, 1.0 - rr * rr))) / i0b;
+    }
+    part[threadIdx.x] = local;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double scale = (double)up / part[0];
+    for (int e = threadIdx.x; e < down * kMrNJ; e += blockDim.x) {
+        const int p = e / kMrNJ, i = e % kMrNJ;
+        const int m = p - HL + i * down;
+        float v = 0.0f;
+        if (m <= HL) {
+            const double lp = (m == 0) ? 1.0 / mx : sinpi((double)m / mx) / (3.14159265358979323846 * m);
+            const double rr = (double)m / HL;
+            v = (float)(scale * lp * dev_i0(5.0 * sqrt(fmax(0.0, 1.0 - rr * rr))) / i0b);
+        }
+        a.mr_tab[e] = v;
+    }
+}
+
+// ---- stage A ------------------------------------------------------------------------------
+__device__ __forceinline__ int64_t ceil_div(int64_t n, int64_t d)   // d > 0
+{
+    return n >= 0 ? (n + d - 1) / d : -((-n) / d);
+}
+
+// Intermediate-signal geometry of room b: L_h, L_m and the offset of channel (s, m).
+struct MrChan {
+    int64_t Lh, Lm, off;
+};
+
+__device__ __forceinline__ MrChan mr_chan(const LaunchArgs& a, const RoomConst& rc, int b, int s, int m)
+{
+    MrChan c;
+    c.Lh = (int64_t)ceil(__dmul_rn((double)a.rt60[b], a.fh));
+    c.Lm = ceil_div(c.Lh * a.up, a.down);
+    // L_m <= r_l L_b + 2 when the device T60 matches the host layout; a channel holds r_l L_b + 8.
+    const int64_t cap = (int64_t)a.rl * rc.len + 8;
+    if (c.Lm > cap || c.Lh < 1) {
+        atomicOr(&a.hdr->status, FRAM_DEV_BAD_GEOMETRY);
+        c.Lm = c.Lh < 1 ? 0 : cap;
+        if (c.Lh < 1) c.Lh = 1;
+    }
+    const int64_t chan = ((int64_t)b * a.S + s) * a.M + m;
+    c.off = (int64_t)a.rl * (rc.rir_off + ((int64_t)s * a.M + m) * rc.len) + 8 * chan;
+    return c;
+}
+
+__host__ __device__ inline int mr_warp_floats(int TA) { return 2 * (TA + 64) + 2 * 32; }
+
+// Adds the impulse (q, A) to the buffers: lane j takes the intermediate sample kmin + j.
+__device__ __forceinline__ void mr_add(const float* __restrict__ tab, float* buf, float* bufe, int64_t q, float A,
+                                       bool in_early, int64_t K0, int TA, int up, int down, int HL, int lane)
+{
+    const int64_t c = q * up;
+    const int64_t kmin = ceil_div(c - HL, down);
+    const int m0 = (int)(kmin * down - c + HL);                  // in [0, down)
+    const float f = tab[m0 * kMrNJ + lane];
+    const int64_t bi = kmin + lane - K0 + 32;                    // buffer index
+    if (bi >= 0 && bi < TA + 64 && f != 0.0f) {
+        buf[bi] = __fmaf_rn(A, f, buf[bi]);
+        if (bufe && in_early) bufe[bi] = __fmaf_rn(A, f, bufe[bi]);
+    }
+}
+
+__global__ void __launch_bounds__(kMrThreads) mr_stage_a(LaunchArgs a, bool want_early)
+{
+    extern __shared__ __align__(16) float mr_smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int T = a.tile, M = a.M, rl = a.rl, up = a.up, down = a.down, HL = a.HLA;
+    const int TA = 256 * rl, nsub = T / 256;
+    float* tab = mr_smem;                                        // down x 32
+    float* buf = mr_smem + down * kMrNJ + wid * mr_warp_floats(TA);
+    float* bufe = want_early ? buf + TA + 64 : nullptr;
+    float* rA = buf + 2 * (TA + 64);                             // staged impulses: A
+    int* rq = reinterpret_cast<int*>(rA + 32);                   // and q
+    for (int e = threadIdx.x; e < down * kMrNJ; e += blockDim.x) tab[e] = a.mr_tab[e];
+    __syncthreads();
+    const double c0 = a.c0, fh = a.fh;
+    const int64_t n_units = (int64_t)a.hdr->n_items * M * nsub;
+    int u = 0;
+    if (lane == 0) u = atomicAdd(&a.hdr->queue, 1);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    while ((int64_t)u < n_units) {
+        int nxt = 0;
+        if (lane == 0) nxt = atomicAdd(&a.hdr->queue, 1);
+        const int qi = u / (M * nsub);
+        const int rem = u - qi * M * nsub;
+        const int m = rem / nsub, st = rem - m * nsub;
+        const ItemRec ir = a.irec[qi];
+        const RoomConst rc = a.room[ir.b];
+        const MrChan ch = mr_chan(a, rc, ir.b, ir.s, m);
+        const int64_t K0 = (int64_t)ir.T0 * rl + (int64_t)st * TA;
+        const int64_t tile_end = (int64_t)rc.ntiles * T * rl;
+        const bool last = K0 + TA >= tile_end;
+        const int64_t s_end = last ? ch.Lm : (K0 + TA < ch.Lm ? K0 + TA : ch.Lm);
+        if (K0 < s_end) {
+            for (int k = lane; k < TA + 64; k += 32) {
+                buf[k] = 0.0f;
+                if (bufe) bufe[k] = 0.0f;
+            }
+            __syncwarp();
+            const DirectConst dc = a.direct[((int64_t)ir.b * a.S + ir.s) * M + m];
+            {   // direct path (g = 0), uniform across the warp
+                int64_t q = dc.q_h;
+                if (q > ch.Lh - 1) q = ch.Lh - 1;
+                if (dc.amp > 0.0f)
+                    mr_add(tab, buf, bufe, q, dc.amp, q >= dc.early_lo_h && q <= dc.early_hi_h, K0, TA, up, down,
+                           HL, lane);
+                __syncwarp();
+            }
+            // Images whose taps can reach [K0 - 32, K0 + TA + 32): delay (at fs) within 11 r_l
+            // intermediate samples and the array margin of the binning key; the last sub-tile
+            // also takes every later key (impulses clamped to L_h - 1).
+            const int* p32 = a.pos32 + ((int64_t)ir.b * a.S + ir.s) * ((int64_t)a.nb32 + 1);
+            const int64_t tmin = (K0 - 64) / rl - a.margin_i - 2;
+            const int64_t tmax = (K0 + TA + 64) / rl + a.margin_i + 2;
+            const int bmin = (int)(tmin < 0 ? 0 : (tmin >> 5));
+            const int bmax = (int)((tmax >> 5) + 1 < a.nb32 ? (tmax >> 5) + 1 : a.nb32);
+            const int c_lo = p32[bmin];
+            const int c_hi = last ? rc.n_vs : p32[bmax];
+            const float* pm = a.mic + 3 * ((size_t)ir.b * M + m);
+            const double mx = pm[0], my = pm[1], mz = pm[2];
+            for (int cb = c_lo; cb < c_hi; cb += 32) {
+                const int p = cb + lane;
+                bool valid = false;
+                int64_t q = 0;
+                float A = 0.0f;
+                if (p < c_hi) {
+                    const float4 pa = a.spa[ir.v0 + p];
+                    const float2 pb = a.spb[ir.v0 + p];
+                    const double dx = __dsub_rn(__dadd_rn((double)pa.x, (double)pa.w), mx);
+                    const double dy = __dsub_rn(__dadd_rn((double)pa.y, (double)pb.x), my);
+                    const double dz = __dsub_rn(__dadd_rn((double)pa.z, (double)pb.y), mz);
+                    const double D = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                                                          __dmul_rn(dz, dz)));
+                    const double qh = ceil(__dmul_rn(__ddiv_rn(D, c0), fh));
+                    q = (qh > (double)(ch.Lh - 1)) ? ch.Lh - 1 : (int64_t)qh;
+                    A = a.samp[ir.v0 + p] / (float)D;
+                    const int64_t kmin = ceil_div(q * up - HL, down);
+                    valid = D > 0.0 && A == A && fabsf(A) < 3.0e38f && kmin + 31 >= K0 - 32 && kmin < K0 + TA + 32;
+                }
+                const unsigned vb = __ballot_sync(0xffffffffu, valid);
+                if (valid) {
+                    const int slot = __popc(vb & ((1u << lane) - 1u));
+                    rA[slot] = A;
+                    rq[slot] = (int)q;
+                }
+                __syncwarp();
+                const int nv = __popc(vb);
+                for (int j = 0; j < nv; ++j) {
+                    const int64_t qq = rq[j];
+                    mr_add(tab, buf, bufe, qq, rA[j], qq >= dc.early_lo_h && qq <= dc.early_hi_h, K0, TA, up,
+                           down, HL, lane);
+                    __syncwarp();
+                }
+            }
+            for (int64_t k = K0 + lane; k < s_end; k += 32) {
+                a.mr_y[ch.off + k] = buf[k - K0 + 32];
+                if (bufe) a.mr_ye[ch.off + k] = bufe[k - K0 + 32];
+            }
+            __syncwarp();
+        }
+        u = __shfl_sync(0xffffffffu, nxt, 0);
+    }
+}
+
+// ---- stages B and C: the high-pass (float-pair state) and the resampler 1/RL --------------
+struct HpfState {
+    f2 b0, a1, a2;      // coefficients
+    float x1, x2;       // input history
+    f2 y1, y2;          // output history
+};
+
+// z = z[k] reaches the outputs n = blk + j, j in [-10 + (P > 0), 10], with the tap F_C(j RL - P);
+// acc[j + 10] holds output blk + j.  Tap indices are compile-time, so every tap is a literal.
+template <int RL, int P, int J>
+__device__ __forceinline__ void fir_tap(float z, float (&acc)[21])
+{
+    constexpr int idx = J * RL - P + 10 * RL;
+    if constexpr (idx >= 0 && idx <= 20 * RL) {
+        constexpr float c = kFc<RL>.v[idx];
+        acc[J + 10] = __fmaf_rn(z, c, acc[J + 10]);
+    }
+}
+
+template <int RL, int P, int... J>
+__device__ __forceinline__ void fir_taps(float z, float (&acc)[21], std::integer_sequence<int, J...>)
+{
+    (fir_tap<RL, P, J - 10>(z, acc), ...);
+}
+
+// One intermediate sample k = blk RL + P: the high-pass step, then its taps.
+template <int RL, int P>
+__device__ __forceinline__ void hpf_phase(const float* __restrict__ x, int64_t blk, int64_t Lm, HpfState& h,
+                                          float (&acc)[21])
+{
+    const int64_t kk = blk * RL + P;
+    float z = 0.f;
+    if (kk < Lm) {
+        const float x0 = x[kk];
+        f2 uu = two_sum(x0, h.x2);
+        uu = f2_add_f(uu, -2.0f * h.x1);
+        const f2 y0 = f2_add(f2_mul(h.b0, uu), f2_neg(f2_add(f2_mul(h.a1, h.y1), f2_mul(h.a2, h.y2))));
+        h.x2 = h.x1; h.x1 = x0; h.y2 = h.y1; h.y1 = y0;
+        z = y0.hi + y0.lo;
+    }
+    fir_taps<RL, P>(z, acc, std::make_integer_sequence<int, 21>{});
+}
+
+template <int RL, int... P>
+__device__ __forceinline__ void hpf_block(const float* __restrict__ x, int64_t blk, int64_t Lm, HpfState& h,
+                                          float (&acc)[21], std::integer_sequence<int, P...>)
+{
+    (hpf_phase<RL, P>(x, blk, Lm, h, acc), ...);
+}
+
+template <int RL>
+__global__ void __launch_bounds__(128) mr_hpf_down(LaunchArgs a, float* __restrict__ rir, float* __restrict__ early)
+{
+    const int64_t nch = (int64_t)a.B * a.S * a.M;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool is_early = tid >= nch;
+    if (tid >= (early ? 2 * nch : nch)) return;
+    const int64_t chan = is_early ? tid - nch : tid;
+    const int m = (int)(chan % a.M), s = (int)((chan / a.M) % a.S), b = (int)(chan / ((int64_t)a.M * a.S));
+    const RoomConst rc = a.room[b];
+    if (rc.len < 1) return;
+    const MrChan ch = mr_chan(a, rc, b, s, m);
+    const float* x = (is_early ? a.mr_ye : a.mr_y) + ch.off;
+    float* y = (is_early ? early : rir) + rc.rir_off + ((int64_t)s * a.M + m) * rc.len;
+    const int L = rc.len;
+    // 2nd-order Butterworth high-pass at 80 Hz for r_l fs (bilinear transform, pre-warped):
+    // y0 = b0 (x0 - 2 x1 + x2) - a1 y1 - a2 y2, coefficients and state as float pairs.
+    const double k = tan(3.14159265358979323846 * 80.0 / ((double)RL * a.fs));
+    const double den = 1.0 + sqrt(2.0) * k + k * k;
+    HpfState h;
+    h.b0 = f2_from_double(1.0 / den);
+    h.a1 = f2_from_double(2.0 * (k * k - 1.0) / den);
+    h.a2 = f2_from_double((1.0 - sqrt(2.0) * k + k * k) / den);
+    h.x1 = h.x2 = 0.f;
+    h.y1 = h.y2 = f2{0.f, 0.f};
+    float acc[21];
+#pragma unroll
+    for (int j = 0; j < 21; ++j) acc[j] = 0.f;
+    const int64_t Lm = ch.Lm;
+    for (int64_t blk = 0; blk < (int64_t)L + 10; ++blk) {
+        hpf_block<RL>(x, blk, Lm, h, acc, std::make_integer_sequence<int, RL>{});
+        const int64_t n = blk - 10;            // complete: every z reaching it has been added
+        if (n >= 0 && n < L) y[n] = acc[0];
+#pragma unroll
+        for (int j = 0; j < 20; ++j) acc[j] = acc[j + 1];
+        acc[20] = 0.f;
+    }
+}
+
+template <int RL>
+cudaError_t launch_hpf_down(const LaunchArgs& a, float* rir, float* early, cudaStream_t st)
+{
+    const int64_t n = (int64_t)a.B * a.S * a.M * (early ? 2 : 1);
+    if (n == 0) return cudaSuccess;
+    mr_hpf_down<RL><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a, rir, early);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_synthesize_mr(const LaunchArgs& a, const float* pos_hi, const float* pos_lo, float* rir,
+                                 float* early, cudaStream_t st)
+{
+    (void)pos_hi;
+    (void)pos_lo;     // stage A reads the sorted copies the preparation made
+    if (a.B == 0) return cudaSuccess;
+    mr_table<<<1, 256, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int TA = 256 * a.rl;
+    const int smem = (int)sizeof(float) * (a.down * kMrNJ + (kMrThreads / 32) * mr_warp_floats(TA));
+    int per_sm = 0;
+    if ((e = kernel_residency((const void*)mr_stage_a, kMrThreads, smem, &per_sm)) != cudaSuccess) return e;
+    mr_stage_a<<<device_sm_count() * per_sm, kMrThreads, smem, st>>>(a, early != nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    switch (a.rl) {
+    case 2: return launch_hpf_down<2>(a, rir, early, st);
+    case 3: return launch_hpf_down<3>(a, rir, early, st);
+    case 4: return launch_hpf_down<4>(a, rir, early, st);
+    case 5: return launch_hpf_down<5>(a, rir, early, st);
+    case 6: return launch_hpf_down<6>(a, rir, early, st);
+    case 7: return launch_hpf_down<7>(a, rir, early, st);
+    case 8: return launch_hpf_down<8>(a, rir, early, st);
+    case 9: return launch_hpf_down<9>(a, rir, early, st);
+    case 10: return launch_hpf_down<10>(a, rir, early, st);
+    case 11: return launch_hpf_down<11>(a, rir, early, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace fram

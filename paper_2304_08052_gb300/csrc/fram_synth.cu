@@ -114,6 +114,16 @@ __global__ void room_prologue(LaunchArgs a, const float* __restrict__ r_in)
         const double n0 = ceil(t);
         dc.early_lo = (int)(n0 - a.early_pre);
         dc.early_hi = (int)(n0 + a.early_post);
+        dc.q_h = dc.early_lo_h = dc.early_hi_h = 0;
+        if (a.mode == 1) {
+            // The high-rate grid decides integers: evaluated in the oracle's order, with
+            // separately rounded products and sums (no fused multiply-add).
+            const double Dr = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+            const double qh = ceil(__dmul_rn(__ddiv_rn(Dr, c0), a.fh));
+            dc.q_h = (int)fmin(qh, 2.0e9);
+            dc.early_lo_h = (int)fmax(qh - ceil(__ddiv_rn(__dmul_rn(a.early_pre_ms, a.fh), 1000.0)), -2.0e9);
+            dc.early_hi_h = (int)fmin(qh + ceil(__ddiv_rn(__dmul_rn(a.early_post_ms, a.fh), 1000.0)), 2.0e9);
+        }
         dc.pad_ = 0;
         if (!(D > 0) || !isfinite(D)) atomicOr(&a.hdr->status, FRAM_DEV_BAD_GEOMETRY);
         a.direct[tid] = dc;
@@ -619,17 +629,23 @@ static cudaError_t launch_synth_nr(const LaunchArgs& a, float* rir, float* early
     return cudaGetLastError();
 }
 
+cudaError_t launch_amp_gather(const LaunchArgs& a, const float* g, cudaStream_t st)
+{
+    const int64_t segs = (int64_t)a.B * a.S;
+    if (segs > 0) {
+        amp_gather<<<(unsigned)segs, 256, 0, st>>>(a, g);
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_synthesize(const LaunchArgs& a, const float* pos_hi, const float* pos_lo, const float* g,
                               float* rir, float* early, cudaStream_t st)
 {
     (void)pos_hi;
     (void)pos_lo;   // the kernel reads the sorted copies the preparation made
-    const int64_t segs = (int64_t)a.B * a.S;
-    if (segs > 0) {
-        amp_gather<<<(unsigned)segs, 256, 0, st>>>(a, g);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = launch_amp_gather(a, g, st);
+    if (e != cudaSuccess) return e;
     switch ((2 * a.K + 31) / 32) {
     case 1: return launch_synth_nr<1>(a, rir, early, st);
     case 2: return launch_synth_nr<2>(a, rir, early, st);
