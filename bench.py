@@ -341,6 +341,7 @@ def main():
     if not args.no_extras and rank == 0:
         line["graph_vs_per_room"] = graph_vs_per_room(torch, api, scenes)
         line["single_room_latency"] = single_room_latency(torch, api, scenes)
+        line["multirate_vs_continuous"] = multirate_vs_continuous(torch, api, scenes, peaks)
         u, dt, cores = cpu_baseline(sc, 1, list(range(args.cpu_rooms)), params)
         line["cpu_baseline"] = {"value": u / dt, "unit": "RIRs/s", "cores": cores, "kind": "oracle",
                                 "sample": f"first {args.cpu_rooms} rooms of {args.workload} (sample + synthesize, "
@@ -420,6 +421,57 @@ def single_room_latency(torch, api, scenes):
         ms.append(a.elapsed_time(b))
     return {"workload": "single_room (1 room x 1 source x 4 mics, 2000 images, 16 kHz, K=40)",
             "ms_median": statistics.median(ms), "ms_min": min(ms), "calls": len(ms)}
+
+
+def multirate_vs_continuous(torch, api, scenes, peaks):
+    """The paper's multi-rate output path (delay_mode 1: ~1 MHz impulse grid, two polyphase
+    resamplers, 80 Hz high-pass) against the continuous path on batch_1024 with early RIRs:
+    fram_sample + fram_synthesize per step.  The multi-rate stages stream an intermediate signal
+    at r_l fs (7x the output at 16 kHz): written once by the first resampler, read by the two
+    high-pass passes (the second rewrites it) and by the second resampler."""
+    import math
+    sc = scenes.batch_1024(0)
+    out = {"workload": "batch_1024 (1024 rooms x 3 src x 8 mics, 16 kHz, + early RIR)"}
+    for mode in (0, 1):
+        params = api.Params(fs=sc.fs, half_len=sc.half_len, delay_mode=mode)
+        ds = api.DeviceScene(sc, params)
+        N = ds.n_vs_total
+        vs = api.Images(torch.empty((N, 3), device="cuda"), torch.empty((N, 3), device="cuda"),
+                        torch.empty(N, device="cuda"), torch.empty(sc.B, device="cuda"))
+        rir = torch.empty(ds.rir_total, device="cuda")
+        early = torch.empty(ds.rir_total, device="cuda")
+
+        def step(k):
+            api.sample(ds, seed=500 + k, out=vs)
+            api.synthesize_raw(ds, vs.pos_hi, vs.pos_lo, vs.g, vs.r, early=True, rir=rir, early_out=early)
+
+        for k in range(3):
+            step(k)
+        torch.cuda.synchronize()
+        t = _time_steps(torch, step, 5, False) / 5
+        assert ds.status() == 0, "device status flags set"
+        entry = {"ms_per_step": 1000.0 * t, "value": sc.B * sc.S / t, "unit": "RIRs/s"}
+        if mode == 1:
+            rh = math.floor(1e6 / sc.fs)
+            rl = math.floor(math.sqrt(rh))
+            inter = 2 * 4 * rl * ds.rir_total                 # RIR + early intermediate signals, bytes
+            moved = 5 * inter + 2 * 4 * ds.rir_total          # 1 write + 3 reads + 1 rewrite, outputs
+            peak = float(peaks.get("hbm_gbs", 6800.0))
+            entry["roofline"] = {"bound": "hbm", "achieved": moved / t / 1e9, "peak": peak, "unit": "GB/s",
+                                 "frac": moved / t / 1e9 / peak, "bytes_per_step": moved,
+                                 "note": "stream bytes of the multi-rate stages only"}
+        out["continuous" if mode == 0 else "multirate"] = entry
+    import oracle
+    rooms = list(range(16))
+    sub = sc.subset(rooms)
+    op = oracle.Params(fs=sc.fs, half_len=sc.half_len)
+    t0 = time.perf_counter()
+    ref = oracle.sample(sub, op, 1, room_ids=rooms)
+    oracle.synthesize_mr(sub, op, ref.pos, ref.g, ref.r, early=True)
+    dt = time.perf_counter() - t0
+    out["multirate"]["cpu_oracle"] = {"value": len(rooms) * sc.S / dt, "unit": "RIRs/s", "cores": oracle.num_threads(),
+                                      "sample": f"first {len(rooms)} rooms (sample + multi-rate synthesize, FP64, {dt:.1f} s)"}
+    return out
 
 
 def graph_vs_per_room(torch, api, scenes):

@@ -219,6 +219,7 @@ static LaunchArgs make_args(const fram_scene* sc, const fram_params* p, const Ws
     a.part_mic = reinterpret_cast<float*>(base + w.part_mic);
     a.part_src = reinterpret_cast<float*>(base + w.part_src);
     a.part_r = reinterpret_cast<float*>(base + w.part_r);
+    a.max_len = sc->max_len;
     a.mode = p->delay_mode;
     a.early_pre_ms = p->early_pre_ms;
     a.early_post_ms = p->early_post_ms;
@@ -230,6 +231,7 @@ static LaunchArgs make_args(const fram_scene* sc, const fram_params* p, const Ws
         a.mr_y = reinterpret_cast<float*>(base + w.mr_y);
         a.mr_ye = reinterpret_cast<float*>(base + w.mr_ye);
         a.mr_tab = reinterpret_cast<float*>(base + w.mr_tab);
+        a.mr_seg = base + w.mr_seg;
     }
     return a;
 }

@@ -233,7 +233,8 @@ struct Header {             // first 256 bytes of the workspace
 struct WsLayout {
     size_t header, room, direct, src_tile, item_off, items, bin_off, perm, key, skey;
     size_t spa, spb, pos32, samp, irec;
-    size_t mr_y, mr_ye, mr_tab;     // multi-rate mode: intermediate signals, resampling table
+    size_t mr_y, mr_ye, mr_tab, mr_seg;   // multi-rate mode: intermediate signals, resampling
+                                          // table, high-pass segment records
     size_t part_mic, part_src, part_r;
     size_t total;
     int tile;
@@ -290,10 +291,12 @@ inline WsLayout ws_layout(const fram_scene& sc, int tile, int delay_mode = 0, do
         // per channel (room, source, mic): r_l L_b + 8 intermediate samples, and the same for
         // the early RIR; the polyphase table is down x 32 floats.
         const MrRates mr = mr_rates(fs);
-        const size_t inter = (size_t)mr.rl * (size_t)sc.rir_total + 8 * (size_t)sc.B * sc.S * sc.M;
+        const size_t inter = (size_t)mr.rl * (size_t)sc.rir_total + 8 * (size_t)sc.B * sc.S * sc.M + 4;
         w.mr_y = take(sizeof(float) * inter);
         w.mr_ye = take(sizeof(float) * inter);
         w.mr_tab = take(sizeof(float) * 32 * (size_t)mr.down);
+        const size_t nseg = ((size_t)mr.rl * (size_t)sc.max_len + 8 + 2047) / 2048;
+        w.mr_seg = take(48 * nseg * 2 * (size_t)sc.B * sc.S * sc.M);
     }
     w.part_mic = take(sizeof(float) * 3 * (size_t)w.max_items * sc.M);
     w.part_src = take(sizeof(float) * 3 * (size_t)w.max_items);
@@ -349,6 +352,8 @@ struct LaunchArgs {
     float* mr_y;                     // intermediate signals at r_l fs, per channel
     float* mr_ye;                    // the same for the early RIR
     float* mr_tab;                   // first resampling filter, polyphase rows of 32
+    void* mr_seg;                    // high-pass segment records
+    int32_t max_len;                 // max_b L_b
     float* part_mic;
     float* part_src;
     float* part_r;

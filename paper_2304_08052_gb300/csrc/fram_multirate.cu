@@ -21,10 +21,12 @@
 //                   reference, no fused multiply-add), then each impulse is added with one lane
 //                   per tap into the warp's shared buffer (and into the early buffer when q lies
 //                   in the Eq. 9 window on the high-rate grid).  Tiles go to y1 in global memory.
-//   mr_hpf_down     one thread per channel: the high-pass recursion with its state as float
-//                   pairs (poles near z = 1 at 80 Hz make a float32 recursion lose ~1e-5 of the
-//                   peak), and the second resampler (ratio 1/r_l, compile-time taps) as 21
-//                   running output accumulators, streaming y1 once.
+//   mr_hpf_seg, mr_hpf_scan   the high-pass, its state as float pairs (poles near z = 1 at
+//                   80 Hz make a float32 recursion lose ~1e-5 of the peak), run on segments of
+//                   2048 samples in parallel: a zero-state pass, a per-channel propagation of the
+//                   true segment start states, and a second pass writing the result in place.
+//   mr_down         the second resampler (ratio 1/r_l, compile-time taps), one thread per output
+//                   sample from a window staged in shared memory.
 #include <cmath>
 #include <utility>
 
@@ -162,19 +164,22 @@ __device__ __forceinline__ MrChan mr_chan(const LaunchArgs& a, const RoomConst& 
     MrChan c;
     c.Lh = (int64_t)ceil(__dmul_rn((double)a.rt60[b], a.fh));
     c.Lm = ceil_div(c.Lh * a.up, a.down);
-    // L_m <= r_l L_b + 2 when the device T60 matches the host layout; a channel holds r_l L_b + 8.
-    const int64_t cap = (int64_t)a.rl * rc.len + 8;
+    // L_m <= r_l L_b + 2 when the device T60 matches the host layout; a channel holds r_l L_b + 5.
+    const int64_t cap = (int64_t)a.rl * rc.len + 4;
     if (c.Lm > cap || c.Lh < 1) {
         atomicOr(&a.hdr->status, FRAM_DEV_BAD_GEOMETRY);
         c.Lm = c.Lh < 1 ? 0 : cap;
         if (c.Lh < 1) c.Lh = 1;
     }
     const int64_t chan = ((int64_t)b * a.S + s) * a.M + m;
-    c.off = (int64_t)a.rl * (rc.rir_off + ((int64_t)s * a.M + m) * rc.len) + 8 * chan;
+    // rounded up to 4 floats (16 bytes): consecutive channels stay >= r_l L_b + 5 apart
+    c.off = ((int64_t)a.rl * (rc.rir_off + ((int64_t)s * a.M + m) * rc.len) + 8 * chan + 3) & ~(int64_t)3;
     return c;
 }
 
-__host__ __device__ inline int mr_warp_floats(int TA) { return 2 * (TA + 64) + 2 * 32; }
+// Per-warp shared memory (floats): the tile buffer (TA + 64), the early buffer when wanted, and
+// 32 staged impulses (A, q).
+__host__ __device__ inline int mr_warp_floats(int TA, bool early) { return (early ? 2 : 1) * (TA + 64) + 2 * 32; }
 
 // Adds the impulse (q, A) to the buffers: lane j takes the intermediate sample kmin + j.
 __device__ __forceinline__ void mr_add(const float* __restrict__ tab, float* buf, float* bufe, int64_t q, float A,
@@ -198,9 +203,9 @@ __global__ void __launch_bounds__(kMrThreads) mr_stage_a(LaunchArgs a, bool want
     const int T = a.tile, M = a.M, rl = a.rl, up = a.up, down = a.down, HL = a.HLA;
     const int TA = 256 * rl, nsub = T / 256;
     float* tab = mr_smem;                                        // down x 32
-    float* buf = mr_smem + down * kMrNJ + wid * mr_warp_floats(TA);
+    float* buf = mr_smem + down * kMrNJ + wid * mr_warp_floats(TA, want_early);
     float* bufe = want_early ? buf + TA + 64 : nullptr;
-    float* rA = buf + 2 * (TA + 64);                             // staged impulses: A
+    float* rA = buf + (want_early ? 2 : 1) * (TA + 64);          // staged impulses: A
     int* rq = reinterpret_cast<int*>(rA + 32);                   // and q
     for (int e = threadIdx.x; e < down * kMrNJ; e += blockDim.x) tab[e] = a.mr_tab[e];
     __syncthreads();
@@ -293,101 +298,204 @@ __global__ void __launch_bounds__(kMrThreads) mr_stage_a(LaunchArgs a, bool want
     }
 }
 
-// ---- stages B and C: the high-pass (float-pair state) and the resampler 1/RL --------------
-struct HpfState {
-    f2 b0, a1, a2;      // coefficients
-    float x1, x2;       // input history
-    f2 y1, y2;          // output history
+// ---- stage B: the high-pass, segmented -------------------------------------------------------
+// The recursion y0 = b0 (x0 - 2 x1 + x2) - a1 y1 - a2 y2 is linear, so each channel is cut into
+// segments of kMrSeg samples that run in parallel:
+//   mr_hpf_seg (pass 0)  every segment from a zero output state (with its true input history):
+//                        its end state, in float pairs;
+//   mr_hpf_scan          one thread per channel: the true start state of every segment,
+//                        s_{j+1} = zs_end_j + A^kMrSeg s_j with A = [[-a1, -a2], [1, 0]] in FP64;
+//   mr_hpf_seg (pass 1)  every segment again from its true start state, writing the high-passed
+//                        signal over its input (the input history was saved by the scan).
+constexpr int kMrSeg = 2048;
+
+struct HpfCoef {
+    f2 b0, a1, a2;
+    double a1d, a2d;
 };
 
-// z = z[k] reaches the outputs n = blk + j, j in [-10 + (P > 0), 10], with the tap F_C(j RL - P);
-// acc[j + 10] holds output blk + j.  Tap indices are compile-time, so every tap is a literal.
-template <int RL, int P, int J>
-__device__ __forceinline__ void fir_tap(float z, float (&acc)[21])
+__device__ __forceinline__ HpfCoef hpf_coef(double fsr)
 {
-    constexpr int idx = J * RL - P + 10 * RL;
-    if constexpr (idx >= 0 && idx <= 20 * RL) {
-        constexpr float c = kFc<RL>.v[idx];
-        acc[J + 10] = __fmaf_rn(z, c, acc[J + 10]);
-    }
+    const double k = tan(3.14159265358979323846 * 80.0 / fsr);
+    const double den = 1.0 + sqrt(2.0) * k + k * k;
+    HpfCoef c;
+    c.a1d = 2.0 * (k * k - 1.0) / den;
+    c.a2d = (1.0 - sqrt(2.0) * k + k * k) / den;
+    c.b0 = f2_from_double(1.0 / den);
+    c.a1 = f2_from_double(c.a1d);
+    c.a2 = f2_from_double(c.a2d);
+    return c;
 }
 
-template <int RL, int P, int... J>
-__device__ __forceinline__ void fir_taps(float z, float (&acc)[21], std::integer_sequence<int, J...>)
+// Per (channel, segment) record: zero-state end state (y[e], y[e-1]) as pairs, true start state
+// (y[s-1], y[s-2]) as pairs, input history (x[s-1], x[s-2]).
+struct SegRec {
+    float zy1h, zy1l, zy2h, zy2l;
+    float sy1h, sy1l, sy2h, sy2l;
+    float x1, x2, pad0, pad1;
+};
+
+__device__ __forceinline__ void mr_channel_of(const LaunchArgs& a, int64_t chan, int& b, int& s, int& m)
 {
-    (fir_tap<RL, P, J - 10>(z, acc), ...);
+    m = (int)(chan % a.M);
+    s = (int)((chan / a.M) % a.S);
+    b = (int)(chan / ((int64_t)a.M * a.S));
 }
 
-// One intermediate sample k = blk RL + P: the high-pass step, then its taps.
-template <int RL, int P>
-__device__ __forceinline__ void hpf_phase(const float* __restrict__ x, int64_t blk, int64_t Lm, HpfState& h,
-                                          float (&acc)[21])
-{
-    const int64_t kk = blk * RL + P;
-    float z = 0.f;
-    if (kk < Lm) {
-        const float x0 = x[kk];
-        f2 uu = two_sum(x0, h.x2);
-        uu = f2_add_f(uu, -2.0f * h.x1);
-        const f2 y0 = f2_add(f2_mul(h.b0, uu), f2_neg(f2_add(f2_mul(h.a1, h.y1), f2_mul(h.a2, h.y2))));
-        h.x2 = h.x1; h.x1 = x0; h.y2 = h.y1; h.y1 = y0;
-        z = y0.hi + y0.lo;
-    }
-    fir_taps<RL, P>(z, acc, std::make_integer_sequence<int, 21>{});
-}
-
-template <int RL, int... P>
-__device__ __forceinline__ void hpf_block(const float* __restrict__ x, int64_t blk, int64_t Lm, HpfState& h,
-                                          float (&acc)[21], std::integer_sequence<int, P...>)
-{
-    (hpf_phase<RL, P>(x, blk, Lm, h, acc), ...);
-}
-
-template <int RL>
-__global__ void __launch_bounds__(128) mr_hpf_down(LaunchArgs a, float* __restrict__ rir, float* __restrict__ early)
+template <int PASS>
+__global__ void __launch_bounds__(128) mr_hpf_seg(LaunchArgs a, SegRec* __restrict__ seg, int nseg_max, bool with_early)
 {
     const int64_t nch = (int64_t)a.B * a.S * a.M;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool is_early = tid >= nch;
-    if (tid >= (early ? 2 * nch : nch)) return;
-    const int64_t chan = is_early ? tid - nch : tid;
-    const int m = (int)(chan % a.M), s = (int)((chan / a.M) % a.S), b = (int)(chan / ((int64_t)a.M * a.S));
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t chans = with_early ? 2 * nch : nch;
+    if (t >= chans * nseg_max) return;
+    const int64_t cidx = t / nseg_max;
+    const int j = (int)(t - cidx * nseg_max);
+    const bool is_early = cidx >= nch;
+    const int64_t chan = is_early ? cidx - nch : cidx;
+    int b, s, m;
+    mr_channel_of(a, chan, b, s, m);
+    const RoomConst rc = a.room[b];
+    if (rc.len < 1) return;
+    const MrChan ch = mr_chan(a, rc, b, s, m);
+    const int64_t s0 = (int64_t)j * kMrSeg;
+    if (s0 >= ch.Lm) return;
+    const int64_t s1 = s0 + kMrSeg < ch.Lm ? s0 + kMrSeg : ch.Lm;
+    float* x = (is_early ? a.mr_ye : a.mr_y) + ch.off;
+    SegRec& R = seg[cidx * nseg_max + j];
+    const HpfCoef c = hpf_coef((double)a.rl * a.fs);
+    float x1, x2;
+    f2 y1, y2;
+    if (PASS == 0) {
+        x1 = s0 >= 1 ? x[s0 - 1] : 0.f;
+        x2 = s0 >= 2 ? x[s0 - 2] : 0.f;
+        y1 = y2 = f2{0.f, 0.f};
+    } else {
+        x1 = R.x1; x2 = R.x2;
+        y1 = f2{R.sy1h, R.sy1l};
+        y2 = f2{R.sy2h, R.sy2l};
+    }
+    // Segments start on multiples of kMrSeg and rows on 16 bytes: whole float4s, then a tail.
+    auto step = [&](float x0) {
+        f2 uu = two_sum(x0, x2);
+        uu = f2_add_f(uu, -2.0f * x1);
+        const f2 y0 = f2_add(f2_mul(c.b0, uu), f2_neg(f2_add(f2_mul(c.a1, y1), f2_mul(c.a2, y2))));
+        x2 = x1; x1 = x0; y2 = y1; y1 = y0;
+        return y0.hi + y0.lo;
+    };
+    const int64_t s4 = s0 + ((s1 - s0) & ~(int64_t)3);
+    for (int64_t k = s0; k < s4; k += 4) {
+        float4 v = *reinterpret_cast<const float4*>(x + k);
+        float4 o;
+        o.x = step(v.x); o.y = step(v.y); o.z = step(v.z); o.w = step(v.w);
+        if (PASS == 1) *reinterpret_cast<float4*>(x + k) = o;
+    }
+    for (int64_t k = s4; k < s1; ++k) {
+        const float o = step(x[k]);
+        if (PASS == 1) x[k] = o;
+    }
+    if (PASS == 0) {
+        R.zy1h = y1.hi; R.zy1l = y1.lo;
+        R.zy2h = y2.hi; R.zy2l = y2.lo;
+    }
+}
+
+__global__ void __launch_bounds__(128) mr_hpf_scan(LaunchArgs a, SegRec* __restrict__ seg, int nseg_max, bool with_early)
+{
+    const int64_t nch = (int64_t)a.B * a.S * a.M;
+    const int64_t cidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cidx >= (with_early ? 2 * nch : nch)) return;
+    const bool is_early = cidx >= nch;
+    const int64_t chan = is_early ? cidx - nch : cidx;
+    int b, s, m;
+    mr_channel_of(a, chan, b, s, m);
     const RoomConst rc = a.room[b];
     if (rc.len < 1) return;
     const MrChan ch = mr_chan(a, rc, b, s, m);
     const float* x = (is_early ? a.mr_ye : a.mr_y) + ch.off;
-    float* y = (is_early ? early : rir) + rc.rir_off + ((int64_t)s * a.M + m) * rc.len;
+    const HpfCoef c = hpf_coef((double)a.rl * a.fs);
+    // P = A^kMrSeg by repeated squaring (kMrSeg is a power of two).
+    double p00 = -c.a1d, p01 = -c.a2d, p10 = 1.0, p11 = 0.0;
+    for (int sq = 1; sq < kMrSeg; sq <<= 1) {
+        const double q00 = p00 * p00 + p01 * p10, q01 = p00 * p01 + p01 * p11;
+        const double q10 = p10 * p00 + p11 * p10, q11 = p10 * p01 + p11 * p11;
+        p00 = q00; p01 = q01; p10 = q10; p11 = q11;
+    }
+    const int nseg = (int)((ch.Lm + kMrSeg - 1) / kMrSeg);
+    double v1 = 0.0, v2 = 0.0;      // true (y[s-1], y[s-2]) at the start of segment j
+    for (int j = 0; j < nseg; ++j) {
+        SegRec& R = seg[cidx * nseg_max + j];
+        const int64_t s0 = (int64_t)j * kMrSeg;
+        R.sy1h = (float)v1; R.sy1l = (float)(v1 - (double)R.sy1h);
+        R.sy2h = (float)v2; R.sy2l = (float)(v2 - (double)R.sy2h);
+        R.x1 = s0 >= 1 ? x[s0 - 1] : 0.f;
+        R.x2 = s0 >= 2 ? x[s0 - 2] : 0.f;
+        const double e1 = (double)R.zy1h + (double)R.zy1l + p00 * v1 + p01 * v2;
+        const double e2 = (double)R.zy2h + (double)R.zy2l + p10 * v1 + p11 * v2;
+        v1 = e1; v2 = e2;
+    }
+}
+
+// ---- stage C: the resampler 1/RL, one thread per output sample ------------------------------
+// y[n] = sum_k z[k] F_C(n RL - k), k in [0, L_m); a block stages z over its outputs' window.
+constexpr int kMrOut = 256;
+
+template <int RL, int I>
+__device__ __forceinline__ void fir_step(const float* __restrict__ w, float& acc)
+{
+    constexpr float c = kFc<RL>.v[20 * RL - I];
+    acc = __fmaf_rn(w[I], c, acc);
+}
+
+template <int RL, int... I>
+__device__ __forceinline__ float fir_dot(const float* __restrict__ w, std::integer_sequence<int, I...>)
+{
+    float acc = 0.f;
+    (fir_step<RL, I>(w, acc), ...);
+    return acc;
+}
+
+template <int RL>
+__global__ void __launch_bounds__(kMrOut) mr_down(LaunchArgs a, float* __restrict__ rir, float* __restrict__ early)
+{
+    constexpr int HLC = 10 * RL;
+    constexpr int W = kMrOut * RL + 2 * HLC;
+    __shared__ float zw[W];
+    const int64_t nch = (int64_t)a.B * a.S * a.M;
+    const int64_t cidx = blockIdx.x;
+    const bool is_early = cidx >= nch;
+    const int64_t chan = is_early ? cidx - nch : cidx;
+    int b, s, m;
+    mr_channel_of(a, chan, b, s, m);
+    const RoomConst rc = a.room[b];
     const int L = rc.len;
-    // 2nd-order Butterworth high-pass at 80 Hz for r_l fs (bilinear transform, pre-warped):
-    // y0 = b0 (x0 - 2 x1 + x2) - a1 y1 - a2 y2, coefficients and state as float pairs.
-    const double k = tan(3.14159265358979323846 * 80.0 / ((double)RL * a.fs));
-    const double den = 1.0 + sqrt(2.0) * k + k * k;
-    HpfState h;
-    h.b0 = f2_from_double(1.0 / den);
-    h.a1 = f2_from_double(2.0 * (k * k - 1.0) / den);
-    h.a2 = f2_from_double((1.0 - sqrt(2.0) * k + k * k) / den);
-    h.x1 = h.x2 = 0.f;
-    h.y1 = h.y2 = f2{0.f, 0.f};
-    float acc[21];
-#pragma unroll
-    for (int j = 0; j < 21; ++j) acc[j] = 0.f;
-    const int64_t Lm = ch.Lm;
-    for (int64_t blk = 0; blk < (int64_t)L + 10; ++blk) {
-        hpf_block<RL>(x, blk, Lm, h, acc, std::make_integer_sequence<int, RL>{});
-        const int64_t n = blk - 10;            // complete: every z reaching it has been added
-        if (n >= 0 && n < L) y[n] = acc[0];
-#pragma unroll
-        for (int j = 0; j < 20; ++j) acc[j] = acc[j + 1];
-        acc[20] = 0.f;
+    const int64_t n0 = (int64_t)blockIdx.y * kMrOut;
+    if (L < 1 || n0 >= L) return;
+    const MrChan ch = mr_chan(a, rc, b, s, m);
+    const float* z = (is_early ? a.mr_ye : a.mr_y) + ch.off;
+    const int64_t k0 = n0 * RL - HLC;                 // window [k0, k0 + W)
+    for (int i = threadIdx.x; i < W; i += kMrOut) {
+        const int64_t k = k0 + i;
+        zw[i] = (k >= 0 && k < ch.Lm) ? z[k] : 0.f;
+    }
+    __syncthreads();
+    const int64_t n = n0 + threadIdx.x;
+    if (n < L) {
+        // taps k = n RL - HLC .. n RL + HLC, i.e. window offsets threadIdx.x RL + i, i in [0, 2 HLC]
+        const float v = fir_dot<RL>(zw + threadIdx.x * RL, std::make_integer_sequence<int, 2 * HLC + 1>{});
+        float* y = (is_early ? early : rir) + rc.rir_off + ((int64_t)s * a.M + m) * L;
+        y[n] = v;
     }
 }
 
 template <int RL>
-cudaError_t launch_hpf_down(const LaunchArgs& a, float* rir, float* early, cudaStream_t st)
+cudaError_t launch_down(const LaunchArgs& a, float* rir, float* early, cudaStream_t st)
 {
-    const int64_t n = (int64_t)a.B * a.S * a.M * (early ? 2 : 1);
-    if (n == 0) return cudaSuccess;
-    mr_hpf_down<RL><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a, rir, early);
+    const int64_t nch = (int64_t)a.B * a.S * a.M * (early ? 2 : 1);
+    if (nch == 0) return cudaSuccess;
+    const int maxlen = a.max_len;
+    dim3 grid((unsigned)nch, (unsigned)((maxlen + kMrOut - 1) / kMrOut));   // channels on x (no 65535 cap)
+    mr_down<RL><<<grid, kMrOut, 0, st>>>(a, rir, early);
     return cudaGetLastError();
 }
 
@@ -403,22 +511,34 @@ cudaError_t launch_synthesize_mr(const LaunchArgs& a, const float* pos_hi, const
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int TA = 256 * a.rl;
-    const int smem = (int)sizeof(float) * (a.down * kMrNJ + (kMrThreads / 32) * mr_warp_floats(TA));
+    const int smem = (int)sizeof(float) * (a.down * kMrNJ + (kMrThreads / 32) * mr_warp_floats(TA, early != nullptr));
     int per_sm = 0;
     if ((e = kernel_residency((const void*)mr_stage_a, kMrThreads, smem, &per_sm)) != cudaSuccess) return e;
     mr_stage_a<<<device_sm_count() * per_sm, kMrThreads, smem, st>>>(a, early != nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // stage B: the segmented high-pass
+    const int nseg_max = (int)(((int64_t)a.rl * a.max_len + 8 + kMrSeg - 1) / kMrSeg);
+    const int64_t chans = (int64_t)a.B * a.S * a.M * (early ? 2 : 1);
+    SegRec* seg = reinterpret_cast<SegRec*>(a.mr_seg);
+    const int64_t nt = chans * nseg_max;
+    mr_hpf_seg<0><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(a, seg, nseg_max, early != nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    mr_hpf_scan<<<(unsigned)((chans + 127) / 128), 128, 0, st>>>(a, seg, nseg_max, early != nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    mr_hpf_seg<1><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(a, seg, nseg_max, early != nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // stage C
     switch (a.rl) {
-    case 2: return launch_hpf_down<2>(a, rir, early, st);
-    case 3: return launch_hpf_down<3>(a, rir, early, st);
-    case 4: return launch_hpf_down<4>(a, rir, early, st);
-    case 5: return launch_hpf_down<5>(a, rir, early, st);
-    case 6: return launch_hpf_down<6>(a, rir, early, st);
-    case 7: return launch_hpf_down<7>(a, rir, early, st);
-    case 8: return launch_hpf_down<8>(a, rir, early, st);
-    case 9: return launch_hpf_down<9>(a, rir, early, st);
-    case 10: return launch_hpf_down<10>(a, rir, early, st);
-    case 11: return launch_hpf_down<11>(a, rir, early, st);
+    case 2: return launch_down<2>(a, rir, early, st);
+    case 3: return launch_down<3>(a, rir, early, st);
+    case 4: return launch_down<4>(a, rir, early, st);
+    case 5: return launch_down<5>(a, rir, early, st);
+    case 6: return launch_down<6>(a, rir, early, st);
+    case 7: return launch_down<7>(a, rir, early, st);
+    case 8: return launch_down<8>(a, rir, early, st);
+    case 9: return launch_down<9>(a, rir, early, st);
+    case 10: return launch_down<10>(a, rir, early, st);
+    case 11: return launch_down<11>(a, rir, early, st);
     default: return cudaErrorInvalidValue;
     }
 }
