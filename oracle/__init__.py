@@ -13,6 +13,7 @@ Functions and the passages they follow:
   sample(scene, params, seed) Eq. 3-6 and Sec. III-B: image positions and reflection counts
   synthesize(...)             Eq. 1 with windowed-sinc fractional delays; Eq. 9 early RIR
   backward(...)               analytic gradient of a loss on h (and h_e)
+  sample_backward(...)        that gradient carried back through the sampler (draws held fixed)
   synthesize_mr(...)          the paper's multi-rate output path (Sec. II-B, Eq. 7-9): impulses
                               on the r_h fs grid, down to r_l fs, 80 Hz high-pass, down to fs
   mr_rates, resample_filter, hpf_coeffs   its rates and filters (readings: see fram_oracle.c)
@@ -196,8 +197,9 @@ def synthesize(scene, params: Params, vs_pos, vs_g, r, early: bool = False):
     return (rir, he) if early else rir
 
 
-def backward(scene, params: Params, vs_pos, vs_g, r, grad_rir, grad_early=None):
-    """Analytic FP64 gradient: (grad_vs [N,3], grad_mic [B,M,3], grad_src [B,S,3], grad_r [B])."""
+def backward(scene, params: Params, vs_pos, vs_g, r, grad_rir, grad_early=None, with_g: bool = False):
+    """Analytic FP64 gradient: (grad_vs [N,3], grad_mic [B,M,3], grad_src [B,S,3], grad_r [B])
+    and, with with_g, also grad_g [N] (dL/dg_i through the amplitudes r^g_i)."""
     rir_len, rir_off, vs_off, src, mic, n_vs = _scene_arrays(scene, params)
     vs_pos, vs_g, r = _f64(vs_pos).reshape(-1, 3), _f64(vs_g).reshape(-1), _f64(r).reshape(-1)
     grad_rir = _f64(grad_rir).reshape(-1) if grad_rir is not None else None
@@ -207,14 +209,39 @@ def backward(scene, params: Params, vs_pos, vs_g, r, grad_rir, grad_early=None):
     gm = np.empty((scene.B, scene.M, 3))
     gs = np.empty((scene.B, scene.S, 3))
     gr = np.empty(scene.B)
+    gg = np.empty(N) if with_g else None
     pc = params._c()
     rc = _load().fo_backward(ctypes.c_int32(scene.B), ctypes.c_int32(scene.S), ctypes.c_int32(scene.M),
                              _p(src), _p(mic), _p(n_vs), _p(vs_off), _p(rir_len), _p(rir_off),
                              _p(vs_pos), _p(vs_g), _p(r), ctypes.byref(pc), _p(grad_rir), _p(grad_early),
-                             _p(gv), _p(gm), _p(gs), _p(gr))
+                             _p(gv), _p(gm), _p(gs), _p(gr), _p(gg))
     if rc != 0:
         raise ValueError("oracle backward: invalid parameters")
-    return gv, gm, gs, gr
+    return (gv, gm, gs, gr, gg) if with_g else (gv, gm, gs, gr)
+
+
+def sample_backward(scene, params: Params, seed: int, grad_vs, grad_g, grad_r, grad_src_dir, grad_mic_dir,
+                    room_ids=None):
+    """Gradients through the sampler with the draws held fixed (reparameterised): from the
+    synthesis adjoint's (grad_vs, grad_g, grad_r, grad_src, grad_mic) to the total
+    (grad_src [B,S,3], grad_mic [B,M,3], grad_t60 [B], grad_dims [B,3])."""
+    _, _, vs_off = layout(scene.rt60, scene.n_vs, scene.S, scene.M, params.fs)
+    dims, rt60, src, mic = _f64(scene.dims), _f64(scene.rt60), _f64(scene.src), _f64(scene.mic)
+    n_vs = np.ascontiguousarray(scene.n_vs, dtype=np.int32)
+    rid = np.ascontiguousarray(room_ids, dtype=np.int32) if room_ids is not None else None
+    gs = np.empty((scene.B, scene.S, 3))
+    gm = np.empty((scene.B, scene.M, 3))
+    gt = np.empty(scene.B)
+    gd = np.empty((scene.B, 3))
+    pc = params._c()
+    rc = _load().fo_sample_backward(ctypes.c_int32(scene.B), ctypes.c_int32(scene.S), ctypes.c_int32(scene.M),
+                                    _p(dims), _p(rt60), _p(src), _p(mic), _p(n_vs), _p(vs_off), ctypes.byref(pc),
+                                    ctypes.c_uint64(seed), _p(rid), _p(_f64(grad_vs)), _p(_f64(grad_g)),
+                                    _p(_f64(grad_r)), _p(_f64(grad_src_dir)), _p(_f64(grad_mic_dir)),
+                                    _p(gs), _p(gm), _p(gt), _p(gd))
+    if rc != 0:
+        raise ValueError("oracle sample_backward: invalid scene or parameters")
+    return gs, gm, gt, gd
 
 
 def mr_rates(fs: float):

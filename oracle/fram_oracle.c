@@ -26,7 +26,10 @@
  *                     at the output rate; direct path with g = 0 (Sec. III-D); early RIR of
  *                     Eq. 9 as a mask on h.
  *   fo_backward       analytic gradient of a loss on h (and h_e) with respect to source, mic
- *                     and virtual-source positions and the reflection coefficient.
+ *                     and virtual-source positions, reflection counts and the coefficient.
+ *   fo_sample_backward  the same gradient carried back through the sampler (Eq. 2-6): with
+ *                     the random draws held fixed, images move with the source, the array and
+ *                     T60, so source, mic, T60 and room-size gradients collect those paths.
  *   fo_synthesize_mr  the paper's own multi-rate output path (Sec. II-B, Eq. 7-9): impulses
  *                     quantised to the r_h fs grid, resampled to r_l fs, high-passed at 80 Hz,
  *                     resampled to fs (filter readings stated with the function).
@@ -322,7 +325,7 @@ int fo_backward(int32_t B, int32_t S, int32_t M, const double* src, const double
                 const int32_t* n_vs, const int64_t* vs_off, const int32_t* rir_len, const int64_t* rir_off,
                 const double* vs_pos, const double* vs_g, const double* r, const fo_params* P,
                 const double* grad_rir, const double* grad_early,
-                double* grad_vs, double* grad_mic, double* grad_src, double* grad_r)
+                double* grad_vs, double* grad_mic, double* grad_src, double* grad_r, double* grad_g)
 {
     const int K = P->half_len;
     if (K < 1) return -1;
@@ -334,6 +337,7 @@ int fo_backward(int32_t B, int32_t S, int32_t M, const double* src, const double
         double gr = 0.0;
         if (grad_mic) for (int j = 0; j < 3 * M; ++j) grad_mic[(int64_t)3 * M * b + j] = 0.0;
         if (grad_vs) for (int64_t v = 3 * vs_off[b]; v < 3 * vs_off[b + 1]; ++v) grad_vs[v] = 0.0;
+        if (grad_g) for (int64_t v = vs_off[b]; v < vs_off[b + 1]; ++v) grad_g[v] = 0.0;
         for (int32_t s = 0; s < S; ++s) {
             const double* ps = src + 3 * ((int64_t)b * S + s);
             double gsrc[3] = { 0.0, 0.0, 0.0 };
@@ -379,6 +383,7 @@ int fo_backward(int32_t B, int32_t S, int32_t M, const double* src, const double
                         else if (grad_vs) grad_vs[3 * v + k] += dLdD * e[k];
                     }
                     if (i >= 0) gr += dLdA * g * A / r[b];
+                    if (i >= 0 && grad_g) grad_g[v] += dLdA * A * log(r[b]);   /* dA/dg = A ln r */
                 }
             }
             if (grad_src) for (int k = 0; k < 3; ++k) grad_src[3 * ((int64_t)b * S + s) + k] = gsrc[k];
@@ -387,6 +392,113 @@ int fo_backward(int32_t B, int32_t S, int32_t M, const double* src, const double
         free(G);
     }
     return 0;
+}
+
+/*
+ * Reparameterised gradient through the sampler (Sec. III-B, III-C; Eq. 2-6), for the continuous
+ * synthesis.  With the Philox draws (u0..u3) of every image held fixed, an image is
+ *   p_i = c + D_i nu_i,  D_i = D0 DR_i,  DR_i = 1 + k_i (c0 T60 / D0 - 1),  k_i = (x_i - alpha)/(beta - alpha),
+ *   g_i = clamp(1 + (D_i / (c0 T60))^2 (RR_max - 1) + p_i DR_i^tau, 1, RR_max),
+ * with c the mean of the mics, D0 = |src - c|, RR_max from Eq. 5 and r from Eq. 2 (R = V/S).
+ * Inputs: dL/dp_i (grad_vs), dL/dg_i (grad_g), dL/dr through the amplitudes (grad_r_amp) and the
+ * direct-path source and mic gradients (grad_src_dir, grad_mic_dir), all from fo_backward.
+ * Outputs (each overwritten): total source and mic gradients, dL/dT60 and dL/d(room size).
+ */
+int fo_sample_backward(int32_t B, int32_t S, int32_t M,
+                       const double* dims, const double* rt60, const double* src, const double* mic,
+                       const int32_t* n_vs, const int64_t* vs_off, const fo_params* P, uint64_t seed,
+                       const int32_t* room_ids,
+                       const double* grad_vs, const double* grad_g, const double* grad_r_amp,
+                       const double* grad_src_dir, const double* grad_mic_dir,
+                       double* grad_src, double* grad_mic, double* grad_t60, double* grad_dims)
+{
+    const double alpha = P->alpha, beta = P->beta, c0 = P->c0, tau = P->tau;
+    if (!(alpha > 0) || !(beta > alpha) || !(beta <= 1.0) || !(c0 > 0) || !(tau > 0)) return -1;
+    const uint32_t key[2] = { (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) };
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int32_t b = 0; b < B; ++b) {
+        const double t60 = rt60[b];
+        const double* d = dims + 3 * b;
+        double R, r;
+        fo_room(d, t60, &R, &r);
+        double c[3];
+        fo_centre(M, mic + (int64_t)3 * M * b, c);
+        const double cT = c0 * t60, lnr = log(r);
+        double dLdc[3] = { 0.0, 0.0, 0.0 };
+        double dLdcT = 0.0, dLdr = grad_r_amp ? grad_r_amp[b] : 0.0;
+        for (int32_t s = 0; s < S; ++s) {
+            const double* ps = src + 3 * ((int64_t)b * S + s);
+            const double D0 = fo_dist(ps, c);
+            if (!(cT > D0) || !(D0 > 0)) { bad = 1; continue; }
+            const double RRmax = fo_rrmax(c0, t60, D0, r);
+            double dLdD0 = 0.0, dLdRR = 0.0;
+            for (int32_t i = 0; i < n_vs[b]; ++i) {
+                const int64_t v = vs_off[b] + (int64_t)s * n_vs[b] + i;
+                const uint32_t rid = room_ids ? (uint32_t)room_ids[b] : (uint32_t)b;
+                const uint32_t ctr[4] = { (uint32_t)i, (uint32_t)s, rid, 0u };
+                uint32_t w[4];
+                fo_philox4x32_10(ctr, key, w);
+                const double u0 = fo_uniform(w[0]), u1 = fo_uniform(w[1]);
+                const double u2 = fo_uniform(w[2]), u3 = fo_uniform(w[3]);
+                const double x = cbrt(alpha * alpha * alpha + u0 * (beta * beta * beta - alpha * alpha * alpha));
+                const double k = (x - alpha) / (beta - alpha);
+                const double DR = 1.0 + alpha / (beta - alpha) * (x / alpha - 1.0) * (cT / D0 - 1.0);
+                const double Di = D0 * DR;
+                const double theta = 2.0 * FO_PI * u1, phi = FO_PI * (u2 - 0.5);
+                const double nu[3] = { cos(phi) * cos(theta), cos(phi) * sin(theta), sin(phi) };
+                const double p = P->a + (P->b - P->a) * u3;
+                const double graw = 1.0 + (Di / cT) * (Di / cT) * (RRmax - 1.0) + p * pow(DR, tau);
+                const double* gp = grad_vs + 3 * v;
+                const double gg = grad_g ? grad_g[v] : 0.0;
+                /* position path: p_i = c + D_i nu_i */
+                double dLdDi = gp[0] * nu[0] + gp[1] * nu[1] + gp[2] * nu[2];
+                for (int j = 0; j < 3; ++j) dLdc[j] += gp[j];
+                /* reflection-count path (Eq. 6), zero where the clamp holds g at 1 */
+                double dLdD0_g = 0.0, dLdcT_g = 0.0;
+                if (graw > RRmax) {
+                    dLdRR += gg;
+                } else if (graw >= 1.0) {
+                    dLdDi += gg * (2.0 * Di / (cT * cT) * (RRmax - 1.0) + p * tau * pow(DR, tau - 1.0) / D0);
+                    dLdD0_g = gg * (-p * tau * pow(DR, tau - 1.0) * Di / (D0 * D0));
+                    dLdcT_g = gg * (-2.0 * Di * Di / (cT * cT * cT) * (RRmax - 1.0));
+                    dLdRR += gg * (Di / cT) * (Di / cT);
+                }
+                /* D_i = D0 (1 - k) + k c0 T60 (Eq. 4) */
+                dLdD0 += dLdDi * (1.0 - k) + dLdD0_g;
+                dLdcT += dLdDi * k + dLdcT_g;
+            }
+            /* Eq. 5: RR_max = (log10(c0 T60) - log10(D0) - 3) / log10(r) */
+            dLdD0 += dLdRR * (-1.0 / (D0 * lnr));
+            dLdcT += dLdRR * (1.0 / (cT * lnr));
+            dLdr += dLdRR * (-RRmax / (r * lnr));
+            /* D0 = |src - c| */
+            for (int j = 0; j < 3; ++j) {
+                const double u = (ps[j] - c[j]) / D0;
+                grad_src[3 * ((int64_t)b * S + s) + j] = (grad_src_dir ? grad_src_dir[3 * ((int64_t)b * S + s) + j] : 0.0)
+                                                         + dLdD0 * u;
+                dLdc[j] -= dLdD0 * u;
+            }
+        }
+        /* c = mean of the mics */
+        for (int32_t m = 0; m < M; ++m)
+            for (int j = 0; j < 3; ++j)
+                grad_mic[3 * ((int64_t)b * M + m) + j] = (grad_mic_dir ? grad_mic_dir[3 * ((int64_t)b * M + m) + j] : 0.0)
+                                                         + dLdc[j] / M;
+        /* Eq. 2: r = sqrt(1 - e^2), e = 1 - exp(-0.16 R / T60), R = V / S */
+        const double ex = exp(-0.16 * R / t60);
+        const double e = 1.0 - ex;
+        const double dr_de = -e / r;
+        const double dLde = dLdr * dr_de;
+        grad_t60[b] = dLdcT * c0 + dLde * (-ex * 0.16 * R / (t60 * t60));
+        const double dLdR = dLde * (ex * 0.16 / t60);
+        const double V = d[0] * d[1] * d[2];
+        const double Sa = 2.0 * (d[0] * d[1] + d[0] * d[2] + d[1] * d[2]);
+        const double dVd[3] = { d[1] * d[2], d[0] * d[2], d[0] * d[1] };
+        const double dSd[3] = { 2.0 * (d[1] + d[2]), 2.0 * (d[0] + d[2]), 2.0 * (d[0] + d[1]) };
+        for (int j = 0; j < 3; ++j) grad_dims[3 * b + j] = dLdR * (dVd[j] / Sa - V * dSd[j] / (Sa * Sa));
+    }
+    return bad ? -1 : 0;
 }
 
 /* ------------------------------------------------------------------------------------ */
