@@ -181,16 +181,43 @@ int fram_synthesize(const fram_scene* scene, const fram_params* p,
  *   dL/dt_j = -A_j sum_n G[n] tap'(n - t_j),  dL/dA_j = sum_n G[n] tap(n - t_j),
  *   G = grad_rir + (Eq. 9 mask) * grad_early,
  * and chains them to positions and r:  dL/dD = dL/dt fs/c0 - dL/dA A/D,
- * dD_{i,m}/dp_i = (p_i - mic_m)/D_{i,m} = -dD_{i,m}/dmic_m, dA/dr = g A / r.
- * Images are leaves: the source gradient comes from the direct path only.
+ * dD_{i,m}/dp_i = (p_i - mic_m)/D_{i,m} = -dD_{i,m}/dmic_m, dA/dr = g A / r, dA/dg = A ln r.
+ * Images are leaves here: the source gradient comes from the direct path only (see
+ * fram_sample_backward for the path through the sampler).
  * Outputs (each nullable, overwritten): grad_vs [N,3], grad_mic [B,M,3], grad_src [B,S,3],
- * grad_r [B].  Reductions run in a fixed order (bit-reproducible).
+ * grad_r [B], grad_g [N] (dL/dg_i summed over mics).  Reductions run in a fixed order
+ * (bit-reproducible).  Requires p->delay_mode == 0 (FRAM_EINVAL otherwise).
  */
 int fram_synthesize_backward(const fram_scene* scene, const fram_params* p,
                              const float* vs_pos_hi, const float* vs_pos_lo, const float* vs_g,
                              const float* r, const float* grad_rir, const float* grad_early,
                              float* grad_vs, float* grad_mic, float* grad_src, float* grad_r,
-                             void* workspace, size_t workspace_bytes, void* stream);
+                             float* grad_g, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Gradient through the sampler (reparameterised: with seed fixed, every image's Philox draws
+ * u0..u3 are constants, so p_i, g_i and r are differentiable functions of the source, the mics,
+ * T60 and the room size; Sec. III-A to III-C, Eq. 2-6 as fram_sample evaluates them).
+ * With k_i = (x_i - alpha)/(beta - alpha), Eq. 4 reads D_i = D0 (1 - k_i) + k_i c0 T60, and
+ *   p_i = c + D_i nu_i,      D0 = |src - c|,      c = mean of the mics,
+ *   g_i: Eq. 6 (derivative 0 where the clamp holds g_i at 1; dg_i/dRR_max = 1 where it holds
+ *   g_i at RR_max),  RR_max: Eq. 5,  r: Eq. 2 with R = V/S of the room.
+ * Inputs (device): grad_vs [N,3] = dL/dp_i (required), grad_g [N] = dL/dg_i (nullable = 0),
+ * grad_r [B] = dL/dr from the synthesis (nullable = 0), grad_src_in [B,S,3] and grad_mic_in
+ * [B,M,3] = the direct gradients (nullable = 0), typically fram_synthesize_backward's grad_src
+ * and grad_mic; they may alias grad_src / grad_mic (each element is read before it is written).
+ * seed / d_seed must be those of the fram_sample call that drew the images.
+ * Outputs (device, nullable, overwritten): grad_src [B,S,3], grad_mic [B,M,3] (totals: direct
+ * plus sampler paths), grad_t60 [B], grad_dims [B,3].  Per (room, source) sums run in FP64 in a
+ * fixed order (bit-reproducible).  Device status FRAM_DEV_BAD_GEOMETRY as for fram_sample (that
+ * (room, source) contributes no sampler path).  Uses the workspace (sized by
+ * fram_workspace_size for this scene).
+ */
+int fram_sample_backward(const fram_scene* scene, const fram_params* p, uint64_t seed, const uint64_t* d_seed,
+                         const float* grad_vs, const float* grad_g, const float* grad_r,
+                         const float* grad_src_in, const float* grad_mic_in,
+                         float* grad_src, float* grad_mic, float* grad_t60, float* grad_dims,
+                         void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * The two stages of fram_synthesize / fram_synthesize_backward, for callers that reuse one
@@ -211,7 +238,7 @@ int fram_synthesize_prepared(const fram_scene* scene, const fram_params* p, cons
 int fram_synthesize_backward_prepared(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi,
                                       const float* vs_pos_lo, const float* vs_g, const float* r,
                                       const float* grad_rir, const float* grad_early, float* grad_vs,
-                                      float* grad_mic, float* grad_src, float* grad_r,
+                                      float* grad_mic, float* grad_src, float* grad_r, float* grad_g,
                                       void* workspace, size_t workspace_bytes, void* stream);
 
 /*

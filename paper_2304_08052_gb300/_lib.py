@@ -25,7 +25,7 @@ FRAM_DEV_NONFINITE = 0x4
 EXPORTED = ("fram_version", "fram_last_error", "fram_default_params", "fram_layout", "fram_workspace_size",
             "fram_sample", "fram_synthesize", "fram_synthesize_backward", "fram_status", "fram_prepare",
             "fram_synthesize_prepared", "fram_synthesize_backward_prepared", "fram_synthesize_noalloc",
-            "fram_autotune")
+            "fram_autotune", "fram_sample_backward")
 
 
 class FramParams(ctypes.Structure):
@@ -70,7 +70,9 @@ def lib():
         L.fram_workspace_size.argtypes = [S, P, ctypes.POINTER(ctypes.c_size_t)]
         L.fram_sample.argtypes = [S, P, u64, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         L.fram_synthesize.argtypes = [S, P, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
-        L.fram_synthesize_backward.argtypes = [S, P, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        L.fram_synthesize_backward.argtypes = [S, P, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t,
+                                               vp]
+        L.fram_sample_backward.argtypes = [S, P, u64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         L.fram_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
         L.fram_prepare.argtypes = [S, P, vp, vp, vp, vp, ctypes.c_size_t, vp]
         L.fram_synthesize_prepared.argtypes = L.fram_synthesize.argtypes

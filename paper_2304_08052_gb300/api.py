@@ -104,12 +104,19 @@ class DeviceScene:
         self._ws_raw = raw
         self.ws = raw[off:off + self.ws_bytes]
 
-    def c_scene(self, src: Optional[torch.Tensor] = None, mic: Optional[torch.Tensor] = None) -> FramScene:
+    def c_scene(self, src: Optional[torch.Tensor] = None, mic: Optional[torch.Tensor] = None,
+                dims: Optional[torch.Tensor] = None, rt60: Optional[torch.Tensor] = None) -> FramScene:
+        """The C scene; src, mic, dims and rt60 may be replaced by other device tensors of the
+        same shapes (the layout -- RIR lengths and offsets -- stays the one made here)."""
         src = self.src if src is None else src
         mic = self.mic if mic is None else mic
+        dims = getattr(self, "dims", None) if dims is None else dims
+        rt60 = getattr(self, "rt60", None) if rt60 is None else rt60
+        for t in (src, mic, dims, rt60):
+            assert t is None or (t.is_cuda and t.is_contiguous() and t.dtype == torch.float32)
         cp = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
         return FramScene(self.B, self.S, self.M, self.max_len, self.n_vs_total, self.rir_total, self.array_radius,
-                         cp(getattr(self, "dims", None)), cp(getattr(self, "rt60", None)), cp(src), cp(mic),
+                         cp(dims), cp(rt60), cp(src), cp(mic),
                          cp(getattr(self, "n_vs", None)), cp(getattr(self, "vs_off_d", None)),
                          cp(getattr(self, "rir_len_d", None)), cp(getattr(self, "rir_off_d", None)))
 
@@ -136,8 +143,9 @@ class Images:
 
 
 def sample(sc: DeviceScene, seed: int = 0, d_seed: Optional[torch.Tensor] = None, words: bool = False,
-           out: Optional[Images] = None) -> Images:
-    """fram_sample: draw every (room, source)'s images on the GPU."""
+           out: Optional[Images] = None, src=None, mic=None, dims=None, rt60=None) -> Images:
+    """fram_sample: draw every (room, source)'s images on the GPU (src, mic, dims, rt60: optional
+    replacements for the scene's own device tensors)."""
     dev = sc.dims.device
     N = sc.n_vs_total
     if out is None:
@@ -147,7 +155,8 @@ def sample(sc: DeviceScene, seed: int = 0, d_seed: Optional[torch.Tensor] = None
                      torch.empty(sc.B, dtype=torch.float32, device=dev),
                      torch.empty((N, 4), dtype=torch.int32, device=dev) if words else None)
     ds = _ptr(d_seed) if d_seed is not None else None
-    check(lib().fram_sample(ctypes.byref(sc.c_scene()), ctypes.byref(sc.params.c()), ctypes.c_uint64(seed & (2**64 - 1)),
+    check(lib().fram_sample(ctypes.byref(sc.c_scene(src, mic, dims, rt60)), ctypes.byref(sc.params.c()),
+                            ctypes.c_uint64(seed & (2**64 - 1)),
                             ds, _ptr(out.pos_hi), _ptr(out.pos_lo), _ptr(out.g), _ptr(out.r), _ptr(out.words),
                             ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes), _stream()))
     return out
@@ -175,8 +184,10 @@ def synthesize(sc: DeviceScene, vs: Images, early: bool = False, **kw):
 
 def synthesize_backward_raw(sc: DeviceScene, pos_hi, pos_lo, g, r, grad_rir, grad_early=None, src=None, mic=None,
                             want=("vs", "mic", "src", "r")):
-    """fram_synthesize_backward.  Returns (grad_vs [N,3], grad_mic [B,M,3], grad_src [B,S,3], grad_r [B])."""
+    """fram_synthesize_backward.  Returns (grad_vs [N,3], grad_mic [B,M,3], grad_src [B,S,3], grad_r [B]),
+    plus grad_g [N] last when "g" is in `want`."""
     dev = sc.dims.device
+    gg = torch.empty(sc.n_vs_total, dtype=torch.float32, device=dev) if "g" in want else None
     gv = torch.empty((sc.n_vs_total, 3), dtype=torch.float32, device=dev) if "vs" in want else None
     gm = torch.empty((sc.B, sc.M, 3), dtype=torch.float32, device=dev) if "mic" in want else None
     gs = torch.empty((sc.B, sc.S, 3), dtype=torch.float32, device=dev) if "src" in want else None
@@ -185,9 +196,28 @@ def synthesize_backward_raw(sc: DeviceScene, pos_hi, pos_lo, g, r, grad_rir, gra
     mic = sc.mic if mic is None else mic
     check(lib().fram_synthesize_backward(ctypes.byref(sc.c_scene(src, mic)), ctypes.byref(sc.params.c()),
                                          _ptr(pos_hi), _ptr(pos_lo), _ptr(g), _ptr(r), _ptr(grad_rir),
-                                         _ptr(grad_early), _ptr(gv), _ptr(gm), _ptr(gs), _ptr(gr),
+                                         _ptr(grad_early), _ptr(gv), _ptr(gm), _ptr(gs), _ptr(gr), _ptr(gg),
                                          ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes), _stream()))
-    return gv, gm, gs, gr
+    return (gv, gm, gs, gr, gg) if "g" in want else (gv, gm, gs, gr)
+
+
+def sample_backward(sc: DeviceScene, seed: int, grad_vs, grad_g=None, grad_r=None, grad_src_in=None,
+                    grad_mic_in=None, d_seed: Optional[torch.Tensor] = None, src=None, mic=None, dims=None,
+                    rt60=None):
+    """fram_sample_backward: carry image and r gradients back through the sampler (draws of
+    `seed` held fixed).  Returns (grad_src [B,S,3], grad_mic [B,M,3], grad_t60 [B], grad_dims [B,3]),
+    source and mic gradients including grad_src_in / grad_mic_in (the direct paths)."""
+    dev = sc.dims.device
+    gs = torch.empty((sc.B, sc.S, 3), dtype=torch.float32, device=dev)
+    gm = torch.empty((sc.B, sc.M, 3), dtype=torch.float32, device=dev)
+    gt = torch.empty(sc.B, dtype=torch.float32, device=dev)
+    gd = torch.empty((sc.B, 3), dtype=torch.float32, device=dev)
+    check(lib().fram_sample_backward(ctypes.byref(sc.c_scene(src, mic, dims, rt60)), ctypes.byref(sc.params.c()),
+                                     ctypes.c_uint64(seed & (2**64 - 1)), _ptr(d_seed), _ptr(grad_vs), _ptr(grad_g),
+                                     _ptr(grad_r), _ptr(grad_src_in), _ptr(grad_mic_in), _ptr(gs), _ptr(gm), _ptr(gt),
+                                     _ptr(gd), ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes),
+                                     _stream()))
+    return gs, gm, gt, gd
 
 
 class _FramRIR(torch.autograd.Function):
@@ -223,6 +253,37 @@ def rir(sc: DeviceScene, src, mic, vs_pos, r, g, vs_pos_lo=None, early: bool = F
     return _FramRIR.apply(src, mic, vs_pos, r, g, vs_pos_lo, sc, early)
 
 
+class _FramSampledRIR(torch.autograd.Function):
+    """Sampling and synthesis in one differentiable step: leaves src [B,S,3], mic [B,M,3],
+    rt60 [B] and dims [B,3]; the draws of `seed` are held fixed (reparameterised), so the images
+    move with the geometry and the gradient runs through the sampler (fram_sample_backward)."""
+
+    @staticmethod
+    def forward(ctx, src, mic, rt60, dims, sc, seed, early):
+        geo = tuple(t.detach().contiguous() for t in (src, mic, rt60, dims))
+        vs = sample(sc, seed, src=geo[0], mic=geo[1], rt60=geo[2], dims=geo[3])
+        out = synthesize_raw(sc, vs.pos_hi, vs.pos_lo, vs.g, vs.r, src=geo[0], mic=geo[1], early=early)
+        ctx.sc, ctx.seed, ctx.early = sc, seed, early
+        ctx.save_for_backward(*geo, vs.pos_hi, vs.pos_lo, vs.g, vs.r)
+        return out
+
+    @staticmethod
+    def backward(ctx, *grads):
+        src, mic, rt60, dims, pos_hi, pos_lo, g, r = ctx.saved_tensors
+        g_rir = grads[0].contiguous() if grads[0] is not None else None
+        g_early = grads[1].contiguous() if ctx.early and grads[1] is not None else None
+        gv, gm, gs, gr, gg = synthesize_backward_raw(ctx.sc, pos_hi, pos_lo, g, r, g_rir, g_early, src=src, mic=mic,
+                                                     want=("vs", "mic", "src", "r", "g"))
+        gs, gm, gt, gd = sample_backward(ctx.sc, ctx.seed, gv, gg, gr, gs, gm, src=src, mic=mic, dims=dims, rt60=rt60)
+        return gs, gm, gt, gd, None, None, None
+
+
+def sampled_rir(sc: DeviceScene, src, mic, rt60, dims, seed: int, early: bool = False):
+    """Differentiable sample + synthesize: gradients w.r.t. source, mic, T60 and room size with
+    the draws of `seed` held fixed.  RIR lengths stay those of the DeviceScene's own T60."""
+    return _FramSampledRIR.apply(src, mic, rt60, dims, sc, seed, early)
+
+
 def prepare(sc: DeviceScene, pos_hi, pos_lo, r, src=None, mic=None):
     """fram_prepare: per-room tables, work items and delay bins in the workspace."""
     src = sc.src if src is None else src
@@ -256,7 +317,7 @@ def synthesize_backward_prepared(sc: DeviceScene, pos_hi, pos_lo, g, r, grad_rir
     mic = sc.mic if mic is None else mic
     check(lib().fram_synthesize_backward_prepared(ctypes.byref(sc.c_scene(src, mic)), ctypes.byref(sc.params.c()),
                                                   _ptr(pos_hi), _ptr(pos_lo), _ptr(g), _ptr(r), _ptr(grad_rir),
-                                                  _ptr(grad_early), _ptr(gv), _ptr(gm), _ptr(gs), _ptr(gr),
+                                                  _ptr(grad_early), _ptr(gv), _ptr(gm), _ptr(gs), _ptr(gr), None,
                                                   ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes),
                                                   _stream()))
     return out

@@ -219,6 +219,7 @@ static LaunchArgs make_args(const fram_scene* sc, const fram_params* p, const Ws
     a.part_mic = reinterpret_cast<float*>(base + w.part_mic);
     a.part_src = reinterpret_cast<float*>(base + w.part_src);
     a.part_r = reinterpret_cast<float*>(base + w.part_r);
+    a.sb_part = reinterpret_cast<double*>(base + w.sb_part);
     a.max_len = sc->max_len;
     a.mode = p->delay_mode;
     a.early_pre_ms = p->early_pre_ms;
@@ -242,7 +243,7 @@ using namespace fram;
 
 extern "C" {
 
-int fram_version(void) { return 10000; }
+int fram_version(void) { return 10100; }
 
 const char* fram_last_error(void) { return g_last_error.c_str(); }
 
@@ -386,8 +387,8 @@ int fram_synthesize(const fram_scene* scene, const fram_params* p, const float* 
 int fram_synthesize_backward_prepared(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi,
                                       const float* vs_pos_lo, const float* vs_g, const float* r,
                                       const float* grad_rir, const float* grad_early, float* grad_vs, float* grad_mic,
-                                      float* grad_src, float* grad_r, void* workspace, size_t workspace_bytes,
-                                      void* stream)
+                                      float* grad_src, float* grad_r, float* grad_g, void* workspace,
+                                      size_t workspace_bytes, void* stream)
 {
     WsLayout w;
     int rc = common_checks(scene, p, vs_pos_hi, vs_g, r, workspace, workspace_bytes, &w);
@@ -400,7 +401,7 @@ int fram_synthesize_backward_prepared(const fram_scene* scene, const fram_params
     cudaError_t e = cudaMemsetAsync(&a.hdr->queue_bwd, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return cuda_fail(e, "fram_synthesize_backward: resetting the work counter");
     e = launch_backward(a, vs_pos_hi, vs_pos_lo, vs_g, r, grad_rir, grad_early, grad_vs, grad_mic, grad_src, grad_r,
-                        st);
+                        grad_g, st);
     if (e != cudaSuccess) return cuda_fail(e, "fram_synthesize_backward: launch");
     return FRAM_OK;
 }
@@ -408,7 +409,7 @@ int fram_synthesize_backward_prepared(const fram_scene* scene, const fram_params
 int fram_synthesize_backward(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi,
                              const float* vs_pos_lo, const float* vs_g, const float* r, const float* grad_rir,
                              const float* grad_early, float* grad_vs, float* grad_mic, float* grad_src, float* grad_r,
-                             void* workspace, size_t workspace_bytes, void* stream)
+                             float* grad_g, void* workspace, size_t workspace_bytes, void* stream)
 {
     WsLayout w;
     int rc = common_checks(scene, p, vs_pos_hi, vs_g, r, workspace, workspace_bytes, &w);
@@ -418,7 +419,30 @@ int fram_synthesize_backward(const fram_scene* scene, const fram_params* p, cons
     if ((rc = fram_prepare(scene, p, vs_pos_hi, vs_pos_lo, r, workspace, workspace_bytes, stream)) != FRAM_OK)
         return rc;
     return fram_synthesize_backward_prepared(scene, p, vs_pos_hi, vs_pos_lo, vs_g, r, grad_rir, grad_early, grad_vs,
-                                             grad_mic, grad_src, grad_r, workspace, workspace_bytes, stream);
+                                             grad_mic, grad_src, grad_r, grad_g, workspace, workspace_bytes, stream);
+}
+
+int fram_sample_backward(const fram_scene* scene, const fram_params* p, uint64_t seed, const uint64_t* d_seed,
+                         const float* grad_vs, const float* grad_g, const float* grad_r, const float* grad_src_in,
+                         const float* grad_mic_in, float* grad_src, float* grad_mic, float* grad_t60, float* grad_dims,
+                         void* workspace, size_t workspace_bytes, void* stream)
+{
+    int rc;
+    if ((rc = check_params(p)) != FRAM_OK) return rc;
+    if ((rc = check_scene(scene, true)) != FRAM_OK) return rc;
+    WsLayout w;
+    if ((rc = check_ws(scene, p, workspace, workspace_bytes, &w)) != FRAM_OK) return rc;
+    if (scene->n_vs_total > 0 && !grad_vs) return fail(FRAM_EINVAL, "grad_vs must not be null");
+    if (scene->B == 0) return FRAM_OK;
+    const LaunchArgs a = make_args(scene, p, w, workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // Only the status word: the tables a fram_prepare left in the workspace stay valid.
+    cudaError_t e = cudaMemsetAsync(&a.hdr->status, 0, sizeof(a.hdr->status), st);
+    if (e != cudaSuccess) return cuda_fail(e, "fram_sample_backward: clearing the status word");
+    e = launch_sample_backward(a, *p, seed, d_seed, grad_vs, grad_g, grad_r, grad_src_in, grad_mic_in, grad_src,
+                               grad_mic, grad_t60, grad_dims, a.sb_part, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fram_sample_backward: launch");
+    return FRAM_OK;
 }
 
 int fram_autotune(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi, const float* vs_pos_lo,

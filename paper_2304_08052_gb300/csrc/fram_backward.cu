@@ -17,7 +17,7 @@
 // That quotient cancels on the tap nearest to t (|n - t| <= 1/2), which instead takes
 // d/dt [sinc w] from a Taylor series of sinc'.  With A = r^g / D the chain rule gives
 //   dL/dA = S1,  dL/dt = A S2,  dL/dD = A S2 fs/c0 - S1 A / D,  dD/dp = (p - mic)/D,
-//   dL/dr = S1 A g / r.
+//   dL/dr = S1 A g / r,  dL/dg = S1 A ln r (summed over mics; for the gradient through the sampler).
 // Image gradients are summed over mics in mic order by the owning lane; mic, source and r
 // gradients are reduced per item in a fixed warp tree and then per room in item order, so the
 // result does not depend on scheduling.
@@ -253,7 +253,8 @@ __device__ __forceinline__ void gather_taps(const float* __restrict__ Gs, int K,
 
 // Per-warp shared memory (floats): two staging buffers of the upstream gradient (each covers a
 // key span of up to smax samples plus a halo of K + margin + 2 on both sides) and the
-// image-gradient accumulators of one pass ([chunk][xyz][lane]).
+// image-gradient accumulators of one pass ([chunk][xyz][lane], then [chunk][lane] of dL/dA A
+// summed over mics when dL/dg is wanted).
 __host__ __device__ inline int bwd_span(int T) { return T < 1024 ? T : 1024; }
 __host__ __device__ inline int bwd_glen(int T, int K, int margin_i)
 {
@@ -261,9 +262,9 @@ __host__ __device__ inline int bwd_glen(int T, int K, int margin_i)
     const int sp = bwd_span(T) > 2 * margin_i + 2 ? bwd_span(T) : 2 * margin_i + 2;
     return (sp + 2 * K + 2 * margin_i + 6 + 3) & ~3;
 }
-__host__ __device__ inline int bwd_warp_floats(int T, int K, int margin_i)
+__host__ __device__ inline int bwd_warp_floats(int T, int K, int margin_i, bool with_g)
 {
-    return 2 * bwd_glen(T, K, margin_i) + kBwdChunks * 3 * 32;
+    return 2 * bwd_glen(T, K, margin_i) + kBwdChunks * (with_g ? 4 : 3) * 32;
 }
 __host__ __device__ inline int bwd_tab_floats(int K) { return (4 * K + 3) & ~3; }
 
@@ -376,7 +377,7 @@ __device__ __forceinline__ void stage_g(float* Gs, const float* grad_rir, const 
 template <int KT>
 __global__ void __launch_bounds__(kBwdThreads, 5) bwd_kernel(LaunchArgs a, const float* __restrict__ grad_rir,
                                                              const float* __restrict__ grad_early,
-                                                             float* __restrict__ grad_vs)
+                                                             float* __restrict__ grad_vs, float* __restrict__ grad_g)
 {
     extern __shared__ __align__(16) float bwd_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -385,8 +386,10 @@ __global__ void __launch_bounds__(kBwdThreads, 5) bwd_kernel(LaunchArgs a, const
     const int glen = bwd_glen(T, K, Mg);
     const int tabf = (KT == 0) ? bwd_tab_floats(K) : 0;
     float2* tab = reinterpret_cast<float2*>(bwd_smem);
-    float* Gbuf = bwd_smem + tabf + wid * bwd_warp_floats(T, K, Mg);
+    const bool with_g = grad_g != nullptr;
+    float* Gbuf = bwd_smem + tabf + wid * bwd_warp_floats(T, K, Mg, with_g);
     float* gv = Gbuf + 2 * glen;
+    float* gq = gv + kBwdChunks * 96;      // dL/dA A per image (only with grad_g)
     if (KT == 0) {
         for (int j = threadIdx.x; j < 2 * K; j += blockDim.x) {
             float sn, cs;
@@ -434,6 +437,8 @@ __global__ void __launch_bounds__(kBwdThreads, 5) bwd_kernel(LaunchArgs a, const
             for (bool first = true;; first = false) {
                 const int nch = (P.p1 - P.p0 + 31) / 32;
                 for (int k = 0; k < nch * 3; ++k) gv[k * 32 + lane] = 0.f;
+                if (with_g)
+                    for (int k = 0; k < nch; ++k) gq[k * 32 + lane] = 0.f;
                 BwdPass Pn = P;
                 bool more = false, next_direct_only = false;
                 for (int m = 0; m < M; ++m, ++stage) {
@@ -510,6 +515,7 @@ __global__ void __launch_bounds__(kBwdThreads, 5) bwd_kernel(LaunchArgs a, const
                                     g3[32] = __fmaf_rn(dLdD, ey, g3[32]);
                                     g3[64] = __fmaf_rn(dLdD, ez, g3[64]);
                                     rpart = __fmaf_rn(S1 * A * gg, rc.inv_r, rpart);
+                                    if (with_g) gq[ch * 32 + lane] = __fmaf_rn(S1, A, gq[ch * 32 + lane]);
                                 } else {
                                     dsx = __fmaf_rn(dLdD, ex, dsx);
                                     dsy = __fmaf_rn(dLdD, ey, dsy);
@@ -541,15 +547,19 @@ __global__ void __launch_bounds__(kBwdThreads, 5) bwd_kernel(LaunchArgs a, const
                     }
                 }
                 __syncwarp();
-                if (grad_vs) {
+                if (grad_vs || with_g) {
+                    const float lnr = rc.log2r * 0.69314718055994531f;   // dA/dg = A ln r
                     for (int ch = 0; ch < nch; ++ch) {
                         const int slot = P.p0 + 32 * ch + lane;
                         if (slot < P.p1) {
                             const int64_t v = v0 + a.perm[v0 + slot];
                             const float* g3 = gv + ch * 96 + lane;
-                            grad_vs[3 * v] = g3[0];
-                            grad_vs[3 * v + 1] = g3[32];
-                            grad_vs[3 * v + 2] = g3[64];
+                            if (grad_vs) {
+                                grad_vs[3 * v] = g3[0];
+                                grad_vs[3 * v + 1] = g3[32];
+                                grad_vs[3 * v + 2] = g3[64];
+                            }
+                            if (with_g) grad_g[v] = gq[ch * 32 + lane] * lnr;
                         }
                     }
                 }
@@ -604,14 +614,15 @@ __global__ void bwd_reduce(LaunchArgs a, float* __restrict__ grad_mic, float* __
 
 template <int KT>
 cudaError_t launch_bwd_t(const LaunchArgs& a, const float* grad_rir, const float* grad_early, float* grad_vs,
-                         cudaStream_t st)
+                         float* grad_g, cudaStream_t st)
 {
     const int smem = (int)sizeof(float) * ((KT == 0 ? bwd_tab_floats(a.K) : 0) +
-                                           (kBwdThreads / 32) * bwd_warp_floats(a.tile, a.K, a.margin_i));
+                                           (kBwdThreads / 32) * bwd_warp_floats(a.tile, a.K, a.margin_i,
+                                                                                grad_g != nullptr));
     int per_sm = 0;
     cudaError_t e = kernel_residency((const void*)bwd_kernel<KT>, kBwdThreads, smem, &per_sm);
     if (e != cudaSuccess) return e;
-    bwd_kernel<KT><<<device_sm_count() * per_sm, kBwdThreads, smem, st>>>(a, grad_rir, grad_early, grad_vs);
+    bwd_kernel<KT><<<device_sm_count() * per_sm, kBwdThreads, smem, st>>>(a, grad_rir, grad_early, grad_vs, grad_g);
     return cudaGetLastError();
 }
 
@@ -619,7 +630,7 @@ cudaError_t launch_bwd_t(const LaunchArgs& a, const float* grad_rir, const float
 
 cudaError_t launch_backward(const LaunchArgs& a, const float* pos_hi, const float* pos_lo, const float* g,
                             const float* r, const float* grad_rir, const float* grad_early, float* grad_vs,
-                            float* grad_mic, float* grad_src, float* grad_r, cudaStream_t st)
+                            float* grad_mic, float* grad_src, float* grad_r, float* grad_g, cudaStream_t st)
 {
     (void)r;
     (void)pos_hi;
@@ -631,9 +642,9 @@ cudaError_t launch_backward(const LaunchArgs& a, const float* pos_hi, const floa
         g_gather<<<(unsigned)segs, 256, 0, st>>>(a, g);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (a.K == 40) e = launch_bwd_t<40>(a, grad_rir, grad_early, grad_vs, st);
-    else if (a.K == 63) e = launch_bwd_t<63>(a, grad_rir, grad_early, grad_vs, st);
-    else e = launch_bwd_t<0>(a, grad_rir, grad_early, grad_vs, st);
+    if (a.K == 40) e = launch_bwd_t<40>(a, grad_rir, grad_early, grad_vs, grad_g, st);
+    else if (a.K == 63) e = launch_bwd_t<63>(a, grad_rir, grad_early, grad_vs, grad_g, st);
+    else e = launch_bwd_t<0>(a, grad_rir, grad_early, grad_vs, grad_g, st);
     if (e != cudaSuccess) return e;
     const int64_t n = std::max<int64_t>({(int64_t)a.B * a.M * 3, (int64_t)a.B * a.S * 3, (int64_t)a.B});
     if (n > 0 && (grad_mic || grad_src || grad_r)) {

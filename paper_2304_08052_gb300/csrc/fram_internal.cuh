@@ -235,7 +235,7 @@ struct WsLayout {
     size_t spa, spb, pos32, samp, irec;
     size_t mr_y, mr_ye, mr_tab, mr_seg;   // multi-rate mode: intermediate signals, resampling
                                           // table, high-pass segment records
-    size_t part_mic, part_src, part_r;
+    size_t part_mic, part_src, part_r, sb_part;
     size_t total;
     int tile;
     int max_tiles;          // ceil(max_len / tile)
@@ -301,6 +301,7 @@ inline WsLayout ws_layout(const fram_scene& sc, int tile, int delay_mode = 0, do
     w.part_mic = take(sizeof(float) * 3 * (size_t)w.max_items * sc.M);
     w.part_src = take(sizeof(float) * 3 * (size_t)w.max_items);
     w.part_r = take(sizeof(float) * (size_t)w.max_items);
+    w.sb_part = take(sizeof(double) * 5 * (size_t)sc.B * sc.S);
     w.total = off;
     return w;
 }
@@ -357,6 +358,7 @@ struct LaunchArgs {
     float* part_mic;
     float* part_src;
     float* part_r;
+    double* sb_part;        // gradient through the sampler: per (room, source) partial sums
 };
 
 // Host-side launchers (defined in the .cu files; return cudaError_t of the launch).
@@ -367,11 +369,15 @@ cudaError_t launch_prepare(const LaunchArgs& a, const float* pos_hi, const float
 cudaError_t launch_synthesize(const LaunchArgs& a, const float* pos_hi, const float* pos_lo, const float* g,
                               float* rir, float* early, cudaStream_t st);
 cudaError_t launch_amp_gather(const LaunchArgs& a, const float* g, cudaStream_t st);
+cudaError_t launch_sample_backward(const LaunchArgs& a, const fram_params& p, uint64_t seed, const uint64_t* d_seed,
+                                   const float* grad_vs, const float* grad_g, const float* grad_r,
+                                   const float* grad_src_dir, const float* grad_mic_dir, float* grad_src,
+                                   float* grad_mic, float* grad_t60, float* grad_dims, double* part, cudaStream_t st);
 cudaError_t launch_synthesize_mr(const LaunchArgs& a, const float* pos_hi, const float* pos_lo, float* rir,
                                  float* early, cudaStream_t st);
 cudaError_t launch_backward(const LaunchArgs& a, const float* pos_hi, const float* pos_lo, const float* g,
                             const float* r, const float* grad_rir, const float* grad_early, float* grad_vs,
-                            float* grad_mic, float* grad_src, float* grad_r, cudaStream_t st);
+                            float* grad_mic, float* grad_src, float* grad_r, float* grad_g, cudaStream_t st);
 
 int device_sm_count();
 

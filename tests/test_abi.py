@@ -34,7 +34,7 @@ def test_exports_every_declared_symbol(L):
 
 
 def test_version_and_defaults(L):
-    assert L.fram_version() == 10000
+    assert L.fram_version() == 10100
     p = _lib.FramParams()
     L.fram_default_params(ctypes.byref(p))
     assert (p.alpha, p.beta, p.a, p.b, p.tau, p.c0) == (0.25, 1.0, -2.0, 2.0, 0.25, 343.0)
@@ -94,7 +94,9 @@ def test_entry_points_reject_bad_arguments_before_any_launch(L):
     assert L.fram_synthesize(ctypes.byref(sc), ctypes.byref(p.c()), null, null, null, null, null, null, null, 0,
                              None) == _lib.FRAM_EINVAL
     assert L.fram_synthesize_backward(ctypes.byref(sc), ctypes.byref(p.c()), null, null, null, null, null, null,
-                                      null, null, null, null, null, 0, None) == _lib.FRAM_EINVAL
+                                      null, null, null, null, null, null, 0, None) == _lib.FRAM_EINVAL
+    assert L.fram_sample_backward(ctypes.byref(sc), ctypes.byref(p.c()), 0, None, null, null, null, null, null,
+                                  null, null, null, null, null, 0, None) == _lib.FRAM_EINVAL
     assert L.fram_status(null, None, None) == _lib.FRAM_EINVAL
     # A fake (never dereferenced) device pointer set: the workspace checks fail first.
     fake = ctypes.c_void_p(0x1000)

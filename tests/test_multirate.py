@@ -42,7 +42,8 @@ def test_backward_is_refused_in_the_multirate_mode():
     n = ctypes.c_size_t(0)
     assert L.fram_workspace_size(ctypes.byref(sc), ctypes.byref(p.c()), ctypes.byref(n)) == 0
     rc = L.fram_synthesize_backward(ctypes.byref(sc), ctypes.byref(p.c()), fake, None, fake, fake, fake, None,
-                                    None, None, None, None, ctypes.c_void_p(0x100000), ctypes.c_size_t(n.value), None)
+                                    None, None, None, None, None, ctypes.c_void_p(0x100000), ctypes.c_size_t(n.value),
+                                    None)
     assert rc == _lib.FRAM_EINVAL
     assert b"delay_mode" in L.fram_last_error()
 
