@@ -6,6 +6,7 @@ Workload (default): large_4096 -- 4096 rooms x 2 sources x 16-mic circle at 48 k
 A step is one pass of the whole hot path over the batch:
   fwd:      fram_sample (Philox images) -> fram_synthesize (prologue, delay bins, synthesis)
   fwd+bwd:  fwd -> fram_synthesize_backward_prepared (adjoint, reusing the forward's bins)
+  fwd+bwd through the sampler (reported beside): fwd+bwd with dL/dg -> fram_sample_backward
 value = RIRs/s of the fwd step (one RIR = one 16-channel filter per room x source), whole job.
 
 Also reported: taps/s; the synthesis kernel alone against the ALU roofline; the adjoint kernel
@@ -35,9 +36,9 @@ METRIC = "multi-ch RIRs/s and sinc-taps/s (fwd, fwd+bwd) at 1 GB300, % of roofli
 # forward 8 FP32-pipe operations and 1 reciprocal on the MUFU (special function) pipe; adjoint
 # 14 FP32 and 1 MUFU.  Per arrival (image x mic) 40 FP32 + 6 MUFU more, spread over its 2K+1 taps.
 # DRAM bytes (read + write) of one synth_kernel launch per output sample, from one ncu capture
-# (large_4096, first 256 rooms, 283357184 output samples: 0.0825 GB read + 1.0746 GB written);
+# (large_4096, first 256 rooms, 283357184 output samples: 0.0816 GB read + 1.0738 GB written);
 # reported only while the synthesis source is the one that was measured (its SHA-256 prefix).
-SYNTH_TRAFFIC = {"source_sha256": "493a3c033a1bdeac", "bytes_per_sample": (0.0825e9 + 1.0746e9) / 283357184}
+SYNTH_TRAFFIC = {"source_sha256": "d43039a66a5596cf", "bytes_per_sample": (81627136 + 1073798912) / 283357184}
 
 # Kernels of libfram per fwd step: sample_kernel; room_prologue, item_scan, bin_images,
 # sort_positions, item_ranges (preparation); amp_gather, synth_kernel (synthesis).
@@ -265,6 +266,9 @@ def main():
     G = torch.empty(T, device="cuda").normal_(generator=torch.Generator(device="cuda").manual_seed(7))
     grads = (torch.empty((N, 3), device="cuda"), torch.empty((sc.B, sc.M, 3), device="cuda"),
              torch.empty((sc.B, sc.S, 3), device="cuda"), torch.empty(sc.B, device="cuda"))
+    grad_g = torch.empty(N, device="cuda")
+    sgrads = (torch.empty((sc.B, sc.S, 3), device="cuda"), torch.empty((sc.B, sc.M, 3), device="cuda"),
+              torch.empty(sc.B, device="cuda"), torch.empty((sc.B, 3), device="cuda"))
     taps = api.algorithmic_taps(ds)
     rirs = sc.B * sc.S
 
@@ -276,6 +280,14 @@ def main():
         fwd(k)
         api.synthesize_backward_prepared(ds, vs.pos_hi, vs.pos_lo, vs.g, vs.r, G, None, out=grads)
 
+    def sampler_bwd(k):
+        api.sample_backward(ds, 1000 + k, grads[0], grad_g, grads[3], grads[2], grads[1], out=sgrads)
+
+    def fwd_bwd_sampler(k):
+        fwd(k)
+        api.synthesize_backward_prepared(ds, vs.pos_hi, vs.pos_lo, vs.g, vs.r, G, None, out=grads, grad_g=grad_g)
+        sampler_bwd(k)
+
     api.sample(ds, seed=999, out=vs)
     tile = api.autotune(ds, vs, rir)       # picks the tile length; tile = 0 launches use it
 
@@ -284,12 +296,14 @@ def main():
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
 
     for k in range(args.warmup):
-        fwd_bwd(k)
+        fwd_bwd_sampler(k)
     torch.cuda.synchronize()
     assert ds.status() == 0, "device status flags set"
     with ClockSampler(_gpu_uuid(torch)) as clk:
         t_fwd = _time_steps(torch, fwd, args.steps, dist_ok)
         t_fb = _time_steps(torch, fwd_bwd, args.steps, dist_ok)
+        t_fbs = _time_steps(torch, fwd_bwd_sampler, args.steps, dist_ok)
+        t_sb = _time_steps(torch, sampler_bwd, args.steps, False)
         # Kernels alone on the same stream, after one preparation.
         api.prepare(ds, vs.pos_hi, vs.pos_lo, vs.r)
         t_syn = _time_steps(torch, lambda k: api.synthesize_prepared(ds, vs.pos_hi, vs.pos_lo, vs.g, vs.r, rir),
@@ -328,6 +342,12 @@ def main():
                                    f"{clock_hz / 1e6:.0f} MHz ({peak_kind} sm_max_mhz); per tap "
                                    f"{FWD_FP32:.0f} FP32 + {TAP_MUFU:.0f} MUFU, per arrival {ARR_FP32:.0f} FP32 + "
                                    f"{ARR_MUFU:.0f} MUFU"},
+        "fwd_bwd_through_sampler": {
+            "value": world * args.steps * rirs / t_fbs, "unit": "RIRs/s", "ms_per_step": 1000.0 * t_fbs / args.steps,
+            "sample_backward_ms": 1000.0 * t_sb / args.steps,
+            "sample_backward_hbm_gbs": 16.0 * N / (t_sb / args.steps) / 1e9,
+            "note": "fwd -> adjoint with dL/dg -> fram_sample_backward (source, mic, T60, room-size gradients "
+                    "with the draws held fixed); sample_backward reads 16 B per image"},
         "roofline_bwd": {"bound": "alu", "achieved": ach_bwd / 1e9, "peak": peak_bwd / 1e9, "unit": "Gtap/s",
                          "frac": ach_bwd / peak_bwd, "kernel": "bwd_kernel", "limit": lim_bwd,
                          "kernel_ms": 1000.0 * bwd_s},

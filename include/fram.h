@@ -208,8 +208,9 @@ int fram_synthesize_backward(const fram_scene* scene, const fram_params* p,
  * and grad_mic; they may alias grad_src / grad_mic (each element is read before it is written).
  * seed / d_seed must be those of the fram_sample call that drew the images.
  * Outputs (device, nullable, overwritten): grad_src [B,S,3], grad_mic [B,M,3] (totals: direct
- * plus sampler paths), grad_t60 [B], grad_dims [B,3].  Per (room, source) sums run in FP64 in a
- * fixed order (bit-reproducible).  Device status FRAM_DEV_BAD_GEOMETRY as for fram_sample (that
+ * plus sampler paths), grad_t60 [B], grad_dims [B,3].  Per (room, source) sums over images run
+ * in FP32 per thread (strided images), then in FP64 across threads, in a fixed order
+ * (bit-reproducible).  Device status FRAM_DEV_BAD_GEOMETRY as for fram_sample (that
  * (room, source) contributes no sampler path).  Uses the workspace (sized by
  * fram_workspace_size for this scene).
  */

@@ -203,15 +203,17 @@ def synthesize_backward_raw(sc: DeviceScene, pos_hi, pos_lo, g, r, grad_rir, gra
 
 def sample_backward(sc: DeviceScene, seed: int, grad_vs, grad_g=None, grad_r=None, grad_src_in=None,
                     grad_mic_in=None, d_seed: Optional[torch.Tensor] = None, src=None, mic=None, dims=None,
-                    rt60=None):
+                    rt60=None, out=None):
     """fram_sample_backward: carry image and r gradients back through the sampler (draws of
     `seed` held fixed).  Returns (grad_src [B,S,3], grad_mic [B,M,3], grad_t60 [B], grad_dims [B,3]),
     source and mic gradients including grad_src_in / grad_mic_in (the direct paths)."""
     dev = sc.dims.device
-    gs = torch.empty((sc.B, sc.S, 3), dtype=torch.float32, device=dev)
-    gm = torch.empty((sc.B, sc.M, 3), dtype=torch.float32, device=dev)
-    gt = torch.empty(sc.B, dtype=torch.float32, device=dev)
-    gd = torch.empty((sc.B, 3), dtype=torch.float32, device=dev)
+    if out is None:
+        out = (torch.empty((sc.B, sc.S, 3), dtype=torch.float32, device=dev),
+               torch.empty((sc.B, sc.M, 3), dtype=torch.float32, device=dev),
+               torch.empty(sc.B, dtype=torch.float32, device=dev),
+               torch.empty((sc.B, 3), dtype=torch.float32, device=dev))
+    gs, gm, gt, gd = out
     check(lib().fram_sample_backward(ctypes.byref(sc.c_scene(src, mic, dims, rt60)), ctypes.byref(sc.params.c()),
                                      ctypes.c_uint64(seed & (2**64 - 1)), _ptr(d_seed), _ptr(grad_vs), _ptr(grad_g),
                                      _ptr(grad_r), _ptr(grad_src_in), _ptr(grad_mic_in), _ptr(gs), _ptr(gm), _ptr(gt),
@@ -304,7 +306,7 @@ def synthesize_prepared(sc: DeviceScene, pos_hi, pos_lo, g, r, rir, early_out=No
 
 
 def synthesize_backward_prepared(sc: DeviceScene, pos_hi, pos_lo, g, r, grad_rir, grad_early=None, out=None,
-                                 src=None, mic=None):
+                                 src=None, mic=None, grad_g=None):
     """fram_synthesize_backward_prepared: the adjoint kernels alone, after prepare()."""
     dev = sc.dims.device
     if out is None:
@@ -317,7 +319,8 @@ def synthesize_backward_prepared(sc: DeviceScene, pos_hi, pos_lo, g, r, grad_rir
     mic = sc.mic if mic is None else mic
     check(lib().fram_synthesize_backward_prepared(ctypes.byref(sc.c_scene(src, mic)), ctypes.byref(sc.params.c()),
                                                   _ptr(pos_hi), _ptr(pos_lo), _ptr(g), _ptr(r), _ptr(grad_rir),
-                                                  _ptr(grad_early), _ptr(gv), _ptr(gm), _ptr(gs), _ptr(gr), None,
+                                                  _ptr(grad_early), _ptr(gv), _ptr(gm), _ptr(gs), _ptr(gr),
+                                                  _ptr(grad_g),
                                                   ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes),
                                                   _stream()))
     return out

@@ -49,6 +49,7 @@ struct SampledImage {
     float nx, ny, nz;       // unit direction of the image from the array centre
     float k;                // (x - alpha) / (beta - alpha)
     float D, DR, pert;      // D_i, D_i / D0, a + (b - a) u3
+    float DRt;              // DR^tau
 };
 
 __device__ __forceinline__ SampledImage sample_image(const SampleConst& C, u4 w)
@@ -84,7 +85,8 @@ __device__ __forceinline__ SampledImage sample_image(const SampleConst& C, u4 w)
     f2 trend = f2_add_f(f2_mul(f2_mul(ratio, ratio), C.rrm1), 1.0f);
     const float DR = __fadd_rn(f2_mul(D, C.inv_d0).hi, 0.0f);
     const float pp = __fmaf_rn(C.bma, u3, C.a);
-    const float pert = __fmul_rn(pp, exp2f(C.tau * log2f(DR)));
+    const float DRt = exp2f(C.tau * log2f(DR));
+    const float pert = __fmul_rn(pp, DRt);
     f2 g = f2_add_f(trend, pert);
     float gf = __fadd_rn(g.hi, g.lo);
     // Clamp in pair precision against RR_max and 1.
@@ -99,6 +101,7 @@ __device__ __forceinline__ SampledImage sample_image(const SampleConst& C, u4 w)
     im.D = D.hi + D.lo;
     im.DR = DR;
     im.pert = pp;
+    im.DRt = DRt;
     return im;
 }
 
@@ -242,7 +245,8 @@ __global__ void __launch_bounds__(256) sample_backward_kernel(LaunchArgs a, doub
     if (n < 0 || row0 < 0 || row0 + n > a.n_vs_total || !C.valid) n = 0;
     const float D0 = (float)X[0], cT = (float)X[1], RR = (float)X[2];
     const float inv_cT2 = 1.0f / (cT * cT), rrm1 = RR - 1.0f;
-    double dD0 = 0.0, dcT = 0.0, dRR = 0.0, dc0 = 0.0, dc1 = 0.0, dc2 = 0.0;
+    // Per-thread sums in FP32 over the thread's images (a few dozen), then FP64 across threads.
+    float dD0 = 0.f, dcT = 0.f, dRR = 0.f, dc0 = 0.f, dc1 = 0.f, dc2 = 0.f;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int64_t v = row0 + i;
         const u4 w = philox4x32_10(u4{(uint32_t)i, (uint32_t)s, (uint32_t)b, 0u}, key_s[0], key_s[1]);
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(256) sample_backward_kernel(LaunchArgs a, doub
         if (im.clamp == 1) {
             dRR += gg;
         } else if (im.clamp == 0) {                                // Eq. 6 inside the clamp
-            const float drt = C.tau * exp2f(C.tau * log2f(im.DR)) / im.DR;   // d(DR^tau)/dDR
+            const float drt = C.tau * im.DRt / im.DR;                  // d(DR^tau)/dDR
             dDi += gg * (2.0f * im.D * inv_cT2 * rrm1 + im.pert * drt / D0);
             dD0g = gg * (-im.pert * drt * im.D / (D0 * D0));
             dcTg = gg * (-2.0f * im.D * im.D * inv_cT2 / cT * rrm1);
@@ -264,7 +268,7 @@ __global__ void __launch_bounds__(256) sample_backward_kernel(LaunchArgs a, doub
         dD0 += dDi * (1.0f - im.k) + dD0g;                        // Eq. 4 as D_i = D0 (1-k) + k c0 T60
         dcT += dDi * im.k + dcTg;
     }
-    double v6[6] = {dD0, dcT, dRR, dc0, dc1, dc2};
+    double v6[6] = {(double)dD0, (double)dcT, (double)dRR, (double)dc0, (double)dc1, (double)dc2};
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < 6; ++k) v6[k] = warp_sum_d(v6[k]);
