@@ -17,6 +17,9 @@ Functions and the passages they follow:
   synthesize_mr(...)          the paper's multi-rate output path (Sec. II-B, Eq. 7-9): impulses
                               on the r_h fs grid, down to r_l fs, 80 Hz high-pass, down to fs
   mr_rates, resample_filter, hpf_coeffs   its rates and filters (readings: see fram_oracle.c)
+  spatialize(...)             Sec. IV-A's use of the RIRs: signals convolved with them, mixed at
+                              the given SIR / SNR, optional per-speaker targets (readings: see
+                              fram_oracle.c)
 
 Every function is pinned by tests that do not reuse its own arithmetic (see the module
 docstrings of tests/test_oracle_*.py).  No function here is "parity unpinned".
@@ -283,3 +286,28 @@ def synthesize_mr(scene, params: Params, vs_pos, vs_g, r, early: bool = False):
     if rc != 0:
         raise ValueError("oracle synthesize_mr: invalid parameters or out of memory")
     return (rir, he) if early else rir
+
+
+def spatialize(rir_len, rir_off, rir, signals, n_speech: int, level_db, target_rir=None, M: int = None):
+    """Mixture [B,M,N], targets [B,n_speech,M,N] (None without target_rir) and gains [B,S] of
+    the Sec. IV-A spatialisation: signals [B,S,N] convolved with the ragged RIR buffer (room b
+    at rir_off[b], [S][M][L_b]), speakers scaled to level_db (SIR, dB) against speaker 0, noise
+    sources (s >= n_speech) to level_db (SNR, dB) against the speech at mic 0."""
+    x = _f64(signals)
+    B, S, N = x.shape
+    rir_len = np.ascontiguousarray(rir_len, dtype=np.int32)
+    rir_off = np.ascontiguousarray(rir_off, dtype=np.int64)
+    if M is None:
+        M = int((rir_off[1] - rir_off[0]) // (S * rir_len[0])) if B else 1
+    h = _f64(rir)
+    ht = _f64(target_rir) if target_rir is not None else None
+    lv = _f64(level_db).reshape(B, S)
+    mix = np.empty((B, M, N))
+    tg = np.empty((B, n_speech, M, N)) if ht is not None else None
+    g = np.empty((B, S))
+    rc = _load().fo_spatialize(ctypes.c_int32(B), ctypes.c_int32(S), ctypes.c_int32(M), _p(rir_len), _p(rir_off),
+                               _p(h), _p(ht), ctypes.c_int64(N), _p(x), ctypes.c_int32(n_speech), _p(lv),
+                               _p(mix), _p(tg), _p(g))
+    if rc != 0:
+        raise ValueError("oracle spatialize: invalid arguments")
+    return mix, tg, g

@@ -33,6 +33,11 @@
  *   fo_synthesize_mr  the paper's own multi-rate output path (Sec. II-B, Eq. 7-9): impulses
  *                     quantised to the r_h fs grid, resampled to r_l fs, high-passed at 80 Hz,
  *                     resampled to fs (filter readings stated with the function).
+ *   fo_spatialize     the training-data use of the RIRs (Sec. IV-A): each source signal
+ *                     convolved with its RIRs, speakers scaled to a signal-to-interference
+ *                     ratio against the first speaker, point-source noise to a signal-to-noise
+ *                     ratio against the speech, summed into the microphone mixture; optional
+ *                     per-speaker targets through a second RIR set (e.g. the early RIR, Eq. 9).
  *
  * Parity pins (what fixes each function independently of itself) live in the tests:
  *   Philox against the curand host generator; Eq. 2 against Eyring's reverberation formula;
@@ -687,6 +692,88 @@ int fo_synthesize_mr(int32_t B, int32_t S, int32_t M, const double* src, const d
     }
     free(FA);
     free(FC);
+    return err ? -2 : 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Spatialisation (Sec. IV-A).  Readings (the paper names the quantities, not the formulas): */
+/*   image   y_{s,m}[n] = sum_{k=0}^{min(L-1, n)} h_{s,m}[k] x_s[n - k],  n in [0, N)       */
+/*           (causal convolution kept on the mixture's N samples);                           */
+/*   energy  E_s = sum_n y_{s,0}[n]^2 at the reference mic 0;                                 */
+/*   gains   g_0 = 1; speaker s in [1, n_speech): g_s = sqrt(E_0 / E_s * 10^(-l_s/10)), so    */
+/*           10 log10(E_0 / (g_s^2 E_s)) = l_s (the SIR in dB); the speech at mic 0           */
+/*           v[n] = sum_{s < n_speech} g_s y_{s,0}[n]; noise s >= n_speech:                     */
+/*           g_s = sqrt(E_v / E_s * 10^(-l_s/10)), E_v = sum_n v[n]^2 (l_s = the SNR in dB);   */
+/*           a silent image (E_s = 0) gets g_s = 0;                                             */
+/*   outputs mix_m[n] = sum_s g_s y_{s,m}[n]; targets t_{s,m}[n] = g_s (h'_{s,m} * x_s)[n] for */
+/*           s < n_speech with a second RIR set h' (the early RIR of Eq. 9, or h itself).      */
+/* ------------------------------------------------------------------------------------ */
+static void fo_conv_trunc(const double* h, int32_t L, const double* x, int64_t N, double* y)
+{
+    for (int64_t n = 0; n < N; ++n) {
+        double acc = 0.0;
+        const int64_t kmax = n < (int64_t)L - 1 ? n : (int64_t)L - 1;
+        for (int64_t k = 0; k <= kmax; ++k) acc += h[k] * x[n - k];
+        y[n] = acc;
+    }
+}
+
+int fo_spatialize(int32_t B, int32_t S, int32_t M, const int32_t* rir_len, const int64_t* rir_off,
+                  const double* rir, const double* target_rir, int64_t N, const double* x, int32_t n_speech,
+                  const double* level_db, double* mix, double* targets, double* gains)
+{
+    if (B < 0 || S < 1 || M < 1 || N < 0 || n_speech < 1 || n_speech > S) return -1;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+    for (int32_t b = 0; b < B; ++b) {
+        const int32_t L = rir_len[b];
+        double* y = (double*)malloc(sizeof(double) * (size_t)(S * (int64_t)M * N + N + 1));
+        double* E = (double*)malloc(sizeof(double) * (size_t)S);
+        if (!y || !E) { err = 1; free(y); free(E); continue; }
+        double* v = y + (int64_t)S * M * N;
+        for (int32_t s = 0; s < S; ++s)
+            for (int32_t m = 0; m < M; ++m)
+                fo_conv_trunc(rir + rir_off[b] + ((int64_t)s * M + m) * L, L, x + ((int64_t)b * S + s) * N, N,
+                              y + ((int64_t)s * M + m) * N);
+        for (int32_t s = 0; s < S; ++s) {
+            double e = 0.0;
+            const double* y0 = y + (int64_t)s * M * N;
+            for (int64_t n = 0; n < N; ++n) e += y0[n] * y0[n];
+            E[s] = e;
+        }
+        double* g = gains + (int64_t)b * S;
+        g[0] = 1.0;
+        for (int32_t s = 1; s < n_speech; ++s)
+            g[s] = E[s] > 0.0 ? sqrt(E[0] / E[s] * pow(10.0, -level_db[(int64_t)b * S + s] / 10.0)) : 0.0;
+        double Ev = 0.0;
+        for (int64_t n = 0; n < N; ++n) {
+            double acc = 0.0;
+            for (int32_t s = 0; s < n_speech; ++s) acc += g[s] * y[(int64_t)s * M * N + n];
+            v[n] = acc;
+            Ev += acc * acc;
+        }
+        for (int32_t s = n_speech; s < S; ++s)
+            g[s] = E[s] > 0.0 ? sqrt(Ev / E[s] * pow(10.0, -level_db[(int64_t)b * S + s] / 10.0)) : 0.0;
+        for (int32_t m = 0; m < M; ++m) {
+            double* out = mix + ((int64_t)b * M + m) * N;
+            for (int64_t n = 0; n < N; ++n) {
+                double acc = 0.0;
+                for (int32_t s = 0; s < S; ++s) acc += g[s] * y[((int64_t)s * M + m) * N + n];
+                out[n] = acc;
+            }
+        }
+        if (targets) {
+            for (int32_t s = 0; s < n_speech; ++s)
+                for (int32_t m = 0; m < M; ++m) {
+                    double* t = targets + (((int64_t)b * n_speech + s) * M + m) * N;
+                    fo_conv_trunc(target_rir + rir_off[b] + ((int64_t)s * M + m) * L, L,
+                                  x + ((int64_t)b * S + s) * N, N, t);
+                    for (int64_t n = 0; n < N; ++n) t[n] *= g[s];
+                }
+        }
+        free(y);
+        free(E);
+    }
     return err ? -2 : 0;
 }
 

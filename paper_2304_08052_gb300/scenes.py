@@ -19,6 +19,14 @@ benchmark workloads built on it:
                  (10 cm), 2 sources, round(6000*T60) images, 48 kHz, K = 63.
   tiny(...)      small scenes for exhaustive CPU/GPU comparisons.
 
+Source signals for the spatialisation (mixture) path, mixtures(...): the paper mixes two
+LibriSpeech utterances and one noise recording per training example (Sec. IV-A); no dataset is
+used here.  Speakers are Gaussian noise shaped by a random syllable-rate envelope (3-6 Hz) and a
+random one-pole spectral tilt, active over a stretch of the mixture so that the two speakers
+overlap on a fraction U[0.5, 1] of it (the paper's minimum overlap ratio of 0.5); noise is
+stationary Gaussian noise with its own tilt spanning the whole mixture.  SIR ~ U[-6, 6] dB per
+extra speaker and SNR ~ U[10, 20] dB per noise source, as in Sec. IV-A.
+
 Conventions: linear arrays lie along +x centred on the array point; circular arrays lie in
 the horizontal plane with mic k at angle 2*pi*k/M + psi, psi drawn per room.  A source
 closer than 0.3 m to the array centre is redrawn (up to 16 attempts, then pushed radially).
@@ -186,3 +194,45 @@ def synthetic_vs(seed: int, scene: Scene, max_dist: float = 60.0):
         g.append(rng.uniform(1.0, 40.0, size=n))
     return (np.concatenate(pos).astype(np.float32) if pos else np.zeros((0, 3), np.float32),
             np.concatenate(g).astype(np.float32) if g else np.zeros(0, np.float32))
+
+
+@dataclass
+class Mixtures:
+    signals: np.ndarray   # [B,S,N] float32, sources on the mixture's timeline
+    level_db: np.ndarray  # [B,S] float32: SIR (speakers s >= 1) or SNR (noise) in dB; entry 0 unused
+    n_speech: int
+
+
+def _tilt(rng, x, lo, hi):
+    from scipy.signal import lfilter
+    return lfilter([1.0], [1.0, -rng.uniform(lo, hi)], x)     # y[n] = x[n] + a y[n-1]
+
+
+def mixtures(seed: int, B: int, S: int, N: int, fs: float, n_speech: int = None) -> Mixtures:
+    """Seeded synthetic sources for B examples of S sources (the last S - n_speech are noise;
+    default n_speech = S - 1 when S > 1), N samples each at fs."""
+    if n_speech is None:
+        n_speech = S - 1 if S > 1 else 1
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sig = np.zeros((B, S, N), np.float64)
+    lev = np.zeros((B, S), np.float64)
+    t = np.arange(N) / fs
+    for b in range(B):
+        rho = rng.uniform(0.5, 1.0)                 # overlap ratio of the first two speakers
+        span = int(round(N * (1.0 + rho) / 2.0))
+        for s in range(S):
+            w = rng.standard_normal(N)
+            if s < n_speech:
+                env = np.abs(np.sin(np.pi * rng.uniform(3.0, 6.0) * t + rng.uniform(0, np.pi)))
+                env *= np.sqrt(env)
+                x = _tilt(rng, w, 0.3, 0.95) * env
+                if n_speech > 1:
+                    first = (s == 0) == (rng.uniform() < 0.5)
+                    lo, hi = (0, span) if first else (N - span, N)
+                    x[:lo] = 0.0
+                    x[hi:] = 0.0
+            else:
+                x = _tilt(rng, w, 0.0, 0.8)
+            sig[b, s] = x / max(np.abs(x).max(), 1e-12)
+            lev[b, s] = 0.0 if s == 0 else (rng.uniform(-6.0, 6.0) if s < n_speech else rng.uniform(10.0, 20.0))
+    return Mixtures(sig.astype(np.float32), lev.astype(np.float32), int(n_speech))
