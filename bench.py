@@ -234,10 +234,21 @@ def main():
     ap.add_argument("--cpu-rooms-1core", type=int, default=32)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-room comparison and the CPU baseline")
+    ap.add_argument("--spatialize-rooms", type=int, default=0,
+                    help="only time fram_spatialize on the first N rooms of batch_1024 (for profiling) and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.spatialize_rooms > 0:
+        import torch
+
+        from paper_2304_08052_gb300 import api, build, scenes
+        build.build()
+        peaks, _ = _measured_peaks()
+        print(json.dumps({"spatialize_only": spatialize_batch(torch, api, scenes, peaks, cpu_rooms=0,
+                                                              rooms=args.spatialize_rooms)}), flush=True)
+        return 0
 
     import numpy as np
     import torch
@@ -362,6 +373,7 @@ def main():
         line["graph_vs_per_room"] = graph_vs_per_room(torch, api, scenes)
         line["single_room_latency"] = single_room_latency(torch, api, scenes)
         line["multirate_vs_continuous"] = multirate_vs_continuous(torch, api, scenes, peaks)
+        line["spatialize"] = spatialize_batch(torch, api, scenes, peaks)
         u, dt, cores = cpu_baseline(sc, 1, list(range(args.cpu_rooms)), params)
         line["cpu_baseline"] = {"value": u / dt, "unit": "RIRs/s", "cores": cores, "kind": "oracle",
                                 "sample": f"first {args.cpu_rooms} rooms of {args.workload} (sample + synthesize, "
@@ -492,6 +504,74 @@ def multirate_vs_continuous(torch, api, scenes, peaks):
     out["multirate"]["cpu_oracle"] = {"value": len(rooms) * sc.S / dt, "unit": "RIRs/s", "cores": oracle.num_threads(),
                                       "sample": f"first {len(rooms)} rooms (sample + multi-rate synthesize, FP64, {dt:.1f} s)"}
     return out
+
+
+def spatialize_batch(torch, api, scenes, peaks, n_samples=64000, cpu_rooms=2, rooms=0):
+    """The paper's consumer of the RIRs (Sec. IV-A): each training example is a room with two
+    speakers and one point-source noise, spatialised by the room's RIRs into an 8-channel mixture
+    at SIR U[-6, 6] dB and SNR U[10, 20] dB, with the speakers' early-RIR (Eq. 9) images as
+    dereverberation targets.  batch_1024 (1024 rooms x 3 sources x 8 mics, 16 kHz), 4 s sources.
+    Timed: fram_spatialize alone, and the whole on-the-fly step (sample + synthesize with early
+    RIRs + spatialize).  Algorithmic bytes: RIRs + early RIRs + signals read, mixture + targets
+    written."""
+    sc = scenes.batch_1024(0)
+    if rooms > 0:
+        sc = sc.subset(range(min(rooms, sc.B)))
+    params = api.Params(fs=sc.fs, half_len=sc.half_len)
+    ds = api.DeviceScene(sc, params)
+    N = ds.n_vs_total
+    vs = api.Images(torch.empty((N, 3), device="cuda"), torch.empty((N, 3), device="cuda"),
+                    torch.empty(N, device="cuda"), torch.empty(sc.B, device="cuda"))
+    rir = torch.empty(ds.rir_total, device="cuda")
+    early = torch.empty(ds.rir_total, device="cuda")
+    mx = scenes.mixtures(3, sc.B, sc.S, n_samples, sc.fs)
+    sig = torch.from_numpy(mx.signals).cuda()
+    lev = torch.from_numpy(mx.level_db).cuda()
+    out = (torch.empty((sc.B, sc.M, n_samples), device="cuda"),
+           torch.empty((sc.B, mx.n_speech, sc.M, n_samples), device="cuda"), torch.empty((sc.B, sc.S), device="cuda"))
+
+    def rirs(k):
+        api.sample(ds, seed=700 + k, out=vs)
+        api.synthesize_raw(ds, vs.pos_hi, vs.pos_lo, vs.g, vs.r, early=True, rir=rir, early_out=early)
+
+    def spat(k):
+        api.spatialize(ds, rir, sig, lev, mx.n_speech, target_rir=early, targets=True, out=out)
+
+    def step(k):
+        rirs(k)
+        spat(k)
+
+    for k in range(3):
+        step(k)
+    torch.cuda.synchronize()
+    t_sp = _time_steps(torch, spat, 5, False) / 5
+    t_step = _time_steps(torch, step, 5, False) / 5
+    assert ds.status() == 0 and api.spatialize_status(ds) == 0, "device status flags set"
+    moved = 4 * (2 * ds.rir_total + sig.numel() + out[0].numel() + out[1].numel())
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    res = {"workload": f"batch_1024 ({sc.B} rooms x (2 speakers + 1 noise) x 8 mics, 16 kHz), {n_samples / sc.fs:.0f} s "
+                       "sources, mixture + early-RIR targets",
+           "spatialize": {"ms_per_batch": 1000.0 * t_sp, "value": sc.B / t_sp, "unit": "examples/s",
+                          "roofline": {"bound": "hbm", "achieved": moved / t_sp / 1e9, "peak": peak, "unit": "GB/s",
+                                       "frac": moved / t_sp / 1e9 / peak, "bytes_per_batch": moved,
+                                       "note": "algorithmic bytes (inputs read once, outputs written once)"}},
+           "on_the_fly_step": {"ms_per_batch": 1000.0 * t_step, "value": sc.B / t_step, "unit": "examples/s",
+                               "note": "sample + synthesize (RIR and early RIR) + spatialize"}}
+    if cpu_rooms <= 0:
+        return res
+    import oracle
+    rl_ = list(range(cpu_rooms))
+    sub = sc.subset(rl_)
+    op = oracle.Params(fs=sc.fs, half_len=sc.half_len)
+    ref = oracle.sample(sub, op, 1, room_ids=rl_)
+    h, he = oracle.synthesize(sub, op, ref.pos, ref.g, ref.r, early=True)
+    rl, ro, _ = oracle.layout(sub.rt60, sub.n_vs, sub.S, sub.M, sub.fs)
+    t0 = time.perf_counter()
+    oracle.spatialize(rl, ro, h, mx.signals[rl_], mx.n_speech, mx.level_db[rl_], target_rir=he, M=sc.M)
+    dt = time.perf_counter() - t0
+    res["spatialize"]["cpu_oracle"] = {"value": len(rl_) / dt, "unit": "examples/s", "cores": oracle.num_threads(),
+                                       "sample": f"first {len(rl_)} rooms (direct FP64 convolution, {dt:.1f} s)"}
+    return res
 
 
 def graph_vs_per_room(torch, api, scenes):

@@ -282,6 +282,47 @@ int fram_synthesize_noalloc(const fram_scene* scene, const fram_params* p, const
                             const float* vs_pos_lo, const float* vs_g, const float* r, float* rir,
                             float* early, void* stream);
 
+/*
+ * Spatialisation: the paper's use of the RIRs for training data (Sec. IV-A).  For every room
+ * b, source s < S, mic m and sample n < N:
+ *   y_{s,m}[n] = sum_{k=0}^{min(L_b-1, n)} h_{s,m}[k] x_s[n-k]          (image of source s)
+ *   E_s = sum_n y_{s,0}[n]^2                                              (energy at mic 0)
+ *   g_0 = 1;  speakers 1 <= s < n_speech: g_s = sqrt(E_0/E_s 10^(-level_s/10))   (level = SIR, dB)
+ *   speech at mic 0 v = sum_{s<n_speech} g_s y_{s,0}, E_v = sum_n v[n]^2;
+ *   noise s >= n_speech: g_s = sqrt(E_v/E_s 10^(-level_s/10))                   (level = SNR, dB)
+ *   (g_s = 0 for a silent image, E_s = 0)
+ *   mixture_m[n] = sum_s g_s y_{s,m}[n];  targets_{s,m}[n] = g_s (h'_{s,m} * x_s)[n], s < n_speech,
+ * with h' = target_rir (the early RIR of Eq. 9 for dereverberation targets, or rir itself).
+ * The paper mixes two speakers (SIR in [-6, 6] dB, overlap >= 0.5) and one point-source noise
+ * (SNR in [10, 20] dB); signals are given already placed on the mixture's timeline.
+ * Computed by FFT overlap-save convolution in FP32 (error ~1e-6 of each channel's peak) with
+ * FP64 energies; results are bit-reproducible run to run.
+ * Inputs (device): rir / target_rir in fram_synthesize's ragged layout (scene->rir_len,
+ * rir_off, max_len; dims, src and the image fields of the scene are not read); signals
+ * [B,S,N]; level_db [B,S] (entry 0 of each room unused).  Outputs (device, caller-owned,
+ * overwritten): mixture [B,M,N]; targets [B,n_speech,M,N] (nullable; needs target_rir);
+ * gains [B,S] (nullable).  Host errors: FRAM_EINVAL (S > 8, n_speech outside [1, S], N < 1,
+ * bad block), FRAM_EWORKSPACE.  Device status: FRAM_DEV_BAD_GEOMETRY if a room's rir_len /
+ * rir_off disagree with max_len / rir_total (that RIR is read as zeros).
+ * The workspace (256-byte aligned, fram_spatialize_workspace_size with separate_targets = 1
+ * when targets come from a different RIR buffer) holds the spectra of one chunk of rooms.
+ */
+typedef struct {
+    int64_t n_samples;         /* N: samples of every source signal and output channel       */
+    int32_t n_speech;          /* sources [0, n_speech) are speakers, the rest noise           */
+    int32_t block;             /* overlap-save block (= FFT length / 2): 0 = auto (the least  */
+                               /* of 4096, 8192, 16384 that holds max_len, else 16384), or one */
+                               /* of those; S x ceil(max_len / block) must be <= 128           */
+    int32_t chunk_rooms;       /* rooms per pipeline chunk: 0 = auto (spectra ~1 GiB)          */
+    int32_t reserved;
+} fram_spatial;
+
+int fram_spatialize_workspace_size(const fram_scene* scene, const fram_spatial* sp, int32_t separate_targets,
+                                   size_t* bytes);
+int fram_spatialize(const fram_scene* scene, const fram_spatial* sp, const float* rir, const float* target_rir,
+                    const float* signals, const float* level_db, float* mixture, float* targets, float* gains,
+                    void* workspace, size_t workspace_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

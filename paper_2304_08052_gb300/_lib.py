@@ -25,7 +25,7 @@ FRAM_DEV_NONFINITE = 0x4
 EXPORTED = ("fram_version", "fram_last_error", "fram_default_params", "fram_layout", "fram_workspace_size",
             "fram_sample", "fram_synthesize", "fram_synthesize_backward", "fram_status", "fram_prepare",
             "fram_synthesize_prepared", "fram_synthesize_backward_prepared", "fram_synthesize_noalloc",
-            "fram_autotune", "fram_sample_backward")
+            "fram_autotune", "fram_sample_backward", "fram_spatialize_workspace_size", "fram_spatialize")
 
 
 class FramParams(ctypes.Structure):
@@ -42,6 +42,11 @@ class FramScene(ctypes.Structure):
                 ("dims", ctypes.c_void_p), ("rt60", ctypes.c_void_p), ("src", ctypes.c_void_p),
                 ("mic", ctypes.c_void_p), ("n_vs", ctypes.c_void_p), ("vs_off", ctypes.c_void_p),
                 ("rir_len", ctypes.c_void_p), ("rir_off", ctypes.c_void_p)]
+
+
+class FramSpatial(ctypes.Structure):
+    _fields_ = [("n_samples", ctypes.c_int64), ("n_speech", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("chunk_rooms", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class FramError(RuntimeError):
@@ -73,6 +78,9 @@ def lib():
         L.fram_synthesize_backward.argtypes = [S, P, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t,
                                                vp]
         L.fram_sample_backward.argtypes = [S, P, u64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        SP = ctypes.POINTER(FramSpatial)
+        L.fram_spatialize_workspace_size.argtypes = [S, SP, i32, ctypes.POINTER(ctypes.c_size_t)]
+        L.fram_spatialize.argtypes = [S, SP, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         L.fram_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
         L.fram_prepare.argtypes = [S, P, vp, vp, vp, vp, ctypes.c_size_t, vp]
         L.fram_synthesize_prepared.argtypes = L.fram_synthesize.argtypes

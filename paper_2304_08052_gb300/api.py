@@ -21,7 +21,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import FramParams, FramScene, check, lib
+from ._lib import FramParams, FramScene, FramSpatial, check, lib
 
 
 @dataclass
@@ -324,6 +324,47 @@ def synthesize_backward_prepared(sc: DeviceScene, pos_hi, pos_lo, g, r, grad_rir
                                                   ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes),
                                                   _stream()))
     return out
+
+
+def spatialize(sc: DeviceScene, rir, signals, level_db, n_speech: int, target_rir=None, targets: bool = False,
+               block: int = 0, chunk_rooms: int = 0, out=None):
+    """fram_spatialize: mixture [B,M,N] of signals [B,S,N] (device, float32) through the ragged
+    RIRs `rir`, speakers at level_db SIR and noise at level_db SNR (dB, [B,S]); with targets=True
+    also the per-speaker targets [B,n_speech,M,N] through target_rir (default: rir).  Returns
+    (mixture, targets or None, gains [B,S])."""
+    dev = sc.dims.device
+    B, S, N = (int(v) for v in signals.shape)
+    assert B == sc.B and S == sc.S
+    spc = FramSpatial(N, int(n_speech), int(block), int(chunk_rooms), 0)
+    trir = (target_rir if target_rir is not None else rir) if targets else None
+    sep = 1 if (trir is not None and trir.data_ptr() != rir.data_ptr()) else 0
+    n = ctypes.c_size_t(0)
+    check(lib().fram_spatialize_workspace_size(ctypes.byref(sc.c_scene()), ctypes.byref(spc), sep, ctypes.byref(n)))
+    key = ("spatial", int(n.value))
+    ws = getattr(sc, "_sp_ws", None)
+    if ws is None or ws[0] != key:
+        raw = torch.empty(int(n.value) + 256, dtype=torch.uint8, device=dev)
+        off = (-raw.data_ptr()) % 256
+        ws = (key, raw, raw[off:off + int(n.value)])
+        sc._sp_ws = ws
+    if out is None:
+        out = (torch.empty((B, sc.M, N), dtype=torch.float32, device=dev),
+               torch.empty((B, int(n_speech), sc.M, N), dtype=torch.float32, device=dev) if targets else None,
+               torch.empty((B, S), dtype=torch.float32, device=dev))
+    mix, tg, gains = out
+    check(lib().fram_spatialize(ctypes.byref(sc.c_scene()), ctypes.byref(spc), _ptr(rir), _ptr(trir),
+                                _ptr(signals), _ptr(level_db), _ptr(mix), _ptr(tg), _ptr(gains),
+                                ctypes.c_void_p(ws[2].data_ptr()), ctypes.c_size_t(int(n.value)), _stream()))
+    return mix, tg, gains
+
+
+def spatialize_status(sc: DeviceScene) -> int:
+    """Device status bits of the last fram_spatialize on this scene's spatialisation workspace."""
+    flags = ctypes.c_int32(0)
+    rc = lib().fram_status(ctypes.c_void_p(sc._sp_ws[2].data_ptr()), _stream(), ctypes.byref(flags))
+    if rc not in (_lib.FRAM_OK, _lib.FRAM_EDEVICE):
+        check(rc)
+    return int(flags.value)
 
 
 def algorithmic_taps(sc) -> int:

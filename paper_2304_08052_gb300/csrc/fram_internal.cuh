@@ -380,6 +380,7 @@ cudaError_t launch_backward(const LaunchArgs& a, const float* pos_hi, const floa
                             float* grad_mic, float* grad_src, float* grad_r, float* grad_g, cudaStream_t st);
 
 int device_sm_count();
+int record_error(int code, const char* msg);   // sets fram_last_error's text, returns code
 
 // Dynamic shared memory of one synthesis CTA for tile length T.
 int synth_smem_total(int T);

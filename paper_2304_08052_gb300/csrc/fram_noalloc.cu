@@ -19,7 +19,6 @@
 #include "fram_internal.cuh"
 
 namespace fram {
-int record_error(int code, const char* msg);
 }
 
 namespace {

@@ -1,0 +1,657 @@
+// fram_spatialize.cu -- spatialisation of the RIRs, the paper's use of them for training data
+// (Sec. IV-A): every source signal convolved with its M-channel RIR, speakers scaled to a
+// signal-to-interference ratio against speaker 0, point-source noise to a signal-to-noise ratio
+// against the speech at mic 0, all summed into the microphone mixture; optionally per-speaker
+// targets through a second RIR set (the early RIR of Eq. 9 for dereverberation targets).
+//
+// Convolution: uniformly partitioned overlap-save in the frequency domain.  With block Bk and
+// FFT length P = 2 Bk (real), the RIR of length L splits into Q = ceil(L / Bk) partitions
+// h_q = h[q Bk, (q+1) Bk) and the signal into J = ceil(N / Bk) windows
+// x_j = x[(j-1) Bk, (j+1) Bk); output block j (samples [j Bk, (j+1) Bk)) is the second half of
+// IFFT(sum_q X_{j-q} H_q) (the first half wraps around).  Real transforms of length P run as
+// complex transforms of length NC = P/2 = Bk on even/odd pairs, with the usual split
+// post-processing; the half spectrum is stored as NC complex bins with the Nyquist bin's real
+// part packed into the imaginary part of bin 0, so the bin-wise product is elementwise.
+//
+// The complex transform is one CTA's Stockham autosort FFT in shared memory: radix-8 stages
+// (one 8-point DFT per thread and column, twiddles from a table in global memory), then one
+// radix-4 or radix-2 stage; each stage reads all its inputs into registers, synchronises and
+// writes, so one NC-element buffer suffices.
+//
+// Pipeline per chunk of rooms (by default about 1 GiB of spectra, so every launch fills the GPU):
+//   sp_forward  spectra of every signal window and RIR partition (and target-RIR partition)
+//   sp_image0   mic-0 image of every source, block by block (for the levels)
+//   sp_gains    per room: energies and speech cross terms at mic 0 -> gains (FP64)
+//   sp_mix      per (room, mic, block): IFFT(sum_s g_s sum_q X H) -> mixture; per (room,
+//               speaker, mic, block): IFFT(g_s sum_q X H') -> targets
+#include <algorithm>
+#include <cmath>
+
+#include "fram_internal.cuh"
+
+namespace fram {
+namespace {
+
+constexpr int kMaxTerms = 8 * 16;      // sources x RIR partitions per output block
+
+struct SpArgs {
+    int B, S, M, ns;
+    int64_t N;
+    int Bk, J, Q;
+    int room0, rooms;
+    bool sep;                      // targets use a second RIR set
+    int max_len;
+    int64_t rir_total;
+    const int32_t* rir_len;
+    const int64_t* rir_off;
+    const float* rir;
+    const float* trir;
+    const float* x;                // [B,S,N]
+    const float* level;            // [B,S] dB
+    float* mix;                    // [B,M,N]
+    float* tg;                     // [B,ns,M,N] or null
+    float* gains;                  // [B,S]
+    const float2* tw_c;            // exp(-2 pi i k / NC), k < NC
+    const float2* tw_r;            // exp(-2 pi i k / P),  k < NC
+    float2* XS;                    // [rooms][S][J][NC]
+    float2* HS;                    // [rooms][S][M][Q][NC]
+    float2* HT;                    // [rooms][ns][M][Q][NC] (== HS when !sep)
+    float* img0;                   // [rooms][S][N]
+    Header* hdr;
+};
+
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 c_mul(float2 a, float2 b)
+{
+    return make_float2(__fmaf_rn(a.x, b.x, -a.y * b.y), __fmaf_rn(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
+// a * (-i) for the forward transform, a * (+i) for the inverse
+template <bool INV>
+__device__ __forceinline__ float2 c_rot(float2 a)
+{
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2& v3)
+{
+    const float2 t0 = c_add(v0, v2), t1 = c_sub(v0, v2), t2 = c_add(v1, v3), t3 = c_rot<INV>(c_sub(v1, v3));
+    v0 = c_add(t0, t2);
+    v1 = c_add(t1, t3);
+    v2 = c_sub(t0, t2);
+    v3 = c_sub(t1, t3);
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2* v)
+{
+    if constexpr (R == 2) {
+        const float2 a = v[0];
+        v[0] = c_add(a, v[1]);
+        v[1] = c_sub(a, v[1]);
+    } else if constexpr (R == 4) {
+        dft4<INV>(v[0], v[1], v[2], v[3]);
+    } else {
+        static_assert(R == 8, "radix 2, 4 or 8");
+        // Even and odd halves, then X[k] = E[k] + w^k O[k], X[k+4] = E[k] - w^k O[k], w = e^(-+2 pi i/8).
+        dft4<INV>(v[0], v[2], v[4], v[6]);
+        dft4<INV>(v[1], v[3], v[5], v[7]);
+        constexpr float h = 0.70710678118654752f;
+        const float2 o1 = v[3], o2 = v[5], o3 = v[7];
+        const float2 w1 = INV ? make_float2((o1.x - o1.y) * h, (o1.x + o1.y) * h)
+                              : make_float2((o1.x + o1.y) * h, (o1.y - o1.x) * h);
+        const float2 w2 = c_rot<INV>(o2);
+        const float2 w3 = INV ? make_float2((-o3.x - o3.y) * h, (o3.x - o3.y) * h)
+                              : make_float2((o3.y - o3.x) * h, (-o3.x - o3.y) * h);
+        const float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+        v[0] = c_add(e0, o0);
+        v[4] = c_sub(e0, o0);
+        v[1] = c_add(e1, w1);
+        v[5] = c_sub(e1, w1);
+        v[2] = c_add(e2, w2);
+        v[6] = c_sub(e2, w2);
+        v[3] = c_add(e3, w3);
+        v[7] = c_sub(e3, w3);
+    }
+}
+
+// Shared-memory layout of the NC-point buffer: element e lives at e ^ ((e >> 4) & 15), a
+// permutation inside each 16-element (128-byte) row, so that the strided writes of the first
+// two stages spread over all banks while unit-stride accesses stay conflict-free.
+__device__ __forceinline__ int sw(int e) { return e ^ ((e >> 4) & 15); }
+
+// exp(-2 pi i k / NC) as TA[k >> 7] * TB[k & 127] from two small tables in shared memory.
+struct Twiddles {
+    const float2* TA;
+    const float2* TB;
+    __device__ __forceinline__ float2 operator()(int k) const { return c_mul(TA[k >> 7], TB[k & 127]); }
+};
+
+// One Stockham stage of radix R over the NC-point buffer, stride Ns (the length already done).
+// Column j takes buf[j + r NC/R] (r < R), twiddles them by w^(r (j mod Ns) NC/(Ns R)), runs an
+// R-point DFT and writes buf[(j - j mod Ns) R + j mod Ns + r Ns].
+template <int NC, int NT, int R, bool INV, int Ns>
+__device__ __forceinline__ void fft_stage(float2* buf, const Twiddles& tw)
+{
+    constexpr int NJ = NC / R;
+    static_assert(NJ % NT == 0, "threads must divide the columns");
+    static_assert(NJ % 256 == 0, "column stride keeps the swizzle bits");
+    constexpr int PER = NJ / NT;
+    float2 v[PER][R];
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int j = tid + p * NT;
+        const int sj = sw(j);                  // sw(j + r NJ) = sw(j) + r NJ: NJ is a multiple of 256
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[p][r] = buf[sj + r * NJ];
+        if constexpr (Ns > 1) {
+            // w^r for r < R from two table entries (w and w^4 for radix 8), at most 2 products deep
+            const int step = (j & (Ns - 1)) * (NC / (Ns * R));
+            float2 w[R];
+            w[1] = tw(step);
+            if (INV) w[1].y = -w[1].y;
+            if constexpr (R >= 4) {
+                w[2] = c_mul(w[1], w[1]);
+                w[3] = c_mul(w[2], w[1]);
+            }
+            if constexpr (R == 8) {
+                w[4] = tw(4 * step);
+                if (INV) w[4].y = -w[4].y;
+                w[5] = c_mul(w[4], w[1]);
+                w[6] = c_mul(w[4], w[2]);
+                w[7] = c_mul(w[4], w[3]);
+            }
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[p][r] = c_mul(v[p][r], w[r]);
+        }
+        dft<R, INV>(v[p]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int j = tid + p * NT;
+        const int jm = j & (Ns - 1);
+        const int base = (j - jm) * R + jm;
+        if constexpr (Ns % 256 == 0) {
+            const int sb = sw(base);
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[sb + r * Ns] = v[p][r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[sw(base + r * Ns)] = v[p][r];
+        }
+    }
+    __syncthreads();
+}
+
+// In-place complex FFT of NC points (a power of two >= 8) in shared memory; the buffer must be
+// complete (synchronised) on entry and is complete on exit.  Forward: X[k] = sum x[n] w^(nk),
+// w = e^(-2 pi i/NC); inverse: w = e^(+2 pi i/NC), unscaled.
+template <int NC, int NT, bool INV, int Ns = 1>
+__device__ __forceinline__ void cfft(float2* buf, const Twiddles& tw)
+{
+    if constexpr (Ns * 8 <= NC) {
+        fft_stage<NC, NT, 8, INV, Ns>(buf, tw);
+        cfft<NC, NT, INV, Ns * 8>(buf, tw);
+    } else if constexpr (Ns * 4 == NC) {
+        fft_stage<NC, NT, 4, INV, Ns>(buf, tw);
+    } else if constexpr (Ns * 2 == NC) {
+        fft_stage<NC, NT, 2, INV, Ns>(buf, tw);
+    }
+}
+
+__global__ void sp_twiddles(float2* tw_c, float2* tw_r, int NC)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= NC) return;
+    double s, c;
+    sincospi(-2.0 * (double)k / (double)NC, &s, &c);
+    tw_c[k] = make_float2((float)c, (float)s);
+    sincospi(-(double)k / (double)NC, &s, &c);
+    tw_r[k] = make_float2((float)c, (float)s);
+}
+
+// The two twiddle tables of the NC-point transform, copied from the global table into shared
+// memory (valid after the caller's next __syncthreads).
+template <int NC, int NT>
+__device__ __forceinline__ Twiddles load_twiddles(const float2* __restrict__ tw_c)
+{
+    static_assert(NC >= 128 && NC / 128 <= 128, "two-level table covers 128 x 128 entries");
+    __shared__ float2 ta[NC / 128], tb[128];
+    for (int i = threadIdx.x; i < 128; i += NT) {
+        tb[i] = __ldg(&tw_c[i]);
+        if (i < NC / 128) ta[i] = __ldg(&tw_c[i * 128]);
+    }
+    return Twiddles{ta, tb};
+}
+
+// Spectra: one CTA per signal window, RIR partition or target-RIR partition of the chunk.
+template <int NC, int NT>
+__global__ void __launch_bounds__(NT, NC <= 8192 ? 2 : 1) sp_forward(SpArgs A)
+{
+    extern __shared__ __align__(16) float2 sp_buf[];
+    const int nsig = A.rooms * A.S * A.J;
+    const int nrir = A.rooms * A.S * A.M * A.Q;
+    int jid = blockIdx.x;
+    const float* src;
+    int64_t start, len;
+    int lim;               // window samples taken from the source (the rest are zero)
+    float2* dst;
+    if (jid < nsig) {
+        const int cb = jid / (A.S * A.J), s = (jid / A.J) % A.S, j = jid % A.J;
+        src = A.x + ((int64_t)(A.room0 + cb) * A.S + s) * A.N;
+        start = (int64_t)(j - 1) * A.Bk;
+        len = A.N;
+        lim = 2 * A.Bk;
+        dst = A.XS + (int64_t)jid * NC;
+    } else {
+        jid -= nsig;
+        const bool tgt = jid >= nrir;
+        if (tgt) jid -= nrir;
+        const int ss = tgt ? A.ns : A.S;
+        const int cb = jid / (ss * A.M * A.Q), s = (jid / (A.M * A.Q)) % ss, m = (jid / A.Q) % A.M,
+                  q = jid % A.Q;
+        const int b = A.room0 + cb;
+        const int L = A.rir_len[b];
+        const int64_t off = A.rir_off[b] + ((int64_t)s * A.M + m) * L;
+        if (L < 1 || L > A.max_len || off < 0 || off + L > A.rir_total) {   // layout disagrees with the host
+            if (threadIdx.x == 0) atomicOr(&A.hdr->status, FRAM_DEV_BAD_GEOMETRY);
+            len = 0;
+        } else {
+            len = L;
+        }
+        src = (tgt ? A.trir : A.rir) + (len ? off : 0);
+        start = (int64_t)q * A.Bk;
+        lim = A.Bk;
+        dst = (tgt ? A.HT : A.HS) + (int64_t)jid * NC;
+    }
+    for (int n = threadIdx.x; n < NC; n += NT) {
+        const int t0 = 2 * n, t1 = 2 * n + 1;
+        const int64_t i0 = start + t0, i1 = start + t1;
+        const float a = (t0 < lim && i0 >= 0 && i0 < len) ? src[i0] : 0.f;
+        const float b = (t1 < lim && i1 >= 0 && i1 < len) ? src[i1] : 0.f;
+        sp_buf[sw(n)] = make_float2(a, b);
+    }
+    const Twiddles tw = load_twiddles<NC, NT>(A.tw_c);
+    __syncthreads();
+    cfft<NC, NT, false>(sp_buf, tw);
+    // Split: with Zc = conj(Z[NC-k]), E = (Z[k] + Zc)/2, O = -i (Z[k] - Zc)/2,
+    // X[k] = E + w_P^k O and X[NC-k] = conj(E - w_P^k O).
+    for (int k = threadIdx.x; k <= NC / 2; k += NT) {
+        if (k == 0) {
+            const float2 z = sp_buf[sw(0)];
+            dst[0] = make_float2(z.x + z.y, z.x - z.y);       // DC, Nyquist
+            continue;
+        }
+        const float2 zk = sp_buf[sw(k)], zc = c_conj(sp_buf[sw(NC - k)]);
+        const float2 E = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y));
+        const float2 D = c_sub(zk, zc);
+        const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
+        const float2 WO = c_mul(__ldg(&A.tw_r[k]), O);
+        dst[k] = c_add(E, WO);
+        if (k != NC - k) dst[NC - k] = c_conj(c_sub(E, WO));
+    }
+}
+
+__device__ __forceinline__ float2 packed_mul(float2 a, float2 b, bool dc)
+{
+    return dc ? make_float2(a.x * b.x, a.y * b.y) : c_mul(a, b);
+}
+
+// sp_buf[k] = sum_t g_t X_t[k] H_t[k] (packed products) over nt terms.  Each thread owns bin
+// pairs (2p, 2p+1), p = tid + i NT, loaded as float4 with all of a term's loads in flight before
+// the products; accumulators stay in registers, in term order (deterministic).
+struct SpTerm {
+    const float2* X;
+    const float2* H;
+    float g;
+};
+
+template <int NC, int NT>
+__device__ __forceinline__ void spectral_sum(float2* sp_buf, const SpTerm* terms, int nt)
+{
+    constexpr int KP = NC / (2 * NT);          // bin pairs per thread
+    constexpr int KH = KP >= 4 ? 4 : KP;       // pairs per pass (register budget)
+    static_assert(KP % KH == 0, "pairs per pass must divide the pairs per thread");
+#pragma unroll 1
+    for (int h0 = 0; h0 < KP; h0 += KH) {
+        float4 acc[KH];
+#pragma unroll
+        for (int i = 0; i < KH; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+        for (int t = 0; t < nt; ++t) {
+            const float4* X4 = reinterpret_cast<const float4*>(terms[t].X);
+            const float4* H4 = reinterpret_cast<const float4*>(terms[t].H);
+            const float g = terms[t].g;
+            float4 xv[KH], hv[KH];
+#pragma unroll
+            for (int i = 0; i < KH; ++i) {
+                const int p = threadIdx.x + (h0 + i) * NT;
+                xv[i] = __ldg(&X4[p]);
+                hv[i] = __ldg(&H4[p]);
+            }
+#pragma unroll
+            for (int i = 0; i < KH; ++i) {
+                const int p = threadIdx.x + (h0 + i) * NT;
+                const float2 a = packed_mul(make_float2(xv[i].x, xv[i].y), make_float2(hv[i].x, hv[i].y), p == 0);
+                const float2 b = c_mul(make_float2(xv[i].z, xv[i].w), make_float2(hv[i].z, hv[i].w));
+                acc[i].x = __fmaf_rn(g, a.x, acc[i].x);
+                acc[i].y = __fmaf_rn(g, a.y, acc[i].y);
+                acc[i].z = __fmaf_rn(g, b.x, acc[i].z);
+                acc[i].w = __fmaf_rn(g, b.y, acc[i].w);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < KH; ++i) {
+            const int p = threadIdx.x + (h0 + i) * NT;
+            sp_buf[sw(2 * p)] = make_float2(acc[i].x, acc[i].y);
+            sp_buf[sw(2 * p + 1)] = make_float2(acc[i].z, acc[i].w);
+        }
+    }
+}
+
+// sp_buf <- inverse real transform of the packed spectrum already in sp_buf (complete on entry);
+// real sample t of the window is then sp_buf[t/2].x or .y times 1/NC.
+template <int NC, int NT>
+__device__ void inverse_real(float2* sp_buf, const Twiddles& tw, const float2* __restrict__ tw_r)
+{
+    for (int k = threadIdx.x; k <= NC / 2; k += NT) {
+        if (k == 0) {
+            const float2 a = sp_buf[sw(0)];
+            sp_buf[sw(0)] = make_float2(0.5f * (a.x + a.y), 0.5f * (a.x - a.y));
+            continue;
+        }
+        const float2 xk = sp_buf[sw(k)], xc = c_conj(sp_buf[sw(NC - k)]);
+        const float2 E = make_float2(0.5f * (xk.x + xc.x), 0.5f * (xk.y + xc.y));
+        const float2 D = c_sub(xk, xc);
+        const float2 O = c_mul(make_float2(0.5f * D.x, 0.5f * D.y), c_conj(__ldg(&tw_r[k])));
+        sp_buf[sw(k)] = make_float2(E.x - O.y, E.y + O.x);                   // E + i O
+        if (k != NC - k) sp_buf[sw(NC - k)] = make_float2(E.x + O.y, O.x - E.y);   // conj(E - i O)
+    }
+    __syncthreads();
+    cfft<NC, NT, true>(sp_buf, tw);
+}
+
+// Writes the second half of the inverse window (output block j) to out[j Bk + u], u < Bk, < N.
+template <int NC, int NT>
+__device__ __forceinline__ void store_block(const float2* sp_buf, float* out, int64_t N, int j, float scale)
+{
+    const int64_t base = (int64_t)j * NC;
+    for (int n = NC / 2 + threadIdx.x; n < NC; n += NT) {
+        const float2 z = sp_buf[sw(n)];
+        const int64_t u = base + 2 * (int64_t)(n - NC / 2);
+        if (u < N) out[u] = z.x * scale;
+        if (u + 1 < N) out[u + 1] = z.y * scale;
+    }
+}
+
+// Mic-0 image of every (room, source), block by block.
+template <int NC, int NT>
+__global__ void __launch_bounds__(NT, NC <= 8192 ? 2 : 1) sp_image0(SpArgs A)
+{
+    extern __shared__ __align__(16) float2 sp_buf[];
+    const int jid = blockIdx.x;
+    const int cb = jid / (A.S * A.J), s = (jid / A.J) % A.S, j = jid % A.J;
+    __shared__ SpTerm terms[kMaxTerms];
+    const float2* X = A.XS + ((int64_t)cb * A.S + s) * A.J * NC;
+    const float2* H = A.HS + (((int64_t)cb * A.S + s) * A.M) * A.Q * NC;      // mic 0
+    const int nt = min(A.Q, j + 1);
+    const Twiddles tw = load_twiddles<NC, NT>(A.tw_c);
+    if (threadIdx.x < nt)
+        terms[threadIdx.x] = SpTerm{X + (int64_t)(j - threadIdx.x) * NC, H + (int64_t)threadIdx.x * NC, 1.0f};
+    __syncthreads();
+    spectral_sum<NC, NT>(sp_buf, terms, nt);
+    __syncthreads();
+    inverse_real<NC, NT>(sp_buf, tw, A.tw_r);
+    store_block<NC, NT>(sp_buf, A.img0 + ((int64_t)cb * A.S + s) * A.N, A.N, j, 1.0f / NC);
+}
+
+// Block-wide FP64 sum in a fixed tree; the result is valid in thread 0.
+__device__ double block_sum(double v, double* red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nw; ++i) t += red[i];
+    return t;
+}
+
+// Per room: E_s = sum y_s0^2, speech cross terms, then the gains (FP64, as the levels define them).
+__global__ void __launch_bounds__(256) sp_gains(SpArgs A)
+{
+    __shared__ double red[8];
+    __shared__ double E[8], Cx[8][8];
+    const int cb = blockIdx.x;
+    const float* y = A.img0 + (int64_t)cb * A.S * A.N;
+    // pairs (s, t): s == t energies for every source, s < t cross terms between speakers
+    for (int s = 0; s < A.S; ++s)
+        for (int t = s; t < (s < A.ns ? A.ns : s + 1); ++t) {
+            const float* ys = y + (int64_t)s * A.N;
+            const float* yt = y + (int64_t)t * A.N;
+            double acc = 0.0;
+            float part = 0.f;
+            int cnt = 0;
+            for (int64_t n = threadIdx.x; n < A.N; n += blockDim.x) {
+                part = __fmaf_rn(ys[n], yt[n], part);
+                if (++cnt == 32) { acc += part; part = 0.f; cnt = 0; }   // FP32 runs of 32, FP64 across
+            }
+            acc += part;
+            const double tot = block_sum(acc, red);
+            if (threadIdx.x == 0) {
+                if (s == t) E[s] = tot;
+                else Cx[s][t] = Cx[t][s] = tot;
+            }
+        }
+    if (threadIdx.x == 0) {
+        const int b = A.room0 + cb;
+        double g[8];
+        g[0] = 1.0;
+        for (int s = 1; s < A.ns; ++s)
+            g[s] = E[s] > 0.0 ? sqrt(E[0] / E[s] * pow(10.0, -(double)A.level[(int64_t)b * A.S + s] / 10.0)) : 0.0;
+        double Ev = 0.0;
+        for (int s = 0; s < A.ns; ++s)
+            for (int t = 0; t < A.ns; ++t) Ev += g[s] * g[t] * (s == t ? E[s] : Cx[s][t]);
+        for (int s = A.ns; s < A.S; ++s)
+            g[s] = E[s] > 0.0 ? sqrt(Ev / E[s] * pow(10.0, -(double)A.level[(int64_t)b * A.S + s] / 10.0)) : 0.0;
+        for (int s = 0; s < A.S; ++s) A.gains[(int64_t)b * A.S + s] = (float)g[s];
+    }
+}
+
+// Mixture blocks (room, mic, block) and target blocks (room, speaker, mic, block).
+template <int NC, int NT>
+__global__ void __launch_bounds__(NT, NC <= 8192 ? 2 : 1) sp_mix(SpArgs A)
+{
+    extern __shared__ __align__(16) float2 sp_buf[];
+    const int nmix = A.rooms * A.M * A.J;
+    int jid = blockIdx.x;
+    const bool tgt = jid >= nmix;
+    int cb, s0, s1, m, j;
+    if (!tgt) {
+        cb = jid / (A.M * A.J); m = (jid / A.J) % A.M; j = jid % A.J;
+        s0 = 0; s1 = A.S;
+    } else {
+        jid -= nmix;
+        cb = jid / (A.ns * A.M * A.J); s0 = (jid / (A.M * A.J)) % A.ns; m = (jid / A.J) % A.M; j = jid % A.J;
+        s1 = s0 + 1;
+    }
+    const int b = A.room0 + cb;
+    const float2* Hb = tgt ? A.HT : A.HS;
+    const int hs = (tgt && A.sep) ? A.ns : A.S;
+    __shared__ SpTerm terms[kMaxTerms];
+    const int nq = min(A.Q, j + 1);
+    const int nt = (s1 - s0) * nq;
+    const Twiddles tw = load_twiddles<NC, NT>(A.tw_c);
+    if (threadIdx.x < nt) {
+        const int s = s0 + threadIdx.x / nq, q = threadIdx.x % nq;
+        terms[threadIdx.x] = SpTerm{A.XS + (((int64_t)cb * A.S + s) * A.J + (j - q)) * NC,
+                                    Hb + ((((int64_t)cb * hs + s) * A.M + m) * A.Q + q) * NC,
+                                    A.gains[(int64_t)b * A.S + s]};
+    }
+    __syncthreads();
+    spectral_sum<NC, NT>(sp_buf, terms, nt);
+    __syncthreads();
+    inverse_real<NC, NT>(sp_buf, tw, A.tw_r);
+    float* out = tgt ? A.tg + (((int64_t)b * A.ns + s0) * A.M + m) * A.N : A.mix + ((int64_t)b * A.M + m) * A.N;
+    store_block<NC, NT>(sp_buf, out, A.N, j, 1.0f / NC);
+}
+
+template <int NC, int NT>
+cudaError_t launch_chunk(const SpArgs& A, cudaStream_t st)
+{
+    const int smem = NC * (int)sizeof(float2);
+    int per_sm = 0;
+    cudaError_t e;
+    if ((e = kernel_residency((const void*)sp_forward<NC, NT>, NT, smem, &per_sm)) != cudaSuccess) return e;
+    if ((e = kernel_residency((const void*)sp_image0<NC, NT>, NT, smem, &per_sm)) != cudaSuccess) return e;
+    if ((e = kernel_residency((const void*)sp_mix<NC, NT>, NT, smem, &per_sm)) != cudaSuccess) return e;
+    const int nfwd = A.rooms * (A.S * A.J + A.S * A.M * A.Q + (A.sep ? A.ns * A.M * A.Q : 0));
+    sp_forward<NC, NT><<<nfwd, NT, smem, st>>>(A);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    sp_image0<NC, NT><<<A.rooms * A.S * A.J, NT, smem, st>>>(A);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    sp_gains<<<A.rooms, 256, 0, st>>>(A);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int nmix = A.rooms * A.J * A.M * (1 + (A.tg ? A.ns : 0));
+    sp_mix<NC, NT><<<nmix, NT, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+struct SpLayout {
+    int Bk, J, Q, chunk;
+    bool sep;
+    size_t header, tw_c, tw_r, XS, HS, HT, img0, gains, total;
+};
+
+SpLayout sp_layout(const fram_scene& sc, const fram_spatial& sp, bool sep)
+{
+    SpLayout w{};
+    const int Lmax = std::max(sc.max_len, 1);
+    w.Bk = sp.block ? sp.block : (Lmax <= 4096 ? 4096 : (Lmax <= 8192 ? 8192 : 16384));
+    w.J = (int)((sp.n_samples + w.Bk - 1) / w.Bk);
+    w.Q = (Lmax + w.Bk - 1) / w.Bk;
+    w.sep = sep;
+    const size_t spec = sizeof(float2) * (size_t)w.Bk;
+    const size_t per_room = spec * ((size_t)sc.S * w.J + (size_t)sc.S * sc.M * w.Q +
+                                    (sep ? (size_t)sp.n_speech * sc.M * w.Q : 0)) +
+                            sizeof(float) * (size_t)sc.S * (size_t)sp.n_samples;
+    int chunk = sp.chunk_rooms;
+    if (chunk <= 0) {
+        // Large chunks: each kernel needs thousands of CTAs to fill 152 SMs; the spectra then
+        // stream through HBM rather than staying in L2, which costs less than idle SMs.
+        const size_t target = (size_t)1 << 30;
+        chunk = (int)std::max<size_t>(1, target / std::max<size_t>(per_room, 1));
+    }
+    w.chunk = std::max(1, std::min(chunk, std::max(sc.B, 1)));
+    size_t off = 0;
+    auto take = [&](size_t n) {
+        const size_t o = off;
+        off += (n + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t C = (size_t)w.chunk;
+    w.header = take(sizeof(Header));
+    w.tw_c = take(spec);
+    w.tw_r = take(spec);
+    w.XS = take(spec * C * sc.S * w.J);
+    w.HS = take(spec * C * sc.S * sc.M * w.Q);
+    w.HT = sep ? take(spec * C * sp.n_speech * sc.M * w.Q) : w.HS;
+    w.img0 = take(sizeof(float) * C * sc.S * (size_t)sp.n_samples);
+    w.gains = take(sizeof(float) * (size_t)std::max(sc.B, 1) * sc.S);
+    w.total = off;
+    return w;
+}
+
+int sp_check(const fram_scene* sc, const fram_spatial* sp)
+{
+    if (!sc || !sp) return record_error(FRAM_EINVAL, "scene and spatial parameters must not be null");
+    if (sc->B < 0 || sc->S < 1 || sc->M < 1) return record_error(FRAM_EINVAL, "need B >= 0, S >= 1, M >= 1");
+    if (sc->S > 8) return record_error(FRAM_EINVAL, "spatialisation takes at most 8 sources per room");
+    if (sc->B > 0 && sc->max_len < 1) return record_error(FRAM_EINVAL, "max_len must be >= 1");
+    if (sp->n_samples < 1 || sp->n_samples > 0x7fffffffLL) return record_error(FRAM_EINVAL, "n_samples must be in [1, 2^31)");
+    if (sp->n_speech < 1 || sp->n_speech > sc->S) return record_error(FRAM_EINVAL, "need 1 <= n_speech <= S");
+    if (sp->block != 0 && sp->block != 4096 && sp->block != 8192 && sp->block != 16384)
+        return record_error(FRAM_EINVAL, "block must be 0, 4096, 8192 or 16384");
+    if (sp->chunk_rooms < 0) return record_error(FRAM_EINVAL, "chunk_rooms must be >= 0");
+    {
+        const int Lmax = std::max(sc->max_len, 1);
+        const int Bk = sp->block ? sp->block : (Lmax <= 4096 ? 4096 : (Lmax <= 8192 ? 8192 : 16384));
+        if ((int64_t)sc->S * ((Lmax + Bk - 1) / Bk) > kMaxTerms)
+            return record_error(FRAM_EINVAL, "S x RIR partitions exceeds 128 (raise block)");
+    }
+    return FRAM_OK;
+}
+
+}  // namespace
+}  // namespace fram
+
+using namespace fram;
+
+extern "C" int fram_spatialize_workspace_size(const fram_scene* scene, const fram_spatial* sp, int32_t separate_targets,
+                                              size_t* bytes)
+{
+    int rc = sp_check(scene, sp);
+    if (rc != FRAM_OK) return rc;
+    if (!bytes) return record_error(FRAM_EINVAL, "bytes is null");
+    *bytes = sp_layout(*scene, *sp, separate_targets != 0).total;
+    return FRAM_OK;
+}
+
+extern "C" int fram_spatialize(const fram_scene* scene, const fram_spatial* sp, const float* rir,
+                               const float* target_rir, const float* signals, const float* level_db, float* mixture,
+                               float* targets, float* gains, void* workspace, size_t workspace_bytes, void* stream)
+{
+    int rc = sp_check(scene, sp);
+    if (rc != FRAM_OK) return rc;
+    const bool sep = targets && target_rir && target_rir != rir;
+    const SpLayout w = sp_layout(*scene, *sp, sep);
+    if (!workspace) return record_error(FRAM_EWORKSPACE, "workspace is null");
+    if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
+        return record_error(FRAM_EWORKSPACE, "workspace must be 256-byte aligned");
+    if (workspace_bytes < w.total) return record_error(FRAM_EWORKSPACE, "workspace too small for fram_spatialize");
+    if (scene->B == 0) return FRAM_OK;
+    if (!scene->rir_len || !scene->rir_off) return record_error(FRAM_EINVAL, "scene rir_len / rir_off must not be null");
+    if (!rir || !signals || !level_db || !mixture) return record_error(FRAM_EINVAL, "rir, signals, level_db and mixture must not be null");
+    if (targets && !target_rir) return record_error(FRAM_EINVAL, "targets need target_rir (pass rir for reverberant targets)");
+    char* base = static_cast<char*>(workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SpArgs A{};
+    A.B = scene->B; A.S = scene->S; A.M = scene->M; A.ns = sp->n_speech;
+    A.N = sp->n_samples;
+    A.Bk = w.Bk; A.J = w.J; A.Q = w.Q;
+    A.sep = sep;
+    A.max_len = scene->max_len;
+    A.rir_total = scene->rir_total;
+    A.rir_len = scene->rir_len; A.rir_off = scene->rir_off;
+    A.rir = rir; A.trir = targets ? target_rir : rir;
+    A.x = signals; A.level = level_db; A.mix = mixture; A.tg = targets;
+    A.gains = gains ? gains : reinterpret_cast<float*>(base + w.gains);
+    A.tw_c = reinterpret_cast<const float2*>(base + w.tw_c);
+    A.tw_r = reinterpret_cast<const float2*>(base + w.tw_r);
+    A.XS = reinterpret_cast<float2*>(base + w.XS);
+    A.HS = reinterpret_cast<float2*>(base + w.HS);
+    A.HT = reinterpret_cast<float2*>(base + w.HT);
+    A.img0 = reinterpret_cast<float*>(base + w.img0);
+    A.hdr = reinterpret_cast<Header*>(base + w.header);
+    cudaError_t e = cudaMemsetAsync(A.hdr, 0, sizeof(Header), st);
+    if (e != cudaSuccess) return record_error(FRAM_ECUDA, cudaGetErrorString(e));
+    sp_twiddles<<<(w.Bk + 255) / 256, 256, 0, st>>>(reinterpret_cast<float2*>(base + w.tw_c),
+                                                    reinterpret_cast<float2*>(base + w.tw_r), w.Bk);
+    if ((e = cudaGetLastError()) != cudaSuccess) return record_error(FRAM_ECUDA, cudaGetErrorString(e));
+    for (int r0 = 0; r0 < scene->B; r0 += w.chunk) {
+        A.room0 = r0;
+        A.rooms = std::min(w.chunk, scene->B - r0);
+        if (w.Bk == 4096) e = launch_chunk<4096, 512>(A, st);
+        else if (w.Bk == 8192) e = launch_chunk<8192, 512>(A, st);
+        else e = launch_chunk<16384, 1024>(A, st);
+        if (e != cudaSuccess) return record_error(FRAM_ECUDA, cudaGetErrorString(e));
+    }
+    return FRAM_OK;
+}

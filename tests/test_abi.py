@@ -121,3 +121,22 @@ def test_auto_tile_workspace_covers_every_candidate(L):
         n = ctypes.c_size_t(0)
         L.fram_workspace_size(ctypes.byref(sc), ctypes.byref(api.Params(tile=tile).c()), ctypes.byref(n))
         assert n.value <= n_auto.value
+
+
+def test_spatialize_rejects_bad_arguments_on_the_host(L):
+    sc = _scene_struct()
+    n = ctypes.c_size_t(0)
+    ok = _lib.FramSpatial(16000, 1, 0, 0, 0)
+    assert L.fram_spatialize_workspace_size(ctypes.byref(sc), ctypes.byref(ok), 0, ctypes.byref(n)) == 0
+    assert n.value > 0
+    n_sep = ctypes.c_size_t(0)
+    assert L.fram_spatialize_workspace_size(ctypes.byref(sc), ctypes.byref(ok), 1, ctypes.byref(n_sep)) == 0
+    assert n_sep.value > n.value                          # room for the target-RIR spectra
+    for bad in (_lib.FramSpatial(0, 1, 0, 0, 0), _lib.FramSpatial(100, 0, 0, 0, 0),
+                _lib.FramSpatial(100, sc.S + 1, 0, 0, 0), _lib.FramSpatial(100, 1, 1000, 0, 0),
+                _lib.FramSpatial(100, 1, 0, -1, 0)):
+        assert L.fram_spatialize_workspace_size(ctypes.byref(sc), ctypes.byref(bad), 0,
+                                                ctypes.byref(n)) == _lib.FRAM_EINVAL
+    null = ctypes.c_void_p(0)
+    assert L.fram_spatialize(ctypes.byref(sc), ctypes.byref(ok), null, null, null, null, null, null, null, null, 0,
+                             None) == _lib.FRAM_EWORKSPACE
