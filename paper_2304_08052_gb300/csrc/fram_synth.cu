@@ -438,8 +438,9 @@ __device__ __forceinline__ void add_arrival_edge(char* __restrict__ smem, const 
 
 // Per-warp shared memory (floats): the tile buffer (T + 68: sample T0 + k sits at index h + k,
 // h = 32 + the output's word offset mod 4, so the store runs in aligned float4s and at least 32
-// samples of halo remain on each side), 32 arrival records (float4) and their buffer offsets.
-__host__ __device__ inline int synth_warp_floats(int T) { return (T + 68) + 4 * 32 + 32; }
+// samples of halo remain on each side), 32 arrival records (float4) and their buffer offsets,
+// each with one spare entry so the next record can be prefetched without a bound check.
+__host__ __device__ inline int synth_warp_floats(int T) { return (T + 68) + 4 * 33 + 36; }
 
 // Work unit = (room, source, tile, mic), one warp each, pulled from a counter (the next unit is
 // requested when the current one starts).  Per unit: zero the tile buffer; add the direct path;
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(kSynthThreads, 3) synth_kernel(LaunchArgs a, f
     float* buf = synth_smem + wid * synth_warp_floats(T);
     const int buf_b = 4 * wid * synth_warp_floats(T);     // byte offset of buf
     float4* rec = reinterpret_cast<float4*>(buf + T + 68);
-    int* rrb = reinterpret_cast<int*>(rec + 32);
+    int* rrb = reinterpret_cast<int*>(rec + 33);
     TapLanes<NR> L;
     init_tap_lanes<NR>(L, lane, K);
     const float invK = 1.0f / (float)K;
@@ -545,8 +546,8 @@ __global__ void __launch_bounds__(kSynthThreads, 3) synth_kernel(LaunchArgs a, f
             for (int q = 0; q < ni; ++q) {
                 const float4 r = rn;
                 const int rb = bn;
-                rn = rec[min(q + 1, 31)];
-                bn = rrb[min(q + 1, 31)];
+                rn = rec[q + 1];
+                bn = rrb[q + 1];
                 add_arrival_inner<NR>(smem, L, r, rb, lane4);
                 __syncwarp();
             }
