@@ -310,10 +310,10 @@ int fram_synthesize_noalloc(const fram_scene* scene, const fram_params* p, const
 typedef struct {
     int64_t n_samples;         /* N: samples of every source signal and output channel       */
     int32_t n_speech;          /* sources [0, n_speech) are speakers, the rest noise           */
-    int32_t block;             /* overlap-save block (= FFT length / 2): 0 = auto (the least  */
-                               /* of 4096, 8192, 16384 that holds max_len, else 16384), or one */
-                               /* of those; S x ceil(max_len / block) must be <= 128           */
-    int32_t chunk_rooms;       /* rooms per pipeline chunk: 0 = auto (spectra ~1 GiB)          */
+    int32_t block;             /* overlap-save block (= FFT length / 2): 0 = auto (4096, or   */
+                               /* the least of 8192, 16384 with S x ceil(max_len / block) <=  */
+                               /* 128), or one of 4096, 8192, 16384 meeting that limit         */
+    int32_t chunk_rooms;       /* rooms per pipeline chunk: 0 = auto (spectra ~4 GiB)          */
     int32_t reserved;
 } fram_spatial;
 

@@ -13,12 +13,12 @@
 // post-processing; the half spectrum is stored as NC complex bins with the Nyquist bin's real
 // part packed into the imaginary part of bin 0, so the bin-wise product is elementwise.
 //
-// The complex transform is one CTA's Stockham autosort FFT in shared memory: radix-8 stages
-// (one 8-point DFT per thread and column, twiddles from a table in global memory), then one
-// radix-4 or radix-2 stage; each stage reads all its inputs into registers, synchronises and
-// writes, so one NC-element buffer suffices.
+// The complex transform is one CTA's Stockham autosort FFT in shared memory: radix-16 stages
+// (one 16-point DFT per thread and column, computed as 4 x 4 in registers), then one radix-8, -4
+// or -2 stage; each stage reads all its inputs into registers, synchronises and writes, so one
+// NC-element buffer suffices.
 //
-// Pipeline per chunk of rooms (by default about 1 GiB of spectra, so every launch fills the GPU):
+// Pipeline per chunk of rooms (by default about 4 GiB of spectra, so every launch fills the GPU):
 //   sp_forward  spectra of every signal window and RIR partition (and target-RIR partition)
 //   sp_image0   mic-0 image of every source, block by block (for the levels)
 //   sp_gains    per room: energies and speech cross terms at mic 0 -> gains (FP64)
@@ -84,6 +84,35 @@ __device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2&
     v3 = c_sub(t1, t3);
 }
 
+// v * (c, +-s): multiply by the constant e^(-+i theta) given as (cos theta, sin theta).
+template <bool INV>
+__device__ __forceinline__ float2 c_mulk(float2 v, float c, float s)
+{
+    const float t = INV ? s : -s;
+    return make_float2(__fmaf_rn(v.x, c, -v.y * t), __fmaf_rn(v.x, t, v.y * c));
+}
+
+// 16-point DFT as 4 x 4: DFT4 over n1 of v[4 n1 + n2], twiddle by w16^(n2 k1), DFT4 over n2; the
+// result X[k1 + 4 k2] is left in v[4 k1 + k2] (the caller stores with that transposed index).
+template <bool INV>
+__device__ __forceinline__ void dft16_t(float2* v)
+{
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+    constexpr float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, h = 0.70710678118654752f;
+    v[5] = c_mulk<INV>(v[5], c1, s1);          // (n2, k1) = (1, 1): w^1
+    v[9] = c_mulk<INV>(v[9], h, h);            // (1, 2): w^2
+    v[13] = c_mulk<INV>(v[13], s1, c1);        // (1, 3): w^3
+    v[6] = c_mulk<INV>(v[6], h, h);            // (2, 1): w^2
+    v[10] = c_rot<INV>(v[10]);                 // (2, 2): w^4
+    v[14] = c_mulk<INV>(v[14], -h, h);         // (2, 3): w^6
+    v[7] = c_mulk<INV>(v[7], s1, c1);          // (3, 1): w^3
+    v[11] = c_mulk<INV>(v[11], -h, h);         // (3, 2): w^6
+    v[15] = c_mulk<INV>(v[15], -c1, -s1);      // (3, 3): w^9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2* v)
 {
@@ -93,8 +122,10 @@ __device__ __forceinline__ void dft(float2* v)
         v[1] = c_sub(a, v[1]);
     } else if constexpr (R == 4) {
         dft4<INV>(v[0], v[1], v[2], v[3]);
+    } else if constexpr (R == 16) {
+        dft16_t<INV>(v);
     } else {
-        static_assert(R == 8, "radix 2, 4 or 8");
+        static_assert(R == 8, "radix 2, 4, 8 or 16");
         // Even and odd halves, then X[k] = E[k] + w^k O[k], X[k+4] = E[k] - w^k O[k], w = e^(-+2 pi i/8).
         dft4<INV>(v[0], v[2], v[4], v[6]);
         dft4<INV>(v[1], v[3], v[5], v[7]);
@@ -150,22 +181,46 @@ __device__ __forceinline__ void fft_stage(float2* buf, const Twiddles& tw)
         if constexpr (Ns > 1) {
             // w^r for r < R from two table entries (w and w^4 for radix 8), at most 2 products deep
             const int step = (j & (Ns - 1)) * (NC / (Ns * R));
-            float2 w[R];
-            w[1] = tw(step);
-            if (INV) w[1].y = -w[1].y;
-            if constexpr (R >= 4) {
-                w[2] = c_mul(w[1], w[1]);
-                w[3] = c_mul(w[2], w[1]);
-            }
-            if constexpr (R == 8) {
-                w[4] = tw(4 * step);
-                if (INV) w[4].y = -w[4].y;
-                w[5] = c_mul(w[4], w[1]);
-                w[6] = c_mul(w[4], w[2]);
-                w[7] = c_mul(w[4], w[3]);
-            }
+            auto get = [&](int k) {
+                float2 w = tw(k);
+                if (INV) w.y = -w.y;
+                return w;
+            };
+            if constexpr (R == 16) {
+                // w^1, w^2, w^4, w^8 from the tables, the rest as one product of two of them
+                const float2 w1 = get(step), w2 = get(2 * step), w4 = get(4 * step), w8 = get(8 * step);
+                const float2 w3 = c_mul(w1, w2), w12 = c_mul(w8, w4);
+                v[p][1] = c_mul(v[p][1], w1);
+                v[p][2] = c_mul(v[p][2], w2);
+                v[p][3] = c_mul(v[p][3], w3);
+                v[p][4] = c_mul(v[p][4], w4);
+                v[p][5] = c_mul(v[p][5], c_mul(w4, w1));
+                v[p][6] = c_mul(v[p][6], c_mul(w4, w2));
+                v[p][7] = c_mul(v[p][7], c_mul(w4, w3));
+                v[p][8] = c_mul(v[p][8], w8);
+                v[p][9] = c_mul(v[p][9], c_mul(w8, w1));
+                v[p][10] = c_mul(v[p][10], c_mul(w8, w2));
+                v[p][11] = c_mul(v[p][11], c_mul(w8, w3));
+                v[p][12] = c_mul(v[p][12], w12);
+                v[p][13] = c_mul(v[p][13], c_mul(w12, w1));
+                v[p][14] = c_mul(v[p][14], c_mul(w12, w2));
+                v[p][15] = c_mul(v[p][15], c_mul(w12, w3));
+            } else {
+                float2 w[R];
+                w[1] = get(step);
+                if constexpr (R >= 4) {
+                    w[2] = c_mul(w[1], w[1]);
+                    w[3] = c_mul(w[2], w[1]);
+                }
+                if constexpr (R == 8) {
+                    w[4] = get(4 * step);
+                    w[5] = c_mul(w[4], w[1]);
+                    w[6] = c_mul(w[4], w[2]);
+                    w[7] = c_mul(w[4], w[3]);
+                }
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[p][r] = c_mul(v[p][r], w[r]);
+                for (int r = 1; r < R; ++r) v[p][r] = c_mul(v[p][r], w[r]);
+            }
         }
         dft<R, INV>(v[p]);
     }
@@ -175,13 +230,15 @@ __device__ __forceinline__ void fft_stage(float2* buf, const Twiddles& tw)
         const int j = tid + p * NT;
         const int jm = j & (Ns - 1);
         const int base = (j - jm) * R + jm;
+        // output r of the DFT sits in v[p][r], or in v[p][4 (r % 4) + r / 4] after the 4 x 4 DFT16
+        auto out = [&](int r) { return R == 16 ? v[p][4 * (r & 3) + (r >> 2)] : v[p][r]; };
         if constexpr (Ns % 256 == 0) {
             const int sb = sw(base);
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[sb + r * Ns] = v[p][r];
+            for (int r = 0; r < R; ++r) buf[sb + r * Ns] = out(r);
         } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[sw(base + r * Ns)] = v[p][r];
+            for (int r = 0; r < R; ++r) buf[sw(base + r * Ns)] = out(r);
         }
     }
     __syncthreads();
@@ -193,9 +250,11 @@ __device__ __forceinline__ void fft_stage(float2* buf, const Twiddles& tw)
 template <int NC, int NT, bool INV, int Ns = 1>
 __device__ __forceinline__ void cfft(float2* buf, const Twiddles& tw)
 {
-    if constexpr (Ns * 8 <= NC) {
+    if constexpr (Ns * 16 <= NC) {
+        fft_stage<NC, NT, 16, INV, Ns>(buf, tw);
+        cfft<NC, NT, INV, Ns * 16>(buf, tw);
+    } else if constexpr (Ns * 8 == NC) {
         fft_stage<NC, NT, 8, INV, Ns>(buf, tw);
-        cfft<NC, NT, INV, Ns * 8>(buf, tw);
     } else if constexpr (Ns * 4 == NC) {
         fft_stage<NC, NT, 4, INV, Ns>(buf, tw);
     } else if constexpr (Ns * 2 == NC) {
@@ -230,7 +289,7 @@ __device__ __forceinline__ Twiddles load_twiddles(const float2* __restrict__ tw_
 
 // Spectra: one CTA per signal window, RIR partition or target-RIR partition of the chunk.
 template <int NC, int NT>
-__global__ void __launch_bounds__(NT, NC <= 8192 ? 2 : 1) sp_forward(SpArgs A)
+__global__ void __launch_bounds__(NT, NC == 4096 ? 4 : (NC == 8192 ? 2 : 1)) sp_forward(SpArgs A)
 {
     extern __shared__ __align__(16) float2 sp_buf[];
     const int nsig = A.rooms * A.S * A.J;
@@ -390,7 +449,7 @@ __device__ __forceinline__ void store_block(const float2* sp_buf, float* out, in
 
 // Mic-0 image of every (room, source), block by block.
 template <int NC, int NT>
-__global__ void __launch_bounds__(NT, NC <= 8192 ? 2 : 1) sp_image0(SpArgs A)
+__global__ void __launch_bounds__(NT, NC == 4096 ? 4 : (NC == 8192 ? 2 : 1)) sp_image0(SpArgs A)
 {
     extern __shared__ __align__(16) float2 sp_buf[];
     const int jid = blockIdx.x;
@@ -467,7 +526,7 @@ __global__ void __launch_bounds__(256) sp_gains(SpArgs A)
 
 // Mixture blocks (room, mic, block) and target blocks (room, speaker, mic, block).
 template <int NC, int NT>
-__global__ void __launch_bounds__(NT, NC <= 8192 ? 2 : 1) sp_mix(SpArgs A)
+__global__ void __launch_bounds__(NT, NC == 4096 ? 4 : (NC == 8192 ? 2 : 1)) sp_mix(SpArgs A)
 {
     extern __shared__ __align__(16) float2 sp_buf[];
     const int nmix = A.rooms * A.M * A.J;
@@ -530,11 +589,21 @@ struct SpLayout {
     size_t header, tw_c, tw_r, XS, HS, HT, img0, gains, total;
 };
 
+// Default block: 4096 (the smallest transform: more CTAs per SM hide the stage barriers better
+// than fewer, larger transforms, even though each output block then sums more partitions),
+// larger only when the sources x partitions exceed the term limit.
+int auto_block(int S, int Lmax)
+{
+    for (int Bk = 4096; Bk < 16384; Bk *= 2)
+        if ((int64_t)S * ((Lmax + Bk - 1) / Bk) <= kMaxTerms) return Bk;
+    return 16384;
+}
+
 SpLayout sp_layout(const fram_scene& sc, const fram_spatial& sp, bool sep)
 {
     SpLayout w{};
     const int Lmax = std::max(sc.max_len, 1);
-    w.Bk = sp.block ? sp.block : (Lmax <= 4096 ? 4096 : (Lmax <= 8192 ? 8192 : 16384));
+    w.Bk = sp.block ? sp.block : auto_block(sc.S, Lmax);
     w.J = (int)((sp.n_samples + w.Bk - 1) / w.Bk);
     w.Q = (Lmax + w.Bk - 1) / w.Bk;
     w.sep = sep;
@@ -546,7 +615,7 @@ SpLayout sp_layout(const fram_scene& sc, const fram_spatial& sp, bool sep)
     if (chunk <= 0) {
         // Large chunks: each kernel needs thousands of CTAs to fill 152 SMs; the spectra then
         // stream through HBM rather than staying in L2, which costs less than idle SMs.
-        const size_t target = (size_t)1 << 30;
+        const size_t target = (size_t)4 << 30;
         chunk = (int)std::max<size_t>(1, target / std::max<size_t>(per_room, 1));
     }
     w.chunk = std::max(1, std::min(chunk, std::max(sc.B, 1)));
@@ -582,7 +651,7 @@ int sp_check(const fram_scene* sc, const fram_spatial* sp)
     if (sp->chunk_rooms < 0) return record_error(FRAM_EINVAL, "chunk_rooms must be >= 0");
     {
         const int Lmax = std::max(sc->max_len, 1);
-        const int Bk = sp->block ? sp->block : (Lmax <= 4096 ? 4096 : (Lmax <= 8192 ? 8192 : 16384));
+        const int Bk = sp->block ? sp->block : auto_block(sc->S, Lmax);
         if ((int64_t)sc->S * ((Lmax + Bk - 1) / Bk) > kMaxTerms)
             return record_error(FRAM_EINVAL, "S x RIR partitions exceeds 128 (raise block)");
     }
@@ -648,7 +717,7 @@ extern "C" int fram_spatialize(const fram_scene* scene, const fram_spatial* sp, 
     for (int r0 = 0; r0 < scene->B; r0 += w.chunk) {
         A.room0 = r0;
         A.rooms = std::min(w.chunk, scene->B - r0);
-        if (w.Bk == 4096) e = launch_chunk<4096, 512>(A, st);
+        if (w.Bk == 4096) e = launch_chunk<4096, 256>(A, st);
         else if (w.Bk == 8192) e = launch_chunk<8192, 512>(A, st);
         else e = launch_chunk<16384, 1024>(A, st);
         if (e != cudaSuccess) return record_error(FRAM_ECUDA, cudaGetErrorString(e));
