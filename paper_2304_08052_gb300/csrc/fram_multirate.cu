@@ -16,17 +16,19 @@
 //                   i = 0..31, so the 21 taps of one impulse are one row read by 32 lanes.
 //   mr_stage_a      persistent warps over (room, source, tile, mic, sub-tile of 256 r_l
 //                   intermediate samples); the images that can reach the sub-tile come from the
-//                   32-sample key blocks; each lane evaluates one image's q in FP64 (the grid
-//                   decides an integer: the same operations in the same order as an FP64
-//                   reference, no fused multiply-add), then each impulse is added with one lane
+//                   32-sample key blocks; each lane evaluates one image's q (the grid decides an
+//                   integer): in float-pair arithmetic when that is more than 4e-6 from a grid
+//                   point, else in FP64 with the same operations in the same order as an FP64
+//                   reference (no fused multiply-add), then each impulse is added with one lane
 //                   per tap into the warp's shared buffer (and into the early buffer when q lies
 //                   in the Eq. 9 window on the high-rate grid).  Tiles go to y1 in global memory.
 //   mr_hpf_seg, mr_hpf_scan   the high-pass, its state as float pairs (poles near z = 1 at
 //                   80 Hz make a float32 recursion lose ~1e-5 of the peak), run on segments of
 //                   2048 samples in parallel: a zero-state pass, a per-channel propagation of the
 //                   true segment start states, and a second pass writing the result in place.
-//   mr_down         the second resampler (ratio 1/r_l, compile-time taps), one thread per output
-//                   sample from a window staged in shared memory.
+//   mr_down         the second resampler (ratio 1/r_l, compile-time taps), three consecutive output
+//                   samples per thread (each window value read once) from a window staged in
+//                   shared memory.
 #include <cmath>
 #include <utility>
 
@@ -178,8 +180,21 @@ __device__ __forceinline__ MrChan mr_chan(const LaunchArgs& a, const RoomConst& 
 }
 
 // Per-warp shared memory (floats): the tile buffer (TA + 64), the early buffer when wanted, and
-// 32 staged impulses (A, q).
-__host__ __device__ inline int mr_warp_floats(int TA, bool early) { return (early ? 2 : 1) * (TA + 64) + 2 * 32; }
+// 32 staged impulses (A; buffer index of tap 0; filter row and Eq. 9 flag).
+__host__ __device__ inline int mr_warp_floats(int TA, bool early) { return (early ? 2 : 1) * (TA + 64) + 3 * 32; }
+
+// Adds a staged impulse: lane j adds A F(m0 + j down) to buffer index bi0 + j.
+__device__ __forceinline__ void mr_add_staged(const float* __restrict__ tab, float* buf, float* bufe, int bi0, int row,
+                                              float A, int TA, int lane)
+{
+    const int m0 = row >> 1;
+    const float f = tab[m0 * kMrNJ + lane];
+    const int bi = bi0 + lane;
+    if (bi >= 0 && bi < TA + 64 && f != 0.0f) {
+        buf[bi] = __fmaf_rn(A, f, buf[bi]);
+        if (bufe && (row & 1)) bufe[bi] = __fmaf_rn(A, f, bufe[bi]);
+    }
+}
 
 // Adds the impulse (q, A) to the buffers: lane j takes the intermediate sample kmin + j.
 __device__ __forceinline__ void mr_add(const float* __restrict__ tab, float* buf, float* bufe, int64_t q, float A,
@@ -196,6 +211,35 @@ __device__ __forceinline__ void mr_add(const float* __restrict__ tab, float* buf
     }
 }
 
+// q = ceil(D r_h fs / c0) from the float-pair image position, when the float-pair value of
+// D r_h fs / c0 (error below 1e-7 samples) lies more than 4e-6 from an integer: then the FP64
+// evaluation, within 1e-9 of the exact value, has the same ceiling.  Returns false otherwise
+// (about one image in 10^5), and the caller decides in FP64.
+__device__ __forceinline__ bool mr_delay_pair(float4 pa, float2 pb, float mx, float my, float mz, f2 q2, float rhf,
+                                              int64_t Lh, float beyond, int64_t& q, float& D_out)
+{
+    f2 dx = two_sum(pa.x, -mx); dx.lo = __fadd_rn(dx.lo, pa.w);
+    f2 dy = two_sum(pa.y, -my); dy.lo = __fadd_rn(dy.lo, pb.x);
+    f2 dz = two_sum(pa.z, -mz); dz.lo = __fadd_rn(dz.lo, pb.y);
+    f2 sx = two_prod(dx.hi, dx.hi); sx.lo = __fmaf_rn(__fmul_rn(2.0f, dx.hi), dx.lo, sx.lo);
+    f2 sy = two_prod(dy.hi, dy.hi); sy.lo = __fmaf_rn(__fmul_rn(2.0f, dy.hi), dy.lo, sy.lo);
+    f2 sz = two_prod(dz.hi, dz.hi); sz.lo = __fmaf_rn(__fmul_rn(2.0f, dz.hi), dz.lo, sz.lo);
+    f2 ss = f2_add(f2_add(fast_two_sum(sx.hi, sx.lo), fast_two_sum(sy.hi, sy.lo)), fast_two_sum(sz.hi, sz.lo));
+    const f2 D = f2_sqrt_fast(ss);
+    const f2 v = f2_mul_f(f2_mul(D, q2), rhf);
+    D_out = D.hi;
+    if (v.hi > beyond) {                      // beyond = L_h + 2 rounded up: past the clamp either way
+        q = Lh - 1;
+        return true;
+    }
+    const float n = rintf(v.hi);
+    const float fr = __fadd_rn(__fsub_rn(v.hi, n), v.lo);
+    if (!(fabsf(fr) > 4.0e-6f)) return false;
+    q = (int64_t)n + (fr > 0.0f ? 1 : 0);
+    if (q > Lh - 1) q = Lh - 1;
+    return true;
+}
+
 __global__ void __launch_bounds__(kMrThreads) mr_stage_a(LaunchArgs a, bool want_early)
 {
     extern __shared__ __align__(16) float mr_smem[];
@@ -205,8 +249,9 @@ __global__ void __launch_bounds__(kMrThreads) mr_stage_a(LaunchArgs a, bool want
     float* tab = mr_smem;                                        // down x 32
     float* buf = mr_smem + down * kMrNJ + wid * mr_warp_floats(TA, want_early);
     float* bufe = want_early ? buf + TA + 64 : nullptr;
-    float* rA = buf + (want_early ? 2 : 1) * (TA + 64);          // staged impulses: A
-    int* rq = reinterpret_cast<int*>(rA + 32);                   // and q
+    float* rA = buf + (want_early ? 2 : 1) * (TA + 64);          // staged impulses: A,
+    int* rbi = reinterpret_cast<int*>(rA + 32);                  // buffer index of tap 0,
+    int* rrow = rbi + 32;                                        // 2 m0 + (q in the Eq. 9 window)
     for (int e = threadIdx.x; e < down * kMrNJ; e += blockDim.x) tab[e] = a.mr_tab[e];
     __syncthreads();
     const double c0 = a.c0, fh = a.fh;
@@ -253,38 +298,49 @@ __global__ void __launch_bounds__(kMrThreads) mr_stage_a(LaunchArgs a, bool want
             const int c_lo = p32[bmin];
             const int c_hi = last ? rc.n_vs : p32[bmax];
             const float* pm = a.mic + 3 * ((size_t)ir.b * M + m);
-            const double mx = pm[0], my = pm[1], mz = pm[2];
+            const float mxf = pm[0], myf = pm[1], mzf = pm[2];
+            const double mx = mxf, my = myf, mz = mzf;
+            const float rhf = (float)a.rh;
+            const float beyond = __ll2float_ru(ch.Lh + 2);
             for (int cb = c_lo; cb < c_hi; cb += 32) {
                 const int p = cb + lane;
                 bool valid = false;
                 int64_t q = 0;
                 float A = 0.0f;
+                int bi0 = 0, row = 0;
                 if (p < c_hi) {
                     const float4 pa = a.spa[ir.v0 + p];
                     const float2 pb = a.spb[ir.v0 + p];
-                    const double dx = __dsub_rn(__dadd_rn((double)pa.x, (double)pa.w), mx);
-                    const double dy = __dsub_rn(__dadd_rn((double)pa.y, (double)pb.x), my);
-                    const double dz = __dsub_rn(__dadd_rn((double)pa.z, (double)pb.y), mz);
-                    const double D = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
-                                                          __dmul_rn(dz, dz)));
-                    const double qh = ceil(__dmul_rn(__ddiv_rn(D, c0), fh));
-                    q = (qh > (double)(ch.Lh - 1)) ? ch.Lh - 1 : (int64_t)qh;
-                    A = a.samp[ir.v0 + p] / (float)D;
-                    const int64_t kmin = ceil_div(q * up - HL, down);
-                    valid = D > 0.0 && A == A && fabsf(A) < 3.0e38f && kmin + 31 >= K0 - 32 && kmin < K0 + TA + 32;
+                    float Df;
+                    if (!mr_delay_pair(pa, pb, mxf, myf, mzf, a.q2, rhf, ch.Lh, beyond, q, Df)) {
+                        // near a grid point: the reference's FP64 operations in its order
+                        const double dx = __dsub_rn(__dadd_rn((double)pa.x, (double)pa.w), mx);
+                        const double dy = __dsub_rn(__dadd_rn((double)pa.y, (double)pb.x), my);
+                        const double dz = __dsub_rn(__dadd_rn((double)pa.z, (double)pb.y), mz);
+                        const double D = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                                                              __dmul_rn(dz, dz)));
+                        const double qh = ceil(__dmul_rn(__ddiv_rn(D, c0), fh));
+                        q = (qh > (double)(ch.Lh - 1)) ? ch.Lh - 1 : (int64_t)qh;
+                        Df = (float)D;
+                    }
+                    A = a.samp[ir.v0 + p] / Df;
+                    const int64_t c = q * up;
+                    const int64_t kmin = ceil_div(c - HL, down);
+                    valid = Df > 0.0f && A == A && fabsf(A) < 3.0e38f && kmin + 31 >= K0 - 32 && kmin < K0 + TA + 32;
+                    bi0 = (int)(kmin - K0 + 32);
+                    row = 2 * (int)(kmin * down - c + HL) + ((q >= dc.early_lo_h && q <= dc.early_hi_h) ? 1 : 0);
                 }
                 const unsigned vb = __ballot_sync(0xffffffffu, valid);
                 if (valid) {
                     const int slot = __popc(vb & ((1u << lane) - 1u));
                     rA[slot] = A;
-                    rq[slot] = (int)q;
+                    rbi[slot] = bi0;
+                    rrow[slot] = row;
                 }
                 __syncwarp();
                 const int nv = __popc(vb);
                 for (int j = 0; j < nv; ++j) {
-                    const int64_t qq = rq[j];
-                    mr_add(tab, buf, bufe, qq, rA[j], qq >= dc.early_lo_h && qq <= dc.early_hi_h, K0, TA, up,
-                           down, HL, lane);
+                    mr_add_staged(tab, buf, bufe, rbi[j], rrow[j], rA[j], TA, lane);
                     __syncwarp();
                 }
             }
@@ -438,25 +494,38 @@ __global__ void __launch_bounds__(128) mr_hpf_scan(LaunchArgs a, SegRec* __restr
 
 // ---- stage C: the resampler 1/RL, one thread per output sample ------------------------------
 // y[n] = sum_k z[k] F_C(n RL - k), k in [0, L_m); a block stages z over its outputs' window.
-constexpr int kMrOut = 256;
+constexpr int kMrOutT = 256;           // threads per block
+constexpr int kMrPer = 3;              // consecutive outputs per thread (3 RL window stride: odd for odd RL)
+constexpr int kMrOut = kMrOutT * kMrPer;
 
-template <int RL, int I>
-__device__ __forceinline__ void fir_step(const float* __restrict__ w, float& acc)
+// Window value w[M] (M = 0 .. (kMrPer - 1) RL + 2 HLC) read once and added to every output j whose
+// taps cover it: output j uses offsets j RL + i, i in [0, 2 HLC], with coefficient F_C(HLC - i).
+template <int RL, int M, int J>
+__device__ __forceinline__ void fir_tap(float x, float* acc)
 {
-    constexpr float c = kFc<RL>.v[20 * RL - I];
-    acc = __fmaf_rn(w[I], c, acc);
+    constexpr int HLC2 = 20 * RL;
+    constexpr int i = M - J * RL;
+    if constexpr (i >= 0 && i <= HLC2) {
+        constexpr float c = kFc<RL>.v[HLC2 - i];
+        acc[J] = __fmaf_rn(x, c, acc[J]);
+    }
 }
 
-template <int RL, int... I>
-__device__ __forceinline__ float fir_dot(const float* __restrict__ w, std::integer_sequence<int, I...>)
+template <int RL, int M, int... J>
+__device__ __forceinline__ void fir_step(const float* __restrict__ w, float* acc, std::integer_sequence<int, J...>)
 {
-    float acc = 0.f;
-    (fir_step<RL, I>(w, acc), ...);
-    return acc;
+    const float x = w[M];
+    (fir_tap<RL, M, J>(x, acc), ...);
+}
+
+template <int RL, int... Mi>
+__device__ __forceinline__ void fir_dot(const float* __restrict__ w, float* acc, std::integer_sequence<int, Mi...>)
+{
+    (fir_step<RL, Mi>(w, acc, std::make_integer_sequence<int, kMrPer>{}), ...);
 }
 
 template <int RL>
-__global__ void __launch_bounds__(kMrOut) mr_down(LaunchArgs a, float* __restrict__ rir, float* __restrict__ early)
+__global__ void __launch_bounds__(kMrOutT) mr_down(LaunchArgs a, float* __restrict__ rir, float* __restrict__ early)
 {
     constexpr int HLC = 10 * RL;
     constexpr int W = kMrOut * RL + 2 * HLC;
@@ -474,17 +543,23 @@ __global__ void __launch_bounds__(kMrOut) mr_down(LaunchArgs a, float* __restric
     const MrChan ch = mr_chan(a, rc, b, s, m);
     const float* z = (is_early ? a.mr_ye : a.mr_y) + ch.off;
     const int64_t k0 = n0 * RL - HLC;                 // window [k0, k0 + W)
-    for (int i = threadIdx.x; i < W; i += kMrOut) {
+    for (int i = threadIdx.x; i < W; i += kMrOutT) {
         const int64_t k = k0 + i;
         zw[i] = (k >= 0 && k < ch.Lm) ? z[k] : 0.f;
     }
     __syncthreads();
-    const int64_t n = n0 + threadIdx.x;
-    if (n < L) {
-        // taps k = n RL - HLC .. n RL + HLC, i.e. window offsets threadIdx.x RL + i, i in [0, 2 HLC]
-        const float v = fir_dot<RL>(zw + threadIdx.x * RL, std::make_integer_sequence<int, 2 * HLC + 1>{});
-        float* y = (is_early ? early : rir) + rc.rir_off + ((int64_t)s * a.M + m) * L;
-        y[n] = v;
+    // outputs n = n0 + kMrPer t + j: taps k = n RL - HLC .. n RL + HLC, i.e. window offsets
+    // (kMrPer t + j) RL + i, i in [0, 2 HLC]
+    float acc[kMrPer];
+#pragma unroll
+    for (int j = 0; j < kMrPer; ++j) acc[j] = 0.f;
+    fir_dot<RL>(zw + threadIdx.x * kMrPer * RL, acc,
+                std::make_integer_sequence<int, (kMrPer - 1) * RL + 2 * HLC + 1>{});
+    float* y = (is_early ? early : rir) + rc.rir_off + ((int64_t)s * a.M + m) * L;
+#pragma unroll
+    for (int j = 0; j < kMrPer; ++j) {
+        const int64_t n = n0 + (int64_t)threadIdx.x * kMrPer + j;
+        if (n < L) y[n] = acc[j];
     }
 }
 
@@ -495,7 +570,7 @@ cudaError_t launch_down(const LaunchArgs& a, float* rir, float* early, cudaStrea
     if (nch == 0) return cudaSuccess;
     const int maxlen = a.max_len;
     dim3 grid((unsigned)nch, (unsigned)((maxlen + kMrOut - 1) / kMrOut));   // channels on x (no 65535 cap)
-    mr_down<RL><<<grid, kMrOut, 0, st>>>(a, rir, early);
+    mr_down<RL><<<grid, kMrOutT, 0, st>>>(a, rir, early);
     return cudaGetLastError();
 }
 
