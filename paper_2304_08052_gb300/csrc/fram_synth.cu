@@ -194,28 +194,38 @@ __device__ __forceinline__ int block_of_key(float key, int nb)
     return j < 0 ? 0 : (j > nb - 1 ? nb - 1 : j);
 }
 
-__global__ void __launch_bounds__(64) bin_images(LaunchArgs a, const float* __restrict__ pos_hi)
+// One CTA of W warps per (room, source).  Warp w owns the contiguous index range
+// [w chunk, (w + 1) chunk) of the images and its own histogram row hist[w][0..NB); the exclusive
+// offsets are taken in (block, warp) order, so every warp's scatter lands exactly where a single
+// pass in index order would put it (the sort stays stable).  Shared memory: (W + 1) x (NB + 1)
+// ints (the last row holds the block prefix) and 33 ints of scan scratch.
+__host__ __device__ inline int bin_smem_ints(int W, int NB) { return (W + 1) * (NB + 1) + 33; }
+
+__global__ void __launch_bounds__(256) bin_images(LaunchArgs a, const float* __restrict__ pos_hi)
 {
     extern __shared__ int bin_smem[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t seg = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
-    if (seg >= (int64_t)a.B * a.S) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
+    const int64_t seg = blockIdx.x;
     const int b = (int)(seg / a.S), s = (int)(seg % a.S);
     const RoomConst rc = a.room[b];
     const int T = a.tile, NB = a.nb32;
-    int* hist = bin_smem + wib * (NB + 1);
     const int n = rc.n_vs, nt = rc.ntiles;
     const int64_t v0 = rc.vs_off + (int64_t)s * n;
     int* bo = a.bin_off + seg * (a.max_tiles + 1);
     int* p32 = a.pos32 + seg * ((int64_t)NB + 1);
     if (nt < 1) {   // a room the prologue rejected: no work items reference its bins
-        if (lane == 0) bo[0] = 0;
+        if (threadIdx.x == 0) bo[0] = 0;
         return;
     }
-    for (int j = lane; j <= NB; j += 32) hist[j] = 0;
-    __syncwarp();
+    int* hist = bin_smem + w * (NB + 1);
+    int* pre = bin_smem + W * (NB + 1);
+    int* scan = pre + (NB + 1);
+    for (int k = threadIdx.x; k < W * (NB + 1); k += blockDim.x) bin_smem[k] = 0;
+    __syncthreads();
+    const int chunk = ((n + W - 1) / W + 31) & ~31;
+    const int i0 = w * chunk, i1 = min(i0 + chunk, n);
     bool bad = false;
-    for (int i = lane; i < n; i += 32) {
+    for (int i = i0 + lane; i < i1; i += 32) {
         const float* p = pos_hi + 3 * (v0 + i);
         const float dx = p[0] - rc.cx, dy = p[1] - rc.cy, dz = p[2] - rc.cz;
         const float key = sqrtf(dx * dx + dy * dy + dz * dz) * a.q;
@@ -224,31 +234,45 @@ __global__ void __launch_bounds__(64) bin_images(LaunchArgs a, const float* __re
         atomicAdd(&hist[block_of_key(key, NB)], 1);
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&a.hdr->status, FRAM_DEV_NONFINITE);
-    __syncwarp();
-    // Exclusive prefix over the blocks -> p32 and the running offsets.
-    int carry = 0;
-    for (int base = 0; base < NB; base += 32) {
-        const int j = base + lane;
-        const int v = j < NB ? hist[j] : 0;
-        int x = v;
+    __syncthreads();
+    // Column totals over warps, exclusive prefix over blocks (each thread a contiguous range).
+    const int per = (NB + blockDim.x - 1) / blockDim.x;
+    const int j0 = threadIdx.x * per, j1 = min(j0 + per, NB);
+    int local = 0;
+    for (int j = j0; j < j1; ++j)
+        for (int u = 0; u < W; ++u) local += bin_smem[u * (NB + 1) + j];
+    int x = local;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        const int excl = carry + x - v;
-        if (j < NB) { p32[j] = excl; hist[j] = excl; }
-        carry = __shfl_sync(0xffffffffu, carry + x, 31);
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
     }
-    if (lane == 0) p32[NB] = n;
+    if (lane == 31) scan[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int u = 0; u < W; ++u) { const int t = scan[u]; scan[u] = run; run += t; }
+    }
+    __syncthreads();
+    int run = scan[w] + x - local;           // exclusive prefix of this thread's first block
+    for (int j = j0; j < j1; ++j) {
+        pre[j] = run;
+        p32[j] = run;
+        for (int u = 0; u < W; ++u) {        // warp u's first position in block j
+            const int c = bin_smem[u * (NB + 1) + j];
+            bin_smem[u * (NB + 1) + j] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) p32[NB] = n;
     const int bpt = T >> 5;
-    for (int t = lane; t < nt; t += 32) bo[t] = hist[t * bpt];
-    if (lane == 0) bo[nt] = n;
-    __syncwarp();
-    // Stable scatter by block (index order inside a block).
-    for (int base = 0; base < n; base += 32) {
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) bo[t] = pre[t * bpt];
+    if (threadIdx.x == 0) bo[nt] = n;
+    // Stable scatter by block, warp w over its own range in index order.
+    for (int base = i0; base < i1; base += 32) {
         const int i = base + lane;
-        const bool act = i < n;
+        const bool act = i < i1;
         const int j = act ? block_of_key(a.key[v0 + i], NB) : -1;
         const unsigned peers = __match_any_sync(0xffffffffu, j);
         const int leader = __ffs(peers) - 1;
@@ -604,10 +628,13 @@ cudaError_t launch_prepare(const LaunchArgs& a, const float* pos_hi, const float
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int64_t segs = (int64_t)a.B * a.S;
     if (segs > 0) {
-        const int sm = (int)(sizeof(int) * 2 * ((size_t)a.nb32 + 1));
+        // warps per (room, source): 8, fewer when the histogram rows would not fit in 200 KiB
+        int W = 8;
+        while (W > 1 && (size_t)bin_smem_ints(W, a.nb32) * sizeof(int) > (size_t)200 * 1024) --W;
+        const int sm = (int)(sizeof(int) * (size_t)bin_smem_ints(W, a.nb32));
         int per_sm = 0;
-        if ((e = kernel_residency((const void*)bin_images, 64, sm, &per_sm)) != cudaSuccess) return e;
-        bin_images<<<(unsigned)((segs + 1) / 2), 64, sm, st>>>(a, pos_hi);
+        if ((e = kernel_residency((const void*)bin_images, 32 * W, sm, &per_sm)) != cudaSuccess) return e;
+        bin_images<<<(unsigned)segs, 32 * W, sm, st>>>(a, pos_hi);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         sort_positions<<<(unsigned)segs, 256, 0, st>>>(a, pos_hi, pos_lo);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
