@@ -40,9 +40,9 @@ METRIC = "multi-ch RIRs/s and sinc-taps/s (fwd, fwd+bwd) at 1 GB300, % of roofli
 # reported only while the synthesis source is the one that was measured (its SHA-256 prefix).
 SYNTH_TRAFFIC = {"source_sha256": "3200b732e000a6c0", "bytes_per_sample": (85302016 + 1073871872) / 283357184}
 
-# Kernels of libfram per fwd step: sample_kernel; room_prologue, item_scan, bin_images,
-# sort_positions, item_ranges (preparation); amp_gather, synth_kernel (synthesis).
-FWD_LAUNCHES = 8
+# Kernels of libfram per fwd step: sample_prologue, sample_kernel; room_prologue, item_scan,
+# bin_images, sort_positions, item_ranges (preparation); amp_gather, synth_kernel (synthesis).
+FWD_LAUNCHES = 9
 FWD_FP32, BWD_FP32, ARR_FP32 = 8.0, 14.0, 40.0
 TAP_MUFU, ARR_MUFU = 1.0, 6.0
 FP32_LANES_PER_SM, MUFU_LANES_PER_SM = 128, 16

@@ -220,6 +220,7 @@ static LaunchArgs make_args(const fram_scene* sc, const fram_params* p, const Ws
     a.part_src = reinterpret_cast<float*>(base + w.part_src);
     a.part_r = reinterpret_cast<float*>(base + w.part_r);
     a.sb_part = reinterpret_cast<double*>(base + w.sb_part);
+    a.sconst = reinterpret_cast<char*>(base + w.sconst);
     a.max_len = sc->max_len;
     a.mode = p->delay_mode;
     a.early_pre_ms = p->early_pre_ms;

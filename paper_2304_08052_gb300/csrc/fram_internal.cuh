@@ -230,8 +230,10 @@ struct Header {             // first 256 bytes of the workspace
     int32_t pad_[60];
 };
 
+constexpr int kSampleRec = 256;   // bytes per (room, source) record of the sampler's constants
+
 struct WsLayout {
-    size_t header, room, direct, src_tile, item_off, items, bin_off, perm, key, skey;
+    size_t header, room, direct, src_tile, item_off, items, bin_off, perm, key, skey, sconst;
     size_t spa, spb, pos32, samp, irec;
     size_t mr_y, mr_ye, mr_tab, mr_seg;   // multi-rate mode: intermediate signals, resampling
                                           // table, high-pass segment records
@@ -287,6 +289,7 @@ inline WsLayout ws_layout(const fram_scene& sc, int tile, int delay_mode = 0, do
     w.pos32 = take(sizeof(int32_t) * (size_t)sc.B * sc.S * ((size_t)w.nb32 + 1));
     w.samp = take(sizeof(float) * (size_t)sc.n_vs_total);
     w.irec = take(sizeof(ItemRec) * (size_t)w.max_items);
+    w.sconst = take((size_t)kSampleRec * sc.B * sc.S);
     if (delay_mode == 1) {
         // per channel (room, source, mic): r_l L_b + 8 intermediate samples, and the same for
         // the early RIR; the polyphase table is down x 32 floats.
@@ -345,6 +348,7 @@ struct LaunchArgs {
                             // whose key is >= 32 j (rows of nb32 + 1 entries)
     float* samp;            // per sorted position: r^g of the image (written per synthesis)
     ItemRec* irec;          // per work item
+    char* sconst;           // per (room, source): the sampler's constants (kSampleRec bytes each)
     // multi-rate mode (delay_mode 1)
     int32_t mode;
     int32_t rh, rl, up, down, HLA;   // rates, first resampling ratio, its filter's half length

@@ -1,8 +1,9 @@
 // fram_sample.cu -- virtual-image sampler kernel (FRAM-RIR Sec. III-A to III-C, Eq. 2-6) and
 // the gradient through it (sample_backward_kernel, sample_backward_room).
 //
-// One CTA per (room, source).  Thread 0 evaluates the per-(room, source) constants in FP64
-// (a few dozen double operations per CTA); every thread then draws images i = tid, tid +
+// sample_prologue evaluates the per-(room, source) constants in FP64 (one thread each, a few
+// dozen double operations) into the workspace; then one CTA per (room, source) draws images
+// i = tid, tid +
 // blockDim, ... with one Philox4x32-10 call each and maps the four words to
 //   u0 -> distance ratio x (inverse CDF of Eq. 3) -> D_i = D0 + (c0 T60 - D0)(x - alpha)/(beta - alpha)
 //         (Eq. 4 written as a single affine map: x = alpha gives D0, x = beta gives c0 T60),
@@ -156,24 +157,52 @@ __device__ void sample_consts(const LaunchArgs& a, int b, int s, double alpha, d
     }
 }
 
-__global__ void __launch_bounds__(256) sample_kernel(LaunchArgs a, double alpha, double beta, double pa, double pb,
-                                                     double tau, double c0, uint64_t seed, const uint64_t* d_seed,
+// Record of (room, source) bs in the workspace: SampleConst, then the 10 doubles of `extra`.
+static_assert(sizeof(SampleConst) <= 128 && sizeof(SampleConst) % 4 == 0, "sampler record layout");
+static_assert(128 + 10 * sizeof(double) <= kSampleRec, "sampler record size");
+
+// The per-(room, source) constants, one thread each, so the image kernels need not wait on a
+// serial FP64 prologue per CTA.
+__global__ void __launch_bounds__(128) sample_prologue(LaunchArgs a, double alpha, double beta, double pa, double pb,
+                                                       double tau, double c0, float* __restrict__ r_out)
+{
+    const int bs = blockIdx.x * blockDim.x + threadIdx.x;
+    if (bs >= a.B * a.S) return;
+    const int b = bs / a.S, s = bs % a.S;
+    SampleConst C;
+    double X[10];
+    double r;
+    sample_consts(a, b, s, alpha, beta, pa, pb, tau, c0, C, &r, X);
+    if (s == 0 && r_out) r_out[b] = (float)r;
+    if (!C.valid) atomicOr(&a.hdr->status, FRAM_DEV_BAD_GEOMETRY);
+    char* rec = a.sconst + (int64_t)bs * kSampleRec;
+    *reinterpret_cast<SampleConst*>(rec) = C;
+    double* xr = reinterpret_cast<double*>(rec + 128);
+    for (int k = 0; k < 10; ++k) xr[k] = X[k];
+}
+
+// Copies record bs into shared memory (C and, if X is given, the extras); the caller syncs.
+__device__ __forceinline__ void load_record(const LaunchArgs& a, int bs, SampleConst* C, double* X)
+{
+    const int* src = reinterpret_cast<const int*>(a.sconst + (int64_t)bs * kSampleRec);
+    constexpr int nc = (int)(sizeof(SampleConst) / 4);
+    if (threadIdx.x < nc) reinterpret_cast<int*>(C)[threadIdx.x] = src[threadIdx.x];
+    if (X && threadIdx.x >= 32 && threadIdx.x < 52) reinterpret_cast<int*>(X)[threadIdx.x - 32] = src[32 + threadIdx.x - 32];
+}
+
+__global__ void __launch_bounds__(256) sample_kernel(LaunchArgs a, uint64_t seed, const uint64_t* d_seed,
                                                      float* __restrict__ pos_hi, float* __restrict__ pos_lo,
-                                                     float* __restrict__ g_out, float* __restrict__ r_out,
-                                                     uint32_t* __restrict__ words)
+                                                     float* __restrict__ g_out, uint32_t* __restrict__ words)
 {
     const int bs = blockIdx.x;
     const int b = bs / a.S, s = bs % a.S;
     __shared__ SampleConst C;
     __shared__ uint32_t key_s[2];
+    load_record(a, bs, &C, nullptr);
     if (threadIdx.x == 0) {
         const uint64_t sd = d_seed ? *d_seed : seed;
         key_s[0] = (uint32_t)(sd & 0xffffffffu);
         key_s[1] = (uint32_t)(sd >> 32);
-        double r;
-        sample_consts(a, b, s, alpha, beta, pa, pb, tau, c0, C, &r, nullptr);
-        if (s == 0 && r_out) r_out[b] = (float)r;
-        if (!C.valid) atomicOr(&a.hdr->status, FRAM_DEV_BAD_GEOMETRY);
     }
     __syncthreads();
     int n = a.n_vs[b];
@@ -218,9 +247,7 @@ __device__ __forceinline__ double warp_sum_d(double x)
 
 constexpr int kSbParts = 5;     // per (room, source): dL/dc (3), dL/d(c0 T60), dL/dr via RR_max
 
-__global__ void __launch_bounds__(256) sample_backward_kernel(LaunchArgs a, double alpha, double beta, double pa,
-                                                              double pb, double tau, double c0, uint64_t seed,
-                                                              const uint64_t* d_seed,
+__global__ void __launch_bounds__(256) sample_backward_kernel(LaunchArgs a, uint64_t seed, const uint64_t* d_seed,
                                                               const float* __restrict__ grad_vs,
                                                               const float* __restrict__ grad_g,
                                                               const float* __restrict__ grad_src_dir,
@@ -232,12 +259,11 @@ __global__ void __launch_bounds__(256) sample_backward_kernel(LaunchArgs a, doub
     __shared__ double X[10];
     __shared__ uint32_t key_s[2];
     __shared__ double red[8][6];
+    load_record(a, bs, &C, X);
     if (threadIdx.x == 0) {
         const uint64_t sd = d_seed ? *d_seed : seed;
         key_s[0] = (uint32_t)(sd & 0xffffffffu);
         key_s[1] = (uint32_t)(sd >> 32);
-        sample_consts(a, b, s, alpha, beta, pa, pb, tau, c0, C, nullptr, X);
-        if (!C.valid) atomicOr(&a.hdr->status, FRAM_DEV_BAD_GEOMETRY);
     }
     __syncthreads();
     int n = a.n_vs[b];
@@ -341,8 +367,10 @@ cudaError_t launch_sample(const LaunchArgs& a, const fram_params& p, uint64_t se
 {
     const int nblocks = a.B * a.S;
     if (nblocks == 0) return cudaSuccess;
-    sample_kernel<<<nblocks, 256, 0, st>>>(a, p.alpha, p.beta, p.a, p.b, p.tau, p.c0, seed, d_seed, pos_hi, pos_lo,
-                                          g, r, words);
+    sample_prologue<<<(nblocks + 127) / 128, 128, 0, st>>>(a, p.alpha, p.beta, p.a, p.b, p.tau, p.c0, r);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sample_kernel<<<nblocks, 256, 0, st>>>(a, seed, d_seed, pos_hi, pos_lo, g, words);
     return cudaGetLastError();
 }
 
@@ -357,9 +385,11 @@ cudaError_t launch_sample_backward(const LaunchArgs& a, const fram_params& p, ui
 {
     const int nblocks = a.B * a.S;
     if (nblocks == 0) return cudaSuccess;
-    sample_backward_kernel<<<nblocks, 256, 0, st>>>(a, p.alpha, p.beta, p.a, p.b, p.tau, p.c0, seed, d_seed, grad_vs,
-                                                    grad_g, grad_src_dir, grad_src, part);
+    sample_prologue<<<(nblocks + 127) / 128, 128, 0, st>>>(a, p.alpha, p.beta, p.a, p.b, p.tau, p.c0, nullptr);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sample_backward_kernel<<<nblocks, 256, 0, st>>>(a, seed, d_seed, grad_vs, grad_g, grad_src_dir, grad_src, part);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     sample_backward_room<<<(a.B + 127) / 128, 128, 0, st>>>(a, p.c0, grad_r, grad_mic_dir, part, grad_mic, grad_t60,
                                                             grad_dims);
