@@ -56,6 +56,9 @@ struct SpArgs {
     float2* XS;                    // [rooms][S][J][NC]
     float2* HS;                    // [rooms][S][M][Q][NC]
     float2* HT;                    // [rooms][ns][M][Q][NC] (== HS when !sep)
+    int* XF;                       // 1 where the spectrum is nonzero (same indexing, one int each)
+    int* HF;
+    int* HTF;                      // (== HF when !sep)
     float* img0;                   // [rooms][S][N]
     Header* hdr;
 };
@@ -299,6 +302,7 @@ __global__ void __launch_bounds__(NT, NC == 4096 ? 4 : (NC == 8192 ? 2 : 1)) sp_
     int64_t start, len;
     int lim;               // window samples taken from the source (the rest are zero)
     float2* dst;
+    int* flag;
     if (jid < nsig) {
         const int cb = jid / (A.S * A.J), s = (jid / A.J) % A.S, j = jid % A.J;
         src = A.x + ((int64_t)(A.room0 + cb) * A.S + s) * A.N;
@@ -306,6 +310,7 @@ __global__ void __launch_bounds__(NT, NC == 4096 ? 4 : (NC == 8192 ? 2 : 1)) sp_
         len = A.N;
         lim = 2 * A.Bk;
         dst = A.XS + (int64_t)jid * NC;
+        flag = A.XF + jid;
     } else {
         jid -= nsig;
         const bool tgt = jid >= nrir;
@@ -326,16 +331,23 @@ __global__ void __launch_bounds__(NT, NC == 4096 ? 4 : (NC == 8192 ? 2 : 1)) sp_
         start = (int64_t)q * A.Bk;
         lim = A.Bk;
         dst = (tgt ? A.HT : A.HS) + (int64_t)jid * NC;
+        flag = (tgt ? A.HTF : A.HF) + jid;
     }
+    bool nonzero = false;
     for (int n = threadIdx.x; n < NC; n += NT) {
         const int t0 = 2 * n, t1 = 2 * n + 1;
         const int64_t i0 = start + t0, i1 = start + t1;
         const float a = (t0 < lim && i0 >= 0 && i0 < len) ? src[i0] : 0.f;
         const float b = (t1 < lim && i1 >= 0 && i1 < len) ? src[i1] : 0.f;
         sp_buf[sw(n)] = make_float2(a, b);
+        nonzero = nonzero || a != 0.0f || b != 0.0f;
     }
     const Twiddles tw = load_twiddles<NC, NT>(A.tw_c);
-    __syncthreads();
+    // An all-zero window (a silent stretch of a source, an RIR partition past its end) has a zero
+    // spectrum: it is flagged and skipped by every sum that would read it.
+    const int nz = __syncthreads_or(nonzero ? 1 : 0);
+    if (threadIdx.x == 0) *flag = nz;
+    if (!nz) return;
     cfft<NC, NT, false>(sp_buf, tw);
     // Split: with Zc = conj(Z[NC-k]), E = (Z[k] + Zc)/2, O = -i (Z[k] - Zc)/2,
     // X[k] = E + w_P^k O and X[NC-k] = conj(E - w_P^k O).
@@ -447,6 +459,15 @@ __device__ __forceinline__ void store_block(const float2* sp_buf, float* out, in
     }
 }
 
+// Writes zeros to output block j (every term of its sum was a zero spectrum).
+template <int NC, int NT>
+__device__ __forceinline__ void store_zero_block(float* out, int64_t N, int j)
+{
+    const int64_t base = (int64_t)j * NC;
+    for (int u = threadIdx.x; u < NC; u += NT)
+        if (base + u < N) out[base + u] = 0.0f;
+}
+
 // Mic-0 image of every (room, source), block by block.
 template <int NC, int NT>
 __global__ void __launch_bounds__(NT, NC == 4096 ? 4 : (NC == 8192 ? 2 : 1)) sp_image0(SpArgs A)
@@ -455,17 +476,27 @@ __global__ void __launch_bounds__(NT, NC == 4096 ? 4 : (NC == 8192 ? 2 : 1)) sp_
     const int jid = blockIdx.x;
     const int cb = jid / (A.S * A.J), s = (jid / A.J) % A.S, j = jid % A.J;
     __shared__ SpTerm terms[kMaxTerms];
-    const float2* X = A.XS + ((int64_t)cb * A.S + s) * A.J * NC;
-    const float2* H = A.HS + (((int64_t)cb * A.S + s) * A.M) * A.Q * NC;      // mic 0
-    const int nt = min(A.Q, j + 1);
+    __shared__ int nt_s;
+    const int64_t xi = ((int64_t)cb * A.S + s) * A.J, hi = (((int64_t)cb * A.S + s) * A.M) * A.Q;   // mic 0
     const Twiddles tw = load_twiddles<NC, NT>(A.tw_c);
-    if (threadIdx.x < nt)
-        terms[threadIdx.x] = SpTerm{X + (int64_t)(j - threadIdx.x) * NC, H + (int64_t)threadIdx.x * NC, 1.0f};
+    if (threadIdx.x == 0) {       // nonzero terms only, in q order
+        int nt = 0;
+        for (int q = 0; q < A.Q && q <= j; ++q)
+            if (A.XF[xi + j - q] && A.HF[hi + q])
+                terms[nt++] = SpTerm{A.XS + (xi + j - q) * NC, A.HS + (hi + q) * NC, 1.0f};
+        nt_s = nt;
+    }
     __syncthreads();
+    const int nt = nt_s;
+    float* out = A.img0 + ((int64_t)cb * A.S + s) * A.N;
+    if (nt == 0) {
+        store_zero_block<NC, NT>(out, A.N, j);
+        return;
+    }
     spectral_sum<NC, NT>(sp_buf, terms, nt);
     __syncthreads();
     inverse_real<NC, NT>(sp_buf, tw, A.tw_r);
-    store_block<NC, NT>(sp_buf, A.img0 + ((int64_t)cb * A.S + s) * A.N, A.N, j, 1.0f / NC);
+    store_block<NC, NT>(sp_buf, out, A.N, j, 1.0f / NC);
 }
 
 // Block-wide FP64 sum in a fixed tree; the result is valid in thread 0.
@@ -545,20 +576,31 @@ __global__ void __launch_bounds__(NT, NC == 4096 ? 4 : (NC == 8192 ? 2 : 1)) sp_
     const float2* Hb = tgt ? A.HT : A.HS;
     const int hs = (tgt && A.sep) ? A.ns : A.S;
     __shared__ SpTerm terms[kMaxTerms];
-    const int nq = min(A.Q, j + 1);
-    const int nt = (s1 - s0) * nq;
+    __shared__ int nt_s;
+    const int* Hf = tgt ? A.HTF : A.HF;
     const Twiddles tw = load_twiddles<NC, NT>(A.tw_c);
-    if (threadIdx.x < nt) {
-        const int s = s0 + threadIdx.x / nq, q = threadIdx.x % nq;
-        terms[threadIdx.x] = SpTerm{A.XS + (((int64_t)cb * A.S + s) * A.J + (j - q)) * NC,
-                                    Hb + ((((int64_t)cb * hs + s) * A.M + m) * A.Q + q) * NC,
-                                    A.gains[(int64_t)b * A.S + s]};
+    if (threadIdx.x == 0) {       // nonzero terms only, in (source, q) order
+        int nt = 0;
+        for (int s = s0; s < s1; ++s) {
+            const float g = A.gains[(int64_t)b * A.S + s];
+            for (int q = 0; q < A.Q && q <= j; ++q) {
+                const int64_t xi = ((int64_t)cb * A.S + s) * A.J + (j - q);
+                const int64_t hi = (((int64_t)cb * hs + s) * A.M + m) * A.Q + q;
+                if (g != 0.0f && A.XF[xi] && Hf[hi]) terms[nt++] = SpTerm{A.XS + xi * NC, Hb + hi * NC, g};
+            }
+        }
+        nt_s = nt;
     }
     __syncthreads();
+    const int nt = nt_s;
+    float* out = tgt ? A.tg + (((int64_t)b * A.ns + s0) * A.M + m) * A.N : A.mix + ((int64_t)b * A.M + m) * A.N;
+    if (nt == 0) {
+        store_zero_block<NC, NT>(out, A.N, j);
+        return;
+    }
     spectral_sum<NC, NT>(sp_buf, terms, nt);
     __syncthreads();
     inverse_real<NC, NT>(sp_buf, tw, A.tw_r);
-    float* out = tgt ? A.tg + (((int64_t)b * A.ns + s0) * A.M + m) * A.N : A.mix + ((int64_t)b * A.M + m) * A.N;
     store_block<NC, NT>(sp_buf, out, A.N, j, 1.0f / NC);
 }
 
@@ -586,7 +628,7 @@ cudaError_t launch_chunk(const SpArgs& A, cudaStream_t st)
 struct SpLayout {
     int Bk, J, Q, chunk;
     bool sep;
-    size_t header, tw_c, tw_r, XS, HS, HT, img0, gains, total;
+    size_t header, tw_c, tw_r, XS, HS, HT, XF, HF, HTF, img0, gains, total;
 };
 
 // Default block: 4096 (the smallest transform: more CTAs per SM hide the stage barriers better
@@ -632,6 +674,9 @@ SpLayout sp_layout(const fram_scene& sc, const fram_spatial& sp, bool sep)
     w.XS = take(spec * C * sc.S * w.J);
     w.HS = take(spec * C * sc.S * sc.M * w.Q);
     w.HT = sep ? take(spec * C * sp.n_speech * sc.M * w.Q) : w.HS;
+    w.XF = take(sizeof(int) * C * sc.S * w.J);
+    w.HF = take(sizeof(int) * C * sc.S * sc.M * w.Q);
+    w.HTF = sep ? take(sizeof(int) * C * sp.n_speech * sc.M * w.Q) : w.HF;
     w.img0 = take(sizeof(float) * C * sc.S * (size_t)sp.n_samples);
     w.gains = take(sizeof(float) * (size_t)std::max(sc.B, 1) * sc.S);
     w.total = off;
@@ -708,6 +753,9 @@ extern "C" int fram_spatialize(const fram_scene* scene, const fram_spatial* sp, 
     A.HS = reinterpret_cast<float2*>(base + w.HS);
     A.HT = reinterpret_cast<float2*>(base + w.HT);
     A.img0 = reinterpret_cast<float*>(base + w.img0);
+    A.XF = reinterpret_cast<int*>(base + w.XF);
+    A.HF = reinterpret_cast<int*>(base + w.HF);
+    A.HTF = reinterpret_cast<int*>(base + w.HTF);
     A.hdr = reinterpret_cast<Header*>(base + w.header);
     cudaError_t e = cudaMemsetAsync(A.hdr, 0, sizeof(Header), st);
     if (e != cudaSuccess) return record_error(FRAM_ECUDA, cudaGetErrorString(e));
