@@ -22,10 +22,11 @@
 //                   reference (no fused multiply-add), then each impulse is added with one lane
 //                   per tap into the warp's shared buffer (and into the early buffer when q lies
 //                   in the Eq. 9 window on the high-rate grid).  Tiles go to y1 in global memory.
-//   mr_hpf_seg, mr_hpf_scan   the high-pass, its state as float pairs (poles near z = 1 at
-//                   80 Hz make a float32 recursion lose ~1e-5 of the peak), run on segments of
-//                   2048 samples in parallel: a zero-state pass, a per-channel propagation of the
-//                   true segment start states, and a second pass writing the result in place.
+//   mr_hpf_end, mr_hpf_scan, mr_hpf_seg   the high-pass, its state as float pairs (poles near
+//                   z = 1 at 80 Hz make a float32 recursion lose ~1e-5 of the peak), run on
+//                   segments of 2048 samples in parallel: each segment's zero-state end state as
+//                   a dot product with precomputed weights, a per-channel propagation of the true
+//                   segment start states, and the recursion writing the result in place.
 //   mr_down         the second resampler (ratio 1/r_l, compile-time taps), three consecutive output
 //                   samples per thread (each window value read once) from a window staged in
 //                   shared memory.
@@ -357,12 +358,14 @@ __global__ void __launch_bounds__(kMrThreads) mr_stage_a(LaunchArgs a, bool want
 // ---- stage B: the high-pass, segmented -------------------------------------------------------
 // The recursion y0 = b0 (x0 - 2 x1 + x2) - a1 y1 - a2 y2 is linear, so each channel is cut into
 // segments of kMrSeg samples that run in parallel:
-//   mr_hpf_seg (pass 0)  every segment from a zero output state (with its true input history):
-//                        its end state, in float pairs;
+//   mr_hpf_end           one warp per segment: the state (y[e], y[e-1]) the segment leaves from a
+//                        zero output state (with its true input history), as a dot product of its
+//                        inputs with precomputed weights (mr_hpf_tables) -- no recursion;
 //   mr_hpf_scan          one thread per channel: the true start state of every segment,
 //                        s_{j+1} = zs_end_j + A^kMrSeg s_j with A = [[-a1, -a2], [1, 0]] in FP64;
-//   mr_hpf_seg (pass 1)  every segment again from its true start state, writing the high-passed
-//                        signal over its input (the input history was saved by the scan).
+//   mr_hpf_seg           every segment from its true start state, the recursion in float pairs,
+//                        writing the high-passed signal over its input (the input history was
+//                        saved by the scan).
 constexpr int kMrSeg = 2048;
 
 struct HpfCoef {
@@ -398,7 +401,137 @@ __device__ __forceinline__ void mr_channel_of(const LaunchArgs& a, int64_t chan,
     b = (int)(chan / ((int64_t)a.M * a.S));
 }
 
-template <int PASS>
+// Segment-end weights (FP64, one thread): the all-pole impulse response g_0 = 1,
+// g_k = -a1 g_{k-1} - a2 g_{k-2}; G_k = (g_k, g_{k-1}) is the state (y[e], y[e-1]) that a unit input
+// k samples before the end leaves behind, and K_k = b0 (G_k - 2 G_{k-1} + G_{k-2}) the weight of
+// x[e - k] once the FIR part (1 - 2 z^-1 + z^-2) is folded in (G_{<0} = 0).  The state of a
+// resonator this close to z = 1 amplifies its errors by ~1/sin(theta) (hundreds of samples), so
+// weights and sums are float pairs.  Layout of mr_hk: K_0..K_{kMrSeg-1}, then G_0..G_{kMrSeg+1},
+// each a float4 (hi of both components, then lo of both), then b0 as (hi, lo) padded to a float4,
+// then K again in the order a full segment reads it: entry c kMrSeg/4 + g is the weight of
+// sample 4 g + c, i.e. K_{kMrSeg - 1 - 4 g - c}, so the lanes of a warp read consecutive entries.
+__device__ __forceinline__ float4 pair4(double u, double v)
+{
+    const float uh = (float)u, vh = (float)v;
+    return make_float4(uh, vh, (float)(u - (double)uh), (float)(v - (double)vh));
+}
+
+// The poles are rho e^(+-i theta) with rho = sqrt(a2), cos theta = -a1 / (2 rho), so
+// g_k = rho^k sin((k + 1) theta) / sin theta in closed form: one thread per k.
+__global__ void __launch_bounds__(256) mr_hpf_tables(LaunchArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kMrSeg + 2) return;
+    const double k = tan(3.14159265358979323846 * 80.0 / ((double)a.rl * a.fs));
+    const double den = 1.0 + sqrt(2.0) * k + k * k;
+    const double a1 = 2.0 * (k * k - 1.0) / den, a2 = (1.0 - sqrt(2.0) * k + k * k) / den, b0 = 1.0 / den;
+    const double rho = sqrt(a2), theta = acos(-a1 / (2.0 * rho)), st = sin(theta);
+    auto g = [&](int n) { return n < 0 ? 0.0 : pow(rho, (double)n) * sin((double)(n + 1) * theta) / st; };
+    float4* K = reinterpret_cast<float4*>(a.mr_hk);
+    float4* G = K + kMrSeg;
+    const double g0 = g(i), g1 = g(i - 1), g2 = g(i - 2), g3 = g(i - 3);
+    G[i] = pair4(g0, g1);
+    if (i < kMrSeg) {
+        const float4 kv = pair4(b0 * (g0 - 2.0 * g1 + g2), b0 * (g1 - 2.0 * g2 + g3));
+        K[i] = kv;
+        const int t = kMrSeg - 1 - i;                 // sample position of weight K_i in a full segment
+        (G + kMrSeg + 3)[(t & 3) * (kMrSeg / 4) + (t >> 2)] = kv;
+    }
+    if (i == 0) {
+        float* tail = reinterpret_cast<float*>(G + kMrSeg + 2);
+        tail[0] = (float)b0;
+        tail[1] = (float)(b0 - (double)tail[0]);
+    }
+}
+
+// (sh, sl) += (kh + kl) x, the product exact to a float pair (FMA), the sum a TwoSum.
+__device__ __forceinline__ void pair_fma(float kh, float kl, float x, float& sh, float& sl)
+{
+    const float p = kh * x;
+    const float e = __fmaf_rn(kl, x, __fmaf_rn(kh, x, -p));
+    const float t = sh + p;
+    const float bb = t - sh;
+    sl += ((sh - (t - bb)) + (p - bb)) + e;
+    sh = t;
+}
+
+// Zero-state end state of every segment, one warp each: sum over the segment's inputs of
+// K_{e-m} x[m] (float-pair products and sums per lane, FP64 across lanes), plus the two
+// input-history samples x[s0-1], x[s0-2] with the weights truncated to the segment.
+constexpr int kHpfEndThreads = 512;
+
+__global__ void __launch_bounds__(kHpfEndThreads) mr_hpf_end(LaunchArgs a, SegRec* __restrict__ seg, int nseg_max,
+                                                              bool with_early)
+{
+    // the weights (32 KiB, in lane order) are read by every warp: staged once per CTA
+    __shared__ float4 Ks[kMrSeg];
+    {
+        const float4* Kg = reinterpret_cast<const float4*>(a.mr_hk) + kMrSeg + kMrSeg + 3;
+        for (int i = threadIdx.x; i < kMrSeg; i += blockDim.x) Ks[i] = Kg[i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nch = (int64_t)a.B * a.S * a.M;
+    const int64_t chans = with_early ? 2 * nch : nch;
+    if (wg >= chans * nseg_max) return;
+    const int64_t cidx = wg / nseg_max;
+    const int j = (int)(wg - cidx * nseg_max);
+    const bool is_early = cidx >= nch;
+    const int64_t chan = is_early ? cidx - nch : cidx;
+    int b, s, m;
+    mr_channel_of(a, chan, b, s, m);
+    const RoomConst rc = a.room[b];
+    if (rc.len < 1) return;
+    const MrChan ch = mr_chan(a, rc, b, s, m);
+    const int64_t s0 = (int64_t)j * kMrSeg;
+    if (s0 >= ch.Lm) return;
+    const int L = (int)((s0 + kMrSeg < ch.Lm ? s0 + kMrSeg : ch.Lm) - s0);
+    const float* x = (is_early ? a.mr_ye : a.mr_y) + ch.off + s0;
+    const float4* G = reinterpret_cast<const float4*>(a.mr_hk) + kMrSeg;
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+    if (L == kMrSeg) {           // full segment: lane-order weights from shared memory
+        for (int g = lane; g < kMrSeg / 4; g += 32) {   // x[s0 + 4 g .. + 3]
+            const float4 v = __ldcs(reinterpret_cast<const float4*>(x + 4 * g));
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float4 w = Ks[c * (kMrSeg / 4) + g];
+                pair_fma(w.x, w.z, vv[c], h0, l0);
+                pair_fma(w.y, w.w, vv[c], h1, l1);
+            }
+        }
+    } else {                     // the last, partial segment of a channel: natural-order weights
+        const float4* K = reinterpret_cast<const float4*>(a.mr_hk);
+        for (int i = lane; i < L; i += 32) {
+            const float4 w = __ldg(&K[L - 1 - i]);
+            pair_fma(w.x, w.z, x[i], h0, l0);
+            pair_fma(w.y, w.w, x[i], h1, l1);
+        }
+    }
+    double d0 = (double)h0 + (double)l0, d1 = (double)h1 + (double)l1;
+    if (lane == 0) {   // x[s0-1] (weight b0 (-2 G_{L-1} + G_{L-2})) and x[s0-2] (weight b0 G_{L-1})
+        const float* tail = reinterpret_cast<const float*>(G + kMrSeg + 2);
+        const double b0 = (double)tail[0] + (double)tail[1];
+        const double xm1 = s0 >= 1 ? x[-1] : 0.0, xm2 = s0 >= 2 ? x[-2] : 0.0;
+        const float4 q1 = G[L - 1], q2 = L >= 2 ? G[L - 2] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const double g1a = (double)q1.x + q1.z, g1b = (double)q1.y + q1.w;
+        const double g2a = (double)q2.x + q2.z, g2b = (double)q2.y + q2.w;
+        d0 += b0 * (-2.0 * g1a + g2a) * xm1 + b0 * g1a * xm2;
+        d1 += b0 * (-2.0 * g1b + g2b) * xm1 + b0 * g1b * xm2;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+        d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+    }
+    if (lane == 0) {
+        SegRec& R = seg[cidx * nseg_max + j];
+        R.zy1h = (float)d0; R.zy1l = (float)(d0 - (double)R.zy1h);
+        R.zy2h = (float)d1; R.zy2l = (float)(d1 - (double)R.zy2h);
+    }
+}
+
 __global__ void __launch_bounds__(128) mr_hpf_seg(LaunchArgs a, SegRec* __restrict__ seg, int nseg_max, bool with_early)
 {
     const int64_t nch = (int64_t)a.B * a.S * a.M;
@@ -420,17 +553,8 @@ __global__ void __launch_bounds__(128) mr_hpf_seg(LaunchArgs a, SegRec* __restri
     float* x = (is_early ? a.mr_ye : a.mr_y) + ch.off;
     SegRec& R = seg[cidx * nseg_max + j];
     const HpfCoef c = hpf_coef((double)a.rl * a.fs);
-    float x1, x2;
-    f2 y1, y2;
-    if (PASS == 0) {
-        x1 = s0 >= 1 ? x[s0 - 1] : 0.f;
-        x2 = s0 >= 2 ? x[s0 - 2] : 0.f;
-        y1 = y2 = f2{0.f, 0.f};
-    } else {
-        x1 = R.x1; x2 = R.x2;
-        y1 = f2{R.sy1h, R.sy1l};
-        y2 = f2{R.sy2h, R.sy2l};
-    }
+    float x1 = R.x1, x2 = R.x2;
+    f2 y1{R.sy1h, R.sy1l}, y2{R.sy2h, R.sy2l};
     // Segments start on multiples of kMrSeg and rows on 16 bytes: whole float4s, then a tail.
     auto step = [&](float x0) {
         f2 uu = two_sum(x0, x2);
@@ -444,16 +568,9 @@ __global__ void __launch_bounds__(128) mr_hpf_seg(LaunchArgs a, SegRec* __restri
         float4 v = *reinterpret_cast<const float4*>(x + k);
         float4 o;
         o.x = step(v.x); o.y = step(v.y); o.z = step(v.z); o.w = step(v.w);
-        if (PASS == 1) *reinterpret_cast<float4*>(x + k) = o;
+        *reinterpret_cast<float4*>(x + k) = o;
     }
-    for (int64_t k = s4; k < s1; ++k) {
-        const float o = step(x[k]);
-        if (PASS == 1) x[k] = o;
-    }
-    if (PASS == 0) {
-        R.zy1h = y1.hi; R.zy1l = y1.lo;
-        R.zy2h = y2.hi; R.zy2l = y2.lo;
-    }
+    for (int64_t k = s4; k < s1; ++k) x[k] = step(x[k]);
 }
 
 __global__ void __launch_bounds__(128) mr_hpf_scan(LaunchArgs a, SegRec* __restrict__ seg, int nseg_max, bool with_early)
@@ -596,11 +713,14 @@ cudaError_t launch_synthesize_mr(const LaunchArgs& a, const float* pos_hi, const
     const int64_t chans = (int64_t)a.B * a.S * a.M * (early ? 2 : 1);
     SegRec* seg = reinterpret_cast<SegRec*>(a.mr_seg);
     const int64_t nt = chans * nseg_max;
-    mr_hpf_seg<0><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(a, seg, nseg_max, early != nullptr);
+    mr_hpf_tables<<<(kMrSeg + 2 + 255) / 256, 256, 0, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    mr_hpf_end<<<(unsigned)((nt + kHpfEndThreads / 32 - 1) / (kHpfEndThreads / 32)), kHpfEndThreads, 0, st>>>(
+        a, seg, nseg_max, early != nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     mr_hpf_scan<<<(unsigned)((chans + 127) / 128), 128, 0, st>>>(a, seg, nseg_max, early != nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    mr_hpf_seg<1><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(a, seg, nseg_max, early != nullptr);
+    mr_hpf_seg<<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(a, seg, nseg_max, early != nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // stage C
     switch (a.rl) {
