@@ -375,7 +375,7 @@ __device__ __forceinline__ void stage_g(float* Gs, const float* grad_rir, const 
 }
 
 template <int KT>
-__global__ void __launch_bounds__(kBwdThreads, 5) bwd_kernel(LaunchArgs a, const float* __restrict__ grad_rir,
+__global__ void __launch_bounds__(kBwdThreads, 4) bwd_kernel(LaunchArgs a, const float* __restrict__ grad_rir,
                                                              const float* __restrict__ grad_early,
                                                              float* __restrict__ grad_vs, float* __restrict__ grad_g)
 {
