@@ -14,7 +14,7 @@ synthesis and the adjoint runs in the library's CUDA kernels.
 from __future__ import annotations
 
 import ctypes
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 from typing import Optional
 
 import numpy as np
