@@ -207,7 +207,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RIRs/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload},
+            "config": {"workload": sc.name, "rooms": sc.B, "sources": sc.S, "mics": sc.M, "fs": sc.fs,
+                       "half_len": params.half_len, "rooms_per_step": per_step},
             "cpu_baseline": {"value": value, "unit": "RIRs/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "RIRs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
