@@ -27,9 +27,9 @@
 //                   segments of 2048 samples in parallel: each segment's zero-state end state as
 //                   a dot product with precomputed weights, a per-channel propagation of the true
 //                   segment start states, and the recursion writing the result in place.
-//   mr_down         the second resampler (ratio 1/r_l, compile-time taps), three consecutive output
-//                   samples per thread (each window value read once) from a window staged in
-//                   shared memory.
+//   mr_down         the second resampler (ratio 1/r_l, compile-time taps), four consecutive output
+//                   samples per thread (each window value read once, four per 16-byte load) from a
+//                   window staged in shared memory.
 #include <cmath>
 #include <utility>
 
@@ -612,7 +612,7 @@ __global__ void __launch_bounds__(128) mr_hpf_scan(LaunchArgs a, SegRec* __restr
 // ---- stage C: the resampler 1/RL, one thread per output sample ------------------------------
 // y[n] = sum_k z[k] F_C(n RL - k), k in [0, L_m); a block stages z over its outputs' window.
 constexpr int kMrOutT = 256;           // threads per block
-constexpr int kMrPer = 3;              // consecutive outputs per thread (3 RL window stride: odd for odd RL)
+constexpr int kMrPer = 4;              // consecutive outputs per thread: its window starts 16-byte aligned
 constexpr int kMrOut = kMrOutT * kMrPer;
 
 // Window value w[M] (M = 0 .. (kMrPer - 1) RL + 2 HLC) read once and added to every output j whose
@@ -629,24 +629,35 @@ __device__ __forceinline__ void fir_tap(float x, float* acc)
 }
 
 template <int RL, int M, int... J>
-__device__ __forceinline__ void fir_step(const float* __restrict__ w, float* acc, std::integer_sequence<int, J...>)
+__device__ __forceinline__ void fir_step(float x, float* acc, std::integer_sequence<int, J...>)
 {
-    const float x = w[M];
     (fir_tap<RL, M, J>(x, acc), ...);
 }
 
-template <int RL, int... Mi>
-__device__ __forceinline__ void fir_dot(const float* __restrict__ w, float* acc, std::integer_sequence<int, Mi...>)
+// Window values 4 C .. 4 C + 3, one 16-byte shared load.
+template <int RL, int C>
+__device__ __forceinline__ void fir_chunk(const float4* __restrict__ w4, float* acc)
 {
-    (fir_step<RL, Mi>(w, acc, std::make_integer_sequence<int, kMrPer>{}), ...);
+    const float4 v = w4[C];
+    fir_step<RL, 4 * C + 0>(v.x, acc, std::make_integer_sequence<int, kMrPer>{});
+    fir_step<RL, 4 * C + 1>(v.y, acc, std::make_integer_sequence<int, kMrPer>{});
+    fir_step<RL, 4 * C + 2>(v.z, acc, std::make_integer_sequence<int, kMrPer>{});
+    fir_step<RL, 4 * C + 3>(v.w, acc, std::make_integer_sequence<int, kMrPer>{});
+}
+
+template <int RL, int... C>
+__device__ __forceinline__ void fir_dot(const float4* __restrict__ w4, float* acc, std::integer_sequence<int, C...>)
+{
+    (fir_chunk<RL, C>(w4, acc), ...);
 }
 
 template <int RL>
 __global__ void __launch_bounds__(kMrOutT) mr_down(LaunchArgs a, float* __restrict__ rir, float* __restrict__ early)
 {
     constexpr int HLC = 10 * RL;
-    constexpr int W = kMrOut * RL + 2 * HLC;
-    __shared__ float zw[W];
+    constexpr int NW = (kMrPer - 1) * RL + 2 * HLC + 1;          // window values one thread reads
+    constexpr int W = ((kMrOut * RL + 2 * HLC + 4) + 3) & ~3;     // staged window, whole float4s
+    __shared__ __align__(16) float zw[W];
     const int64_t nch = (int64_t)a.B * a.S * a.M;
     const int64_t cidx = blockIdx.x;
     const bool is_early = cidx >= nch;
@@ -665,13 +676,14 @@ __global__ void __launch_bounds__(kMrOutT) mr_down(LaunchArgs a, float* __restri
         zw[i] = (k >= 0 && k < ch.Lm) ? z[k] : 0.f;
     }
     __syncthreads();
+    static_assert((kMrPer * RL) % 4 == 0, "each thread's window starts on a float4");
     // outputs n = n0 + kMrPer t + j: taps k = n RL - HLC .. n RL + HLC, i.e. window offsets
     // (kMrPer t + j) RL + i, i in [0, 2 HLC]
     float acc[kMrPer];
 #pragma unroll
     for (int j = 0; j < kMrPer; ++j) acc[j] = 0.f;
-    fir_dot<RL>(zw + threadIdx.x * kMrPer * RL, acc,
-                std::make_integer_sequence<int, (kMrPer - 1) * RL + 2 * HLC + 1>{});
+    fir_dot<RL>(reinterpret_cast<const float4*>(zw + threadIdx.x * kMrPer * RL), acc,
+                std::make_integer_sequence<int, (NW + 3) / 4>{});
     float* y = (is_early ? early : rir) + rc.rir_off + ((int64_t)s * a.M + m) * L;
 #pragma unroll
     for (int j = 0; j < kMrPer; ++j) {
