@@ -114,19 +114,18 @@ __device__ __forceinline__ ArrB arrival_bwd(int& nc, float delta, float invK, bo
 {
     ArrB r;
     if (fabsf(delta) < kTinyDelta) delta = kTinyDelta;
-    const float sd = sinpi_poly(delta), cd = cospi_poly(delta);   // at the original delta
-    float su = sd, cu = cd;
     r.shifted = delta > kShiftMin;
     if (r.shifted) {
         const float d1 = __fsub_rn(delta, 1.0f);
         delta = __fadd_rn(d1, 1.0f);                              // the delta the taps use
-        const float s1 = sinpi_poly(delta), c1 = cospi_poly(delta);
-        su = -s1; cu = -c1;
         r.d = d1;
         nc += 1;
     } else {
         r.d = delta;
     }
+    // sin, cos (pi delta) at the delta the taps use (the re-based one negates both)
+    const float sdl = sinpi_poly(delta), cdl = cospi_poly(delta);
+    const float su = r.shifted ? -sdl : sdl, cu = r.shifted ? -cdl : cdl;
     const float piK = kPi * invK;
     float cy, sy, cn, sn;
     if (exact_trig) {
@@ -134,7 +133,11 @@ __device__ __forceinline__ ArrB arrival_bwd(int& nc, float delta, float invK, bo
         sincospif(delta * invK, &sn, &cn);
     } else {
         cy = cospi_poly(r.d * invK); sy = sinpi_poly(r.d * invK);
-        cn = cospi_poly(delta * invK); sn = sinpi_poly(delta * invK);
+        if (r.shifted) {                                          // r.d != delta only when re-based
+            cn = cospi_poly(delta * invK); sn = sinpi_poly(delta * invK);
+        } else {
+            cn = cy; sn = sy;
+        }
     }
     r.P = su * kTwoPiInv;
     r.Pp = 0.5f * cu;
@@ -144,7 +147,7 @@ __device__ __forceinline__ ArrB arrival_bwd(int& nc, float delta, float invK, bo
     r.bp = __fmaf_rn(r.Pp, sy, r.P * piK * cy);
     // Nearest tap: x = n - t = -delta (delta of the original split), tap = sinc(x) w(x), both
     // even, so dtap/dt = sinc'(delta) w(delta) + sinc(delta) w'(delta).
-    const float sinc = (r.shifted ? sinpi_poly(delta) : sd) * kInvPi / delta;
+    const float sinc = sdl * kInvPi / delta;
     const float w = 0.5f * (1.0f + cn);
     const float wp = -0.5f * piK * sn;
     r.dnear = __fmaf_rn(dsinc_small(delta), w, sinc * wp);
