@@ -207,6 +207,7 @@ static LaunchArgs make_args(const fram_scene* sc, const fram_params* p, const Ws
     a.src_tile = reinterpret_cast<int32_t*>(base + w.src_tile);
     a.item_off = reinterpret_cast<int32_t*>(base + w.item_off);
     a.items = reinterpret_cast<int2*>(base + w.items);
+    a.order = reinterpret_cast<int32_t*>(base + w.order);
     a.bin_off = reinterpret_cast<int32_t*>(base + w.bin_off);
     a.perm = reinterpret_cast<int32_t*>(base + w.perm);
     a.key = reinterpret_cast<float*>(base + w.key);

@@ -405,12 +405,13 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_kernel(LaunchArgs a, const
     const bool exact_trig = K < 2;
     const float qf = a.q;
     const int n_items = a.hdr->n_items;
-    int qi = 0;
-    if (lane == 0) qi = atomicAdd(&a.hdr->queue_bwd, 1);
-    qi = __shfl_sync(0xffffffffu, qi, 0);
-    while (qi < n_items) {
+    int qt = 0;
+    if (lane == 0) qt = atomicAdd(&a.hdr->queue_bwd, 1);
+    qt = __shfl_sync(0xffffffffu, qt, 0);
+    while (qt < n_items) {
         int nxt = 0;
         if (lane == 0) nxt = atomicAdd(&a.hdr->queue_bwd, 1);
+        const int qi = a.order[qt];           // heaviest items first; partials stay per item
         const int2 it = a.items[qi];
         const int b = it.x, s = it.y >> 16, tau = it.y & 0xffff;
         const RoomConst rc = a.room[b];
@@ -580,8 +581,51 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_kernel(LaunchArgs a, const
             a.part_src[3 * (int64_t)qi + 1] = dsy;
             a.part_src[3 * (int64_t)qi + 2] = dsz;
         }
-        qi = __shfl_sync(0xffffffffu, nxt, 0);
+        qt = __shfl_sync(0xffffffffu, nxt, 0);
     }
+}
+
+// The adjoint's work order: items by decreasing cost (owned images), so the last items a
+// persistent warp takes are short ones.  One CTA: histogram of cost buckets, exclusive scan from
+// the heaviest bucket down, scatter.  The order only decides which warp takes which item when;
+// every item writes its own partials, reduced later in item order, so results do not depend on it.
+constexpr int kOrderBuckets = 1024;
+
+__global__ void __launch_bounds__(1024) bwd_order(LaunchArgs a)
+{
+    __shared__ int cnt[kOrderBuckets];
+    __shared__ int warp_tot[32];
+    const int n = a.hdr->n_items;
+    for (int k = threadIdx.x; k < kOrderBuckets; k += blockDim.x) cnt[k] = 0;
+    __syncthreads();
+    auto bucket = [&](int qi) {
+        const int2 it = a.items[qi];
+        const int b = it.x, s = it.y >> 16, tau = it.y & 0xffff;
+        const int* bo = a.bin_off + ((int64_t)b * a.S + s) * (a.max_tiles + 1);
+        const int cost = bo[tau + 1] - bo[tau];
+        return kOrderBuckets - 1 - min(cost >> 3, kOrderBuckets - 1);   // heavy -> low bucket
+    };
+    for (int qi = threadIdx.x; qi < n; qi += blockDim.x) atomicAdd(&cnt[bucket(qi)], 1);
+    __syncthreads();
+    // exclusive scan of cnt (one value per thread: blockDim == kOrderBuckets)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int v = cnt[threadIdx.x];
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int k = 0; k < 32; ++k) { const int t = warp_tot[k]; warp_tot[k] = run; run += t; }
+    }
+    __syncthreads();
+    cnt[threadIdx.x] = warp_tot[w] + x - v;
+    __syncthreads();
+    for (int qi = threadIdx.x; qi < n; qi += blockDim.x) a.order[atomicAdd(&cnt[bucket(qi)], 1)] = qi;
 }
 
 // Per-room reductions of the item partials, in item order.
@@ -645,6 +689,8 @@ cudaError_t launch_backward(const LaunchArgs& a, const float* pos_hi, const floa
         g_gather<<<(unsigned)segs, 256, 0, st>>>(a, g);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    bwd_order<<<1, kOrderBuckets, 0, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (a.K == 40) e = launch_bwd_t<40>(a, grad_rir, grad_early, grad_vs, grad_g, st);
     else if (a.K == 63) e = launch_bwd_t<63>(a, grad_rir, grad_early, grad_vs, grad_g, st);
     else e = launch_bwd_t<0>(a, grad_rir, grad_early, grad_vs, grad_g, st);

@@ -233,7 +233,7 @@ struct Header {             // first 256 bytes of the workspace
 constexpr int kSampleRec = 256;   // bytes per (room, source) record of the sampler's constants
 
 struct WsLayout {
-    size_t header, room, direct, src_tile, item_off, items, bin_off, perm, key, skey, sconst;
+    size_t header, room, direct, src_tile, item_off, items, order, bin_off, perm, key, skey, sconst;
     size_t spa, spb, pos32, samp, irec;
     size_t mr_y, mr_ye, mr_tab, mr_seg, mr_hk;   // multi-rate mode: intermediate signals, resampling
                                           // table, high-pass segment records
@@ -280,6 +280,7 @@ inline WsLayout ws_layout(const fram_scene& sc, int tile, int delay_mode = 0, do
     w.src_tile = take(sizeof(int32_t) * (size_t)sc.B * sc.S);
     w.item_off = take(sizeof(int32_t) * ((size_t)sc.B + 1));
     w.items = take(sizeof(int32_t) * 2 * (size_t)w.max_items);
+    w.order = take(sizeof(int32_t) * (size_t)w.max_items);
     w.bin_off = take(sizeof(int32_t) * (size_t)sc.B * sc.S * (w.max_tiles + 1));
     w.perm = take(sizeof(int32_t) * (size_t)sc.n_vs_total);
     w.key = take(sizeof(float) * (size_t)sc.n_vs_total);
@@ -339,6 +340,7 @@ struct LaunchArgs {
     int32_t* src_tile;
     int32_t* item_off;
     int2* items;
+    int32_t* order;         // adjoint work order: item indices by decreasing cost
     int32_t* bin_off;
     int32_t* perm;          // per (room, source): image indices sorted by 32-sample key block
     float* key;             // per image: delay to the array centre in samples (binning key)
