@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 import torch
 
-from paper_2304_08052_gb300 import api, scenes
+from paper_2304_08052_gb300 import _lib, api, scenes
 
 pytestmark = pytest.mark.gpu
 
@@ -245,6 +245,31 @@ def test_bad_geometry_sets_status():
     api.sample(ds, seed=1)
     torch.cuda.synchronize()
     assert ds.status() & 0x1
+
+
+def test_nonfinite_image_sets_status_and_is_skipped(oracle_mod):
+    # A NaN image position: the binning flags FRAM_DEV_NONFINITE and the image contributes
+    # nothing; every other arrival is rendered as usual.  The oracle drops the image by giving it
+    # a reflection count so large that r^g underflows to 0.
+    sc = scenes.tiny(seed=3, B=2, S=1, M=2, images=30)
+    ds = api.DeviceScene(sc, _params(sc))
+    op = _oparams(oracle_mod, sc)
+    ref = oracle_mod.sample(sc, op, 5)
+    pos, g, r = ref.pos.astype(np.float32), ref.g.astype(np.float32), ref.r.astype(np.float32)
+    bad = int(ds.vs_off[1]) + 7
+    pos_bad = pos.copy()
+    pos_bad[bad] = np.nan
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    h = api.synthesize_raw(ds, dev(pos_bad), None, dev(g), dev(r))
+    torch.cuda.synchronize()
+    assert ds.status() & _lib.FRAM_DEV_NONFINITE
+    got = h.cpu().numpy()
+    assert np.isfinite(got).all()
+    g_drop = g.astype(np.float64)
+    g_drop[bad] = 1.0e6
+    h_ref = oracle_mod.synthesize(sc, op, pos.astype(np.float64), g_drop, r.astype(np.float64))
+    e = _rir_errors(sc, ds.rir_len, (ds.rir_off, ds.rir_off), got, h_ref, range(sc.B), range(sc.B))
+    assert e.max() < TOL
 
 
 # ------------------------------------------------------------------------------------------
