@@ -117,3 +117,36 @@ def test_multirate_tiles_and_ragged_ends(oracle_mod):
         torch.cuda.synchronize()
         assert ds.status() == 0
         assert _errors(sc, ds, h.cpu().numpy().astype(np.float64), h_ref).max() <= TOL
+
+
+@pytest.mark.gpu
+def test_multirate_full_training_batch_on_sampled_rooms(oracle_mod):
+    # The benchmark's configuration: batch_1024 (1024 rooms x 3 sources x 8 mics, 16 kHz) with early
+    # RIRs in one launch.  The oracle draws every room's images (FP64), both sides get them rounded
+    # to float pairs, and 6 rooms (including the longest and shortest) are compared.
+    import torch
+    sc = scenes.batch_1024(0)
+    op = oracle_mod.Params(fs=sc.fs, half_len=sc.half_len)
+    ref = oracle_mod.sample(sc, op, 41)
+    hi, lo, pos_q = _pair_exact(ref.pos)
+    g32, r32 = ref.g.astype(np.float32), ref.r.astype(np.float32)
+    ds = api.DeviceScene(sc, api.Params(fs=sc.fs, half_len=sc.half_len, delay_mode=1))
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    h, he = api.synthesize_raw(ds, dev(hi), dev(lo), dev(g32), dev(r32), early=True)
+    torch.cuda.synchronize()
+    assert ds.status() == 0
+    rooms = [int(np.argmax(sc.rt60)), int(np.argmin(sc.rt60)), 0, 333, 700, 1023]
+    sub = sc.subset(rooms)
+    rows = np.concatenate([np.arange(int(ds.vs_off[b]), int(ds.vs_off[b + 1])) for b in rooms])
+    h_ref, he_ref = oracle_mod.synthesize_mr(sub, op, pos_q[rows], g32[rows].astype(np.float64),
+                                             r32[rooms].astype(np.float64), early=True)
+    rl, ro, _ = oracle_mod.layout(sub.rt60, sub.n_vs, sub.S, sub.M, sub.fs)
+    hg, heg = h.cpu().numpy(), he.cpu().numpy()
+    for i, b in enumerate(rooms):
+        o, n = int(ds.rir_off[b]), int(ds.rir_off[b + 1] - ds.rir_off[b])
+        L = int(ds.rir_len[b])
+        for s in range(sc.S):
+            seg_g = slice(o + s * sc.M * L, o + (s + 1) * sc.M * L)
+            seg_r = slice(int(ro[i]) + s * sc.M * L, int(ro[i]) + (s + 1) * sc.M * L)
+            for got, want in ((hg[seg_g], h_ref[seg_r]), (heg[seg_g], he_ref[seg_r])):
+                assert np.abs(got.astype(np.float64) - want).max() <= TOL * np.abs(want).max(), (b, s)
