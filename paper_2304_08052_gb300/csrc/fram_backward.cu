@@ -162,37 +162,112 @@ __device__ __forceinline__ ArrB arrival_bwd(int& nc, float delta, float invK, bo
 // (o = -1, 0), one of which holds the tap nearest to t, stay out of U and V and are added
 // directly (the nearest one with its Taylor-series derivative).  Compile-time K: every per-slot
 // constant is a literal operand.
+//
+// Slots go in pairs (J even, J + 1), the pair's values in the two halves of packed FP32
+// registers: the constant-free products G r and G r^2 and the sums of U0 and V0 use
+// mul/add.rn.f32x2 (two independent IEEE operations per instruction, each half rounded as the
+// scalar operation would be), the products with the per-slot literals stay scalar.  Each
+// accumulator keeps an even-slot and an odd-slot partial sum; V sums are taken without sigma,
+// which is constant within each half (the slot parity fixes the sign of o) and enters when the
+// halves are added.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pack2(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(f32x2 v, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 struct TapAcc {
     float u0, u1, u2, v0, v1, v2;
 };
+// Packed partial sums: low half even slots, high half odd slots; u1/u2/v1/v2 as scalars per half.
+struct TapAccP {
+    f32x2 u0, v0;
+    float u1e, u1o, u2e, u2o, v1e, v1o, v2e, v2o;
+};
 
 template <int KT, int J>
-__device__ __forceinline__ void tap_slot(const float* __restrict__ Gs, float d, TapAcc& q)
+__device__ __forceinline__ void tap_half(const float* __restrict__ Gs, float d, float& u0, float& u1, float& u2,
+                                         float& v0, float& v1, float& v2)
 {
     constexpr int o = J - KT;
-    if constexpr (o != 0 && o != -1) {
-        constexpr float sg = (o & 1) ? -1.0f : 1.0f;
-        constexpr float C = kTrig<KT>.c[J];
-        constexpr float S = kTrig<KT>.s[J];
-        constexpr float kp = -sg * (float)o;
-        const float e = __fmaf_rn(sg, d, kp);
-        const float rc = rcp_approx(e);
-        const float y = Gs[J] * rc;
-        q.u0 += y;
-        q.u1 = __fmaf_rn(C, y, q.u1);
-        q.u2 = __fmaf_rn(S, y, q.u2);
-        const float z = y * rc;
-        q.v0 = __fmaf_rn(sg, z, q.v0);
-        q.v1 = __fmaf_rn(sg * C, z, q.v1);
-        q.v2 = __fmaf_rn(sg * S, z, q.v2);
+    constexpr float sg = (o & 1) ? -1.0f : 1.0f;
+    constexpr float C = kTrig<KT>.c[J];
+    constexpr float S = kTrig<KT>.s[J];
+    constexpr float kp = -sg * (float)o;
+    const float rc = rcp_approx(__fmaf_rn(sg, d, kp));
+    const float y = __fmul_rn(Gs[J], rc);
+    u0 = __fadd_rn(u0, y);
+    u1 = __fmaf_rn(C, y, u1);
+    u2 = __fmaf_rn(S, y, u2);
+    const float z = __fmul_rn(y, rc);
+    v0 = __fadd_rn(v0, z);
+    v1 = __fmaf_rn(C, z, v1);
+    v2 = __fmaf_rn(S, z, v2);
+}
+
+template <int KT, int J>
+__device__ __forceinline__ void tap_pair(const float* __restrict__ Gs, float d, TapAccP& q)
+{
+    constexpr int o0 = J - KT, o1 = J + 1 - KT;
+    constexpr bool c0 = o0 == 0 || o0 == -1, c1 = o1 == 0 || o1 == -1;
+    if constexpr (!c0 && !c1) {
+        constexpr float sg0 = (o0 & 1) ? -1.0f : 1.0f, sg1 = -sg0;
+        constexpr float C0 = kTrig<KT>.c[J], C1 = kTrig<KT>.c[J + 1];
+        constexpr float S0 = kTrig<KT>.s[J], S1 = kTrig<KT>.s[J + 1];
+        const f32x2 rc = pack2(rcp_approx(__fmaf_rn(sg0, d, -sg0 * (float)o0)),
+                               rcp_approx(__fmaf_rn(sg1, d, -sg1 * (float)o1)));
+        const f32x2 y = mul2(pack2(Gs[J], Gs[J + 1]), rc);
+        q.u0 = add2(q.u0, y);
+        float y0, y1;
+        unpack2(y, y0, y1);
+        q.u1e = __fmaf_rn(C0, y0, q.u1e);
+        q.u1o = __fmaf_rn(C1, y1, q.u1o);
+        q.u2e = __fmaf_rn(S0, y0, q.u2e);
+        q.u2o = __fmaf_rn(S1, y1, q.u2o);
+        const f32x2 z = mul2(y, rc);
+        q.v0 = add2(q.v0, z);
+        float z0, z1;
+        unpack2(z, z0, z1);
+        q.v1e = __fmaf_rn(C0, z0, q.v1e);
+        q.v1o = __fmaf_rn(C1, z1, q.v1o);
+        q.v2e = __fmaf_rn(S0, z0, q.v2e);
+        q.v2o = __fmaf_rn(S1, z1, q.v2o);
+    } else if constexpr (!c0 || !c1) {
+        // one central slot in the pair: the other one alone, into its own half
+        float u0e, u0o, v0e, v0o;
+        unpack2(q.u0, u0e, u0o);
+        unpack2(q.v0, v0e, v0o);
+        if constexpr (!c0) tap_half<KT, J>(Gs, d, u0e, q.u1e, q.u2e, v0e, q.v1e, q.v2e);
+        else tap_half<KT, J + 1>(Gs, d, u0o, q.u1o, q.u2o, v0o, q.v1o, q.v2o);
+        q.u0 = pack2(u0e, u0o);
+        q.v0 = pack2(v0e, v0o);
     }
 }
 
-template <int KT, int... J>
-__device__ __forceinline__ void tap_slots(const float* __restrict__ Gs, float d, TapAcc& q,
-                                          std::integer_sequence<int, J...>)
+template <int KT, int... P>
+__device__ __forceinline__ void tap_pairs(const float* __restrict__ Gs, float d, TapAccP& q,
+                                          std::integer_sequence<int, P...>)
 {
-    (tap_slot<KT, J>(Gs, d, q), ...);
+    (tap_pair<KT, 2 * P>(Gs, d, q), ...);
 }
 
 // One central slot o in {-1, 0}: value and derivative added directly.
@@ -213,8 +288,20 @@ __device__ __forceinline__ void central_slot(float G, int o, float C, float S, c
 template <int KT>
 __device__ __forceinline__ void gather_taps_ct(const float* __restrict__ Gs, const ArrB& r, float& S1, float& S2)
 {
-    TapAcc q{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    tap_slots<KT>(Gs, r.d, q, std::make_integer_sequence<int, 2 * KT>{});
+    TapAccP p{0ull, 0ull, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    tap_pairs<KT>(Gs, r.d, p, std::make_integer_sequence<int, KT>{});
+    // sigma of the even slots (o = J - K with J even) and of the odd ones
+    constexpr float sge = (KT & 1) ? -1.0f : 1.0f;
+    float u0e, u0o, v0e, v0o;
+    unpack2(p.u0, u0e, u0o);
+    unpack2(p.v0, v0e, v0o);
+    TapAcc q;
+    q.u0 = u0e + u0o;
+    q.u1 = p.u1e + p.u1o;
+    q.u2 = p.u2e + p.u2o;
+    q.v0 = sge * (v0e - v0o);
+    q.v1 = sge * (p.v1e - p.v1o);
+    q.v2 = sge * (p.v2e - p.v2o);
     S1 = __fmaf_rn(r.P, q.u0, __fmaf_rn(r.a, q.u1, r.b * q.u2));
     S2 = __fmaf_rn(r.Pp, q.u0, __fmaf_rn(r.ap, q.u1, r.bp * q.u2))
          - __fmaf_rn(r.P, q.v0, __fmaf_rn(r.a, q.v1, r.b * q.v2));
@@ -244,14 +331,6 @@ __device__ __forceinline__ void gather_taps_rt(const float* __restrict__ Gs, int
     }
     S1 = s1;
     S2 = s2;
-}
-
-template <int KT>
-__device__ __forceinline__ void gather_taps(const float* __restrict__ Gs, int K, const ArrB& r,
-                                            const float2* __restrict__ tab, float& S1, float& S2)
-{
-    if constexpr (KT > 0) gather_taps_ct<KT>(Gs, r, S1, S2);
-    else gather_taps_rt(Gs, K, r, tab, S1, S2);
 }
 
 // Per-warp shared memory (floats): two staging buffers of the upstream gradient (each covers a
@@ -318,6 +397,15 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool val
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// One round of a pass: one arrival per lane (an image of chunk ch, or the direct path), with
+// what the chain rule needs after the tap gather.
+struct BwdRound {
+    bool go, is_dir;
+    int j0;                 // staged-gradient index of the arrival's slot 0
+    float A, invD, ex, ey, ez, gg;
+    ArrB r;
+};
 
 // One pass of an item: sorted positions [p0, p1) (at most 32 kBwdChunks images whose key blocks
 // start less than bwd_span samples apart); the gradient is staged over [gb, gb + gl).
@@ -469,23 +557,29 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_kernel(LaunchArgs a, const
                     // staged span covers its taps.  One call site of the tap loop serves both.
                     const bool want_direct = lane == 0 && !((dmask >> m) & 1ull);
                     const int nround = nch + (__any_sync(0xffffffffu, want_direct) ? 1 : 0);
-                    for (int ch = 0; ch < nround; ++ch) {
-                        const bool is_dir = ch == nch;
+                    // Round ch: its arrival, ready for the tap gather (go), or nothing to gather.
+                    auto setup = [&](int ch) {
+                        BwdRound R;
+                        R.go = false;
+                        R.is_dir = ch == nch;
+                        R.j0 = 0;
+                        R.A = R.invD = R.ex = R.ey = R.ez = R.gg = 0.f;
+                        if (ch >= nround) return R;
                         bool act;
                         int nc = 0;
-                        float delta = 0.f, A = 0.f, invD = 0.f, ex = 0.f, ey = 0.f, ez = 0.f, gg = 0.f;
-                        if (!is_dir) {
+                        float delta = 0.f;
+                        if (!R.is_dir) {
                             const int slot = P.p0 + 32 * ch + lane;
                             act = slot < P.p1;
                             if (act) {
                                 const float4 pa = a.spa[v0 + slot];
                                 const float2 pb = a.spb[v0 + slot];
-                                gg = a.samp[v0 + slot];
+                                R.gg = a.samp[v0 + slot];
                                 float D, ux, uy, uz;
                                 image_geom(pa, pb, mx, my, mz, a.q2, nc, delta, D, ux, uy, uz);
-                                invD = rcp_approx(D);
-                                A = exp2f(gg * rc.log2r) * invD;
-                                ex = ux * invD; ey = uy * invD; ez = uz * invD;
+                                R.invD = rcp_approx(D);
+                                R.A = exp2f(R.gg * rc.log2r) * R.invD;
+                                R.ex = ux * R.invD; R.ey = uy * R.invD; R.ez = uz * R.invD;
                                 act = D > 0.0f;
                             }
                         } else {
@@ -494,42 +588,57 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_kernel(LaunchArgs a, const
                                 const DirectConst dc = dcs[m];
                                 nc = __float2int_rn(dc.t_hi);
                                 delta = __fadd_rn(__fsub_rn(dc.t_hi, (float)nc), dc.t_lo);
-                                A = dc.amp;
-                                invD = dc.amp;
-                                ex = dc.ex; ey = dc.ey; ez = dc.ez;
+                                R.A = dc.amp;
+                                R.invD = dc.amp;
+                                R.ex = dc.ex; R.ey = dc.ey; R.ez = dc.ez;
                             }
                         }
                         if (act && (nc + K < 0 || nc - K >= Lb)) {      // no tap inside the RIR
                             act = false;
-                            if (is_dir) dmask |= 1ull << m;
+                            if (R.is_dir) dmask |= 1ull << m;
                         }
                         if (act) {
                             const ArrB r = arrival_bwd(nc, delta, invK, exact_trig);
                             const int j0 = nc - K - P.gb;
                             if (j0 >= 0 && j0 + 2 * K <= P.gl) {
-                                float S1, S2;
-                                gather_taps<KT>(Gs + j0, K, r, tab, S1, S2);
-                                const float dLdD = __fmaf_rn(A * S2, qf, -S1 * A * invD);
-                                mpx = __fmaf_rn(-dLdD, ex, mpx);
-                                mpy = __fmaf_rn(-dLdD, ey, mpy);
-                                mpz = __fmaf_rn(-dLdD, ez, mpz);
-                                if (!is_dir) {
-                                    float* g3 = gv + ch * 96 + lane;
-                                    g3[0] = __fmaf_rn(dLdD, ex, g3[0]);
-                                    g3[32] = __fmaf_rn(dLdD, ey, g3[32]);
-                                    g3[64] = __fmaf_rn(dLdD, ez, g3[64]);
-                                    rpart = __fmaf_rn(S1 * A * gg, rc.inv_r, rpart);
-                                    if (with_g) gq[ch * 32 + lane] = __fmaf_rn(S1, A, gq[ch * 32 + lane]);
-                                } else {
-                                    dsx = __fmaf_rn(dLdD, ex, dsx);
-                                    dsy = __fmaf_rn(dLdD, ey, dsy);
-                                    dsz = __fmaf_rn(dLdD, ez, dsz);
-                                    dmask |= 1ull << m;
-                                }
-                            } else if (!is_dir || direct_only) {
+                                R.go = true;
+                                R.j0 = j0;
+                                R.r = r;
+                            } else if (!R.is_dir || direct_only) {
                                 atomicOr(&a.hdr->status, FRAM_DEV_CAPACITY);
-                                if (is_dir) dmask |= 1ull << m;
+                                if (R.is_dir) dmask |= 1ull << m;
                             }
+                        }
+                        return R;
+                    };
+                    // The chain rule of round ch from its tap sums.
+                    auto finish = [&](const BwdRound& R, int ch, float S1, float S2) {
+                        const float A = R.A;
+                        const float dLdD = __fmaf_rn(A * S2, qf, -S1 * A * R.invD);
+                        mpx = __fmaf_rn(-dLdD, R.ex, mpx);
+                        mpy = __fmaf_rn(-dLdD, R.ey, mpy);
+                        mpz = __fmaf_rn(-dLdD, R.ez, mpz);
+                        if (!R.is_dir) {
+                            float* g3 = gv + ch * 96 + lane;
+                            g3[0] = __fmaf_rn(dLdD, R.ex, g3[0]);
+                            g3[32] = __fmaf_rn(dLdD, R.ey, g3[32]);
+                            g3[64] = __fmaf_rn(dLdD, R.ez, g3[64]);
+                            rpart = __fmaf_rn(S1 * A * R.gg, rc.inv_r, rpart);
+                            if (with_g) gq[ch * 32 + lane] = __fmaf_rn(S1, A, gq[ch * 32 + lane]);
+                        } else {
+                            dsx = __fmaf_rn(dLdD, R.ex, dsx);
+                            dsy = __fmaf_rn(dLdD, R.ey, dsy);
+                            dsz = __fmaf_rn(dLdD, R.ez, dsz);
+                            dmask |= 1ull << m;
+                        }
+                    };
+                    for (int ch = 0; ch < nround; ++ch) {
+                        const BwdRound R = setup(ch);
+                        if (R.go) {
+                            float S1, S2;
+                            if constexpr (KT > 0) gather_taps_ct<KT>(Gs + R.j0, R.r, S1, S2);
+                            else gather_taps_rt(Gs + R.j0, K, R.r, tab, S1, S2);
+                            finish(R, ch, S1, S2);
                         }
                     }
                     mpx = warp_sum(mpx); mpy = warp_sum(mpy); mpz = warp_sum(mpz);
