@@ -403,16 +403,41 @@ __device__ __forceinline__ float4 arrival_record(int& nc, float delta, float A, 
 // Per-lane constants of the tap slots j = lane + 32 k (k < NR rounds), tap offset o = j - K:
 // C = cos(pi o / K), S = sin(pi o / K), sg = (-1)^o, kp = -sg o, so that the tap at base + o is
 // (P + a C + b S) / fma(sg, delta, kp).  Slots j >= 2K get kp = +inf: their reciprocal is 0 and
-// their read-modify-write leaves the buffer unchanged.
+// their read-modify-write leaves the buffer unchanged.  Rounds go in pairs (k, k + 1) through
+// packed FP32 (fma.rn.f32x2: two independent IEEE fused multiply-adds, each half rounded exactly
+// as __fmaf_rn), so the constants of a pair sit in one 64-bit register pair; an odd last round
+// stays scalar.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pack2(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(f32x2 v, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 template <int NR>
 struct TapLanes {
-    float C[NR], S[NR], sg[NR], kp[NR];
+    static constexpr int NP = NR / 2 > 0 ? NR / 2 : 1;    // (one unused pair when NR = 1)
+    f32x2 C[NP], S[NP], sg[NP], kp[NP];                   // rounds (2i, 2i + 1)
+    float Cl, Sl, sgl, kpl;                                // round NR - 1 when NR is odd
 };
 
 template <int NR>
 __device__ __forceinline__ void init_tap_lanes(TapLanes<NR>& L, int lane, int K)
 {
     const float invK = 1.0f / (float)K;
+    float C[NR], S[NR], sg[NR], kp[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
         const int j = lane + 32 * k;
@@ -420,10 +445,53 @@ __device__ __forceinline__ void init_tap_lanes(TapLanes<NR>& L, int lane, int K)
         float sn, cs;
         sincospif((float)o * invK, &sn, &cs);
         const bool ok = j < 2 * K;
-        L.C[k] = ok ? cs : 0.0f;
-        L.S[k] = ok ? sn : 0.0f;
-        L.sg[k] = ok ? ((o & 1) ? -1.0f : 1.0f) : 0.0f;
-        L.kp[k] = ok ? -L.sg[k] * (float)o : __int_as_float(0x7f800000);
+        C[k] = ok ? cs : 0.0f;
+        S[k] = ok ? sn : 0.0f;
+        sg[k] = ok ? ((o & 1) ? -1.0f : 1.0f) : 0.0f;
+        kp[k] = ok ? -sg[k] * (float)o : __int_as_float(0x7f800000);
+    }
+#pragma unroll
+    for (int i = 0; i < NR / 2; ++i) {
+        L.C[i] = pack2(C[2 * i], C[2 * i + 1]);
+        L.S[i] = pack2(S[2 * i], S[2 * i + 1]);
+        L.sg[i] = pack2(sg[2 * i], sg[2 * i + 1]);
+        L.kp[i] = pack2(kp[2 * i], kp[2 * i + 1]);
+    }
+    L.Cl = C[NR - 1];
+    L.Sl = S[NR - 1];
+    L.sgl = sg[NR - 1];
+    L.kpl = kp[NR - 1];
+}
+
+// An arrival record with each field duplicated into both halves of a packed pair.
+struct Rec2 {
+    f32x2 x, y, z, w;
+};
+__device__ __forceinline__ Rec2 splat_rec(float4 r)
+{
+    return Rec2{pack2(r.x, r.x), pack2(r.y, r.y), pack2(r.z, r.z), pack2(r.w, r.w)};
+}
+
+// The constants of round k (k a compile-time index after unrolling).
+template <int NR>
+__device__ __forceinline__ void lane_consts(const TapLanes<NR>& L, int k, float& C, float& S, float& sg, float& kp)
+{
+    if (k < 2 * (NR / 2)) {
+        float c0, c1, s0, s1, g0, g1, p0, p1;
+        unpack2(L.C[k >> 1], c0, c1);
+        unpack2(L.S[k >> 1], s0, s1);
+        unpack2(L.sg[k >> 1], g0, g1);
+        unpack2(L.kp[k >> 1], p0, p1);
+        const bool hi = k & 1;
+        C = hi ? c1 : c0;
+        S = hi ? s1 : s0;
+        sg = hi ? g1 : g0;
+        kp = hi ? p1 : p0;
+    } else {
+        C = L.Cl;
+        S = L.Sl;
+        sg = L.sgl;
+        kp = L.kpl;
     }
 }
 
@@ -437,11 +505,21 @@ __device__ __forceinline__ void add_arrival_inner(char* __restrict__ smem, const
                                                   int lane4)
 {
     float* dst = reinterpret_cast<float*>(smem + (rb + lane4));
+    const Rec2 r2 = splat_rec(r);
 #pragma unroll
-    for (int k = 0; k < NR; ++k) {
-        const float e = __fmaf_rn(L.sg[k], r.x, L.kp[k]);
-        const float num = __fmaf_rn(L.C[k], r.z, __fmaf_rn(L.S[k], r.w, r.y));
-        dst[32 * k] = __fmaf_rn(num, rcp_approx(e), dst[32 * k]);
+    for (int i = 0; i < NR / 2; ++i) {
+        float e0, e1;
+        unpack2(fma2(L.sg[i], r2.x, L.kp[i]), e0, e1);
+        const f32x2 num = fma2(L.C[i], r2.z, fma2(L.S[i], r2.w, r2.y));
+        float a0, a1;
+        unpack2(fma2(num, pack2(rcp_approx(e0), rcp_approx(e1)), pack2(dst[64 * i], dst[64 * i + 32])), a0, a1);
+        dst[64 * i] = a0;
+        dst[64 * i + 32] = a1;
+    }
+    if constexpr ((NR & 1) != 0) {
+        const float e = __fmaf_rn(L.sgl, r.x, L.kpl);
+        const float num = __fmaf_rn(L.Cl, r.z, __fmaf_rn(L.Sl, r.w, r.y));
+        dst[32 * (NR - 1)] = __fmaf_rn(num, rcp_approx(e), dst[32 * (NR - 1)]);
     }
 }
 
@@ -453,8 +531,10 @@ __device__ __forceinline__ void add_arrival_edge(char* __restrict__ smem, const 
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
         if (s0 + 32 * k > -32 && s0 + 32 * k < T) {
-            const float e = __fmaf_rn(L.sg[k], r.x, L.kp[k]);
-            const float num = __fmaf_rn(L.C[k], r.z, __fmaf_rn(L.S[k], r.w, r.y));
+            float C, S, sg, kp;
+            lane_consts<NR>(L, k, C, S, sg, kp);
+            const float e = __fmaf_rn(sg, r.x, kp);
+            const float num = __fmaf_rn(C, r.z, __fmaf_rn(S, r.w, r.y));
             dst[32 * k] = __fmaf_rn(num, rcp_approx(e), dst[32 * k]);
         }
     }
@@ -564,19 +644,19 @@ __global__ void __launch_bounds__(kSynthThreads, 3) synth_kernel(LaunchArgs a, f
                 rrb[slot] = inner ? hb + 4 * rel : rel;
             }
             __syncwarp();
-            // The records are read-only here: the next one is loaded before the current taps.
+            // The records are read-only here: the next one is loaded before the current taps.  The
+            // buffer offsets come from one load per batch (lane q holds slot q's) and a shuffle.
+            const int rbq = rrb[lane];
             float4 rn = rec[0];
-            int bn = rrb[0];
             for (int q = 0; q < ni; ++q) {
                 const float4 r = rn;
-                const int rb = bn;
+                const int rb = __shfl_sync(0xffffffffu, rbq, q);
                 rn = rec[q + 1];
-                bn = rrb[q + 1];
                 add_arrival_inner<NR>(smem, L, r, rb, lane4);
                 __syncwarp();
             }
             for (int q = ni; q < nv; ++q) {
-                const int rl = rrb[q];
+                const int rl = __shfl_sync(0xffffffffu, rbq, q);
                 add_arrival_edge<NR>(smem, L, rec[q], hb + 4 * rl, lane4, rl, T);
                 __syncwarp();
             }
