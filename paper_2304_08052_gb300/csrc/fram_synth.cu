@@ -407,25 +407,6 @@ __device__ __forceinline__ float4 arrival_record(int& nc, float delta, float A, 
 // packed FP32 (fma.rn.f32x2: two independent IEEE fused multiply-adds, each half rounded exactly
 // as __fmaf_rn), so the constants of a pair sit in one 64-bit register pair; an odd last round
 // stays scalar.
-typedef unsigned long long f32x2;
-
-__device__ __forceinline__ f32x2 pack2(float lo, float hi)
-{
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void unpack2(f32x2 v, float& lo, float& hi)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
-{
-    f32x2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
 template <int NR>
 struct TapLanes {
     static constexpr int NP = NR / 2 > 0 ? NR / 2 : 1;    // (one unused pair when NR = 1)
