@@ -607,7 +607,9 @@ __global__ void __launch_bounds__(kSynthThreads, 3) synth_kernel(LaunchArgs a, f
                     rr = arrival_record(nc, delta, A, invK, exact_trig);
                     rel = nc - K - T0;
                     valid = rel >= reach_lo && rel < T;
-                    inner = rel > -32 && rel < inner_hi;
+                    // inside the buffer for every round; a subset of valid (for K < 16 the
+                    // offsets -31 .. -2K reach no sample of the tile and have no record)
+                    inner = valid && rel > -32 && rel < inner_hi;
                 }
             }
             if (c + 32 + lane < ir.c_hi) {      // next 32 images, in flight during the taps below

@@ -165,6 +165,20 @@ def test_large_4096_48k_sampled_rooms(oracle_mod):
     assert res["rir"].max() < TOL, np.sort(res["rir"])[-5:]
 
 
+@pytest.mark.parametrize("K,tile", [(1, 0), (5, 0), (16, 0), (17, 0), (33, 0), (64, 0), (100, 0), (128, 0),
+                                    (128, 256)])
+def test_other_half_lengths(oracle_mod, K, tile):
+    # Every round count of the synthesis (one lane per tap offset: 1 to 8 rounds of 32, packed
+    # in pairs with a scalar last round when odd), K = 1 (whose delta / K may leave [-1/2, 1/2]),
+    # and the adjoint's path for a K without compile-time constants.  tile = 2K: a window spans
+    # two tiles at most.
+    sc = scenes.tiny(seed=40 + K, B=3, S=2, M=2, images=90, K=K, t60_lo=0.08, t60_hi=0.2)
+    e, ds, vs, ref = _compare_rooms(oracle_mod, sc, seed=K, rooms=None, early=True, tile=tile)
+    assert e["rir"].max() < TOL and e["early"].max() < TOL, (K, e["rir"].max(), e["early"].max())
+    g = _grad_compare(oracle_mod, sc, seed=K, early=True)
+    assert max(g.values()) < TOL, (K, g)
+
+
 def test_cartesian_float32_inputs(oracle_mod):
     # User-supplied float32 image positions (no low parts) and arbitrary g.
     sc = scenes.tiny(seed=4, B=3, S=2, M=4, images=300, t60_lo=0.2, t60_hi=0.4)
