@@ -179,6 +179,24 @@ def test_other_half_lengths(oracle_mod, K, tile):
     assert max(g.values()) < TOL, (K, g)
 
 
+@pytest.mark.parametrize("fs,M,S,geometry,spacing,K,t60", [
+    (8000.0, 1, 1, "circular", 0.05, 40, (0.1, 0.3)),      # one mic, low rate
+    (22050.0, 64, 1, "circular", 0.1, 40, (0.05, 0.1)),    # the most mics the adjoint takes
+    (44100.0, 9, 3, "linear", 0.1, 63, (0.05, 0.12)),
+    (16000.0, 3, 7, "circular", 0.02, 40, (0.3, 0.5)),     # many sources
+    (48000.0, 5, 2, "linear", 0.25, 63, (0.03, 0.05)),     # 1 m array: a 140-sample margin, short RIRs
+])
+def test_scene_shapes(oracle_mod, fs, M, S, geometry, spacing, K, t60):
+    # Sample rates, array sizes and shapes, and source counts outside the benchmark workloads:
+    # RIRs, early RIRs and the adjoint against the oracle on every room.
+    sc = scenes.make_batch("shape", 60 + M + S, 3, S, M, geometry, spacing, [3, 3, 2.5], [6, 5, 3.5],
+                           t60[0], t60[1], fs, K, images_fixed=70)
+    e, ds, vs, ref = _compare_rooms(oracle_mod, sc, seed=M + S, rooms=None, early=True)
+    assert e["rir"].max() < TOL and e["early"].max() < TOL, (e["rir"].max(), e["early"].max())
+    g = _grad_compare(oracle_mod, sc, seed=M + S, early=True)
+    assert max(g.values()) < TOL, g
+
+
 def test_cartesian_float32_inputs(oracle_mod):
     # User-supplied float32 image positions (no low parts) and arbitrary g.
     sc = scenes.tiny(seed=4, B=3, S=2, M=4, images=300, t60_lo=0.2, t60_hi=0.4)
