@@ -101,6 +101,18 @@ def test_multirate_48k_with_early_matches_the_oracle(oracle_mod):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("fs,t60", [(8000.0, (0.1, 0.3)), (11025.0, (0.1, 0.2)), (22050.0, (0.05, 0.15)),
+                                    (32000.0, (0.05, 0.1)), (96000.0, (0.03, 0.06)), (250000.0, (0.03, 0.04))])
+def test_multirate_other_rates(oracle_mod, fs, t60):
+    # Every second-resampler rate r_l = floor(sqrt(floor(1e6 / fs))) the benchmark workloads do not
+    # use: 11, 9, 6, 5, 3 and 2 (16 and 48 kHz give 7 and 4), with early RIRs.
+    sc = scenes.tiny(seed=int(fs) % 97, B=2, S=2, M=2, images=80, fs=fs, t60_lo=t60[0], t60_hi=t60[1])
+    ds, h, h_ref, he, he_ref = _run(oracle_mod, sc, 34, early=True)
+    assert _errors(sc, ds, h, h_ref).max() <= TOL
+    assert _errors(sc, ds, he, he_ref).max() <= TOL
+
+
+@pytest.mark.gpu
 def test_multirate_tiles_and_ragged_ends(oracle_mod):
     # RIRs shorter than one tile and several tiles long; every tile length gives the same RIRs.
     sc = scenes.tiny(seed=22, B=3, S=1, M=2, images=120, fs=16000.0, t60_lo=0.02, t60_hi=0.25)
