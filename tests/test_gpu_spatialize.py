@@ -166,6 +166,25 @@ def test_single_sample_rirs_and_silent_sources(oracle_mod):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("fs,K,S,n_speech,M,N,t60", [
+    (48000.0, 63, 2, 1, 3, 48000, (0.6, 1.0)),    # long RIRs: up to 12 partitions per output block
+    (16000.0, 40, 1, 1, 1, 20000, (0.2, 0.4)),    # one speaker, one mic, no noise
+    (16000.0, 40, 5, 3, 4, 30000, (0.1, 0.3)),    # three speakers and two noise sources
+])
+def test_spatialize_shapes(oracle_mod, fs, K, S, n_speech, M, N, t60):
+    sc = scenes.tiny(seed=77 + S, B=2, S=S, M=M, images=100, fs=fs, K=K, t60_lo=t60[0], t60_hi=t60[1])
+    h, he = _oracle_rirs(oracle_mod, sc, 8, early=True)
+    mx = scenes.mixtures(78 + S, sc.B, sc.S, N, sc.fs, n_speech=n_speech)
+    ds = api.DeviceScene(sc, api.Params(fs=sc.fs, half_len=sc.half_len))
+    mix_r, tg_r, g_r = oracle_mod.spatialize(ds.rir_len, ds.rir_off, h, mx.signals, n_speech, mx.level_db,
+                                             target_rir=he, M=sc.M)
+    mix, tg, g = _run(ds, h, mx, targets=True, trir=he)
+    assert _chan_err(mix, mix_r) <= TOL
+    assert _chan_err(tg, tg_r) <= TOL
+    np.testing.assert_allclose(g, g_r, rtol=TOL, atol=0)
+
+
+@pytest.mark.gpu
 def test_training_batch_on_sampled_rooms(oracle_mod):
     # The full configuration: batch_1024 (1024 rooms x 3 sources x 8 mics, 16 kHz) RIRs rendered
     # on the GPU, 4 s sources, the launch configuration the benchmark times; rooms 0 and 517 are
