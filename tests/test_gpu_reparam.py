@@ -65,6 +65,38 @@ def test_sampler_adjoint_matches_the_oracle(oracle_mod, name):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("fs,M,S,geometry,spacing,K", [
+    (44100.0, 64, 1, "circular", 0.1, 63),    # the most mics the adjoint takes
+    (16000.0, 2, 7, "linear", 0.3, 5),        # many sources, a short window
+    (8000.0, 1, 2, "circular", 0.05, 1),      # one mic, K = 1
+])
+def test_sampled_rir_shapes(oracle_mod, fs, M, S, geometry, spacing, K):
+    # The whole differentiable step (sample, synthesize, both adjoints) on scene shapes outside the
+    # benchmark workloads, against the oracle's pipeline.
+    import torch
+    sc = scenes.make_batch("shape", 90 + M + S, 2, S, M, geometry, spacing, [3, 3, 2.5], [6, 5, 3.5],
+                           0.1, 0.25, fs, K, images_fixed=120)
+    seed = 65 + M
+    ds = api.DeviceScene(sc, _params(sc))
+    leaves = [t.clone().requires_grad_() for t in (ds.src, ds.mic, ds.rt60, ds.dims)]
+    h, he = api.sampled_rir(ds, *leaves, seed=seed, early=True)
+    G = np.random.default_rng(9).standard_normal(ds.rir_total).astype(np.float32)
+    Ge = np.random.default_rng(10).standard_normal(ds.rir_total).astype(np.float32)
+    loss = (h * torch.from_numpy(G).cuda()).sum() + (he * torch.from_numpy(Ge).cuda()).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    assert ds.status() == 0
+    got = [t.grad.cpu().numpy() for t in leaves]
+    op = _oparams(oracle_mod, sc)
+    ref = oracle_mod.sample(sc, op, seed)
+    gv, gm, gs, gr, gg = oracle_mod.backward(sc, op, ref.pos, ref.g, ref.r, G.astype(np.float64),
+                                             Ge.astype(np.float64), with_g=True)
+    want = oracle_mod.sample_backward(sc, op, seed, gv, gg, gr, gs, gm)
+    for g_, r_, what in zip(got, want, ("src", "mic", "t60", "dims")):
+        assert _rel(g_, r_) <= TOL, (what, _rel(g_, r_))
+
+
+@pytest.mark.gpu
 def test_adjoint_reflection_count_gradient(oracle_mod):
     import torch
     sc = scenes.tiny(seed=52, B=3, S=2, M=3, images=200, t60_lo=0.1, t60_hi=0.3)
