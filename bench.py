@@ -406,7 +406,8 @@ def e2e(torch, api, sc, params, ds, args, rirs, dist_ok, world, n_copy=4):
     fram_sample + fram_synthesize, D2H of the RIR buffer.  Pipelined: the RIRs alternate between
     two device buffers, and each step's device-to-host copy runs on n_copy side streams (one
     contiguous slice each) while the next step computes; a buffer is reused only after its copy
-    has finished.  The timed region ends when every copy has landed."""
+    has finished.  The timed region (the run's --steps, 3 to 20) ends when every copy has
+    landed."""
     import numpy as np
     host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
             dict(dims=sc.dims, rt60=sc.rt60, src=sc.src, mic=sc.mic, n_vs=sc.n_vs.astype(np.int32),
@@ -451,7 +452,7 @@ def e2e(torch, api, sc, params, ds, args, rirs, dist_ok, world, n_copy=4):
         step(k)
     join()
     torch.cuda.synchronize()
-    steps = max(3, min(args.steps, 5))
+    steps = max(3, min(args.steps, 20))
     t = _time_steps(torch, step, steps, dist_ok, join=join)
     return {"value": world * steps * rirs / t, "unit": "RIRs/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(4 * ds.rir_total), "ms_per_step": 1000.0 * t / steps,
