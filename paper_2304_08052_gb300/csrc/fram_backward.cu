@@ -110,7 +110,8 @@ struct ArrB {
     bool shifted;
 };
 
-__device__ __forceinline__ ArrB arrival_bwd(int& nc, float delta, float invK, bool exact_trig)
+// cK, sK = cos, sin(pi / K): the rotation from the re-based delta to the original one.
+__device__ __forceinline__ ArrB arrival_bwd(int& nc, float delta, float invK, bool exact_trig, float cK, float sK)
 {
     ArrB r;
     if (fabsf(delta) < kTinyDelta) delta = kTinyDelta;
@@ -133,11 +134,9 @@ __device__ __forceinline__ ArrB arrival_bwd(int& nc, float delta, float invK, bo
         sincospif(delta * invK, &sn, &cn);
     } else {
         cy = cospi_poly(r.d * invK); sy = sinpi_poly(r.d * invK);
-        if (r.shifted) {                                          // r.d != delta only when re-based
-            cn = cospi_poly(delta * invK); sn = sinpi_poly(delta * invK);
-        } else {
-            cn = cy; sn = sy;
-        }
+        // re-based: delta = r.d + 1, so (cn, sn) is (cy, sy) rotated by pi / K
+        cn = r.shifted ? __fmaf_rn(cy, cK, -sy * sK) : cy;
+        sn = r.shifted ? __fmaf_rn(sy, cK, cy * sK) : sy;
     }
     r.P = su * kTwoPiInv;
     r.Pp = 0.5f * cu;
@@ -147,7 +146,7 @@ __device__ __forceinline__ ArrB arrival_bwd(int& nc, float delta, float invK, bo
     r.bp = __fmaf_rn(r.Pp, sy, r.P * piK * cy);
     // Nearest tap: x = n - t = -delta (delta of the original split), tap = sinc(x) w(x), both
     // even, so dtap/dt = sinc'(delta) w(delta) + sinc(delta) w'(delta).
-    const float sinc = sdl * kInvPi / delta;
+    const float sinc = sdl * kInvPi * rcp_approx(delta);      // |delta| >= kTinyDelta
     const float w = 0.5f * (1.0f + cn);
     const float wp = -0.5f * piK * sn;
     r.dnear = __fmaf_rn(dsinc_small(delta), w, sinc * wp);
@@ -466,6 +465,8 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_kernel(LaunchArgs a, const
     }
     const float invK = 1.0f / (float)K;
     const bool exact_trig = K < 2;
+    float sK, cK;
+    sincospif(invK, &sK, &cK);
     const float qf = a.q;
     const int n_items = a.hdr->n_items;
     int qt = 0;
@@ -573,7 +574,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_kernel(LaunchArgs a, const
                             if (R.is_dir) dmask |= 1ull << m;
                         }
                         if (act) {
-                            const ArrB r = arrival_bwd(nc, delta, invK, exact_trig);
+                            const ArrB r = arrival_bwd(nc, delta, invK, exact_trig, cK, sK);
                             const int j0 = nc - K - P.gb;
                             if (j0 >= 0 && j0 + 2 * K <= P.gl) {
                                 R.go = true;
