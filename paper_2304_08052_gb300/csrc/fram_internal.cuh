@@ -78,16 +78,6 @@ __device__ __forceinline__ f2 f2_mul_f(f2 a, float b)
 
 __device__ __forceinline__ f2 f2_neg(f2 a) { return {-a.hi, -a.lo}; }
 
-// sqrt of a positive pair: one Newton correction of the correctly rounded float root.
-__device__ __forceinline__ f2 f2_sqrt(f2 a)
-{
-    float y = __fsqrt_rn(a.hi);
-    f2 yy = two_prod(y, y);
-    float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, yy.hi), yy.lo), a.lo);
-    float c = __fdiv_rn(r, __fmul_rn(2.0f, y));
-    return fast_two_sum(y, c);
-}
-
 // --------------------------------------------------------------------------------------
 // Packed FP32 pairs (add/mul/fma.rn.f32x2): one instruction performs two independent IEEE
 // operations, each half rounded exactly as the scalar operation would be.  A pair lives in one
