@@ -60,10 +60,25 @@ def layout(rt60, n_vs, S: int, M: int, fs: float):
     return rir_len, rir_off, vs_off
 
 
-def _ptr(t: Optional[torch.Tensor]):
+_F32 = (torch.float32,)
+_SEED = (torch.int64,) + ((torch.uint64,) if hasattr(torch, "uint64") else ())
+_WORD = (torch.int32,) + ((torch.uint32,) if hasattr(torch, "uint32") else ())
+
+
+def _ptr(t: Optional[torch.Tensor], n: int = 0, dtypes=_F32, name: str = "tensor"):
+    """The data pointer handed to libfram, after the checks the library cannot make itself: a
+    contiguous CUDA tensor of the expected element type holding at least n elements (the kernels
+    index up to the sizes the scene implies, so a smaller buffer would be read out of bounds)."""
     if t is None:
         return None
-    assert t.is_cuda and t.is_contiguous(), "libfram takes contiguous CUDA tensors"
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch.Tensor, got {type(t).__name__}")
+    if t.dtype not in dtypes:
+        raise ValueError(f"{name}: expected dtype {dtypes[0]}, got {t.dtype}")
+    if t.numel() < n:
+        raise ValueError(f"{name}: needs at least {n} elements, has {t.numel()}")
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError(f"{name}: libfram takes contiguous CUDA tensors")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -112,11 +127,11 @@ class DeviceScene:
         mic = self.mic if mic is None else mic
         dims = getattr(self, "dims", None) if dims is None else dims
         rt60 = getattr(self, "rt60", None) if rt60 is None else rt60
-        for t in (src, mic, dims, rt60):
-            assert t is None or (t.is_cuda and t.is_contiguous() and t.dtype == torch.float32)
+        B, S, M = self.B, self.S, self.M
         cp = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
         return FramScene(self.B, self.S, self.M, self.max_len, self.n_vs_total, self.rir_total, self.array_radius,
-                         cp(dims), cp(rt60), cp(src), cp(mic),
+                         _ptr(dims, 3 * B, name="dims"), _ptr(rt60, B, name="rt60"), _ptr(src, 3 * B * S, name="src"),
+                         _ptr(mic, 3 * B * M, name="mic"),
                          cp(getattr(self, "n_vs", None)), cp(getattr(self, "vs_off_d", None)),
                          cp(getattr(self, "rir_len_d", None)), cp(getattr(self, "rir_off_d", None)))
 
@@ -154,12 +169,19 @@ def sample(sc: DeviceScene, seed: int = 0, d_seed: Optional[torch.Tensor] = None
                      torch.empty(N, dtype=torch.float32, device=dev),
                      torch.empty(sc.B, dtype=torch.float32, device=dev),
                      torch.empty((N, 4), dtype=torch.int32, device=dev) if words else None)
-    ds = _ptr(d_seed) if d_seed is not None else None
+    B = sc.B
     check(lib().fram_sample(ctypes.byref(sc.c_scene(src, mic, dims, rt60)), ctypes.byref(sc.params.c()),
-                            ctypes.c_uint64(seed & (2**64 - 1)),
-                            ds, _ptr(out.pos_hi), _ptr(out.pos_lo), _ptr(out.g), _ptr(out.r), _ptr(out.words),
+                            ctypes.c_uint64(seed & (2**64 - 1)), _ptr(d_seed, 1, _SEED, "d_seed"),
+                            _ptr(out.pos_hi, 3 * N, name="pos_hi"), _ptr(out.pos_lo, 3 * N, name="pos_lo"),
+                            _ptr(out.g, N, name="g"), _ptr(out.r, B, name="r"), _ptr(out.words, 4 * N, _WORD, "words"),
                             ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes), _stream()))
     return out
+
+
+def _images(sc: DeviceScene, pos_hi, pos_lo, g, r):
+    N = sc.n_vs_total
+    return (_ptr(pos_hi, 3 * N, name="pos_hi"), _ptr(pos_lo, 3 * N, name="pos_lo"),
+            _ptr(g, N, name="g") if g is not None else None, _ptr(r, sc.B, name="r"))
 
 
 def synthesize_raw(sc: DeviceScene, pos_hi, pos_lo, g, r, src=None, mic=None, early: bool = False,
@@ -172,8 +194,10 @@ def synthesize_raw(sc: DeviceScene, pos_hi, pos_lo, g, r, src=None, mic=None, ea
         early_out = torch.empty(sc.rir_total, dtype=torch.float32, device=dev)
     src = sc.src if src is None else src
     mic = sc.mic if mic is None else mic
-    check(lib().fram_synthesize(ctypes.byref(sc.c_scene(src, mic)), ctypes.byref(sc.params.c()), _ptr(pos_hi),
-                                _ptr(pos_lo), _ptr(g), _ptr(r), _ptr(rir), _ptr(early_out) if early else None,
+    T = sc.rir_total
+    check(lib().fram_synthesize(ctypes.byref(sc.c_scene(src, mic)), ctypes.byref(sc.params.c()),
+                                *_images(sc, pos_hi, pos_lo, g, r), _ptr(rir, T, name="rir"),
+                                _ptr(early_out, T, name="early_out") if early else None,
                                 ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes), _stream()))
     return (rir, early_out) if early else rir
 
@@ -194,11 +218,18 @@ def synthesize_backward_raw(sc: DeviceScene, pos_hi, pos_lo, g, r, grad_rir, gra
     gr = torch.empty(sc.B, dtype=torch.float32, device=dev) if "r" in want else None
     src = sc.src if src is None else src
     mic = sc.mic if mic is None else mic
+    T = sc.rir_total
     check(lib().fram_synthesize_backward(ctypes.byref(sc.c_scene(src, mic)), ctypes.byref(sc.params.c()),
-                                         _ptr(pos_hi), _ptr(pos_lo), _ptr(g), _ptr(r), _ptr(grad_rir),
-                                         _ptr(grad_early), _ptr(gv), _ptr(gm), _ptr(gs), _ptr(gr), _ptr(gg),
+                                         *_images(sc, pos_hi, pos_lo, g, r), _ptr(grad_rir, T, name="grad_rir"),
+                                         _ptr(grad_early, T, name="grad_early"), *_grad_outs(sc, gv, gm, gs, gr, gg),
                                          ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes), _stream()))
     return (gv, gm, gs, gr, gg) if "g" in want else (gv, gm, gs, gr)
+
+
+def _grad_outs(sc: DeviceScene, gv, gm, gs, gr, gg):
+    N, B, S, M = sc.n_vs_total, sc.B, sc.S, sc.M
+    return (_ptr(gv, 3 * N, name="grad_vs"), _ptr(gm, 3 * B * M, name="grad_mic"),
+            _ptr(gs, 3 * B * S, name="grad_src"), _ptr(gr, B, name="grad_r"), _ptr(gg, N, name="grad_g"))
 
 
 def sample_backward(sc: DeviceScene, seed: int, grad_vs, grad_g=None, grad_r=None, grad_src_in=None,
@@ -214,10 +245,15 @@ def sample_backward(sc: DeviceScene, seed: int, grad_vs, grad_g=None, grad_r=Non
                torch.empty(sc.B, dtype=torch.float32, device=dev),
                torch.empty((sc.B, 3), dtype=torch.float32, device=dev))
     gs, gm, gt, gd = out
+    N, B, S, M = sc.n_vs_total, sc.B, sc.S, sc.M
     check(lib().fram_sample_backward(ctypes.byref(sc.c_scene(src, mic, dims, rt60)), ctypes.byref(sc.params.c()),
-                                     ctypes.c_uint64(seed & (2**64 - 1)), _ptr(d_seed), _ptr(grad_vs), _ptr(grad_g),
-                                     _ptr(grad_r), _ptr(grad_src_in), _ptr(grad_mic_in), _ptr(gs), _ptr(gm), _ptr(gt),
-                                     _ptr(gd), ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes),
+                                     ctypes.c_uint64(seed & (2**64 - 1)), _ptr(d_seed, 1, _SEED, "d_seed"),
+                                     _ptr(grad_vs, 3 * N, name="grad_vs"), _ptr(grad_g, N, name="grad_g"),
+                                     _ptr(grad_r, B, name="grad_r"), _ptr(grad_src_in, 3 * B * S, name="grad_src_in"),
+                                     _ptr(grad_mic_in, 3 * B * M, name="grad_mic_in"),
+                                     _ptr(gs, 3 * B * S, name="grad_src"), _ptr(gm, 3 * B * M, name="grad_mic"),
+                                     _ptr(gt, B, name="grad_t60"), _ptr(gd, 3 * B, name="grad_dims"),
+                                     ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes),
                                      _stream()))
     return gs, gm, gt, gd
 
@@ -290,8 +326,9 @@ def prepare(sc: DeviceScene, pos_hi, pos_lo, r, src=None, mic=None):
     """fram_prepare: per-room tables, work items and delay bins in the workspace."""
     src = sc.src if src is None else src
     mic = sc.mic if mic is None else mic
-    check(lib().fram_prepare(ctypes.byref(sc.c_scene(src, mic)), ctypes.byref(sc.params.c()), _ptr(pos_hi),
-                             _ptr(pos_lo), _ptr(r), ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes),
+    ph, pl, _, pr = _images(sc, pos_hi, pos_lo, None, r)
+    check(lib().fram_prepare(ctypes.byref(sc.c_scene(src, mic)), ctypes.byref(sc.params.c()), ph, pl, pr,
+                             ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes),
                              _stream()))
 
 
@@ -299,8 +336,10 @@ def synthesize_prepared(sc: DeviceScene, pos_hi, pos_lo, g, r, rir, early_out=No
     """fram_synthesize_prepared: the synthesis kernel alone, after prepare() on the same inputs."""
     src = sc.src if src is None else src
     mic = sc.mic if mic is None else mic
+    T = sc.rir_total
     check(lib().fram_synthesize_prepared(ctypes.byref(sc.c_scene(src, mic)), ctypes.byref(sc.params.c()),
-                                         _ptr(pos_hi), _ptr(pos_lo), _ptr(g), _ptr(r), _ptr(rir), _ptr(early_out),
+                                         *_images(sc, pos_hi, pos_lo, g, r), _ptr(rir, T, name="rir"),
+                                         _ptr(early_out, T, name="early_out"),
                                          ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes), _stream()))
     return rir
 
@@ -317,10 +356,12 @@ def synthesize_backward_prepared(sc: DeviceScene, pos_hi, pos_lo, g, r, grad_rir
     gv, gm, gs, gr = out
     src = sc.src if src is None else src
     mic = sc.mic if mic is None else mic
+    T = sc.rir_total
     check(lib().fram_synthesize_backward_prepared(ctypes.byref(sc.c_scene(src, mic)), ctypes.byref(sc.params.c()),
-                                                  _ptr(pos_hi), _ptr(pos_lo), _ptr(g), _ptr(r), _ptr(grad_rir),
-                                                  _ptr(grad_early), _ptr(gv), _ptr(gm), _ptr(gs), _ptr(gr),
-                                                  _ptr(grad_g),
+                                                  *_images(sc, pos_hi, pos_lo, g, r),
+                                                  _ptr(grad_rir, T, name="grad_rir"),
+                                                  _ptr(grad_early, T, name="grad_early"),
+                                                  *_grad_outs(sc, gv, gm, gs, gr, grad_g),
                                                   ctypes.c_void_p(sc.ws.data_ptr()), ctypes.c_size_t(sc.ws_bytes),
                                                   _stream()))
     return out
@@ -333,8 +374,13 @@ def spatialize(sc: DeviceScene, rir, signals, level_db, n_speech: int, target_ri
     also the per-speaker targets [B,n_speech,M,N] through target_rir (default: rir).  Returns
     (mixture, targets or None, gains [B,S])."""
     dev = sc.dims.device
+    if signals.dim() != 3:
+        raise ValueError("signals: expected [B, S, N]")
     B, S, N = (int(v) for v in signals.shape)
-    assert B == sc.B and S == sc.S
+    if B != sc.B or S != sc.S:
+        raise ValueError(f"signals: expected [{sc.B}, {sc.S}, N], got {list(signals.shape)}")
+    if not 1 <= int(n_speech) <= S:
+        raise ValueError(f"n_speech must be in [1, {S}]")
     spc = FramSpatial(N, int(n_speech), int(block), int(chunk_rooms), 0)
     trir = (target_rir if target_rir is not None else rir) if targets else None
     sep = 1 if (trir is not None and trir.data_ptr() != rir.data_ptr()) else 0
@@ -352,8 +398,12 @@ def spatialize(sc: DeviceScene, rir, signals, level_db, n_speech: int, target_ri
                torch.empty((B, int(n_speech), sc.M, N), dtype=torch.float32, device=dev) if targets else None,
                torch.empty((B, S), dtype=torch.float32, device=dev))
     mix, tg, gains = out
-    check(lib().fram_spatialize(ctypes.byref(sc.c_scene()), ctypes.byref(spc), _ptr(rir), _ptr(trir),
-                                _ptr(signals), _ptr(level_db), _ptr(mix), _ptr(tg), _ptr(gains),
+    T, M, ns = sc.rir_total, sc.M, int(n_speech)
+    check(lib().fram_spatialize(ctypes.byref(sc.c_scene()), ctypes.byref(spc), _ptr(rir, T, name="rir"),
+                                _ptr(trir, T, name="target_rir"), _ptr(signals, B * S * N, name="signals"),
+                                _ptr(level_db, B * S, name="level_db"), _ptr(mix, B * M * N, name="mixture"),
+                                _ptr(tg, B * ns * M * N, name="targets") if targets else None,
+                                _ptr(gains, B * S, name="gains"),
                                 ctypes.c_void_p(ws[2].data_ptr()), ctypes.c_size_t(int(n.value)), _stream()))
     return mix, tg, gains
 
@@ -380,7 +430,8 @@ def autotune(sc: DeviceScene, vs: Images, rir: Optional[torch.Tensor] = None) ->
     if rir is None:
         rir = torch.empty(sc.rir_total, dtype=torch.float32, device=sc.dims.device)
     out = ctypes.c_int32(0)
-    check(lib().fram_autotune(ctypes.byref(sc.c_scene()), ctypes.byref(sc.params.c()), _ptr(vs.pos_hi),
-                              _ptr(vs.pos_lo), _ptr(vs.g), _ptr(vs.r), _ptr(rir), ctypes.c_void_p(sc.ws.data_ptr()),
+    check(lib().fram_autotune(ctypes.byref(sc.c_scene()), ctypes.byref(sc.params.c()),
+                              *_images(sc, vs.pos_hi, vs.pos_lo, vs.g, vs.r), _ptr(rir, sc.rir_total, name="rir"),
+                              ctypes.c_void_p(sc.ws.data_ptr()),
                               ctypes.c_size_t(sc.ws_bytes), _stream(), ctypes.byref(out)))
     return int(out.value)

@@ -140,3 +140,22 @@ def test_spatialize_rejects_bad_arguments_on_the_host(L):
     null = ctypes.c_void_p(0)
     assert L.fram_spatialize(ctypes.byref(sc), ctypes.byref(ok), null, null, null, null, null, null, null, null, 0,
                              None) == _lib.FRAM_EWORKSPACE
+
+
+def test_binding_checks_tensors_before_handing_pointers():
+    # The binding refuses what the C ABI cannot check: element type, size, device, layout.
+    import torch
+    from paper_2304_08052_gb300 import api
+    assert api._ptr(None, 10) is None
+    with pytest.raises(TypeError):
+        api._ptr([1.0, 2.0], 2, name="g")
+    with pytest.raises(ValueError, match="dtype"):
+        api._ptr(torch.zeros(8, dtype=torch.float64), 8, name="g")
+    with pytest.raises(ValueError, match="dtype"):
+        api._ptr(torch.zeros(1, dtype=torch.int32), 1, api._SEED, "d_seed")
+    with pytest.raises(ValueError, match="at least 9"):
+        api._ptr(torch.zeros(8), 9, name="pos_hi")
+    with pytest.raises(ValueError, match="CUDA"):
+        api._ptr(torch.zeros(8), 8, name="rir")                  # right type and size, host memory
+    with pytest.raises(ValueError, match="dtype"):
+        api._ptr(torch.zeros((4, 4), dtype=torch.int64), 16, api._WORD, "words")
