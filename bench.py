@@ -241,10 +241,22 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the per-room comparison and the CPU baseline")
     ap.add_argument("--spatialize-rooms", type=int, default=0,
                     help="only time fram_spatialize on the first N rooms of batch_1024 (for profiling) and exit")
+    ap.add_argument("--multirate-only", action="store_true",
+                    help="only time the multi-rate path against the continuous one on batch_1024 (for profiling) "
+                         "and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.multirate_only:
+        import torch
+
+        from paper_2304_08052_gb300 import api, build, scenes
+        build.build()
+        peaks, _ = _measured_peaks()
+        print(json.dumps({"multirate_only": multirate_vs_continuous(torch, api, scenes, peaks, cpu=False)}),
+              flush=True)
+        return 0
     if args.spatialize_rooms > 0:
         import torch
 
@@ -486,7 +498,7 @@ def single_room_latency(torch, api, scenes):
             "ms_median": statistics.median(ms), "ms_min": min(ms), "calls": len(ms)}
 
 
-def multirate_vs_continuous(torch, api, scenes, peaks):
+def multirate_vs_continuous(torch, api, scenes, peaks, cpu=True):
     """The paper's multi-rate output path (delay_mode 1: ~1 MHz impulse grid, two polyphase
     resamplers, 80 Hz high-pass) against the continuous path on batch_1024 with early RIRs:
     fram_sample + fram_synthesize per step.  The multi-rate stages stream an intermediate signal
@@ -524,6 +536,8 @@ def multirate_vs_continuous(torch, api, scenes, peaks):
                                  "frac": moved / t / 1e9 / peak, "bytes_per_step": moved,
                                  "note": "stream bytes of the multi-rate stages only"}
         out["continuous" if mode == 0 else "multirate"] = entry
+    if not cpu:
+        return out
     import oracle
     rooms = list(range(16))
     sub = sc.subset(rooms)
