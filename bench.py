@@ -48,23 +48,34 @@ TAP_MUFU, ARR_MUFU = 1.0, 6.0
 FP32_LANES_PER_SM, MUFU_LANES_PER_SM = 128, 16
 
 
-def rank_scene_seed(base: int, rank: int) -> int:
-    """Weak scaling: every rank synthesises its own full batch, drawn from its own seed."""
-    return base + 1000003 * rank
-
-
 def combine(units_per_rank, seconds_per_rank):
     """Whole-job throughput: all ranks' units over the slowest rank's time."""
     return sum(units_per_rank) / max(seconds_per_rank)
 
 
-def alu_peak_taps(sm_count: int, clock_hz: float, K: int, fp32_per_tap: float):
+def alu_peak_taps(sm_count: int, clock_hz: float, K: int, fp32_per_tap: float, fp32_lanes: float = FP32_LANES_PER_SM,
+                  mufu_lanes: float = MUFU_LANES_PER_SM):
+    """Taps/s the FP32 and MUFU pipes allow at `fp32_lanes` and `mufu_lanes` lane operations per SM
+    per clock (nominal by default), and which pipe binds."""
     n = 2 * K + 1
-    p_fp32 = sm_count * FP32_LANES_PER_SM * clock_hz
-    p_mufu = sm_count * MUFU_LANES_PER_SM * clock_hz
+    p_fp32 = sm_count * fp32_lanes * clock_hz
+    p_mufu = sm_count * mufu_lanes * clock_hz
     by_fp32 = p_fp32 / (fp32_per_tap + ARR_FP32 / n)
     by_mufu = p_mufu / (TAP_MUFU + ARR_MUFU / n)
     return min(by_fp32, by_mufu), ("mufu" if by_mufu < by_fp32 else "fp32")
+
+
+def measure_alu_lanes(api, seconds: float = 0.5):
+    """FP32 FMA, packed FP32 FMA and MUFU reciprocal lane operations per SM per clock on this GPU
+    (fram_measure_alu: a calibration run, then one of about `seconds`)."""
+    out = {}
+    for kind, name in ((0, "fp32_fma"), (1, "fp32x2_fma"), (2, "mufu_rcp")):
+        cal = api.measure_alu(kind, 200)
+        iters = max(200, int(200 * seconds * 1e3 / max(cal["ms"], 1e-3)))
+        r = api.measure_alu(kind, iters)
+        out[name] = {"per_sm_per_clock": r["per_sm_per_clock"], "lane_ops_per_s": r["per_s"], "ms": r["ms"],
+                     "clock_mhz_from_cycles": r["clock_mhz"]}
+    return out
 
 
 def _measured_peaks():
@@ -270,7 +281,7 @@ def main():
     import numpy as np
     import torch
 
-    from paper_2304_08052_gb300 import api, build, scenes
+    from paper_2304_08052_gb300 import api, build, scenes, shard
 
     build.build()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -282,11 +293,19 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    sc = scenes.by_name(args.workload, rank_scene_seed(0, rank))
+    # One batch of `world` seeded blocks of the workload (block k: scene seed k), split into
+    # contiguous cost-balanced room ranges, one per rank; every rank draws its rooms' images
+    # with their global room index (room_base), so its rows equal those of the whole batch.
+    glob = shard.global_batch(scenes.by_name, args.workload, world)
     if args.rooms > 0:
-        sc = sc.subset(range(min(args.rooms, sc.B)))
+        glob = glob.subset(range(min(args.rooms * world, glob.B)))
+    ranges = shard.partition(shard.room_costs(glob, glob.half_len), world)
+    room_base, hi = ranges[rank]
+    sc = glob.subset(range(room_base, hi))
     params = api.Params(fs=sc.fs, half_len=sc.half_len)
-    ds = api.DeviceScene(sc, params)
+    ds = api.DeviceScene(sc, params, room_base=room_base)
+    job_rirs = glob.B * glob.S                  # RIRs of the whole job per step
+    job_taps = api.algorithmic_taps(glob)
     N, T = ds.n_vs_total, ds.rir_total
     vs = api.Images(torch.empty((N, 3), device="cuda"), torch.empty((N, 3), device="cuda"),
                     torch.empty(N, device="cuda"), torch.empty(sc.B, device="cuda"))
@@ -298,7 +317,6 @@ def main():
     sgrads = (torch.empty((sc.B, sc.S, 3), device="cuda"), torch.empty((sc.B, sc.M, 3), device="cuda"),
               torch.empty(sc.B, device="cuda"), torch.empty((sc.B, 3), device="cuda"))
     taps = api.algorithmic_taps(ds)
-    rirs = sc.B * sc.S
 
     def fwd(k):
         api.sample(ds, seed=1000 + k, out=vs)
@@ -322,6 +340,9 @@ def main():
     peaks, peak_kind = _measured_peaks()
     clock_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    alu = measure_alu_lanes(api)
+    fp32_lanes = alu["fp32_fma"]["per_sm_per_clock"]
+    mufu_lanes = alu["mufu_rcp"]["per_sm_per_clock"]
 
     for k in range(args.warmup):
         fwd_bwd_sampler(k)
@@ -341,11 +362,13 @@ def main():
     clocks = clk.summary()
     assert ds.status() == 0, "device status flags set"
 
-    value = combine([args.steps * rirs] * world, [t_fwd] * world) if not dist_ok else world * args.steps * rirs / t_fwd
+    value = args.steps * job_rirs / t_fwd
     ms_step = 1000.0 * t_fwd / args.steps
     K = params.half_len
-    peak_fwd, lim_fwd = alu_peak_taps(sm_count, clock_hz, K, FWD_FP32)
-    peak_bwd, lim_bwd = alu_peak_taps(sm_count, clock_hz, K, BWD_FP32)
+    peak_fwd, lim_fwd = alu_peak_taps(sm_count, clock_hz, K, FWD_FP32, fp32_lanes, mufu_lanes)
+    peak_bwd, lim_bwd = alu_peak_taps(sm_count, clock_hz, K, BWD_FP32, fp32_lanes, mufu_lanes)
+    nom_fwd, _ = alu_peak_taps(sm_count, clock_hz, K, FWD_FP32)
+    nom_bwd, _ = alu_peak_taps(sm_count, clock_hz, K, BWD_FP32)
     syn_s = t_syn / args.steps
     bwd_s = t_bwd / args.steps
     ach_fwd = taps / syn_s
@@ -355,36 +378,47 @@ def main():
         "metric": METRIC, "value": value, "unit": "RIRs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": sc.name, "rooms": sc.B, "sources": sc.S, "mics": sc.M, "fs": sc.fs,
-                   "half_len": K, "images": int(N), "rir_samples": int(T), "taps_per_step": taps,
+        "config": {"workload": glob.name, "rooms": glob.B, "sources": sc.S, "mics": sc.M, "fs": sc.fs,
+                   "half_len": K, "images": int(N), "rir_samples": int(T), "taps_per_step": job_taps,
+                   "parallelism": (f"rooms split over {world} GPUs in contiguous cost-balanced ranges, global "
+                                   "Philox room indices, no collective on the data path" if world > 1 else "1 GPU"),
                    "l2": f"outputs {out_bytes / 1e9:.1f} GB per step, larger than L2 (129 MB)",
                    "tile": tile, "tile_choice": "fram_autotune over 256/512/1024/2048"},
-        "taps_per_s": taps * args.steps * world / t_fwd,
-        "fwd_bwd": {"value": world * args.steps * rirs / t_fb, "unit": "RIRs/s",
-                    "ms_per_step": 1000.0 * t_fb / args.steps, "taps_per_s": world * 2 * taps * args.steps / t_fb},
+        "taps_per_s": job_taps * args.steps / t_fwd,
+        "fwd_bwd": {"value": args.steps * job_rirs / t_fb, "unit": "RIRs/s",
+                    "ms_per_step": 1000.0 * t_fb / args.steps, "taps_per_s": 2 * job_taps * args.steps / t_fb},
         "roofline": {"bound": "alu", "achieved": ach_fwd / 1e9, "peak": peak_fwd / 1e9, "unit": "Gtap/s",
                      "frac": ach_fwd / peak_fwd, "traffic": _synth_traffic(T),
                      "kernel": "synth_kernel (timed with amp_gather)",
                      "limit": lim_fwd, "kernel_ms": 1000.0 * syn_s, "hbm_gbs": out_bytes / syn_s / 1e9,
-                     "peak_basis": f"{sm_count} SMs x ({FP32_LANES_PER_SM} FP32, {MUFU_LANES_PER_SM} MUFU) lanes x "
-                                   f"{clock_hz / 1e6:.0f} MHz ({peak_kind} sm_max_mhz); per tap "
-                                   f"{FWD_FP32:.0f} FP32 + {TAP_MUFU:.0f} MUFU, per arrival {ARR_FP32:.0f} FP32 + "
-                                   f"{ARR_MUFU:.0f} MUFU"},
+                     "peak_basis": "measured",
+                     "peak_detail": f"{sm_count} SMs x ({fp32_lanes:.1f} FP32, {mufu_lanes:.2f} MUFU) lane ops per "
+                                    f"SM per clock (measured by fram_measure_alu in this run) x "
+                                    f"{clock_hz / 1e6:.0f} MHz ({peak_kind} sm_max_mhz); per tap "
+                                    f"{FWD_FP32:.0f} FP32 + {TAP_MUFU:.0f} MUFU, per arrival {ARR_FP32:.0f} FP32 + "
+                                    f"{ARR_MUFU:.0f} MUFU",
+                     "nominal": {"peak": nom_fwd / 1e9, "frac": ach_fwd / nom_fwd,
+                                 "basis": f"{FP32_LANES_PER_SM} FP32 and {MUFU_LANES_PER_SM} MUFU lanes per SM per clock"},
+                     "taps_note": "taps counted as 2K+1 per arrival (the paper's window); the kernel evaluates 2K "
+                                  "(the last weight is 0) and drops taps past the RIR end, about 0.8 % fewer "
+                                  "on this workload"},
         "fwd_bwd_through_sampler": {
-            "value": world * args.steps * rirs / t_fbs, "unit": "RIRs/s", "ms_per_step": 1000.0 * t_fbs / args.steps,
+            "value": args.steps * job_rirs / t_fbs, "unit": "RIRs/s", "ms_per_step": 1000.0 * t_fbs / args.steps,
             "sample_backward_ms": 1000.0 * t_sb / args.steps,
             "sample_backward_hbm_gbs": 16.0 * N / (t_sb / args.steps) / 1e9,
             "note": "fwd -> adjoint with dL/dg -> fram_sample_backward (source, mic, T60, room-size gradients "
                     "with the draws held fixed); sample_backward reads 16 B per image"},
         "roofline_bwd": {"bound": "alu", "achieved": ach_bwd / 1e9, "peak": peak_bwd / 1e9, "unit": "Gtap/s",
                          "frac": ach_bwd / peak_bwd, "kernel": "bwd_kernel", "limit": lim_bwd,
-                         "kernel_ms": 1000.0 * bwd_s},
+                         "kernel_ms": 1000.0 * bwd_s, "peak_basis": "measured",
+                         "nominal": {"peak": nom_bwd / 1e9, "frac": ach_bwd / nom_bwd}},
+        "alu_lanes": alu,
         "gpu_launches": FWD_LAUNCHES * args.steps,
         "clocks": clocks,
     }
 
     if not args.no_e2e:
-        line["e2e"] = e2e(torch, api, sc, params, ds, args, rirs, dist_ok, world)
+        line["e2e"] = e2e(torch, api, sc, params, ds, args, job_rirs, dist_ok)
 
     if not args.no_extras and rank == 0:
         line["graph_vs_per_room"] = graph_vs_per_room(torch, api, scenes)
@@ -413,7 +447,7 @@ def main():
     return 0
 
 
-def e2e(torch, api, sc, params, ds, args, rirs, dist_ok, world, n_copy=4):
+def e2e(torch, api, sc, params, ds, args, job_rirs, dist_ok, n_copy=4):
     """Same step through the public API from pinned host buffers: H2D of the scene arrays,
     fram_sample + fram_synthesize, D2H of the RIR buffer.  Pipelined: the RIRs alternate between
     two device buffers, and each step's device-to-host copy runs on n_copy side streams (one
@@ -466,7 +500,7 @@ def e2e(torch, api, sc, params, ds, args, rirs, dist_ok, world, n_copy=4):
     torch.cuda.synchronize()
     steps = max(3, min(args.steps, 20))
     t = _time_steps(torch, step, steps, dist_ok, join=join)
-    return {"value": world * steps * rirs / t, "unit": "RIRs/s", "h2d_bytes_per_step": int(h2d),
+    return {"value": steps * job_rirs / t, "unit": "RIRs/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(4 * ds.rir_total), "ms_per_step": 1000.0 * t / steps,
             "pipeline": f"2 device RIR buffers; D2H on {n_copy} side streams overlapping the next step"}
 

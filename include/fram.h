@@ -105,6 +105,11 @@ typedef struct fram_scene {
     const int64_t* vs_off;     /* [B+1]  image row offset of each room                     */
     const int32_t* rir_len;    /* [B]    L_b                                               */
     const int64_t* rir_off;    /* [B+1]  sample offset of each room                        */
+    int64_t room_base;         /* index of room 0 in a larger batch (host; 0 for a whole    */
+                               /* batch): room b draws its images with the Philox counter  */
+                               /* room word room_base + b, so a shard of a batch drawn with */
+                               /* the same seed gets exactly the images the whole batch     */
+                               /* gives those rooms.  0 <= room_base, room_base + B <= 2^32 */
 } fram_scene;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -134,7 +139,7 @@ int fram_workspace_size(const fram_scene* scene, const fram_params* p, size_t* b
 
 /*
  * Virtual-image sampler (Sec. III-A to III-C).  For room b, source s and image i one
- * Philox4x32-10 call (Salmon et al., SC'11) with counter (i, s, b, 0) and key
+ * Philox4x32-10 call (Salmon et al., SC'11) with counter (i, s, room_base + b, 0) and key
  * (seed mod 2^32, seed div 2^32) gives four words w_k, mapped to u_k = ((w_k >> 9) + 0.5) 2^-23:
  *   x    = (alpha^3 + u0 (beta^3 - alpha^3))^(1/3)              inverse CDF of Eq. 3
  *   DR_i = 1 + alpha/(beta-alpha) (x/alpha - 1)(c0 T60/D0 - 1)  Eq. 4,  D_i = D0 DR_i
@@ -271,16 +276,34 @@ int fram_status(void* workspace, void* stream, int32_t* flags);
  * counterpart: this is a deployment convenience around the same synthesis.
  * Inputs, outputs and results are those of fram_synthesize.  The scratch is a static 16 MiB
  * device array that every GPU loading libfram reserves until the process exits; a scene whose
- * fram_workspace_size exceeds 16 MiB is rejected with FRAM_EWORKSPACE before any GPU work.
- * The first call on a device (with that device current) looks up the array's device address
- * with cudaGetSymbolAddress and caches it; make that first call before any stream capture.
- * All calls on a device share the one array: calls that overlap on the GPU (different streams
+ * workspace at the tile length the call launches with (p->tile, or the tuned or default tile
+ * when p->tile is 0) exceeds 16 MiB is rejected with FRAM_EWORKSPACE before any GPU work.
+ * Contexts: each CUDA context (a device's primary context, a context created through the driver
+ * API, a primary context re-created after cudaDeviceReset) has its own copy of the array.  A call
+ * made while `stream` is not being captured looks up the copy of the current context with
+ * cudaGetSymbolAddress; a call made during stream capture reuses the address an earlier
+ * non-capturing call found in the same context, so the first call in a context must come before
+ * any capture (FRAM_ECUDA otherwise).
+ * All calls in a context share the one array: calls that overlap on the GPU (different streams
  * or threads without ordering) race and corrupt each other's results.  Device status bits of
  * these calls are not reported (fram_status needs the caller's workspace).  Allocates nothing.
  */
 int fram_synthesize_noalloc(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi,
                             const float* vs_pos_lo, const float* vs_g, const float* r, float* rir,
                             float* early, void* stream);
+
+/*
+ * Throughput probe for the roofline denominators of the synthesis and the adjoint (the paper has
+ * no counterpart: it measures this GPU).  kind 0: scalar FP32 fused multiply-add; 1: packed FP32
+ * fma.rn.f32x2 (two lane operations per instruction); 2: MUFU reciprocal rcp.approx.ftz.f32.
+ * Launches 8 CTAs of 256 threads per SM, each thread running 8 independent chains of
+ * iters x 16 operations, and synchronises the stream.  result (host, 4 doubles): kernel time in
+ * ms (CUDA events on `stream`), SM clock cycles of the longest CTA (clock64), total lane
+ * operations, SM count.  Lane operations per SM per clock = result[2] / (result[1] result[3]).
+ * Uses a static device buffer of one cycle count per CTA; allocates nothing.  Returns
+ * FRAM_EINVAL for a bad kind, iters < 1 or a null result.
+ */
+int fram_measure_alu(int32_t kind, int64_t iters, double* result, void* stream);
 
 /*
  * Spatialisation: the paper's use of the RIRs for training data (Sec. IV-A).  For every room

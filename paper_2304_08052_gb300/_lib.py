@@ -25,7 +25,8 @@ FRAM_DEV_NONFINITE = 0x4
 EXPORTED = ("fram_version", "fram_last_error", "fram_default_params", "fram_layout", "fram_workspace_size",
             "fram_sample", "fram_synthesize", "fram_synthesize_backward", "fram_status", "fram_prepare",
             "fram_synthesize_prepared", "fram_synthesize_backward_prepared", "fram_synthesize_noalloc",
-            "fram_autotune", "fram_sample_backward", "fram_spatialize_workspace_size", "fram_spatialize")
+            "fram_autotune", "fram_sample_backward", "fram_spatialize_workspace_size", "fram_spatialize",
+            "fram_measure_alu")
 
 
 class FramParams(ctypes.Structure):
@@ -41,7 +42,7 @@ class FramScene(ctypes.Structure):
                 ("n_vs_total", ctypes.c_int64), ("rir_total", ctypes.c_int64), ("array_radius", ctypes.c_double),
                 ("dims", ctypes.c_void_p), ("rt60", ctypes.c_void_p), ("src", ctypes.c_void_p),
                 ("mic", ctypes.c_void_p), ("n_vs", ctypes.c_void_p), ("vs_off", ctypes.c_void_p),
-                ("rir_len", ctypes.c_void_p), ("rir_off", ctypes.c_void_p)]
+                ("rir_len", ctypes.c_void_p), ("rir_off", ctypes.c_void_p), ("room_base", ctypes.c_int64)]
 
 
 class FramSpatial(ctypes.Structure):
@@ -87,6 +88,7 @@ def lib():
         L.fram_synthesize_backward_prepared.argtypes = L.fram_synthesize_backward.argtypes
         L.fram_synthesize_noalloc.argtypes = [S, P, vp, vp, vp, vp, vp, vp, vp]
         L.fram_autotune.argtypes = [S, P, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_int32)]
+        L.fram_measure_alu.argtypes = [i32, i64, ctypes.POINTER(ctypes.c_double), vp]
         for name in EXPORTED[3:]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L

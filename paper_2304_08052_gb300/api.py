@@ -88,11 +88,13 @@ def _stream():
 
 class DeviceScene:
     """A scene resident on the GPU plus its layout and a workspace.  The workspace is
-    allocated once here (by PyTorch), never by the library."""
+    allocated once here (by PyTorch), never by the library.  room_base is the index of room 0
+    in a larger batch (a shard of that batch draws the images the whole batch gives its rooms)."""
 
-    def __init__(self, scene, params: Params, device: str = "cuda"):
+    def __init__(self, scene, params: Params, device: str = "cuda", room_base: int = 0):
         self.scene = scene
         self.params = params
+        self.room_base = int(room_base)
         self.B, self.S, self.M = int(scene.B), int(scene.S), int(scene.M)
         self.rir_len, self.rir_off, self.vs_off = layout(scene.rt60, scene.n_vs, self.S, self.M, params.fs)
         self.n_vs_total = int(self.vs_off[-1])
@@ -133,7 +135,8 @@ class DeviceScene:
                          _ptr(dims, 3 * B, name="dims"), _ptr(rt60, B, name="rt60"), _ptr(src, 3 * B * S, name="src"),
                          _ptr(mic, 3 * B * M, name="mic"),
                          cp(getattr(self, "n_vs", None)), cp(getattr(self, "vs_off_d", None)),
-                         cp(getattr(self, "rir_len_d", None)), cp(getattr(self, "rir_off_d", None)))
+                         cp(getattr(self, "rir_len_d", None)), cp(getattr(self, "rir_off_d", None)),
+                         getattr(self, "room_base", 0))
 
     def channel(self, buf: torch.Tensor, b: int, s: int, m: int) -> torch.Tensor:
         L = int(self.rir_len[b])
@@ -435,3 +438,14 @@ def autotune(sc: DeviceScene, vs: Images, rir: Optional[torch.Tensor] = None) ->
                               ctypes.c_void_p(sc.ws.data_ptr()),
                               ctypes.c_size_t(sc.ws_bytes), _stream(), ctypes.byref(out)))
     return int(out.value)
+
+
+def measure_alu(kind: int, iters: int) -> dict:
+    """fram_measure_alu: throughput of one instruction kind (0 FP32 FMA, 1 packed FP32 FMA,
+    2 MUFU reciprocal) on this GPU.  Returns the kernel time, SM cycles, lane operations and the
+    derived lane operations per SM per clock and per second."""
+    res = (ctypes.c_double * 4)()
+    check(lib().fram_measure_alu(int(kind), int(iters), res, _stream()))
+    ms, cyc, ops, sms = (float(v) for v in res)
+    return {"ms": ms, "sm_cycles": cyc, "lane_ops": ops, "sms": int(sms),
+            "per_sm_per_clock": ops / (cyc * sms), "per_s": ops / (ms * 1e-3), "clock_mhz": cyc / (ms * 1e3)}

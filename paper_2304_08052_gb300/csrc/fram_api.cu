@@ -8,9 +8,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fram_internal.cuh"
 
 namespace fram {
+
+// A named NVTX range around an entry point's host work and launches, so a timeline tool shows
+// the sampler, the preparation, the synthesis and the adjoint as separate ranges (the NVTX
+// calls do nothing unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 static thread_local std::string g_last_error;
 
@@ -162,6 +174,8 @@ static int check_scene(const fram_scene* sc, bool need_arrays)
     if (sc->n_vs_total < 0 || sc->rir_total < 0 || sc->max_len < 0) return fail(FRAM_EINVAL, "negative totals");
     if (sc->B > 0 && sc->max_len < 1) return fail(FRAM_EINVAL, "max_len must be >= 1");
     if (!(sc->array_radius >= 0.0) || !std::isfinite(sc->array_radius)) return fail(FRAM_EINVAL, "array_radius must be finite and >= 0");
+    if (sc->room_base < 0 || sc->room_base + (int64_t)sc->B > (int64_t(1) << 32))
+        return fail(FRAM_EINVAL, "need 0 <= room_base and room_base + B <= 2^32 (the Philox room word)");
     if (need_arrays && sc->B > 0) {
         if (!sc->dims || !sc->rt60 || !sc->src || !sc->mic || !sc->n_vs || !sc->vs_off || !sc->rir_len || !sc->rir_off)
             return fail(FRAM_EINVAL, "scene device arrays must not be null");
@@ -177,6 +191,18 @@ static int check_ws(const fram_scene* sc, const fram_params* p, void* ws, size_t
     if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(FRAM_EWORKSPACE, "workspace must be 256-byte aligned");
     if (bytes < w.total) return fail(FRAM_EWORKSPACE, "workspace too small: %zu < %zu bytes", bytes, w.total);
     *out = w;
+    return FRAM_OK;
+}
+
+int workspace_bytes_at_launch_tile(const fram_scene* sc, const fram_params* p, size_t* bytes)
+{
+    int rc;
+    if ((rc = check_params(p)) != FRAM_OK) return rc;
+    if ((rc = check_scene(sc, false)) != FRAM_OK) return rc;
+    if (!bytes) return fail(FRAM_EINVAL, "bytes is null");
+    const WsLayout w = ws_layout(*sc, tile_for(sc, p), p->delay_mode, p->fs);
+    if (w.max_tiles > 0xffff) return fail(FRAM_EINVAL, "too many tiles per RIR (raise the tile length)");
+    *bytes = w.total;
     return FRAM_OK;
 }
 
@@ -198,6 +224,7 @@ static LaunchArgs make_args(const fram_scene* sc, const fram_params* p, const Ws
     a.margin_i = (int32_t)std::ceil(sc->array_radius * q) + 3;
     a.n_vs_total = sc->n_vs_total;
     a.rir_total = sc->rir_total;
+    a.room_base = (uint32_t)sc->room_base;
     a.dims = sc->dims; a.rt60 = sc->rt60; a.src = sc->src; a.mic = sc->mic;
     a.n_vs = sc->n_vs; a.vs_off = sc->vs_off; a.rir_len = sc->rir_len; a.rir_off = sc->rir_off;
     unsigned char* base = static_cast<unsigned char*>(ws);
@@ -246,7 +273,7 @@ using namespace fram;
 
 extern "C" {
 
-int fram_version(void) { return 10100; }
+int fram_version(void) { return 10200; }
 
 const char* fram_last_error(void) { return g_last_error.c_str(); }
 
@@ -305,6 +332,7 @@ int fram_sample(const fram_scene* scene, const fram_params* p, uint64_t seed, co
                 float* vs_pos_hi, float* vs_pos_lo, float* vs_g, float* r, uint32_t* words,
                 void* workspace, size_t workspace_bytes, void* stream)
 {
+    NvtxRange nvtx("fram_sample");
     int rc;
     if ((rc = check_params(p)) != FRAM_OK) return rc;
     if ((rc = check_scene(scene, true)) != FRAM_OK) return rc;
@@ -335,6 +363,7 @@ static int common_checks(const fram_scene* scene, const fram_params* p, const fl
 int fram_prepare(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi, const float* vs_pos_lo,
                  const float* r, void* workspace, size_t workspace_bytes, void* stream)
 {
+    NvtxRange nvtx("fram_prepare");
     int rc;
     if ((rc = check_params(p)) != FRAM_OK) return rc;
     if ((rc = check_scene(scene, true)) != FRAM_OK) return rc;
@@ -352,6 +381,7 @@ int fram_synthesize_prepared(const fram_scene* scene, const fram_params* p, cons
                              const float* vs_pos_lo, const float* vs_g, const float* r, float* rir, float* early,
                              void* workspace, size_t workspace_bytes, void* stream)
 {
+    NvtxRange nvtx("fram_synthesize_prepared");
     WsLayout w;
     int rc = common_checks(scene, p, vs_pos_hi, vs_g, r, workspace, workspace_bytes, &w);
     if (rc != FRAM_OK) return rc;
@@ -393,6 +423,7 @@ int fram_synthesize_backward_prepared(const fram_scene* scene, const fram_params
                                       float* grad_src, float* grad_r, float* grad_g, void* workspace,
                                       size_t workspace_bytes, void* stream)
 {
+    NvtxRange nvtx("fram_synthesize_backward_prepared");
     WsLayout w;
     int rc = common_checks(scene, p, vs_pos_hi, vs_g, r, workspace, workspace_bytes, &w);
     if (rc != FRAM_OK) return rc;
@@ -430,6 +461,7 @@ int fram_sample_backward(const fram_scene* scene, const fram_params* p, uint64_t
                          const float* grad_mic_in, float* grad_src, float* grad_mic, float* grad_t60, float* grad_dims,
                          void* workspace, size_t workspace_bytes, void* stream)
 {
+    NvtxRange nvtx("fram_sample_backward");
     int rc;
     if ((rc = check_params(p)) != FRAM_OK) return rc;
     if ((rc = check_scene(scene, true)) != FRAM_OK) return rc;
@@ -452,6 +484,7 @@ int fram_autotune(const fram_scene* scene, const fram_params* p, const float* vs
                   const float* vs_g, const float* r, float* rir, void* workspace, size_t workspace_bytes, void* stream,
                   int32_t* tile_out)
 {
+    NvtxRange nvtx("fram_autotune");
     WsLayout w0;
     fram_params base = *p;
     base.tile = 0;

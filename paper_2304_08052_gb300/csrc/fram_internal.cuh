@@ -351,6 +351,7 @@ struct LaunchArgs {
     int32_t margin_i;       // ceil(array_radius fs/c0) + 3: halo of the adjoint's staged gradient
     int64_t n_vs_total;     // host sizes, used to bound every device index
     int64_t rir_total;
+    uint32_t room_base;     // Philox room word of room 0 (the room's index in a larger batch)
     const float* dims;
     const float* rt60;
     const float* src;
@@ -415,6 +416,11 @@ cudaError_t launch_backward(const LaunchArgs& a, const float* pos_hi, const floa
 
 int device_sm_count();
 int record_error(int code, const char* msg);   // sets fram_last_error's text, returns code
+
+// Workspace bytes that a call with these parameters uses at the tile it actually launches with
+// (p->tile, or the autotuned / default tile when p->tile is 0); fram_workspace_size instead
+// sizes for every tile.  Checks the parameters and the scene like fram_workspace_size.
+int workspace_bytes_at_launch_tile(const fram_scene* scene, const fram_params* p, size_t* bytes);
 
 // Dynamic shared memory of one synthesis CTA for tile length T.
 int synth_smem_total(int T);

@@ -10,26 +10,47 @@
 //
 // How: the scratch lives in one file-scope __device__ array of kStaticScratchBytes (16 MiB).
 // Every GPU that loads libfram reserves it for the life of the process.  Host code cannot use
-// the array's name as a device address, so the first call on each device (with that device
-// current) asks the runtime for the address with cudaGetSymbolAddress and caches it; that
-// first call should happen before any stream capture begins.  No call here allocates memory.
+// the array's name as a device address; the address comes from cudaGetSymbolAddress, and it
+// belongs to the CUDA context that is current (each context -- the device's primary context, a
+// context a host application created with the driver API, or a primary context re-created after
+// cudaDeviceReset -- has its own copy of the array).  So the address is looked up again on every
+// call made outside stream capture, and remembered per context for calls made while the stream is
+// being captured (a capture may not trigger the lookup).  No call here allocates memory.
 #include <cstdio>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "fram_internal.cuh"
-
-namespace fram {
-}
 
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(16) << 20;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
+typedef int (*CtxGetCurrentFn)(void** ctx);   // cuCtxGetCurrent, through the runtime's entry-point query
+
 std::mutex g_scratch_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
+CtxGetCurrentFn g_ctx_get = nullptr;
+bool g_ctx_get_tried = false;
+std::vector<std::pair<void*, void*>> g_scratch_by_ctx;   // (context, scratch address)
+
+// The current context (null on error or when the driver entry point is unavailable).
+void* current_context()
+{
+    if (!g_ctx_get_tried) {
+        g_ctx_get_tried = true;
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get = reinterpret_cast<CtxGetCurrentFn>(fn);
+    }
+    void* ctx = nullptr;
+    if (!g_ctx_get || g_ctx_get(&ctx) != 0) return nullptr;
+    return ctx;
+}
 
 }  // namespace
 
@@ -38,7 +59,7 @@ extern "C" int fram_synthesize_noalloc(const fram_scene* scene, const fram_param
                                        float* early, void* stream)
 {
     size_t need = 0;
-    const int rc = fram_workspace_size(scene, p, &need);
+    const int rc = fram::workspace_bytes_at_launch_tile(scene, p, &need);
     if (rc != FRAM_OK) return rc;
     if (need > kStaticScratchBytes) {
         char msg[256];
@@ -48,21 +69,32 @@ extern "C" int fram_synthesize_noalloc(const fram_scene* scene, const fram_param
                  need, kStaticScratchBytes);
         return fram::record_error(FRAM_EWORKSPACE, msg);
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap);
     if (e != cudaSuccess) return fram::record_error(FRAM_ECUDA, cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return fram::record_error(FRAM_EINVAL, "device index out of range");
     void* ws = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_scratch_mu);
-        if (!g_scratch_ptr[dev]) {
-            void* ptr = nullptr;
-            e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-            if (e != cudaSuccess || !ptr)
+        void* ctx = current_context();
+        if (cap == cudaStreamCaptureStatusNone) {
+            e = cudaGetSymbolAddress(&ws, g_static_scratch);
+            if (e != cudaSuccess || !ws)
                 return fram::record_error(FRAM_ECUDA, e != cudaSuccess ? cudaGetErrorString(e) : "null symbol address");
-            g_scratch_ptr[dev] = ptr;
+            if (ctx) {
+                bool found = false;
+                for (auto& kv : g_scratch_by_ctx)
+                    if (kv.first == ctx) { kv.second = ws; found = true; }
+                if (!found) g_scratch_by_ctx.emplace_back(ctx, ws);
+            }
+        } else {
+            for (const auto& kv : g_scratch_by_ctx)
+                if (ctx && kv.first == ctx) ws = kv.second;
+            if (!ws)
+                return fram::record_error(FRAM_ECUDA,
+                                          "fram_synthesize_noalloc: the first call in this CUDA context must come "
+                                          "before stream capture (the scratch address is looked up outside capture)");
         }
-        ws = g_scratch_ptr[dev];
     }
     // The status word and work counters at the start of the scratch are cleared by the
     // preparation inside fram_synthesize; everything else is rewritten before it is read.

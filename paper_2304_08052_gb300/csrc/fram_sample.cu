@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(256) sample_kernel(LaunchArgs a, uint64_t seed
     const float nanf_ = __int_as_float(0x7fc00000);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int64_t v = row0 + i;
-        const u4 w = philox4x32_10(u4{(uint32_t)i, (uint32_t)s, (uint32_t)b, 0u}, k0, k1);
+        const u4 w = philox4x32_10(u4{(uint32_t)i, (uint32_t)s, a.room_base + (uint32_t)b, 0u}, k0, k1);
         if (words) {
             reinterpret_cast<uint4*>(words)[v] = make_uint4(w.x, w.y, w.z, w.w);
         }
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(256) sample_backward_kernel(LaunchArgs a, uint
     float dD0 = 0.f, dcT = 0.f, dRR = 0.f, dc0 = 0.f, dc1 = 0.f, dc2 = 0.f;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int64_t v = row0 + i;
-        const u4 w = philox4x32_10(u4{(uint32_t)i, (uint32_t)s, (uint32_t)b, 0u}, key_s[0], key_s[1]);
+        const u4 w = philox4x32_10(u4{(uint32_t)i, (uint32_t)s, a.room_base + (uint32_t)b, 0u}, key_s[0], key_s[1]);
         const SampledImage im = sample_image(C, w);
         const float gx = grad_vs[3 * v], gy = grad_vs[3 * v + 1], gz = grad_vs[3 * v + 2];
         const float gg = grad_g ? grad_g[v] : 0.0f;

@@ -62,6 +62,20 @@ class Scene:
                      dict(self.meta, parent=self.name, rooms=rooms.tolist()))
 
 
+def concat(parts, name: str = None) -> Scene:
+    """One scene holding the rooms of `parts` (same S, M, fs and half length) in order."""
+    if not parts:
+        raise ValueError("concat needs at least one scene")
+    p0 = parts[0]
+    for p in parts[1:]:
+        if (p.S, p.M, p.fs, p.half_len) != (p0.S, p0.M, p0.fs, p0.half_len):
+            raise ValueError("concat: scenes differ in sources, mics, sample rate or half length")
+    cat = lambda f: np.concatenate([getattr(p, f) for p in parts])
+    return Scene(name or p0.name, sum(p.B for p in parts), p0.S, p0.M, p0.fs, p0.half_len, cat("dims"),
+                 cat("rt60"), cat("src"), cat("mic"), cat("n_vs"),
+                 dict(p0.meta, blocks=[p.meta.get("seed") for p in parts]))
+
+
 def _linear_array(centre, M, spacing):
     off = (np.arange(M) - (M - 1) / 2.0) * spacing
     pos = np.repeat(np.asarray(centre, np.float64)[None, :], M, axis=0)

@@ -34,7 +34,7 @@ def test_exports_every_declared_symbol(L):
 
 
 def test_version_and_defaults(L):
-    assert L.fram_version() == 10100
+    assert L.fram_version() == 10200
     p = _lib.FramParams()
     L.fram_default_params(ctypes.byref(p))
     assert (p.alpha, p.beta, p.a, p.b, p.tau, p.c0) == (0.25, 1.0, -2.0, 2.0, 0.25, 343.0)
@@ -82,6 +82,11 @@ def test_workspace_size_and_param_validation(L):
     for bad in (dict(S=0), dict(M=0), dict(M=65), dict(B=-1)):
         s = _scene_struct(**bad)
         assert L.fram_workspace_size(ctypes.byref(s), ctypes.byref(p.c()), ctypes.byref(n)) == _lib.FRAM_EINVAL
+    # room_base: the Philox room word of room 0; room_base + B must fit in 32 bits.
+    for base, rc in ((0, 0), (2**32 - 4, 0), (2**32 - 3, _lib.FRAM_EINVAL), (-1, _lib.FRAM_EINVAL)):
+        s = _scene_struct()
+        s.room_base = base
+        assert L.fram_workspace_size(ctypes.byref(s), ctypes.byref(p.c()), ctypes.byref(n)) == rc, base
 
 
 def test_entry_points_reject_bad_arguments_before_any_launch(L):

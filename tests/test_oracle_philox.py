@@ -7,7 +7,7 @@ seed_hi)); a generator offset of 4 * 65536 * (x + 2^32 y) words starts it at cou
 (x, y, 0, 0).  Matching it over more than one 65536-block wrap and at large offsets pins the
 round function, the key schedule, the key words and counter words 0, 1 and 2.  Counter word 3
 is the draw's tag, always 0 in this method.  The device implementation is compared with the
-oracle bit for bit on the GPU (tests/test_gpu_sampler.py).
+oracle bit for bit on the GPU (tests/test_gpu_parity.py, the sampler cases).
 """
 import ctypes
 import os

@@ -6,20 +6,20 @@ allocation (cudaMalloc and cudaFree can synchronise the device), or a service ru
 fixed device-memory budget.  They pass inputs and outputs they already own, and the library
 uses a static 16 MiB scratch array instead of a caller workspace.  This file checks that
 entry point against fram_synthesize on two calls in a row (the second call reuses scratch
-left over from the first) and that an oversized scene is refused before any GPU work.
+left over from the first): both run the same kernels with the same tile on the same inputs and
+sum every sample in a fixed order, so the outputs must be identical bit for bit.  It covers the
+continuous path with and without the early RIR and the multi-rate path (delay_mode 1), and that
+an oversized scene is refused before any GPU work.
 It is named to run last so that a failure here never hides the other tests' results.
 """
 import ctypes
 
-import numpy as np
 import pytest
 import torch
 
 from paper_2304_08052_gb300 import _lib, api, scenes
 
 pytestmark = pytest.mark.gpu
-
-TOL = 1e-5
 
 
 def _call_noalloc(ds, vs, rir, early):
@@ -30,31 +30,37 @@ def _call_noalloc(ds, vs, rir, early):
                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
-def test_noalloc_matches_workspace_entry_point_on_two_calls():
-    # The first 128 rooms of the 256-room batch: their workspace fits the 16 MiB scratch.
-    sc = scenes.batch_256(0).subset(range(128))
-    params = api.Params(fs=sc.fs, half_len=sc.half_len)
-    ds = api.DeviceScene(sc, params)
-    assert ds.ws_bytes <= 16 << 20
-    vs = api.sample(ds, seed=21)
-    ref, ref_e = api.synthesize(ds, vs, early=True)
+def _check_two_calls(ds, vs, with_early):
+    res = api.synthesize(ds, vs, early=with_early)
+    ref, ref_e = res if with_early else (res, None)
     torch.cuda.synchronize()
     assert ds.status() == 0
-    ref_np, ref_e_np = ref.cpu().numpy(), ref_e.cpu().numpy()
     for _ in range(2):
         out = torch.full_like(ref, float("nan"))
-        out_e = torch.full_like(ref, float("nan"))
+        out_e = torch.full_like(ref, float("nan")) if with_early else None
         assert _call_noalloc(ds, vs, out, out_e) == _lib.FRAM_OK, _lib.lib().fram_last_error()
         torch.cuda.synchronize()
-        got, got_e = out.cpu().numpy(), out_e.cpu().numpy()
-        for b in range(sc.B):
-            for s in range(sc.S):
-                L = int(ds.rir_len[b])
-                o = int(ds.rir_off[b]) + s * sc.M * L
-                sl = slice(o, o + sc.M * L)
-                peak = np.abs(ref_np[sl]).max()
-                assert np.abs(got[sl] - ref_np[sl]).max() <= TOL * peak
-                assert np.abs(got_e[sl] - ref_e_np[sl]).max() <= TOL * peak
+        assert torch.equal(out, ref)
+        if with_early:
+            assert torch.equal(out_e, ref_e)
+
+
+@pytest.mark.parametrize("with_early", [True, False])
+def test_noalloc_matches_workspace_entry_point_on_two_calls(with_early):
+    # The first 128 rooms of the 256-room batch: their workspace fits the 16 MiB scratch.
+    sc = scenes.batch_256(0).subset(range(128))
+    ds = api.DeviceScene(sc, api.Params(fs=sc.fs, half_len=sc.half_len))
+    assert ds.ws_bytes <= 16 << 20
+    vs = api.sample(ds, seed=21)
+    _check_two_calls(ds, vs, with_early)
+
+
+def test_noalloc_multirate_path_on_two_calls():
+    sc = scenes.tiny(seed=4, B=3, S=2, M=3, images=60)
+    ds = api.DeviceScene(sc, api.Params(fs=sc.fs, half_len=sc.half_len, delay_mode=1))
+    assert ds.ws_bytes <= 16 << 20
+    vs = api.sample(ds, seed=8)
+    _check_two_calls(ds, vs, True)
 
 
 def test_noalloc_refuses_scenes_beyond_the_static_scratch():
