@@ -341,7 +341,9 @@ def main():
     clock_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     alu = measure_alu_lanes(api)
-    fp32_lanes = alu["fp32_fma"]["per_sm_per_clock"]
+    # The FP32 pipe's lane rate: the better of the scalar and the packed probe (the packed one
+    # issues half as many instructions, so loop overhead hides less of the pipe).
+    fp32_lanes = max(alu["fp32_fma"]["per_sm_per_clock"], alu["fp32x2_fma"]["per_sm_per_clock"])
     mufu_lanes = alu["mufu_rcp"]["per_sm_per_clock"]
 
     for k in range(args.warmup):

@@ -257,10 +257,22 @@ int fram_synthesize_backward_prepared(const fram_scene* scene, const fram_params
  * impulses per CTA.  Writes the choice to *tile_out (nullable).  Overwrites `rir`.
  * Synchronises the stream: call it before capturing a CUDA graph.  The workspace must be sized
  * with p->tile == 0 (fram_workspace_size then covers every candidate).
+ * Persistence (opt-in): if the environment variable FRAM_AUTOTUNE_CACHE names a file, each
+ * choice is also written there (one JSON object per line, keyed by the GPU's name and SM count
+ * and the workload group above; rewritten through a temporary file and a rename), and a later
+ * process's first tile = 0 launch on that GPU model reads it, so it need not re-tune.  Errors
+ * reading or writing the file are ignored (the in-memory choice still applies).
  */
 int fram_autotune(const fram_scene* scene, const fram_params* p, const float* vs_pos_hi, const float* vs_pos_lo,
                   const float* vs_g, const float* r, float* rir, void* workspace, size_t workspace_bytes,
                   void* stream, int32_t* tile_out);
+
+/*
+ * Host only (but queries the current device).  The tile length a call with these parameters
+ * launches with: p->tile if nonzero, else the tile fram_autotune chose for this kind of workload
+ * (in this process, or from the FRAM_AUTOTUNE_CACHE file), else the library default 1024.
+ */
+int fram_tuned_tile(const fram_scene* scene, const fram_params* p, int32_t* tile);
 
 /*
  * Synchronises `stream` and reads the device status word that the last call which used
@@ -295,9 +307,10 @@ int fram_synthesize_noalloc(const fram_scene* scene, const fram_params* p, const
 /*
  * Throughput probe for the roofline denominators of the synthesis and the adjoint (the paper has
  * no counterpart: it measures this GPU).  kind 0: scalar FP32 fused multiply-add; 1: packed FP32
- * fma.rn.f32x2 (two lane operations per instruction); 2: MUFU reciprocal rcp.approx.ftz.f32.
+ * fma.rn.f32x2 (two lane operations per instruction); 2: MUFU reciprocal rcp.approx.ftz.f32
+ * (chained as x -> 1/x + b, the add on the FP32 pipe).
  * Launches 8 CTAs of 256 threads per SM, each thread running 8 independent chains of
- * iters x 16 operations, and synchronises the stream.  result (host, 4 doubles): kernel time in
+ * iters x 64 operations, and synchronises the stream.  result (host, 4 doubles): kernel time in
  * ms (CUDA events on `stream`), SM clock cycles of the longest CTA (clock64), total lane
  * operations, SM count.  Lane operations per SM per clock = result[2] / (result[1] result[3]).
  * Uses a static device buffer of one cycle count per CTA; allocates nothing.  Returns

@@ -26,7 +26,7 @@ EXPORTED = ("fram_version", "fram_last_error", "fram_default_params", "fram_layo
             "fram_sample", "fram_synthesize", "fram_synthesize_backward", "fram_status", "fram_prepare",
             "fram_synthesize_prepared", "fram_synthesize_backward_prepared", "fram_synthesize_noalloc",
             "fram_autotune", "fram_sample_backward", "fram_spatialize_workspace_size", "fram_spatialize",
-            "fram_measure_alu")
+            "fram_measure_alu", "fram_tuned_tile")
 
 
 class FramParams(ctypes.Structure):
@@ -89,6 +89,7 @@ def lib():
         L.fram_synthesize_noalloc.argtypes = [S, P, vp, vp, vp, vp, vp, vp, vp]
         L.fram_autotune.argtypes = [S, P, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_int32)]
         L.fram_measure_alu.argtypes = [i32, i64, ctypes.POINTER(ctypes.c_double), vp]
+        L.fram_tuned_tile.argtypes = [S, P, ctypes.POINTER(ctypes.c_int32)]
         for name in EXPORTED[3:]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L

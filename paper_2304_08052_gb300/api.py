@@ -449,3 +449,10 @@ def measure_alu(kind: int, iters: int) -> dict:
     ms, cyc, ops, sms = (float(v) for v in res)
     return {"ms": ms, "sm_cycles": cyc, "lane_ops": ops, "sms": int(sms),
             "per_sm_per_clock": ops / (cyc * sms), "per_s": ops / (ms * 1e-3), "clock_mhz": cyc / (ms * 1e3)}
+
+
+def tuned_tile(sc: DeviceScene) -> int:
+    """fram_tuned_tile: the tile length a launch with sc.params launches with."""
+    out = ctypes.c_int32(0)
+    check(lib().fram_tuned_tile(ctypes.byref(sc.c_scene()), ctypes.byref(sc.params.c()), ctypes.byref(out)))
+    return int(out.value)

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -138,6 +139,110 @@ struct TuneKey {
 static std::mutex g_tune_mu;
 static std::vector<std::pair<TuneKey, int>> g_tune;
 
+// ---- persistent tile cache (opt-in: the file named by FRAM_AUTOTUNE_CACHE) ------------------
+// One line per tuned workload group, keyed by the GPU's name and SM count (so a cache copied to
+// a different GPU model is not used) and the group of TuneKey:
+//   {"gpu": "<name>", "sms": N, "K": K, "fs": fs, "S": S, "M": M, "len_oct": o, "dens_bin": d, "tile": T}
+// Read once per device the first time a tile = 0 launch finds no in-memory choice; rewritten
+// whole (to a temporary file, then renamed) by fram_autotune.
+struct DevId {
+    char name[256];
+    int sms;
+};
+
+static bool dev_id(int dev, DevId* id)
+{
+    cudaDeviceProp prop;
+    if (dev < 0 || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return false;
+    snprintf(id->name, sizeof id->name, "%s", prop.name);
+    for (char* c = id->name; *c; ++c)
+        if (*c == '"' || *c == '\\') *c = '_';
+    id->sms = prop.multiProcessorCount;
+    return true;
+}
+
+struct CacheLine {
+    DevId id;
+    TuneKey k;
+    int tile;
+};
+
+static std::vector<CacheLine> read_cache_file(const char* path)
+{
+    std::vector<CacheLine> out;
+    FILE* f = path ? fopen(path, "r") : nullptr;
+    if (!f) return out;
+    char line[1024];
+    while (fgets(line, sizeof line, f)) {
+        CacheLine c{};
+        if (sscanf(line,
+                   " {\"gpu\": \"%255[^\"]\", \"sms\": %d, \"K\": %d, \"fs\": %lf, \"S\": %d, \"M\": %d, "
+                   "\"len_oct\": %d, \"dens_bin\": %d, \"tile\": %d}",
+                   c.id.name, &c.id.sms, &c.k.K, &c.k.fs, &c.k.S, &c.k.M, &c.k.len_oct, &c.k.dens_bin, &c.tile) == 9 &&
+            (c.tile == 256 || c.tile == 512 || c.tile == 1024 || c.tile == 2048))
+            out.push_back(c);
+    }
+    fclose(f);
+    return out;
+}
+
+static void write_cache_file(const char* path, const std::vector<CacheLine>& lines)
+{
+    std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return;                       // the cache is an optimisation: failures are silent
+    bool ok = true;
+    for (const CacheLine& c : lines)
+        ok = ok && fprintf(f,
+                           "{\"gpu\": \"%s\", \"sms\": %d, \"K\": %d, \"fs\": %.17g, \"S\": %d, \"M\": %d, "
+                           "\"len_oct\": %d, \"dens_bin\": %d, \"tile\": %d}\n",
+                           c.id.name, c.id.sms, c.k.K, c.k.fs, c.k.S, c.k.M, c.k.len_oct, c.k.dens_bin, c.tile) > 0;
+    ok = (fclose(f) == 0) && ok;
+    if (ok) rename(tmp.c_str(), path);
+    else remove(tmp.c_str());
+}
+
+static bool same_group(const CacheLine& c, const DevId& id, const TuneKey& k)
+{
+    return strcmp(c.id.name, id.name) == 0 && c.id.sms == id.sms && c.k.K == k.K && c.k.fs == k.fs &&
+           c.k.S == k.S && c.k.M == k.M && c.k.len_oct == k.len_oct && c.k.dens_bin == k.dens_bin;
+}
+
+static std::vector<int> g_cache_loaded;   // devices whose cache lines are in g_tune (under g_tune_mu)
+
+// Under g_tune_mu: merge the cache file's lines for device k.dev into g_tune, once per device.
+static void load_cache_locked(int dev)
+{
+    const char* path = getenv("FRAM_AUTOTUNE_CACHE");
+    if (!path || !*path || dev < 0) return;
+    for (int d : g_cache_loaded)
+        if (d == dev) return;
+    g_cache_loaded.push_back(dev);
+    DevId id;
+    if (!dev_id(dev, &id)) return;
+    for (const CacheLine& c : read_cache_file(path)) {
+        if (strcmp(c.id.name, id.name) != 0 || c.id.sms != id.sms) continue;
+        TuneKey k = c.k;
+        k.dev = dev;
+        bool found = false;
+        for (const auto& e : g_tune) found = found || e.first == k;
+        if (!found) g_tune.push_back({k, c.tile});
+    }
+}
+
+static void store_cache(const TuneKey& k, int tile)
+{
+    const char* path = getenv("FRAM_AUTOTUNE_CACHE");
+    DevId id;
+    if (!path || !*path || !dev_id(k.dev, &id)) return;
+    std::vector<CacheLine> lines = read_cache_file(path);
+    bool found = false;
+    for (CacheLine& c : lines)
+        if (same_group(c, id, k)) { c.tile = tile; found = true; }
+    if (!found) lines.push_back(CacheLine{id, k, tile});
+    write_cache_file(path, lines);
+}
+
 static TuneKey tune_key(const fram_scene* sc, const fram_params* p)
 {
     TuneKey k{};
@@ -158,6 +263,9 @@ static int tile_for(const fram_scene* sc, const fram_params* p)
     if (p->tile) return p->tile;
     const TuneKey k = tune_key(sc, p);
     std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto& e : g_tune)
+        if (e.first == k) return e.second;
+    load_cache_locked(k.dev);
     for (const auto& e : g_tune)
         if (e.first == k) return e.second;
     return kDefaultTile;
@@ -529,8 +637,19 @@ int fram_autotune(const fram_scene* scene, const fram_params* p, const float* vs
         for (auto& ent : g_tune)
             if (ent.first == k) { ent.second = best; found = true; }
         if (!found) g_tune.push_back({k, best});
+        store_cache(k, best);
     }
     if (tile_out) *tile_out = best;
+    return FRAM_OK;
+}
+
+int fram_tuned_tile(const fram_scene* scene, const fram_params* p, int32_t* tile)
+{
+    int rc;
+    if ((rc = check_params(p)) != FRAM_OK) return rc;
+    if ((rc = check_scene(scene, false)) != FRAM_OK) return rc;
+    if (!tile) return fail(FRAM_EINVAL, "tile is null");
+    *tile = tile_for(scene, p);
     return FRAM_OK;
 }
 

@@ -15,7 +15,7 @@ namespace {
 constexpr int kProbeThreads = 256;
 constexpr int kProbeCtasPerSm = 8;
 constexpr int kChains = 8;
-constexpr int kUnroll = 16;
+constexpr int kUnroll = 64;
 constexpr int kMaxProbeCtas = 64 * 1024;
 
 __device__ float g_probe_sink[1];                    // written only if a chain hits a sentinel
@@ -28,7 +28,10 @@ __device__ __forceinline__ float rcp_chain(float x)
     return y;
 }
 
-// kind 0: FFMA, kind 1: packed FFMA (two lanes of work per instruction), kind 2: MUFU reciprocal.
+// kind 0: FFMA, kind 1: packed FFMA (two lanes of work per instruction), kind 2: MUFU reciprocal
+// (each followed by an FP32 add of a runtime constant, so that the compiler cannot fold a
+// reciprocal of a reciprocal back into its argument; the add runs on the FP32 pipe, which has
+// several times the MUFU rate).
 template <int KIND>
 __global__ void __launch_bounds__(kProbeThreads, kProbeCtasPerSm) alu_probe(int64_t iters, float a, float b,
                                                                             float* __restrict__ sink,
@@ -51,7 +54,7 @@ __global__ void __launch_bounds__(kProbeThreads, kProbeCtasPerSm) alu_probe(int6
             for (int k = 0; k < kChains; ++k) {
                 if (KIND == 0) x[k] = __fmaf_rn(x[k], a, b);
                 else if (KIND == 1) y[k] = fma2(y[k], a2, b2);
-                else x[k] = rcp_chain(x[k]);
+                else x[k] = __fadd_rn(rcp_chain(x[k]), b);   // x -> 1/x + b: no fold of two reciprocals
             }
         }
     }

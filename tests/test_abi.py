@@ -164,3 +164,10 @@ def test_binding_checks_tensors_before_handing_pointers():
         api._ptr(torch.zeros(8), 8, name="rir")                  # right type and size, host memory
     with pytest.raises(ValueError, match="dtype"):
         api._ptr(torch.zeros((4, 4), dtype=torch.int64), 16, api._WORD, "words")
+
+
+def test_measure_alu_rejects_bad_arguments(L):
+    res = (ctypes.c_double * 4)()
+    assert L.fram_measure_alu(3, 10, res, None) == _lib.FRAM_EINVAL
+    assert L.fram_measure_alu(0, 0, res, None) == _lib.FRAM_EINVAL
+    assert L.fram_measure_alu(0, 10, None, None) == _lib.FRAM_EINVAL

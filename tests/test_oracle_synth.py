@@ -179,10 +179,9 @@ def test_schroeder_decay_tracks_requested_t60(oracle_mod):
     est = np.array(est)
     rho = stats.spearmanr(est, sc.rt60).correlation
     ratio = np.median(est / sc.rt60)
-    # Eq. 5 places the farthest image 60 dB down at c0*T60, but Eq. 6's reflection-count trend
-    # is quadratic in distance and Eq. 3 puts more images at long distances, so the
-    # -5..-25 dB Schroeder slope is shallower than a straight 60 dB per T60.  With this
-    # project's constants the ratio sits near 2 (calibrated once on three seeds: medians
-    # 1.96-1.99); the pin is the monotone tracking and a frozen band around that value.
+    # This test pins only monotone tracking of the requested T60 across rooms (the band is wide).
+    # The level of the ratio is pinned by test_oracle_envelope.py, which derives the expected
+    # energy envelope from Eq. 2-6 by quadrature (about 2x T60 for this project's alpha, beta, a,
+    # b, tau: Eq. 6's trend is quadratic in distance and Eq. 3 puts more images far away).
     assert rho > 0.9, rho
     assert 1.4 < ratio < 2.8, ratio
