@@ -265,8 +265,8 @@ def main():
         from paper_2304_08052_gb300 import api, build, scenes
         build.build()
         peaks, _ = _measured_peaks()
-        print(json.dumps({"multirate_only": multirate_vs_continuous(torch, api, scenes, peaks, cpu=False)}),
-              flush=True)
+        print(json.dumps({"multirate_only": multirate_vs_continuous(torch, api, scenes, peaks, cpu=False,
+                                                                    rooms=args.rooms)}), flush=True)
         return 0
     if args.spatialize_rooms > 0:
         import torch
@@ -534,7 +534,7 @@ def single_room_latency(torch, api, scenes):
             "ms_median": statistics.median(ms), "ms_min": min(ms), "calls": len(ms)}
 
 
-def multirate_vs_continuous(torch, api, scenes, peaks, cpu=True):
+def multirate_vs_continuous(torch, api, scenes, peaks, cpu=True, rooms=0):
     """The paper's multi-rate output path (delay_mode 1: ~1 MHz impulse grid, two polyphase
     resamplers, 80 Hz high-pass) against the continuous path on batch_1024 with early RIRs:
     fram_sample + fram_synthesize per step.  The multi-rate stages stream an intermediate signal
@@ -542,7 +542,9 @@ def multirate_vs_continuous(torch, api, scenes, peaks, cpu=True):
     high-pass passes (the second rewrites it) and by the second resampler."""
     import math
     sc = scenes.batch_1024(0)
-    out = {"workload": "batch_1024 (1024 rooms x 3 src x 8 mics, 16 kHz, + early RIR)"}
+    if rooms > 0:
+        sc = sc.subset(range(min(rooms, sc.B)))
+    out = {"workload": f"batch_1024 ({sc.B} rooms x 3 src x 8 mics, 16 kHz, + early RIR)"}
     for mode in (0, 1):
         params = api.Params(fs=sc.fs, half_len=sc.half_len, delay_mode=mode)
         ds = api.DeviceScene(sc, params)

@@ -369,8 +369,7 @@ static LaunchArgs make_args(const fram_scene* sc, const fram_params* p, const Ws
         a.mr_y = reinterpret_cast<float*>(base + w.mr_y);
         a.mr_ye = reinterpret_cast<float*>(base + w.mr_ye);
         a.mr_tab = reinterpret_cast<float*>(base + w.mr_tab);
-        a.mr_seg = base + w.mr_seg;
-        a.mr_hk = reinterpret_cast<float*>(base + w.mr_hk);
+        a.mr_order = reinterpret_cast<int32_t*>(base + w.mr_order);
     }
     return a;
 }

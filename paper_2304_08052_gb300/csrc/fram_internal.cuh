@@ -261,8 +261,8 @@ constexpr int kSampleRec = 256;   // bytes per (room, source) record of the samp
 struct WsLayout {
     size_t header, room, direct, src_tile, item_off, items, order, bin_off, perm, key, skey, sconst;
     size_t spa, spb, pos32, samp, irec;
-    size_t mr_y, mr_ye, mr_tab, mr_seg, mr_hk;   // multi-rate mode: intermediate signals, resampling
-                                          // table, high-pass segment records
+    size_t mr_y, mr_ye, mr_tab;           // multi-rate mode: intermediate signals, resampling table
+    size_t mr_order;                      // multi-rate mode: rooms by decreasing RIR length
     size_t part_mic, part_src, part_r, sb_part;
     size_t total;
     int tile;
@@ -325,9 +325,7 @@ inline WsLayout ws_layout(const fram_scene& sc, int tile, int delay_mode = 0, do
         w.mr_y = take(sizeof(float) * inter);
         w.mr_ye = take(sizeof(float) * inter);
         w.mr_tab = take(sizeof(float) * 32 * (size_t)mr.down);
-        const size_t nseg = ((size_t)mr.rl * (size_t)sc.max_len + 8 + 2047) / 2048;
-        w.mr_seg = take(48 * nseg * 2 * (size_t)sc.B * sc.S * sc.M);
-        w.mr_hk = take(sizeof(float) * (4 * (3 * 2048 + 2) + 4));   // high-pass segment-end weights K, G, b0, K again
+        w.mr_order = take(sizeof(int32_t) * ((size_t)sc.B + 1));
     }
     w.part_mic = take(sizeof(float) * 3 * (size_t)w.max_items * sc.M);
     w.part_src = take(sizeof(float) * 3 * (size_t)w.max_items);
@@ -387,8 +385,7 @@ struct LaunchArgs {
     float* mr_y;                     // intermediate signals at r_l fs, per channel
     float* mr_ye;                    // the same for the early RIR
     float* mr_tab;                   // first resampling filter, polyphase rows of 32
-    void* mr_seg;                    // high-pass segment records
-    float* mr_hk;                    // high-pass segment-end weights: K[2048], G[2050] (float4 pairs), b0, K in lane order
+    int32_t* mr_order;               // rooms by decreasing RIR length (ties by index)
     int32_t max_len;                 // max_b L_b
     float* part_mic;
     float* part_src;

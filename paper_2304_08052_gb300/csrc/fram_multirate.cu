@@ -22,11 +22,10 @@
 //                   reference (no fused multiply-add), then each impulse is added with one lane
 //                   per tap into the warp's shared buffer (and into the early buffer when q lies
 //                   in the Eq. 9 window on the high-rate grid).  Tiles go to y1 in global memory.
-//   mr_hpf_end, mr_hpf_scan, mr_hpf_seg   the high-pass, its state as float pairs (poles near
-//                   z = 1 at 80 Hz make a float32 recursion lose ~1e-5 of the peak), run on
-//                   segments of 2048 samples in parallel: each segment's zero-state end state as
-//                   a dot product with precomputed weights, a per-channel propagation of the true
-//                   segment start states, and the recursion writing the result in place.
+//   mr_room_order, mr_hpf_seq   the high-pass, its state and products as float pairs (poles near
+//                   z = 1 at 80 Hz make a float32 recursion lose ~1e-5 of the peak), one thread per
+//                   channel over the whole channel from a zero state, channels grouped into warps by
+//                   room length and staged through shared memory in 64-sample chunks.
 //   mr_down         the second resampler (ratio 1/r_l, compile-time taps), four consecutive output
 //                   samples per thread (each window value read once, four per 16-byte load) from a
 //                   window staged in shared memory.
@@ -355,22 +354,18 @@ __global__ void __launch_bounds__(kMrThreads) mr_stage_a(LaunchArgs a, bool want
     }
 }
 
-// ---- stage B: the high-pass, segmented -------------------------------------------------------
-// The recursion y0 = b0 (x0 - 2 x1 + x2) - a1 y1 - a2 y2 is linear, so each channel is cut into
-// segments of kMrSeg samples that run in parallel:
-//   mr_hpf_end           one warp per segment: the state (y[e], y[e-1]) the segment leaves from a
-//                        zero output state (with its true input history), as a dot product of its
-//                        inputs with precomputed weights (mr_hpf_tables) -- no recursion;
-//   mr_hpf_scan          one thread per channel: the true start state of every segment,
-//                        s_{j+1} = zs_end_j + A^kMrSeg s_j with A = [[-a1, -a2], [1, 0]] in FP64;
-//   mr_hpf_seg           every segment from its true start state, the recursion in float pairs,
-//                        writing the high-passed signal over its input (the input history was
-//                        saved by the scan).
-constexpr int kMrSeg = 2048;
-
+// ---- stage B: the high-pass, one thread per channel --------------------------------------------
+// The 80 Hz high-pass runs over each channel's L_m intermediate samples from a zero state, in
+// place, as the direct-form recursion y[n] = b0 (x[n] - 2 x[n-1] + x[n-2]) - a1 y[n-1] - a2 y[n-2]
+// with the state and every product as float pairs (the poles lie close to z = 1 at 80 Hz, so a
+// float32 recursion loses ~1e-5 of the peak and the rounding of b0 times the second difference
+// alone, amplified near z = 1, costs about as much).  One thread walks one channel: the 32 channels
+// of a warp are consecutive in (room rank, RIR channel, early channel) order, rooms ranked by
+// decreasing RIR length (mr_room_order), so a warp's channels have nearly equal lengths.  Chunks of
+// 64 samples of the warp's 32 channels are staged through shared memory, so global loads and
+// stores move whole 256-byte pieces of one channel at a time.
 struct HpfCoef {
     f2 b0, a1, a2;
-    double a1d, a2d;
 };
 
 __device__ __forceinline__ HpfCoef hpf_coef(double fsr)
@@ -378,21 +373,11 @@ __device__ __forceinline__ HpfCoef hpf_coef(double fsr)
     const double k = tan(3.14159265358979323846 * 80.0 / fsr);
     const double den = 1.0 + sqrt(2.0) * k + k * k;
     HpfCoef c;
-    c.a1d = 2.0 * (k * k - 1.0) / den;
-    c.a2d = (1.0 - sqrt(2.0) * k + k * k) / den;
     c.b0 = f2_from_double(1.0 / den);
-    c.a1 = f2_from_double(c.a1d);
-    c.a2 = f2_from_double(c.a2d);
+    c.a1 = f2_from_double(2.0 * (k * k - 1.0) / den);
+    c.a2 = f2_from_double((1.0 - sqrt(2.0) * k + k * k) / den);
     return c;
 }
-
-// Per (channel, segment) record: zero-state end state (y[e], y[e-1]) as pairs, true start state
-// (y[s-1], y[s-2]) as pairs, input history (x[s-1], x[s-2]).
-struct SegRec {
-    float zy1h, zy1l, zy2h, zy2l;
-    float sy1h, sy1l, sy2h, sy2l;
-    float x1, x2, pad0, pad1;
-};
 
 __device__ __forceinline__ void mr_channel_of(const LaunchArgs& a, int64_t chan, int& b, int& s, int& m)
 {
@@ -401,161 +386,84 @@ __device__ __forceinline__ void mr_channel_of(const LaunchArgs& a, int64_t chan,
     b = (int)(chan / ((int64_t)a.M * a.S));
 }
 
-// Segment-end weights (FP64, one thread): the all-pole impulse response g_0 = 1,
-// g_k = -a1 g_{k-1} - a2 g_{k-2}; G_k = (g_k, g_{k-1}) is the state (y[e], y[e-1]) that a unit input
-// k samples before the end leaves behind, and K_k = b0 (G_k - 2 G_{k-1} + G_{k-2}) the weight of
-// x[e - k] once the FIR part (1 - 2 z^-1 + z^-2) is folded in (G_{<0} = 0).  The state of a
-// resonator this close to z = 1 amplifies its errors by ~1/sin(theta) (hundreds of samples), so
-// weights and sums are float pairs.  Layout of mr_hk: K_0..K_{kMrSeg-1}, then G_0..G_{kMrSeg+1},
-// each a float4 (hi of both components, then lo of both), then b0 as (hi, lo) padded to a float4,
-// then K again in the order a full segment reads it: entry c kMrSeg/4 + g is the weight of
-// sample 4 g + c, i.e. K_{kMrSeg - 1 - 4 g - c}, so the lanes of a warp read consecutive entries.
-__device__ __forceinline__ float4 pair4(double u, double v)
+// Rooms whose rank needs the all-pairs count below; larger batches keep their own order.
+constexpr int kOrderMax = 65536;
+
+// rank of room b = the number of rooms longer than b, or as long and earlier.
+__global__ void __launch_bounds__(256) mr_room_order(LaunchArgs a)
 {
-    const float uh = (float)u, vh = (float)v;
-    return make_float4(uh, vh, (float)(u - (double)uh), (float)(v - (double)vh));
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= a.B) return;
+    const int Lb = a.room[b].len;
+    int rank = 0;
+    for (int c = 0; c < a.B; ++c) {
+        const int Lc = __ldg(&a.room[c].len);
+        rank += (Lc > Lb) || (Lc == Lb && c < b);
+    }
+    a.mr_order[rank] = b;
 }
 
-// The poles are rho e^(+-i theta) with rho = sqrt(a2), cos theta = -a1 / (2 rho), so
-// g_k = rho^k sin((k + 1) theta) / sin theta in closed form: one thread per k.
-__global__ void __launch_bounds__(256) mr_hpf_tables(LaunchArgs a)
+constexpr int kSeqThreads = 128;
+constexpr int kSeqChunk = 64;              // samples per staged chunk and channel
+constexpr int kSeqRow = kSeqChunk + 4;     // row stride (floats): 16-byte rows, float4 reads of a row conflict-free
+
+// Asynchronous 8-byte global -> shared copy of n bytes (0, 4 or 8), the rest zero-filled.
+__device__ __forceinline__ void cp_async8(float* dst, const float* src, int n)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= kMrSeg + 2) return;
-    const double k = tan(3.14159265358979323846 * 80.0 / ((double)a.rl * a.fs));
-    const double den = 1.0 + sqrt(2.0) * k + k * k;
-    const double a1 = 2.0 * (k * k - 1.0) / den, a2 = (1.0 - sqrt(2.0) * k + k * k) / den, b0 = 1.0 / den;
-    const double rho = sqrt(a2), theta = acos(-a1 / (2.0 * rho)), st = sin(theta);
-    auto g = [&](int n) { return n < 0 ? 0.0 : pow(rho, (double)n) * sin((double)(n + 1) * theta) / st; };
-    float4* K = reinterpret_cast<float4*>(a.mr_hk);
-    float4* G = K + kMrSeg;
-    const double g0 = g(i), g1 = g(i - 1), g2 = g(i - 2), g3 = g(i - 3);
-    G[i] = pair4(g0, g1);
-    if (i < kMrSeg) {
-        const float4 kv = pair4(b0 * (g0 - 2.0 * g1 + g2), b0 * (g1 - 2.0 * g2 + g3));
-        K[i] = kv;
-        const int t = kMrSeg - 1 - i;                 // sample position of weight K_i in a full segment
-        (G + kMrSeg + 3)[(t & 3) * (kMrSeg / 4) + (t >> 2)] = kv;
-    }
-    if (i == 0) {
-        float* tail = reinterpret_cast<float*>(G + kMrSeg + 2);
-        tail[0] = (float)b0;
-        tail[1] = (float)(b0 - (double)tail[0]);
-    }
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
 
-// (sh, sl) += (kh + kl) x, the product exact to a float pair (FMA), the sum a TwoSum.
-__device__ __forceinline__ void pair_fma(float kh, float kl, float x, float& sh, float& sl)
+// Chunk k0 of the warp's 32 channels into the staging tile T (row q = channel q), as one group.
+// anyp: a valid channel pointer of the warp, the (unread) source of zero-byte copies.
+__device__ __forceinline__ void seq_stage_in(float* T, float* const* ptr, const int* len, const float* anyp, int k0,
+                                             int lane)
 {
-    const float p = kh * x;
-    const float e = __fmaf_rn(kl, x, __fmaf_rn(kh, x, -p));
-    const float t = sh + p;
-    const float bb = t - sh;
-    sl += ((sh - (t - bb)) + (p - bb)) + e;
-    sh = t;
+    const int kk = k0 + 2 * lane;
+#pragma unroll 8
+    for (int q = 0; q < 32; ++q) {
+        const int Lq = len[q];
+        const int n = kk + 1 < Lq ? 8 : (kk < Lq ? 4 : 0);
+        cp_async8(T + q * kSeqRow + 2 * lane, n ? ptr[q] + kk : anyp, n);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-// Zero-state end state of every segment, one warp each: sum over the segment's inputs of
-// K_{e-m} x[m] (float-pair products and sums per lane, FP64 across lanes), plus the two
-// input-history samples x[s0-1], x[s0-2] with the weights truncated to the segment.
-constexpr int kHpfEndThreads = 512;
-
-__global__ void __launch_bounds__(kHpfEndThreads) mr_hpf_end(LaunchArgs a, SegRec* __restrict__ seg, int nseg_max,
-                                                              bool with_early)
+__global__ void __launch_bounds__(kSeqThreads) mr_hpf_seq(LaunchArgs a, bool with_early)
 {
-    // the weights (32 KiB, in lane order) are read by every warp: staged once per CTA
-    __shared__ float4 Ks[kMrSeg];
-    {
-        const float4* Kg = reinterpret_cast<const float4*>(a.mr_hk) + kMrSeg + kMrSeg + 3;
-        for (int i = threadIdx.x; i < kMrSeg; i += blockDim.x) Ks[i] = Kg[i];
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t wg = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int64_t nch = (int64_t)a.B * a.S * a.M;
-    const int64_t chans = with_early ? 2 * nch : nch;
-    if (wg >= chans * nseg_max) return;
-    const int64_t cidx = wg / nseg_max;
-    const int j = (int)(wg - cidx * nseg_max);
-    const bool is_early = cidx >= nch;
-    const int64_t chan = is_early ? cidx - nch : cidx;
-    int b, s, m;
-    mr_channel_of(a, chan, b, s, m);
-    const RoomConst rc = a.room[b];
-    if (rc.len < 1) return;
-    const MrChan ch = mr_chan(a, rc, b, s, m);
-    const int64_t s0 = (int64_t)j * kMrSeg;
-    if (s0 >= ch.Lm) return;
-    const int L = (int)((s0 + kMrSeg < ch.Lm ? s0 + kMrSeg : ch.Lm) - s0);
-    const float* x = (is_early ? a.mr_ye : a.mr_y) + ch.off + s0;
-    const float4* G = reinterpret_cast<const float4*>(a.mr_hk) + kMrSeg;
-    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-    if (L == kMrSeg) {           // full segment: lane-order weights from shared memory
-        for (int g = lane; g < kMrSeg / 4; g += 32) {   // x[s0 + 4 g .. + 3]
-            const float4 v = __ldcs(reinterpret_cast<const float4*>(x + 4 * g));
-            const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float4 w = Ks[c * (kMrSeg / 4) + g];
-                pair_fma(w.x, w.z, vv[c], h0, l0);
-                pair_fma(w.y, w.w, vv[c], h1, l1);
-            }
-        }
-    } else {                     // the last, partial segment of a channel: natural-order weights
-        const float4* K = reinterpret_cast<const float4*>(a.mr_hk);
-        for (int i = lane; i < L; i += 32) {
-            const float4 w = __ldg(&K[L - 1 - i]);
-            pair_fma(w.x, w.z, x[i], h0, l0);
-            pair_fma(w.y, w.w, x[i], h1, l1);
-        }
-    }
-    double d0 = (double)h0 + (double)l0, d1 = (double)h1 + (double)l1;
-    if (lane == 0) {   // x[s0-1] (weight b0 (-2 G_{L-1} + G_{L-2})) and x[s0-2] (weight b0 G_{L-1})
-        const float* tail = reinterpret_cast<const float*>(G + kMrSeg + 2);
-        const double b0 = (double)tail[0] + (double)tail[1];
-        const double xm1 = s0 >= 1 ? x[-1] : 0.0, xm2 = s0 >= 2 ? x[-2] : 0.0;
-        const float4 q1 = G[L - 1], q2 = L >= 2 ? G[L - 2] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const double g1a = (double)q1.x + q1.z, g1b = (double)q1.y + q1.w;
-        const double g2a = (double)q2.x + q2.z, g2b = (double)q2.y + q2.w;
-        d0 += b0 * (-2.0 * g1a + g2a) * xm1 + b0 * g1a * xm2;
-        d1 += b0 * (-2.0 * g1b + g2b) * xm1 + b0 * g1b * xm2;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        d0 += __shfl_xor_sync(0xffffffffu, d0, o);
-        d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-    }
-    if (lane == 0) {
-        SegRec& R = seg[cidx * nseg_max + j];
-        R.zy1h = (float)d0; R.zy1l = (float)(d0 - (double)R.zy1h);
-        R.zy2h = (float)d1; R.zy2l = (float)(d1 - (double)R.zy2h);
-    }
-}
-
-__global__ void __launch_bounds__(128) mr_hpf_seg(LaunchArgs a, SegRec* __restrict__ seg, int nseg_max, bool with_early)
-{
-    const int64_t nch = (int64_t)a.B * a.S * a.M;
+    __shared__ __align__(16) float tile[kSeqThreads / 32][2][32 * kSeqRow];
+    __shared__ float* wptr[kSeqThreads / 32][32];
+    __shared__ int wlen[kSeqThreads / 32][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int SM = a.S * a.M;
+    const int CH = SM * (with_early ? 2 : 1);
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t chans = with_early ? 2 * nch : nch;
-    if (t >= chans * nseg_max) return;
-    const int64_t cidx = t / nseg_max;
-    const int j = (int)(t - cidx * nseg_max);
-    const bool is_early = cidx >= nch;
-    const int64_t chan = is_early ? cidx - nch : cidx;
-    int b, s, m;
-    mr_channel_of(a, chan, b, s, m);
-    const RoomConst rc = a.room[b];
-    if (rc.len < 1) return;
-    const MrChan ch = mr_chan(a, rc, b, s, m);
-    const int64_t s0 = (int64_t)j * kMrSeg;
-    if (s0 >= ch.Lm) return;
-    const int64_t s1 = s0 + kMrSeg < ch.Lm ? s0 + kMrSeg : ch.Lm;
-    float* x = (is_early ? a.mr_ye : a.mr_y) + ch.off;
-    SegRec& R = seg[cidx * nseg_max + j];
+    int Lm = 0;
+    float* x = nullptr;
+    if (t < (int64_t)a.B * CH) {
+        const int k = (int)(t / CH), j = (int)(t - (int64_t)k * CH);
+        const int b = a.B <= kOrderMax ? a.mr_order[k] : k;
+        const RoomConst rc = a.room[b];
+        if (rc.len >= 1) {
+            const bool is_early = j >= SM;
+            const int jj = is_early ? j - SM : j;
+            const int s = jj / a.M, m = jj - s * a.M;
+            const MrChan ch = mr_chan(a, rc, b, s, m);
+            Lm = (int)ch.Lm;
+            x = (is_early ? a.mr_ye : a.mr_y) + ch.off;
+        }
+    }
+    float* const* ptr = wptr[wid];
+    const int* len = wlen[wid];
+    wptr[wid][lane] = x;
+    wlen[wid][lane] = Lm;
+    int Lw = Lm;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) Lw = max(Lw, __shfl_xor_sync(0xffffffffu, Lw, o));
+    __syncwarp();
     const HpfCoef c = hpf_coef((double)a.rl * a.fs);
-    float x1 = R.x1, x2 = R.x2;
-    f2 y1{R.sy1h, R.sy1l}, y2{R.sy2h, R.sy2l};
-    // Segments start on multiples of kMrSeg and rows on 16 bytes: whole float4s, then a tail.
+    float x1 = 0.f, x2 = 0.f;
+    f2 y1{0.f, 0.f}, y2{0.f, 0.f};
     auto step = [&](float x0) {
         f2 uu = two_sum(x0, x2);
         uu = f2_add_f(uu, -2.0f * x1);
@@ -563,49 +471,37 @@ __global__ void __launch_bounds__(128) mr_hpf_seg(LaunchArgs a, SegRec* __restri
         x2 = x1; x1 = x0; y2 = y1; y1 = y0;
         return y0.hi + y0.lo;
     };
-    const int64_t s4 = s0 + ((s1 - s0) & ~(int64_t)3);
-    for (int64_t k = s0; k < s4; k += 4) {
-        float4 v = *reinterpret_cast<const float4*>(x + k);
-        float4 o;
-        o.x = step(v.x); o.y = step(v.y); o.z = step(v.z); o.w = step(v.w);
-        *reinterpret_cast<float4*>(x + k) = o;
-    }
-    for (int64_t k = s4; k < s1; ++k) x[k] = step(x[k]);
-}
-
-__global__ void __launch_bounds__(128) mr_hpf_scan(LaunchArgs a, SegRec* __restrict__ seg, int nseg_max, bool with_early)
-{
-    const int64_t nch = (int64_t)a.B * a.S * a.M;
-    const int64_t cidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cidx >= (with_early ? 2 * nch : nch)) return;
-    const bool is_early = cidx >= nch;
-    const int64_t chan = is_early ? cidx - nch : cidx;
-    int b, s, m;
-    mr_channel_of(a, chan, b, s, m);
-    const RoomConst rc = a.room[b];
-    if (rc.len < 1) return;
-    const MrChan ch = mr_chan(a, rc, b, s, m);
-    const float* x = (is_early ? a.mr_ye : a.mr_y) + ch.off;
-    const HpfCoef c = hpf_coef((double)a.rl * a.fs);
-    // P = A^kMrSeg by repeated squaring (kMrSeg is a power of two).
-    double p00 = -c.a1d, p01 = -c.a2d, p10 = 1.0, p11 = 0.0;
-    for (int sq = 1; sq < kMrSeg; sq <<= 1) {
-        const double q00 = p00 * p00 + p01 * p10, q01 = p00 * p01 + p01 * p11;
-        const double q10 = p10 * p00 + p11 * p10, q11 = p10 * p01 + p11 * p11;
-        p00 = q00; p01 = q01; p10 = q10; p11 = q11;
-    }
-    const int nseg = (int)((ch.Lm + kMrSeg - 1) / kMrSeg);
-    double v1 = 0.0, v2 = 0.0;      // true (y[s-1], y[s-2]) at the start of segment j
-    for (int j = 0; j < nseg; ++j) {
-        SegRec& R = seg[cidx * nseg_max + j];
-        const int64_t s0 = (int64_t)j * kMrSeg;
-        R.sy1h = (float)v1; R.sy1l = (float)(v1 - (double)R.sy1h);
-        R.sy2h = (float)v2; R.sy2l = (float)(v2 - (double)R.sy2h);
-        R.x1 = s0 >= 1 ? x[s0 - 1] : 0.f;
-        R.x2 = s0 >= 2 ? x[s0 - 2] : 0.f;
-        const double e1 = (double)R.zy1h + (double)R.zy1l + p00 * v1 + p01 * v2;
-        const double e2 = (double)R.zy2h + (double)R.zy2l + p10 * v1 + p11 * v2;
-        v1 = e1; v2 = e2;
+    const unsigned has = __ballot_sync(0xffffffffu, x != nullptr);
+    const float* anyp = has ? ptr[__ffs(has) - 1] : nullptr;     // non-null whenever Lw > 0
+    if (Lw > 0) seq_stage_in(tile[wid][0], ptr, len, anyp, 0, lane);
+    for (int k0 = 0, buf = 0; k0 < Lw; k0 += kSeqChunk, buf ^= 1) {
+        float* T = tile[wid][buf];
+        // The next chunk flies while this one is filtered; its buffer was emptied last round.
+        if (k0 + kSeqChunk < Lw) {
+            seq_stage_in(tile[wid][buf ^ 1], ptr, len, anyp, k0 + kSeqChunk, lane);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        __syncwarp();
+        float* row = T + lane * kSeqRow;
+#pragma unroll 4
+        for (int i = 0; i < kSeqChunk; i += 4) {
+            float4 v = *reinterpret_cast<const float4*>(row + i);
+            v.x = step(v.x); v.y = step(v.y); v.z = step(v.z); v.w = step(v.w);
+            *reinterpret_cast<float4*>(row + i) = v;
+        }
+        __syncwarp();
+        const int kk = k0 + 2 * lane;
+#pragma unroll 8
+        for (int q = 0; q < 32; ++q) {
+            float* xq = ptr[q];
+            const int Lq = len[q];
+            const float2 v = *reinterpret_cast<const float2*>(T + q * kSeqRow + 2 * lane);
+            if (kk + 1 < Lq) __stcs(reinterpret_cast<float2*>(xq + kk), v);
+            else if (kk < Lq) xq[kk] = v.x;
+        }
+        __syncwarp();
     }
 }
 
@@ -720,19 +616,13 @@ cudaError_t launch_synthesize_mr(const LaunchArgs& a, const float* pos_hi, const
     if ((e = kernel_residency((const void*)mr_stage_a, kMrThreads, smem, &per_sm)) != cudaSuccess) return e;
     mr_stage_a<<<device_sm_count() * per_sm, kMrThreads, smem, st>>>(a, early != nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // stage B: the segmented high-pass
-    const int nseg_max = (int)(((int64_t)a.rl * a.max_len + 8 + kMrSeg - 1) / kMrSeg);
-    const int64_t chans = (int64_t)a.B * a.S * a.M * (early ? 2 : 1);
-    SegRec* seg = reinterpret_cast<SegRec*>(a.mr_seg);
-    const int64_t nt = chans * nseg_max;
-    mr_hpf_tables<<<(kMrSeg + 2 + 255) / 256, 256, 0, st>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    mr_hpf_end<<<(unsigned)((nt + kHpfEndThreads / 32 - 1) / (kHpfEndThreads / 32)), kHpfEndThreads, 0, st>>>(
-        a, seg, nseg_max, early != nullptr);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    mr_hpf_scan<<<(unsigned)((chans + 127) / 128), 128, 0, st>>>(a, seg, nseg_max, early != nullptr);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    mr_hpf_seg<<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(a, seg, nseg_max, early != nullptr);
+    // stage B: the high-pass, one thread per channel, rooms ranked by length
+    if (a.B <= kOrderMax) {
+        mr_room_order<<<(a.B + 255) / 256, 256, 0, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const int64_t nthr = (int64_t)a.B * a.S * a.M * (early ? 2 : 1);
+    mr_hpf_seq<<<(unsigned)((nthr + kSeqThreads - 1) / kSeqThreads), kSeqThreads, 0, st>>>(a, early != nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // stage C
     switch (a.rl) {
