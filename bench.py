@@ -252,6 +252,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the per-room comparison and the CPU baseline")
     ap.add_argument("--spatialize-rooms", type=int, default=0,
                     help="only time fram_spatialize on the first N rooms of batch_1024 (for profiling) and exit")
+    ap.add_argument("--alu-only", action="store_true",
+                    help="only measure the FP32 and MUFU lane rates the roofline divides by, and exit")
     ap.add_argument("--multirate-only", action="store_true",
                     help="only time the multi-rate path against the continuous one on batch_1024 (for profiling) "
                          "and exit")
@@ -259,6 +261,16 @@ def main():
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.alu_only:
+        import torch
+
+        from paper_2304_08052_gb300 import api, build
+        build.build()
+        with ClockSampler(_gpu_uuid(torch)) as clk:
+            alu = measure_alu_lanes(api, seconds=2.0)
+        print(json.dumps({"alu_only": alu, "clocks": clk.summary(),
+                          "sms": torch.cuda.get_device_properties(0).multi_processor_count}), flush=True)
+        return 0
     if args.multirate_only:
         import torch
 

@@ -370,6 +370,8 @@ static LaunchArgs make_args(const fram_scene* sc, const fram_params* p, const Ws
         a.mr_ye = reinterpret_cast<float*>(base + w.mr_ye);
         a.mr_tab = reinterpret_cast<float*>(base + w.mr_tab);
         a.mr_order = reinterpret_cast<int32_t*>(base + w.mr_order);
+        a.mr_counts = reinterpret_cast<int32_t*>(base + w.mr_counts);
+        a.mr_pstate = base + w.mr_pstate;
     }
     return a;
 }

@@ -11,6 +11,7 @@
 //   * the workspace layout shared by the sampler, the synthesis and the adjoint.
 #pragma once
 
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdint>
@@ -263,6 +264,7 @@ struct WsLayout {
     size_t spa, spb, pos32, samp, irec;
     size_t mr_y, mr_ye, mr_tab;           // multi-rate mode: intermediate signals, resampling table
     size_t mr_order;                      // multi-rate mode: rooms by decreasing RIR length
+    size_t mr_counts, mr_pstate;          // multi-rate mode: rooms per high-pass piece, piece start states
     size_t part_mic, part_src, part_r, sb_part;
     size_t total;
     int tile;
@@ -289,6 +291,28 @@ inline MrRates mr_rates(double fs)
     r.up = r.rl / a;
     r.down = r.rh / a;
     return r;
+}
+
+// Multi-rate mode: the high-pass runs over pieces of P intermediate samples, each starting from
+// the state reached over the W samples before it (the pole radius rho of the 80 Hz high-pass at
+// r_l fs gives rho^W <= 1e-9); pmax pieces cover the longest channel.
+struct MrPieces {
+    int P, W, pmax;
+};
+
+inline MrPieces mr_pieces(double fs, int max_len)
+{
+    const MrRates r = mr_rates(fs);
+    const double k = std::tan(3.14159265358979323846 * 80.0 / ((double)r.rl * fs));
+    const double a2 = (1.0 - std::sqrt(2.0) * k + k * k) / (1.0 + std::sqrt(2.0) * k + k * k);
+    const double rho = std::sqrt(a2);
+    MrPieces pc;
+    pc.W = ((int)std::ceil(std::log(1e-9) / std::log(rho)) + 63) & ~63;
+    pc.P = std::max(16384, 2 * pc.W);
+    pc.P = (pc.P + 63) & ~63;
+    const int64_t lm = (int64_t)r.rl * (max_len > 0 ? max_len : 1) + 8;
+    pc.pmax = (int)((lm + pc.P - 1) / pc.P);
+    return pc;
 }
 
 inline WsLayout ws_layout(const fram_scene& sc, int tile, int delay_mode = 0, double fs = 16000.0)
@@ -326,6 +350,9 @@ inline WsLayout ws_layout(const fram_scene& sc, int tile, int delay_mode = 0, do
         w.mr_ye = take(sizeof(float) * inter);
         w.mr_tab = take(sizeof(float) * 32 * (size_t)mr.down);
         w.mr_order = take(sizeof(int32_t) * ((size_t)sc.B + 1));
+        const MrPieces pc = mr_pieces(fs, sc.max_len);
+        w.mr_counts = take(sizeof(int32_t) * ((size_t)pc.pmax + 1));
+        w.mr_pstate = take(32 * (size_t)pc.pmax * 2 * (size_t)sc.B * sc.S * sc.M);
     }
     w.part_mic = take(sizeof(float) * 3 * (size_t)w.max_items * sc.M);
     w.part_src = take(sizeof(float) * 3 * (size_t)w.max_items);
@@ -386,6 +413,8 @@ struct LaunchArgs {
     float* mr_ye;                    // the same for the early RIR
     float* mr_tab;                   // first resampling filter, polyphase rows of 32
     int32_t* mr_order;               // rooms by decreasing RIR length (ties by index)
+    int32_t* mr_counts;              // rooms with more than p high-pass pieces, per p
+    void* mr_pstate;                 // high-pass piece start states
     int32_t max_len;                 // max_b L_b
     float* part_mic;
     float* part_src;

@@ -22,10 +22,13 @@
 //                   reference (no fused multiply-add), then each impulse is added with one lane
 //                   per tap into the warp's shared buffer (and into the early buffer when q lies
 //                   in the Eq. 9 window on the high-rate grid).  Tiles go to y1 in global memory.
-//   mr_room_order, mr_hpf_seq   the high-pass, its state and products as float pairs (poles near
-//                   z = 1 at 80 Hz make a float32 recursion lose ~1e-5 of the peak), one thread per
-//                   channel over the whole channel from a zero state, channels grouped into warps by
-//                   room length and staged through shared memory in 64-sample chunks.
+//   mr_room_order, mr_hpf_piece   the high-pass, its state and products as float pairs (poles
+//                   near z = 1 at 80 Hz make a float32 recursion lose ~1e-5 of the peak), over
+//                   pieces of P samples of every channel: each piece starts from the state the
+//                   recursion reaches over the W samples before it (rho^W <= 1e-9 of the state it
+//                   forgets), a warm-up pass storing those states and a pass filtering every piece
+//                   in place; units (piece, room rank, channel) grouped so a warp's pieces have
+//                   nearly equal lengths, staged through shared memory in 64-sample chunks.
 //   mr_down         the second resampler (ratio 1/r_l, compile-time taps), four consecutive output
 //                   samples per thread (each window value read once, four per 16-byte load) from a
 //                   window staged in shared memory.
@@ -354,16 +357,13 @@ __global__ void __launch_bounds__(kMrThreads) mr_stage_a(LaunchArgs a, bool want
     }
 }
 
-// ---- stage B: the high-pass, one thread per channel --------------------------------------------
-// The 80 Hz high-pass runs over each channel's L_m intermediate samples from a zero state, in
-// place, as the direct-form recursion y[n] = b0 (x[n] - 2 x[n-1] + x[n-2]) - a1 y[n-1] - a2 y[n-2]
-// with the state and every product as float pairs (the poles lie close to z = 1 at 80 Hz, so a
-// float32 recursion loses ~1e-5 of the peak and the rounding of b0 times the second difference
-// alone, amplified near z = 1, costs about as much).  One thread walks one channel: the 32 channels
-// of a warp are consecutive in (room rank, RIR channel, early channel) order, rooms ranked by
-// decreasing RIR length (mr_room_order), so a warp's channels have nearly equal lengths.  Chunks of
-// 64 samples of the warp's 32 channels are staged through shared memory, so global loads and
-// stores move whole 256-byte pieces of one channel at a time.
+// ---- stage B: the high-pass, in pieces ---------------------------------------------------------
+// The 80 Hz high-pass runs over each channel's L_m intermediate samples, in place, as the
+// direct-form recursion y[n] = b0 (x[n] - 2 x[n-1] + x[n-2]) - a1 y[n-1] - a2 y[n-2] with the
+// state and every product as float pairs (the poles lie close to z = 1 at 80 Hz, so a float32
+// recursion loses ~1e-5 of the peak, and the rounding of b0 times the second difference alone,
+// amplified near z = 1, costs about as much).  A whole channel walked by one thread takes ~190
+// cycles per sample on its longest channels, so channels are cut into pieces (mr_hpf_piece).
 struct HpfCoef {
     f2 b0, a1, a2;
 };
@@ -389,22 +389,34 @@ __device__ __forceinline__ void mr_channel_of(const LaunchArgs& a, int64_t chan,
 // Rooms whose rank needs the all-pairs count below; larger batches keep their own order.
 constexpr int kOrderMax = 65536;
 
-// rank of room b = the number of rooms longer than b, or as long and earlier.
-__global__ void __launch_bounds__(256) mr_room_order(LaunchArgs a)
+// Every channel of room b has L_m intermediate samples (mr_chan) and ceil(L_m / P) pieces; L_m
+// and the RIR length do not decrease with T60, so rooms are ranked by decreasing T60 (ties by
+// index; a room the prologue rejected last).  counts[p] = the number of rooms with more than p
+// pieces, so the rooms that have a piece p are ranks [0, counts[p]).  counts (pmax entries) must
+// be zero on entry.
+__global__ void __launch_bounds__(256) mr_room_order(LaunchArgs a, int P, int pmax, int* __restrict__ counts)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= a.B) return;
-    const int Lb = a.room[b].len;
-    int rank = 0;
-    for (int c = 0; c < a.B; ++c) {
-        const int Lc = __ldg(&a.room[c].len);
-        rank += (Lc > Lb) || (Lc == Lb && c < b);
+    const RoomConst rb = a.room[b];
+    const int64_t Lb = rb.len >= 1 ? mr_chan(a, rb, b, 0, 0).Lm : 0;
+    if (a.B <= kOrderMax) {
+        const float tb = rb.len >= 1 ? a.rt60[b] : -1.0f;
+        int rank = 0;
+        for (int c = 0; c < a.B; ++c) {
+            const float tc = __ldg(&a.room[c].len) >= 1 ? __ldg(&a.rt60[c]) : -1.0f;
+            rank += (tc > tb) || (tc == tb && c < b);
+        }
+        a.mr_order[rank] = b;
+        const int np = (int)((Lb + P - 1) / P);
+        for (int q = 0; q < np && q < pmax; ++q) atomicAdd(&counts[q], 1);
+    } else if (b < pmax) {
+        counts[b] = a.B;        // unsorted: every room is a candidate for every piece
     }
-    a.mr_order[rank] = b;
 }
 
 constexpr int kSeqThreads = 128;
-constexpr int kSeqChunk = 64;              // samples per staged chunk and channel
+constexpr int kSeqChunk = 64;              // samples per staged chunk and unit
 constexpr int kSeqRow = kSeqChunk + 4;     // row stride (floats): 16-byte rows, float4 reads of a row conflict-free
 
 // Asynchronous 8-byte global -> shared copy of n bytes (0, 4 or 8), the rest zero-filled.
@@ -414,8 +426,8 @@ __device__ __forceinline__ void cp_async8(float* dst, const float* src, int n)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
 
-// Chunk k0 of the warp's 32 channels into the staging tile T (row q = channel q), as one group.
-// anyp: a valid channel pointer of the warp, the (unread) source of zero-byte copies.
+// Chunk k0 of the warp's 32 units into the staging tile T (row q = unit q), as one group; anyp:
+// a valid pointer of the warp, the (unread) source of zero-byte copies.
 __device__ __forceinline__ void seq_stage_in(float* T, float* const* ptr, const int* len, const float* anyp, int k0,
                                              int lane)
 {
@@ -429,7 +441,22 @@ __device__ __forceinline__ void seq_stage_in(float* T, float* const* ptr, const 
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-__global__ void __launch_bounds__(kSeqThreads) mr_hpf_seq(LaunchArgs a, bool with_early)
+// Pieces: a channel's L_m samples are cut into pieces of P; piece p starts at S = p P.  The
+// high-pass state forgets where it started: after W samples a start state contributes less than
+// rho^W <= 1e-9 of itself (rho = the pole radius), so piece p's start state is the state the
+// recursion reaches from a zero state over the W samples before S (exact when S <= W, where it
+// starts at sample 0).  warm = true: every piece p >= 1 runs that warm-up (reading only) and
+// stores its state; warm = false: every piece runs from its state (zero for piece 0) over its own
+// samples and writes the result in place.  Units are (piece, room rank, channel) in that order:
+// the rooms with a piece p are ranks [0, counts[p]) (mr_room_order), so a warp's 32 units are
+// pieces of nearly equal length.
+struct PieceState {
+    float y1h, y1l, y2h, y2l, x1, x2, pad0, pad1;
+};
+
+__global__ void __launch_bounds__(kSeqThreads) mr_hpf_piece(LaunchArgs a, bool with_early, bool warm, int P, int W,
+                                                            int pmax, const int* __restrict__ counts,
+                                                            PieceState* __restrict__ state)
 {
     __shared__ __align__(16) float tile[kSeqThreads / 32][2][32 * kSeqRow];
     __shared__ float* wptr[kSeqThreads / 32][32];
@@ -437,10 +464,16 @@ __global__ void __launch_bounds__(kSeqThreads) mr_hpf_seq(LaunchArgs a, bool wit
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int SM = a.S * a.M;
     const int CH = SM * (with_early ? 2 : 1);
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int Lm = 0;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int len = 0, p = -1;
     float* x = nullptr;
-    if (t < (int64_t)a.B * CH) {
+    PieceState* rec = nullptr;
+    for (int q = warm ? 1 : 0; q < pmax; ++q) {      // locate the unit: piece q holds counts[q] CH units
+        const int64_t nq = (int64_t)counts[q] * CH;
+        if (t < nq) { p = q; break; }
+        t -= nq;
+    }
+    if (p >= 0) {
         const int k = (int)(t / CH), j = (int)(t - (int64_t)k * CH);
         const int b = a.B <= kOrderMax ? a.mr_order[k] : k;
         const RoomConst rc = a.room[b];
@@ -449,21 +482,37 @@ __global__ void __launch_bounds__(kSeqThreads) mr_hpf_seq(LaunchArgs a, bool wit
             const int jj = is_early ? j - SM : j;
             const int s = jj / a.M, m = jj - s * a.M;
             const MrChan ch = mr_chan(a, rc, b, s, m);
-            Lm = (int)ch.Lm;
-            x = (is_early ? a.mr_ye : a.mr_y) + ch.off;
+            const int64_t S = (int64_t)p * P;
+            if (S < ch.Lm) {
+                const int64_t gc = ((int64_t)b * a.S + s) * a.M + m + (is_early ? (int64_t)a.B * SM : 0);
+                rec = state + gc * pmax + p;
+                if (warm) {
+                    const int64_t b0 = S > W ? S - W : 0;
+                    x = (is_early ? a.mr_ye : a.mr_y) + ch.off + b0;
+                    len = (int)(S - b0);
+                } else {
+                    x = (is_early ? a.mr_ye : a.mr_y) + ch.off + S;
+                    len = (int)(ch.Lm - S < P ? ch.Lm - S : P);
+                }
+            }
         }
     }
     float* const* ptr = wptr[wid];
-    const int* len = wlen[wid];
+    const int* lens = wlen[wid];
     wptr[wid][lane] = x;
-    wlen[wid][lane] = Lm;
-    int Lw = Lm;
+    wlen[wid][lane] = len;
+    int Lw = len;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) Lw = max(Lw, __shfl_xor_sync(0xffffffffu, Lw, o));
     __syncwarp();
+    if (Lw == 0) return;                     // the whole warp has no unit (uniform)
     const HpfCoef c = hpf_coef((double)a.rl * a.fs);
     float x1 = 0.f, x2 = 0.f;
     f2 y1{0.f, 0.f}, y2{0.f, 0.f};
+    if (!warm && p > 0 && rec) {
+        const PieceState st = *rec;
+        y1 = f2{st.y1h, st.y1l}; y2 = f2{st.y2h, st.y2l}; x1 = st.x1; x2 = st.x2;
+    }
     auto step = [&](float x0) {
         f2 uu = two_sum(x0, x2);
         uu = f2_add_f(uu, -2.0f * x1);
@@ -472,37 +521,44 @@ __global__ void __launch_bounds__(kSeqThreads) mr_hpf_seq(LaunchArgs a, bool wit
         return y0.hi + y0.lo;
     };
     const unsigned has = __ballot_sync(0xffffffffu, x != nullptr);
-    const float* anyp = has ? ptr[__ffs(has) - 1] : nullptr;     // non-null whenever Lw > 0
-    if (Lw > 0) seq_stage_in(tile[wid][0], ptr, len, anyp, 0, lane);
+    const float* anyp = ptr[__ffs(has) - 1];
+    seq_stage_in(tile[wid][0], ptr, lens, anyp, 0, lane);
     for (int k0 = 0, buf = 0; k0 < Lw; k0 += kSeqChunk, buf ^= 1) {
         float* T = tile[wid][buf];
         // The next chunk flies while this one is filtered; its buffer was emptied last round.
         if (k0 + kSeqChunk < Lw) {
-            seq_stage_in(tile[wid][buf ^ 1], ptr, len, anyp, k0 + kSeqChunk, lane);
+            seq_stage_in(tile[wid][buf ^ 1], ptr, lens, anyp, k0 + kSeqChunk, lane);
             asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         }
         __syncwarp();
         float* row = T + lane * kSeqRow;
+        if (warm) {
+            // the state at the end of the warm-up: stop exactly at the unit's last sample
+            const int n = len - k0 < kSeqChunk ? (len - k0 > 0 ? len - k0 : 0) : kSeqChunk;
+            for (int i = 0; i < n; ++i) step(row[i]);
+        } else {
 #pragma unroll 4
-        for (int i = 0; i < kSeqChunk; i += 4) {
-            float4 v = *reinterpret_cast<const float4*>(row + i);
-            v.x = step(v.x); v.y = step(v.y); v.z = step(v.z); v.w = step(v.w);
-            *reinterpret_cast<float4*>(row + i) = v;
-        }
-        __syncwarp();
-        const int kk = k0 + 2 * lane;
+            for (int i = 0; i < kSeqChunk; i += 4) {
+                float4 v = *reinterpret_cast<const float4*>(row + i);
+                v.x = step(v.x); v.y = step(v.y); v.z = step(v.z); v.w = step(v.w);
+                *reinterpret_cast<float4*>(row + i) = v;
+            }
+            __syncwarp();
+            const int kk = k0 + 2 * lane;
 #pragma unroll 8
-        for (int q = 0; q < 32; ++q) {
-            float* xq = ptr[q];
-            const int Lq = len[q];
-            const float2 v = *reinterpret_cast<const float2*>(T + q * kSeqRow + 2 * lane);
-            if (kk + 1 < Lq) __stcs(reinterpret_cast<float2*>(xq + kk), v);
-            else if (kk < Lq) xq[kk] = v.x;
+            for (int q = 0; q < 32; ++q) {
+                float* xq = ptr[q];
+                const int Lq = lens[q];
+                const float2 v = *reinterpret_cast<const float2*>(T + q * kSeqRow + 2 * lane);
+                if (kk + 1 < Lq) __stcs(reinterpret_cast<float2*>(xq + kk), v);
+                else if (kk < Lq) xq[kk] = v.x;
+            }
         }
         __syncwarp();
     }
+    if (warm && rec) *rec = PieceState{y1.hi, y1.lo, y2.hi, y2.lo, x1, x2, 0.f, 0.f};
 }
 
 // ---- stage C: the resampler 1/RL, one thread per output sample ------------------------------
@@ -616,13 +672,20 @@ cudaError_t launch_synthesize_mr(const LaunchArgs& a, const float* pos_hi, const
     if ((e = kernel_residency((const void*)mr_stage_a, kMrThreads, smem, &per_sm)) != cudaSuccess) return e;
     mr_stage_a<<<device_sm_count() * per_sm, kMrThreads, smem, st>>>(a, early != nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // stage B: the high-pass, one thread per channel, rooms ranked by length
-    if (a.B <= kOrderMax) {
-        mr_room_order<<<(a.B + 255) / 256, 256, 0, st>>>(a);
+    // stage B: the high-pass in pieces (warm-up states, then every piece in place)
+    const MrPieces pc = mr_pieces(a.fs, a.max_len);
+    int* counts = a.mr_counts;
+    if ((e = cudaMemsetAsync(counts, 0, sizeof(int) * pc.pmax, st)) != cudaSuccess) return e;
+    mr_room_order<<<(a.B + 255) / 256, 256, 0, st>>>(a, pc.P, pc.pmax, counts);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    PieceState* pstate = reinterpret_cast<PieceState*>(a.mr_pstate);
+    const int64_t nthr = (int64_t)a.B * a.S * a.M * (early ? 2 : 1) * pc.pmax;
+    const unsigned nblk = (unsigned)((nthr + kSeqThreads - 1) / kSeqThreads);
+    if (pc.pmax > 1) {
+        mr_hpf_piece<<<nblk, kSeqThreads, 0, st>>>(a, early != nullptr, true, pc.P, pc.W, pc.pmax, counts, pstate);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const int64_t nthr = (int64_t)a.B * a.S * a.M * (early ? 2 : 1);
-    mr_hpf_seq<<<(unsigned)((nthr + kSeqThreads - 1) / kSeqThreads), kSeqThreads, 0, st>>>(a, early != nullptr);
+    mr_hpf_piece<<<nblk, kSeqThreads, 0, st>>>(a, early != nullptr, false, pc.P, pc.W, pc.pmax, counts, pstate);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // stage C
     switch (a.rl) {
