@@ -316,7 +316,7 @@ __host__ __device__ inline int bwd_glen(int T, int K, int margin_i)
 {
     // an image pass needs at most span + 2K + 2 margin + 6; a direct-only pass 2K + 4 margin + 8
     const int sp = bwd_span(T) > 2 * margin_i + 2 ? bwd_span(T) : 2 * margin_i + 2;
-    return (sp + 2 * K + 2 * margin_i + 6 + 3) & ~3;
+    return (sp + 2 * K + 2 * margin_i + 6 + 3 + 8) & ~3;       // + 8: the staging's shift and last vector
 }
 __host__ __device__ inline int bwd_warp_floats(int T, int K, int margin_i, bool with_g)
 {
@@ -413,30 +413,53 @@ __device__ __forceinline__ BwdPass next_pass(const LaunchArgs& a, int64_t v0, in
     return P;
 }
 
-// Stages G = dL/dh (+ Eq. 9 mask * dL/dh_e) of channel ch0 over [gb, gb + gl) into Gs: with only
-// dL/dh given, as asynchronous copies (committed as one group); otherwise synchronously.
-__device__ __forceinline__ void stage_g(float* Gs, const float* grad_rir, const float* grad_early, int64_t ch0,
-                                        int gb, int gl, int Lb, int elo, int ehi, int lane)
+// Asynchronous 16-byte global -> shared copy (both addresses 16-byte aligned), bypassing L1.
+__device__ __forceinline__ void cp_async16(float* dst, const float* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// Stages G = dL/dh (+ Eq. 9 mask * dL/dh_e) of channel ch0 over [gb, gb + gl) into the buffer Gb
+// and returns the shift sh: sample n sits at Gb[n - gb + sh], so the caller reads Gb + sh as "G
+// from gb".  With only dL/dh given, the range is moved down to a 16-byte boundary of the row
+// (sh = 0..3 floats) and copied as whole 16-byte vectors by asynchronous copies (committed as one
+// group); a vector that straddles the channel's ends goes as four 4-byte copies, the samples
+// outside [0, L_b) zero-filled.  Otherwise (an early-RIR gradient to mask and add) the values are
+// formed synchronously, sh = 0.  The buffer holds gl + 6 floats at most.
+__device__ __forceinline__ int stage_g(float* Gb, const float* grad_rir, const float* grad_early, int64_t ch0, int gb,
+                                       int gl, int Lb, int elo, int ehi, int lane)
 {
     if (grad_rir && !grad_early) {
         const float* row = grad_rir + ch0;
-        for (int j = lane; j < gl; j += 32) {
-            const int n = gb + j;
-            const bool ok = n >= 0 && n < Lb;
-            cp_async4(Gs + j, ok ? row + n : row, ok);
+        const int sh = (int)((reinterpret_cast<uintptr_t>(row + gb) >> 2) & 3);
+        const int g0 = gb - sh;                    // row + g0 is 16-byte aligned
+        const int nvec = (gl + sh + 3) >> 2;
+        for (int v = lane; v < nvec; v += 32) {
+            const int n = g0 + 4 * v;
+            if (n >= 0 && n + 3 < Lb) {
+                cp_async16(Gb + 4 * v, row + n);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const bool ok = n + i >= 0 && n + i < Lb;
+                    cp_async4(Gb + 4 * v + i, ok ? row + n + i : row, ok);
+                }
+            }
         }
         cp_async_commit();
-    } else {
-        for (int j = lane; j < gl; j += 32) {
-            const int n = gb + j;
-            float Gv = 0.f;
-            if (n >= 0 && n < Lb) {
-                if (grad_rir) Gv = grad_rir[ch0 + n];
-                if (grad_early && n >= elo && n <= ehi) Gv += grad_early[ch0 + n];
-            }
-            Gs[j] = Gv;
-        }
+        return sh;
     }
+    for (int j = lane; j < gl; j += 32) {
+        const int n = gb + j;
+        float Gv = 0.f;
+        if (n >= 0 && n < Lb) {
+            if (grad_rir) Gv = grad_rir[ch0 + n];
+            if (grad_early && n >= elo && n <= ehi) Gv += grad_early[ch0 + n];
+        }
+        Gb[j] = Gv;
+    }
+    return 0;
 }
 
 template <int KT>
@@ -501,7 +524,8 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_kernel(LaunchArgs a, const
             BwdPass P = direct_only ? Pdir : next_pass(a, v0, o_lo, o_hi, span, K, Mg, lane);
             int stage = 0;
             __syncwarp();
-            stage_g(Gbuf, grad_rir, grad_early, chan0, P.gb, P.gl, Lb, dcs[0].early_lo, dcs[0].early_hi, lane);
+            int sh_next = stage_g(Gbuf, grad_rir, grad_early, chan0, P.gb, P.gl, Lb, dcs[0].early_lo, dcs[0].early_hi,
+                                  lane);
             for (bool first = true;; first = false) {
                 const int nch = (P.p1 - P.p0 + 31) / 32;
                 for (int k = 0; k < nch * 3; ++k) gv[k * 32 + lane] = 0.f;
@@ -510,7 +534,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_kernel(LaunchArgs a, const
                 BwdPass Pn = P;
                 bool more = false, next_direct_only = false;
                 for (int m = 0; m < M; ++m, ++stage) {
-                    float* Gs = Gbuf + (stage & 1) * glen;
+                    float* Gs = Gbuf + (stage & 1) * glen + sh_next;
                     cp_async_wait_all();
                     __syncwarp();
                     // Prefetch the next stage: mic m + 1 of this pass, or mic 0 of the next pass.
@@ -523,8 +547,9 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_kernel(LaunchArgs a, const
                         }
                     }
                     if (m + 1 < M || more)
-                        stage_g(Gbuf + ((stage + 1) & 1) * glen, grad_rir, grad_early, chan0 + (int64_t)mn * Lb,
-                                Pn.gb, Pn.gl, Lb, dcs[mn].early_lo, dcs[mn].early_hi, lane);
+                        sh_next = stage_g(Gbuf + ((stage + 1) & 1) * glen, grad_rir, grad_early,
+                                          chan0 + (int64_t)mn * Lb, Pn.gb, Pn.gl, Lb, dcs[mn].early_lo,
+                                          dcs[mn].early_hi, lane);
                     const float* pm = a.mic + 3 * ((size_t)b * M + m);
                     const float mx = pm[0], my = pm[1], mz = pm[2];
                     float mpx = 0.f, mpy = 0.f, mpz = 0.f;
@@ -630,8 +655,8 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_kernel(LaunchArgs a, const
                             Pn = Pdir;
                             more = true;
                             next_direct_only = true;
-                            stage_g(Gbuf + ((stage + 1) & 1) * glen, grad_rir, grad_early, chan0, Pn.gb, Pn.gl, Lb,
-                                    dcs[0].early_lo, dcs[0].early_hi, lane);
+                            sh_next = stage_g(Gbuf + ((stage + 1) & 1) * glen, grad_rir, grad_early, chan0, Pn.gb,
+                                              Pn.gl, Lb, dcs[0].early_lo, dcs[0].early_hi, lane);
                         }
                     }
                 }
