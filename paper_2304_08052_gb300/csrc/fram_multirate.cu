@@ -569,11 +569,15 @@ constexpr int kMrOut = kMrOutT * kMrPer;
 
 // Window value w[M] (M = 0 .. (kMrPer - 1) RL + 2 HLC) read once and added to every output j whose
 // taps cover it: output j uses offsets j RL + i, i in [0, 2 HLC], with coefficient F_C(HLC - i).
+// The staged window starts PAD = (-10 RL) mod 4 samples before the first tap, on a 16-byte boundary.
+template <int RL>
+constexpr int kDownPad = (4 - (10 * RL) % 4) % 4;
+
 template <int RL, int M, int J>
 __device__ __forceinline__ void fir_tap(float x, float* acc)
 {
     constexpr int HLC2 = 20 * RL;
-    constexpr int i = M - J * RL;
+    constexpr int i = M - J * RL - kDownPad<RL>;
     if constexpr (i >= 0 && i <= HLC2) {
         constexpr float c = kFc<RL>.v[HLC2 - i];
         acc[J] = __fmaf_rn(x, c, acc[J]);
@@ -607,8 +611,9 @@ template <int RL>
 __global__ void __launch_bounds__(kMrOutT) mr_down(LaunchArgs a, float* __restrict__ rir, float* __restrict__ early)
 {
     constexpr int HLC = 10 * RL;
-    constexpr int NW = (kMrPer - 1) * RL + 2 * HLC + 1;          // window values one thread reads
-    constexpr int W = ((kMrOut * RL + 2 * HLC + 4) + 3) & ~3;     // staged window, whole float4s
+    constexpr int PAD = kDownPad<RL>;
+    constexpr int NW = (kMrPer - 1) * RL + 2 * HLC + 1 + PAD;    // window values one thread reads
+    constexpr int W = ((kMrOut * RL + 2 * HLC + 4 + PAD) + 3) & ~3;   // staged window, whole float4s
     __shared__ __align__(16) float zw[W];
     const int64_t nch = (int64_t)a.B * a.S * a.M;
     const int64_t cidx = blockIdx.x;
@@ -622,15 +627,26 @@ __global__ void __launch_bounds__(kMrOutT) mr_down(LaunchArgs a, float* __restri
     if (L < 1 || n0 >= L) return;
     const MrChan ch = mr_chan(a, rc, b, s, m);
     const float* z = (is_early ? a.mr_ye : a.mr_y) + ch.off;
-    const int64_t k0 = n0 * RL - HLC;                 // window [k0, k0 + W)
-    for (int i = threadIdx.x; i < W; i += kMrOutT) {
-        const int64_t k = k0 + i;
-        zw[i] = (k >= 0 && k < ch.Lm) ? z[k] : 0.f;
+    const int64_t k0 = n0 * RL - HLC - PAD;           // window [k0, k0 + W), 16-byte aligned
+    // whole float4s inside [0, L_m) as one 16-byte load each, the vectors at the ends element-wise
+#pragma unroll 4
+    for (int v = threadIdx.x; v < W / 4; v += kMrOutT) {
+        const int64_t k = k0 + 4 * v;
+        float4 q;
+        if (k >= 0 && k + 3 < ch.Lm) {
+            q = __ldcs(reinterpret_cast<const float4*>(z + k));
+        } else {
+            q.x = (k >= 0 && k < ch.Lm) ? z[k] : 0.f;
+            q.y = (k + 1 >= 0 && k + 1 < ch.Lm) ? z[k + 1] : 0.f;
+            q.z = (k + 2 >= 0 && k + 2 < ch.Lm) ? z[k + 2] : 0.f;
+            q.w = (k + 3 >= 0 && k + 3 < ch.Lm) ? z[k + 3] : 0.f;
+        }
+        reinterpret_cast<float4*>(zw)[v] = q;
     }
     __syncthreads();
     static_assert((kMrPer * RL) % 4 == 0, "each thread's window starts on a float4");
     // outputs n = n0 + kMrPer t + j: taps k = n RL - HLC .. n RL + HLC, i.e. window offsets
-    // (kMrPer t + j) RL + i, i in [0, 2 HLC]
+    // (kMrPer t + j) RL + PAD + i, i in [0, 2 HLC]
     float acc[kMrPer];
 #pragma unroll
     for (int j = 0; j < kMrPer; ++j) acc[j] = 0.f;
