@@ -50,6 +50,8 @@ extern "C" {
 #define FRAM_DEV_BAD_GEOMETRY   0x1  /* c0*T60 <= D0, D0 == 0, T60 <= 0 or dims <= 0        */
 #define FRAM_DEV_CAPACITY       0x2  /* a synthesis tile held more images than it can stage */
 #define FRAM_DEV_NONFINITE      0x4  /* a non-finite position, g or r was read              */
+#define FRAM_DEV_BOUNDS         0x8  /* debug builds only (FRAM_DEBUG_BOUNDS): an index fell  */
+                                     /* outside its buffer; the access was skipped           */
 
 /*
  * Method constants.  The paper fixes only their ranges: 0 <= alpha < beta <= 1 (Eq. 3),

@@ -9,7 +9,8 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libfram.so")
+# FRAM_LIBRARY selects another build of the same library (the bounds-checking debug build).
+LIB_PATH = os.environ.get("FRAM_LIBRARY") or os.path.join(HERE, "_build", "libfram.so")
 
 FRAM_OK = 0
 FRAM_EINVAL = -1
@@ -20,6 +21,7 @@ FRAM_EDEVICE = -4
 FRAM_DEV_BAD_GEOMETRY = 0x1
 FRAM_DEV_CAPACITY = 0x2
 FRAM_DEV_NONFINITE = 0x4
+FRAM_DEV_BOUNDS = 0x8          # the bounds-checking debug build only
 
 # Every symbol include/fram.h declares (checked by tests/test_abi.py).
 EXPORTED = ("fram_version", "fram_last_error", "fram_default_params", "fram_layout", "fram_workspace_size",

@@ -19,6 +19,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfram.so")
+# The bounds-checking debug build (-DFRAM_DEBUG_BOUNDS): guarded accesses record FRAM_DEV_BOUNDS
+# in the status word and are skipped instead of running out of their buffers.
+OUT_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(OUT_DEBUG, "libfram.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills",
          "-I", os.path.join(ROOT, "include")]
@@ -44,15 +48,18 @@ def _newest(paths):
     return max(os.path.getmtime(p) for p in paths)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), debug_bounds: bool = False) -> str:
+    out_dir, lib_path = (OUT_DEBUG, LIB_DEBUG) if debug_bounds else (OUT, LIB)
+    if debug_bounds:
+        extra = tuple(extra) + ("-DFRAM_DEBUG_BOUNDS",)
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     srcs = sources()
     hdr_t = _newest(headers())
     objs = []
     jobs = []
     for s in srcs:
-        o = os.path.join(OUT, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(out_dir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr_t):
             jobs.append([nvcc, *ARCH, *FLAGS, *extra, "-c", s, "-o", o])
@@ -65,19 +72,20 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
                     sys.stderr.write(r.stdout + r.stderr)
                 if r.returncode != 0:
                     raise RuntimeError(f"nvcc failed for {j[-3]}")
-    if force or jobs or not os.path.exists(LIB) or os.path.getmtime(LIB) < _newest(objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or not os.path.exists(lib_path) or os.path.getmtime(lib_path) < _newest(objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-ldl"], capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("linking libfram.so failed")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--force", action="store_true")
     ap.add_argument("--verbose", action="store_true")
+    ap.add_argument("--debug-bounds", action="store_true", help="the bounds-checking debug build")
     args = ap.parse_args()
-    print(build(force=args.force, verbose=args.verbose))
+    print(build(force=args.force, verbose=args.verbose, debug_bounds=args.debug_bounds))

@@ -635,7 +635,8 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_kernel(LaunchArgs a, const
                     };
                     for (int ch = 0; ch < nround; ++ch) {
                         const BwdRound R = setup(ch);
-                        if (R.go) {
+                        if (R.go && FRAM_GUARD(a.hdr, R.j0 >= 0 &&
+                                                          (int)(Gs - (Gbuf + (stage & 1) * glen)) + R.j0 + 2 * K < glen)) {
                             float S1, S2;
                             if constexpr (KT > 0) gather_taps_ct<KT>(Gs + R.j0, R.r, S1, S2);
                             else gather_taps_rt(Gs + R.j0, K, R.r, tab, S1, S2);
@@ -665,8 +666,8 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_kernel(LaunchArgs a, const
                     const float lnr = rc.log2r * 0.69314718055994531f;   // dA/dg = A ln r
                     for (int ch = 0; ch < nch; ++ch) {
                         const int slot = P.p0 + 32 * ch + lane;
-                        if (slot < P.p1) {
-                            const int64_t v = v0 + a.perm[v0 + slot];
+                        const int64_t v = slot < P.p1 ? v0 + a.perm[v0 + slot] : -1;
+                        if (slot < P.p1 && FRAM_GUARD(a.hdr, v >= v0 && v < v0 + rc.n_vs && v < a.n_vs_total)) {
                             const float* g3 = gv + ch * 96 + lane;
                             if (grad_vs) {
                                 grad_vs[3 * v] = g3[0];

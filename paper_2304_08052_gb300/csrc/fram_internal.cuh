@@ -422,6 +422,21 @@ struct LaunchArgs {
     double* sb_part;        // gradient through the sampler: per (room, source) partial sums
 };
 
+// Bounds guards of the debug build (compiled with -DFRAM_DEBUG_BOUNDS): a guarded access runs only
+// if its index lies inside its buffer; otherwise FRAM_DEV_BOUNDS is set in the status word and the
+// access is skipped (no trap).  In the release build every guard is the constant true, so it
+// leaves no code.
+#ifdef FRAM_DEBUG_BOUNDS
+__device__ __forceinline__ bool fram_guard(Header* h, bool ok)
+{
+    if (!ok) atomicOr(&h->status, FRAM_DEV_BOUNDS);
+    return ok;
+}
+#define FRAM_GUARD(hdr, cond) ::fram::fram_guard((hdr), (cond))
+#else
+#define FRAM_GUARD(hdr, cond) true
+#endif
+
 // Host-side launchers (defined in the .cu files; return cudaError_t of the launch).
 cudaError_t launch_sample(const LaunchArgs& a, const fram_params& p, uint64_t seed, const uint64_t* d_seed,
                           float* pos_hi, float* pos_lo, float* g, float* r, uint32_t* words, cudaStream_t st);

@@ -568,6 +568,11 @@ __global__ void __launch_bounds__(kSynthThreads, 3) synth_kernel(LaunchArgs a, f
         const float mx = pm[0], my = pm[1], mz = pm[2];
         const DirectConst dc = a.direct[((int64_t)ir.b * a.S + ir.s) * M + m];
         const int64_t v0 = ir.v0;
+        if (!FRAM_GUARD(a.hdr, ir.out0 >= 0 && ir.out0 + (int64_t)(m + 1) * Lb <= a.rir_total && T0 >= 0 && T0 < Lb &&
+                                   v0 >= 0 && v0 + ir.c_hi <= a.n_vs_total)) {
+            u = __shfl_sync(0xffffffffu, nxt, 0);
+            continue;
+        }
         float4 pa = make_float4(0.f, 0.f, 0.f, 0.f);
         float2 pb = make_float2(0.f, 0.f);
         float am = 0.0f;
@@ -635,12 +640,15 @@ __global__ void __launch_bounds__(kSynthThreads, 3) synth_kernel(LaunchArgs a, f
                 const float4 r = rn;
                 const int rb = __shfl_sync(0xffffffffu, rbq, q);
                 rn = rec[q + 1];
-                add_arrival_inner<NR>(smem, L, r, rb, lane4);
+                if (FRAM_GUARD(a.hdr, rb >= buf_b && rb - buf_b + 4 * (32 * NR - 1) < 4 * (T + 68)))
+                    add_arrival_inner<NR>(smem, L, r, rb, lane4);
                 __syncwarp();
             }
             for (int q = ni; q < nv; ++q) {
                 const int rl = __shfl_sync(0xffffffffu, rbq, q);
-                add_arrival_edge<NR>(smem, L, rec[q], hb + 4 * rl, lane4, rl, T);
+                // every round add_arrival_edge runs starts inside (-32, T) of the tile
+                if (FRAM_GUARD(a.hdr, h - 32 >= 0 && h + T + 31 < T + 68))
+                    add_arrival_edge<NR>(smem, L, rec[q], hb + 4 * rl, lane4, rl, T);
                 __syncwarp();
             }
         }
