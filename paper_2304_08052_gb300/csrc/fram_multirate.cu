@@ -276,9 +276,10 @@ __global__ void __launch_bounds__(kMrThreads) mr_stage_a(LaunchArgs a, bool want
         const bool last = K0 + TA >= tile_end;
         const int64_t s_end = last ? ch.Lm : (K0 + TA < ch.Lm ? K0 + TA : ch.Lm);
         if (K0 < s_end) {
-            for (int k = lane; k < TA + 64; k += 32) {
-                buf[k] = 0.0f;
-                if (bufe) bufe[k] = 0.0f;
+            // TA + 64 is a multiple of 4 and the buffers start on 16 bytes: zero whole float4s
+            for (int k = lane; k < (TA + 64) / 4; k += 32) {
+                reinterpret_cast<float4*>(buf)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (bufe) reinterpret_cast<float4*>(bufe)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
             __syncwarp();
             const DirectConst dc = a.direct[((int64_t)ir.b * a.S + ir.s) * M + m];
@@ -347,9 +348,21 @@ __global__ void __launch_bounds__(kMrThreads) mr_stage_a(LaunchArgs a, bool want
                     __syncwarp();
                 }
             }
-            for (int64_t k = K0 + lane; k < s_end; k += 32) {
-                a.mr_y[ch.off + k] = buf[k - K0 + 32];
-                if (bufe) a.mr_ye[ch.off + k] = bufe[k - K0 + 32];
+            // K0 and the channel offset are multiples of 4 samples and buffer index 32 holds
+            // sample K0, so whole float4s go out as 16-byte stores; then the tail of a channel.
+            const int nk = (int)(s_end - K0), n4 = nk >> 2;
+            float4* y4 = reinterpret_cast<float4*>(a.mr_y + ch.off + K0);
+            float4* ye4 = bufe ? reinterpret_cast<float4*>(a.mr_ye + ch.off + K0) : nullptr;
+            const float4* b4 = reinterpret_cast<const float4*>(buf + 32);
+            const float4* be4 = bufe ? reinterpret_cast<const float4*>(bufe + 32) : nullptr;
+            for (int v = lane; v < n4; v += 32) {
+                y4[v] = b4[v];
+                if (bufe) ye4[v] = be4[v];
+            }
+            if (lane < nk - 4 * n4) {
+                const int k = 4 * n4 + lane;
+                a.mr_y[ch.off + K0 + k] = buf[32 + k];
+                if (bufe) a.mr_ye[ch.off + K0 + k] = bufe[32 + k];
             }
             __syncwarp();
         }
