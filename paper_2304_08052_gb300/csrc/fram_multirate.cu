@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(kSeqThreads) mr_hpf_piece(LaunchArgs a, bool w
     seq_stage_in(tile[wid][0], ptr, lens, anyp, 0, lane);
     for (int k0 = 0, buf = 0; k0 < Lw; k0 += kSeqChunk, buf ^= 1) {
         float* T = tile[wid][buf];
-        // The next chunk flies while this one is filtered; its buffer was emptied last round.
+        // The next chunk flies while this one is filtered; its buffer was emptied by the previous chunk.
         if (k0 + kSeqChunk < Lw) {
             seq_stage_in(tile[wid][buf ^ 1], ptr, lens, anyp, k0 + kSeqChunk, lane);
             asm volatile("cp.async.wait_group 1;\n" ::: "memory");
