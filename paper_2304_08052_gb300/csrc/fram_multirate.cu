@@ -182,6 +182,13 @@ __device__ __forceinline__ MrChan mr_chan(const LaunchArgs& a, const RoomConst& 
     return c;
 }
 
+// Floats in each intermediate buffer (mr_y, mr_ye): the workspace layout's r_l * sum_b S M L_b
+// plus 8 floats of slack per channel and 4 at the end; the debug build's guards check against it.
+__device__ __forceinline__ int64_t mr_inter_floats(const LaunchArgs& a)
+{
+    return (int64_t)a.rl * a.rir_total + 8 * (int64_t)a.B * a.S * a.M + 4;
+}
+
 // Per-warp shared memory (floats): the tile buffer (TA + 64), the early buffer when wanted, and
 // 32 staged impulses (A; buffer index of tap 0; filter row and Eq. 9 flag).
 __host__ __device__ inline int mr_warp_floats(int TA, bool early) { return (early ? 2 : 1) * (TA + 64) + 3 * 32; }
@@ -275,7 +282,9 @@ __global__ void __launch_bounds__(kMrThreads) mr_stage_a(LaunchArgs a, bool want
         const int64_t tile_end = (int64_t)rc.ntiles * T * rl;
         const bool last = K0 + TA >= tile_end;
         const int64_t s_end = last ? ch.Lm : (K0 + TA < ch.Lm ? K0 + TA : ch.Lm);
-        if (K0 < s_end) {
+        if (K0 < s_end &&
+            FRAM_GUARD(a.hdr, K0 >= 0 && (ch.off & 3) == 0 && ch.off + s_end <= mr_inter_floats(a) &&
+                                  ir.v0 >= 0 && (int64_t)ir.v0 + rc.n_vs <= a.n_vs_total)) {
             // TA + 64 is a multiple of 4 and the buffers start on 16 bytes: zero whole float4s
             for (int k = lane; k < (TA + 64) / 4; k += 32) {
                 reinterpret_cast<float4*>(buf)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -332,7 +341,9 @@ __global__ void __launch_bounds__(kMrThreads) mr_stage_a(LaunchArgs a, bool want
                     const int64_t kmin = ceil_div(c - HL, down);
                     valid = Df > 0.0f && A == A && fabsf(A) < 3.0e38f && kmin + 31 >= K0 - 32 && kmin < K0 + TA + 32;
                     bi0 = (int)(kmin - K0 + 32);
-                    row = 2 * (int)(kmin * down - c + HL) + ((q >= dc.early_lo_h && q <= dc.early_hi_h) ? 1 : 0);
+                    const int m0 = (int)(kmin * down - c + HL);
+                    valid = valid && FRAM_GUARD(a.hdr, m0 >= 0 && m0 < down);      // the table row
+                    row = 2 * m0 + ((q >= dc.early_lo_h && q <= dc.early_hi_h) ? 1 : 0);
                 }
                 const unsigned vb = __ballot_sync(0xffffffffu, valid);
                 if (valid) {
@@ -496,7 +507,7 @@ __global__ void __launch_bounds__(kSeqThreads) mr_hpf_piece(LaunchArgs a, bool w
             const int s = jj / a.M, m = jj - s * a.M;
             const MrChan ch = mr_chan(a, rc, b, s, m);
             const int64_t S = (int64_t)p * P;
-            if (S < ch.Lm) {
+            if (S < ch.Lm && FRAM_GUARD(a.hdr, (ch.off & 3) == 0 && ch.off + ch.Lm <= mr_inter_floats(a))) {
                 const int64_t gc = ((int64_t)b * a.S + s) * a.M + m + (is_early ? (int64_t)a.B * SM : 0);
                 rec = state + gc * pmax + p;
                 if (warm) {
@@ -639,6 +650,10 @@ __global__ void __launch_bounds__(kMrOutT) mr_down(LaunchArgs a, float* __restri
     const int64_t n0 = (int64_t)blockIdx.y * kMrOut;
     if (L < 1 || n0 >= L) return;
     const MrChan ch = mr_chan(a, rc, b, s, m);
+    // block-uniform: the window reads stay in the channel, the outputs in the RIR buffer
+    if (!FRAM_GUARD(a.hdr, ch.off >= 0 && ch.off + ch.Lm <= mr_inter_floats(a) && rc.rir_off >= 0 &&
+                               rc.rir_off + ((int64_t)s * a.M + m + 1) * L <= a.rir_total))
+        return;
     const float* z = (is_early ? a.mr_ye : a.mr_y) + ch.off;
     const int64_t k0 = n0 * RL - HLC - PAD;           // window [k0, k0 + W), 16-byte aligned
     // whole float4s inside [0, L_m) as one 16-byte load each, the vectors at the ends element-wise

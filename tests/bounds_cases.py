@@ -1,7 +1,9 @@
 """Cases run against one build of libfram (the library FRAM_LIBRARY names, else the release
 build): sample, synthesise with the early RIR and run the adjoint with early-RIR upstream
-gradients over the half lengths, tile lengths and scene shapes the parity tests sweep, then print,
-per case, the device status bits and a SHA-256 of every output.  tests/test_gpu_debug_bounds.py
+gradients over the half lengths, tile lengths and scene shapes the parity tests sweep, and the
+multi-rate path (delay_mode 1) with the early RIR at every second-resampler rate, ragged tiles and
+a batch whose high-pass runs in several pieces; then print, per case, the device status bits and
+a SHA-256 of every output.  tests/test_gpu_debug_bounds.py
 runs it under the release build and the bounds-checking debug build and compares."""
 import hashlib
 import json
@@ -36,6 +38,14 @@ def run_case(sc, tile, seed):
     return {"status": ds.status(), "out": _digest(h, he, gv, gm, gs, gr)}
 
 
+def run_multirate(sc, tile, seed):
+    ds = api.DeviceScene(sc, api.Params(fs=sc.fs, half_len=sc.half_len, tile=tile, delay_mode=1))
+    vs = api.sample(ds, seed=seed)
+    h, he = api.synthesize(ds, vs, early=True)
+    torch.cuda.synchronize()
+    return {"status": ds.status(), "out": _digest(h, he)}
+
+
 def cases():
     out = {}
     for K in (1, 5, 16, 17, 33, 64, 100, 128):
@@ -49,6 +59,15 @@ def cases():
         sc = scenes.make_batch("shape", M + S, 3, S, M, geometry, spacing, [3, 3, 2.5], [8, 6, 4], 0.1, 0.4, fs, 40,
                                images_fixed=300)
         out[f"shape_{int(fs)}_{M}x{S}"] = run_case(sc, 512, 7)
+    # multi-rate: r_l = 2 .. 11 (250, 96, 48, 32, 22.05, 16, 11.025, 8 kHz), tiles 256 and 2048
+    for fs, t60 in ((250000.0, (0.03, 0.04)), (96000.0, (0.03, 0.06)), (48000.0, (0.1, 0.2)),
+                    (32000.0, (0.05, 0.1)), (22050.0, (0.05, 0.15)), (16000.0, (0.02, 0.25)),
+                    (11025.0, (0.1, 0.2)), (8000.0, (0.1, 0.3))):
+        sc = scenes.tiny(seed=int(fs) % 89, B=3, S=2, M=2, images=120, fs=fs, t60_lo=t60[0], t60_hi=t60[1])
+        for tile in (256, 2048):
+            out[f"mr_{int(fs)}_tile{tile}"] = run_multirate(sc, tile, 40 + tile % 7)
+    # 48 rooms of the 1024-room training batch (T60 0.1-0.7 s): up to five high-pass pieces per channel
+    out["mr_batch_1024_48rooms"] = run_multirate(scenes.batch_1024(0).subset(range(48)), 0, 9)
     return out
 
 
