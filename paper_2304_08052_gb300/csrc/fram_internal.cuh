@@ -295,7 +295,10 @@ inline MrRates mr_rates(double fs)
 
 // Multi-rate mode: the high-pass runs over pieces of P intermediate samples, each starting from
 // the state reached over the W samples before it (the pole radius rho of the 80 Hz high-pass at
-// r_l fs gives rho^W <= 1e-9); pmax pieces cover the longest channel.
+// r_l fs gives rho^W <= 1e-9); pmax pieces cover the longest channel.  The recursion is latency
+// bound per thread (two dependent fused multiply-adds per sample), so the pieces are short enough
+// to give every SM enough independent channels (P = 32768 splits a 16 kHz batch's 0.1-0.7 s
+// channels into 1-3 pieces) and long enough to keep the warm-up reads (W of every P samples) small.
 struct MrPieces {
     int P, W, pmax;
 };
@@ -308,7 +311,7 @@ inline MrPieces mr_pieces(double fs, int max_len)
     const double rho = std::sqrt(a2);
     MrPieces pc;
     pc.W = ((int)std::ceil(std::log(1e-9) / std::log(rho)) + 63) & ~63;
-    pc.P = std::max(16384, 2 * pc.W);
+    pc.P = std::max(32768, 4 * pc.W);
     pc.P = (pc.P + 63) & ~63;
     const int64_t lm = (int64_t)r.rl * (max_len > 0 ? max_len : 1) + 8;
     pc.pmax = (int)((lm + pc.P - 1) / pc.P);

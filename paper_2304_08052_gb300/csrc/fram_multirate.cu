@@ -14,7 +14,7 @@
 // consecutive intermediate samples (|m| <= 10 down).
 //   mr_table        the first filter F in polyphase rows: row p holds F(p - HL + i down),
 //                   i = 0..31, so the 21 taps of one impulse are one row read by 32 lanes.
-//   mr_stage_a      persistent warps over (room, source, tile, mic, sub-tile of 256 r_l
+//   mr_stage_a      persistent warps over (room, source, tile, mic, sub-tile of 128 r_l
 //                   intermediate samples); the images that can reach the sub-tile come from the
 //                   32-sample key blocks; each lane evaluates one image's q (the grid decides an
 //                   integer): in float-pair arithmetic when that is more than 4e-6 from a grid
@@ -22,13 +22,15 @@
 //                   reference (no fused multiply-add), then each impulse is added with one lane
 //                   per tap into the warp's shared buffer (and into the early buffer when q lies
 //                   in the Eq. 9 window on the high-rate grid).  Tiles go to y1 in global memory.
-//   mr_room_order, mr_hpf_piece   the high-pass, its state and products as float pairs (poles
-//                   near z = 1 at 80 Hz make a float32 recursion lose ~1e-5 of the peak), over
+//   mr_room_order, mr_hpf_piece   the high-pass as two complex first-order sections in FP32,
+//                   each pairing one zero at z = 1 with one pole (well conditioned where the
+//                   direct form, with its poles near z = 1, loses ~1e-5 of the peak in FP32), over
 //                   pieces of P samples of every channel: each piece starts from the state the
 //                   recursion reaches over the W samples before it (rho^W <= 1e-9 of the state it
-//                   forgets), a warm-up pass storing those states and a pass filtering every piece
-//                   in place; units (piece, room rank, channel) grouped so a warp's pieces have
-//                   nearly equal lengths, staged through shared memory in 64-sample chunks.
+//                   forgets), a warm-up pass storing those states (only for channels longer than
+//                   P) and a pass filtering every piece in place; units (piece, room rank,
+//                   channel) grouped so a warp's pieces have nearly equal lengths, staged through
+//                   shared memory in 32-sample chunks.
 //   mr_down         the second resampler (ratio 1/r_l, compile-time taps), four consecutive output
 //                   samples per thread (each window value read once, four per 16-byte load) from a
 //                   window staged in shared memory.
@@ -42,6 +44,11 @@ namespace {
 
 constexpr int kMrThreads = 256;
 constexpr int kMrNJ = 32;        // polyphase row length (>= 21 taps per impulse)
+// Stage A sub-tile: kSubA output samples (kSubA r_l intermediate ones) per unit.  A warp's buffers
+// take ~8 KB at r_l = 7 with the early RIR, so three 8-warp CTAs fit an SM (256 took ~15 KB and
+// left one CTA, latency-bound at 8 warps; 64 scans too many images twice at the sub-tile edges);
+// tiles are multiples of 256.
+constexpr int kSubA = 128;
 
 // ---- the second resampler (ratio 1/RL): compile-time Kaiser windowed sinc --------------------
 constexpr double cx_pi = 3.14159265358979323846;
@@ -255,7 +262,7 @@ __global__ void __launch_bounds__(kMrThreads) mr_stage_a(LaunchArgs a, bool want
     extern __shared__ __align__(16) float mr_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int T = a.tile, M = a.M, rl = a.rl, up = a.up, down = a.down, HL = a.HLA;
-    const int TA = 256 * rl, nsub = T / 256;
+    const int TA = kSubA * rl, nsub = T / kSubA;
     float* tab = mr_smem;                                        // down x 32
     float* buf = mr_smem + down * kMrNJ + wid * mr_warp_floats(TA, want_early);
     float* bufe = want_early ? buf + TA + 64 : nullptr;
@@ -382,24 +389,33 @@ __global__ void __launch_bounds__(kMrThreads) mr_stage_a(LaunchArgs a, bool want
 }
 
 // ---- stage B: the high-pass, in pieces ---------------------------------------------------------
-// The 80 Hz high-pass runs over each channel's L_m intermediate samples, in place, as the
-// direct-form recursion y[n] = b0 (x[n] - 2 x[n-1] + x[n-2]) - a1 y[n-1] - a2 y[n-2] with the
-// state and every product as float pairs (the poles lie close to z = 1 at 80 Hz, so a float32
-// recursion loses ~1e-5 of the peak, and the rounding of b0 times the second difference alone,
-// amplified near z = 1, costs about as much).  A whole channel walked by one thread takes ~190
-// cycles per sample on its longest channels, so channels are cut into pieces (mr_hpf_piece).
+// The 80 Hz Butterworth high-pass H(z) = b0 (1 - z^-1)^2 / ((1 - p z^-1)(1 - p* z^-1)) runs over
+// each channel's L_m intermediate samples, in place, as a cascade of two complex first-order
+// sections in FP32, each pairing one zero at z = 1 with one pole:
+//   u[n] = p  u[n-1] + (x[n] - x[n-1]),   v[n] = p* v[n-1] + (u[n] - u[n-1]),   y[n] = b0 Re v[n].
+// The poles lie close to z = 1 (|p| ~ 1 - 2.8e-3 at 112 kHz), where the direct form
+// y[n] = b0 (x[n] - 2 x[n-1] + x[n-2]) - a1 y[n-1] - a2 y[n-2] amplifies every rounding by its DC
+// gain ~ 1/|1 - p|^2 (~1e-5 of the peak in FP32).  A section with its zero at z = 1 has gain <= ~1.4
+// at every frequency, and a rounding inside it grows only by sqrt(1 / (1 - |p|^2)) (~20-50 at the
+// rates used): ~1e-6 of the peak with heavy low-frequency content.  12 FP32 operations per sample,
+// two dependent fused multiply-adds on the critical path of each section.
 struct HpfCoef {
-    f2 b0, a1, a2;
+    float pr, pi, b0;
 };
 
+// p = (1 + s_p) / (1 - s_p) for the analog pole s_p = k (-1 + j) / sqrt(2), k = tan(pi 80 / fsr)
+// (the bilinear map with the cutoff pre-warped): Re p = (1 - k^2) / den, Im p = sqrt(2) k / den,
+// b0 = 1 / den, den = 1 + sqrt(2) k + k^2 -- the same filter as b0 (1 - 2 z^-1 + z^-2) /
+// (1 + a1 z^-1 + a2 z^-2) with a1 = -2 Re p and a2 = |p|^2, in FP64 without cancellation.
 __device__ __forceinline__ HpfCoef hpf_coef(double fsr)
 {
     const double k = tan(3.14159265358979323846 * 80.0 / fsr);
-    const double den = 1.0 + sqrt(2.0) * k + k * k;
+    const double r2k = sqrt(2.0) * k;
+    const double den = 1.0 + r2k + k * k;
     HpfCoef c;
-    c.b0 = f2_from_double(1.0 / den);
-    c.a1 = f2_from_double(2.0 * (k * k - 1.0) / den);
-    c.a2 = f2_from_double((1.0 - sqrt(2.0) * k + k * k) / den);
+    c.pr = (float)((1.0 - k * k) / den);
+    c.pi = (float)(r2k / den);
+    c.b0 = (float)(1.0 / den);
     return c;
 }
 
@@ -440,7 +456,7 @@ __global__ void __launch_bounds__(256) mr_room_order(LaunchArgs a, int P, int pm
 }
 
 constexpr int kSeqThreads = 128;
-constexpr int kSeqChunk = 64;              // samples per staged chunk and unit
+constexpr int kSeqChunk = 32;              // samples per staged chunk and unit (16 lanes x 2 per row)
 constexpr int kSeqRow = kSeqChunk + 4;     // row stride (floats): 16-byte rows, float4 reads of a row conflict-free
 
 // Asynchronous 8-byte global -> shared copy of n bytes (0, 4 or 8), the rest zero-filled.
@@ -450,24 +466,26 @@ __device__ __forceinline__ void cp_async8(float* dst, const float* src, int n)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
 
-// Chunk k0 of the warp's 32 units into the staging tile T (row q = unit q), as one group; anyp:
-// a valid pointer of the warp, the (unread) source of zero-byte copies.
+// Chunk k0 of the warp's 32 units into the staging tile T (row q = unit q), as one group: half-warp
+// h copies rows 2 i + h, lane (lane mod 16) samples k0 + 2 (lane mod 16) and the next; anyp: a
+// valid pointer of the warp, the (unread) source of zero-byte copies.
 __device__ __forceinline__ void seq_stage_in(float* T, float* const* ptr, const int* len, const float* anyp, int k0,
                                              int lane)
 {
-    const int kk = k0 + 2 * lane;
+    const int c2 = 2 * (lane & 15), kk = k0 + c2;
 #pragma unroll 8
-    for (int q = 0; q < 32; ++q) {
+    for (int i = 0; i < 16; ++i) {
+        const int q = 2 * i + (lane >> 4);
         const int Lq = len[q];
         const int n = kk + 1 < Lq ? 8 : (kk < Lq ? 4 : 0);
-        cp_async8(T + q * kSeqRow + 2 * lane, n ? ptr[q] + kk : anyp, n);
+        cp_async8(T + q * kSeqRow + c2, n ? ptr[q] + kk : anyp, n);
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
 // Pieces: a channel's L_m samples are cut into pieces of P; piece p starts at S = p P.  The
 // high-pass state forgets where it started: after W samples a start state contributes less than
-// rho^W <= 1e-9 of itself (rho = the pole radius), so piece p's start state is the state the
+// rho^W <= 1e-9 of itself (rho = |p|, the pole radius), so piece p's start state is the state the
 // recursion reaches from a zero state over the W samples before S (exact when S <= W, where it
 // starts at sample 0).  warm = true: every piece p >= 1 runs that warm-up (reading only) and
 // stores its state; warm = false: every piece runs from its state (zero for piece 0) over its own
@@ -475,7 +493,7 @@ __device__ __forceinline__ void seq_stage_in(float* T, float* const* ptr, const 
 // the rooms with a piece p are ranks [0, counts[p]) (mr_room_order), so a warp's 32 units are
 // pieces of nearly equal length.
 struct PieceState {
-    float y1h, y1l, y2h, y2l, x1, x2, pad0, pad1;
+    float ur, ui, vr, vi, x1, pad0, pad1, pad2;   // section states u, v and the last input
 };
 
 __global__ void __launch_bounds__(kSeqThreads) mr_hpf_piece(LaunchArgs a, bool with_early, bool warm, int P, int W,
@@ -531,18 +549,24 @@ __global__ void __launch_bounds__(kSeqThreads) mr_hpf_piece(LaunchArgs a, bool w
     __syncwarp();
     if (Lw == 0) return;                     // the whole warp has no unit (uniform)
     const HpfCoef c = hpf_coef((double)a.rl * a.fs);
-    float x1 = 0.f, x2 = 0.f;
-    f2 y1{0.f, 0.f}, y2{0.f, 0.f};
+    float ur = 0.f, ui = 0.f, vr = 0.f, vi = 0.f, x1 = 0.f;
     if (!warm && p > 0 && rec) {
         const PieceState st = *rec;
-        y1 = f2{st.y1h, st.y1l}; y2 = f2{st.y2h, st.y2l}; x1 = st.x1; x2 = st.x2;
+        ur = st.ur; ui = st.ui; vr = st.vr; vi = st.vi; x1 = st.x1;
     }
     auto step = [&](float x0) {
-        f2 uu = two_sum(x0, x2);
-        uu = f2_add_f(uu, -2.0f * x1);
-        const f2 y0 = f2_add(f2_mul(c.b0, uu), f2_neg(f2_add(f2_mul(c.a1, y1), f2_mul(c.a2, y2))));
-        x2 = x1; x1 = x0; y2 = y1; y1 = y0;
-        return y0.hi + y0.lo;
+        const float dx = __fsub_rn(x0, x1);
+        x1 = x0;
+        const float nr = __fmaf_rn(c.pr, ur, __fmaf_rn(-c.pi, ui, dx));       // u <- p u + dx
+        const float ni = __fmaf_rn(c.pr, ui, __fmul_rn(c.pi, ur));
+        const float dr = __fsub_rn(nr, ur), di = __fsub_rn(ni, ui);
+        ur = nr;
+        ui = ni;
+        const float mr = __fmaf_rn(c.pr, vr, __fmaf_rn(c.pi, vi, dr));        // v <- p* v + du
+        const float mi = __fmaf_rn(c.pr, vi, __fmaf_rn(-c.pi, vr, di));
+        vr = mr;
+        vi = mi;
+        return __fmul_rn(c.b0, mr);
     };
     const unsigned has = __ballot_sync(0xffffffffu, x != nullptr);
     const float* anyp = ptr[__ffs(has) - 1];
@@ -570,19 +594,20 @@ __global__ void __launch_bounds__(kSeqThreads) mr_hpf_piece(LaunchArgs a, bool w
                 *reinterpret_cast<float4*>(row + i) = v;
             }
             __syncwarp();
-            const int kk = k0 + 2 * lane;
+            const int c2 = 2 * (lane & 15), kk = k0 + c2;
 #pragma unroll 8
-            for (int q = 0; q < 32; ++q) {
+            for (int i = 0; i < 16; ++i) {
+                const int q = 2 * i + (lane >> 4);
                 float* xq = ptr[q];
                 const int Lq = lens[q];
-                const float2 v = *reinterpret_cast<const float2*>(T + q * kSeqRow + 2 * lane);
+                const float2 v = *reinterpret_cast<const float2*>(T + q * kSeqRow + c2);
                 if (kk + 1 < Lq) __stcs(reinterpret_cast<float2*>(xq + kk), v);
                 else if (kk < Lq) xq[kk] = v.x;
             }
         }
         __syncwarp();
     }
-    if (warm && rec) *rec = PieceState{y1.hi, y1.lo, y2.hi, y2.lo, x1, x2, 0.f, 0.f};
+    if (warm && rec) *rec = PieceState{ur, ui, vr, vi, x1, 0.f, 0.f, 0.f};
 }
 
 // ---- stage C: the resampler 1/RL, one thread per output sample ------------------------------
@@ -710,7 +735,7 @@ cudaError_t launch_synthesize_mr(const LaunchArgs& a, const float* pos_hi, const
     mr_table<<<1, 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int TA = 256 * a.rl;
+    const int TA = kSubA * a.rl;
     const int smem = (int)sizeof(float) * (a.down * kMrNJ + (kMrThreads / 32) * mr_warp_floats(TA, early != nullptr));
     int per_sm = 0;
     if ((e = kernel_residency((const void*)mr_stage_a, kMrThreads, smem, &per_sm)) != cudaSuccess) return e;
