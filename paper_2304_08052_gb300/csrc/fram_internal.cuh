@@ -293,14 +293,20 @@ inline MrRates mr_rates(double fs)
     return r;
 }
 
-// Multi-rate mode: the high-pass runs over pieces of P intermediate samples, each starting from
-// the state reached over the W samples before it (the pole radius rho of the 80 Hz high-pass at
-// r_l fs gives rho^W <= 1e-9); pmax pieces cover the longest channel.  The recursion is latency
-// bound per thread (two dependent fused multiply-adds per sample), so the pieces are short enough
-// to give every SM enough independent channels (P = 32768 splits a 16 kHz batch's 0.1-0.7 s
-// channels into 1-3 pieces) and long enough to keep the warm-up reads (W of every P samples) small.
+// Multi-rate mode: the high-pass and the second resampler run fused over pieces of Pn output
+// samples.  The thread of piece p starts its recursion kMrHalo groups of r_l intermediate samples
+// before the piece's first output, at k_s = r_l (p Pn - kMrHalo) (the resampler's window reaches
+// 10 groups back; 12 keeps k_s a multiple of 4 for 16-byte copies), from the state the recursion
+// reaches over the W samples before k_s (the pole radius rho of the 80 Hz high-pass at r_l fs gives
+// rho^W <= 1e-9 of the state it forgets).  pmax pieces cover the longest RIR.  The recursion is
+// latency bound per thread (two dependent fused multiply-adds per sample), so the pieces are short
+// enough to give every SM enough independent channels (~32768 intermediate samples splits a
+// 16 kHz batch's 0.1-0.7 s channels into 1-3 pieces) and long enough to keep the warm-up reads (W
+// of every r_l Pn samples) small.
+constexpr int kMrHalo = 12;
+
 struct MrPieces {
-    int P, W, pmax;
+    int Pn, W, pmax;    // output samples per piece (a multiple of 4), warm-up length, pieces
 };
 
 inline MrPieces mr_pieces(double fs, int max_len)
@@ -311,10 +317,9 @@ inline MrPieces mr_pieces(double fs, int max_len)
     const double rho = std::sqrt(a2);
     MrPieces pc;
     pc.W = ((int)std::ceil(std::log(1e-9) / std::log(rho)) + 63) & ~63;
-    pc.P = std::max(32768, 4 * pc.W);
-    pc.P = (pc.P + 63) & ~63;
-    const int64_t lm = (int64_t)r.rl * (max_len > 0 ? max_len : 1) + 8;
-    pc.pmax = (int)((lm + pc.P - 1) / pc.P);
+    const int P = std::max(32768, 4 * pc.W);
+    pc.Pn = ((P + r.rl - 1) / r.rl + 3) & ~3;
+    pc.pmax = (int)(((int64_t)(max_len > 0 ? max_len : 1) + pc.Pn - 1) / pc.Pn);
     return pc;
 }
 

@@ -22,18 +22,16 @@
 //                   reference (no fused multiply-add), then each impulse is added with one lane
 //                   per tap into the warp's shared buffer (and into the early buffer when q lies
 //                   in the Eq. 9 window on the high-rate grid).  Tiles go to y1 in global memory.
-//   mr_room_order, mr_hpf_piece   the high-pass as two complex first-order sections in FP32,
-//                   each pairing one zero at z = 1 with one pole (well conditioned where the
-//                   direct form, with its poles near z = 1, loses ~1e-5 of the peak in FP32), over
-//                   pieces of P samples of every channel: each piece starts from the state the
-//                   recursion reaches over the W samples before it (rho^W <= 1e-9 of the state it
-//                   forgets), a warm-up pass storing those states (only for channels longer than
-//                   P) and a pass filtering every piece in place; units (piece, room rank,
-//                   channel) grouped so a warp's pieces have nearly equal lengths, staged through
-//                   shared memory in 32-sample chunks.
-//   mr_down         the second resampler (ratio 1/r_l, compile-time taps), four consecutive output
-//                   samples per thread (each window value read once, four per 16-byte load) from a
-//                   window staged in shared memory.
+//   mr_room_order, mr_hpf_warm, mr_hpf_down<RL>   the high-pass as two complex first-order
+//                   sections in FP32, each pairing one zero at z = 1 with one pole (well
+//                   conditioned where the direct form, with its poles near z = 1, loses ~1e-5 of
+//                   the peak in FP32), fused with the second resampler (ratio 1/r_l, compile-time
+//                   taps): one thread walks a piece of Pn output samples of one channel, runs the
+//                   recursion and accumulates the 21 outputs each intermediate sample reaches, so
+//                   the high-passed signal never goes back to memory.  A piece starts from the
+//                   state the recursion reaches over the W samples before it (rho^W <= 1e-9 of
+//                   the state it forgets), stored by a warm-up pass; units (piece, room rank,
+//                   channel) are grouped so a warp's pieces have nearly equal lengths.
 #include <cmath>
 #include <utility>
 
@@ -128,6 +126,8 @@ __device__ double dev_i0(double x)
 
 // F(m), |m| <= HL = 10 max(up, down): lowpass with cutoff pi / max(up, down), Kaiser window,
 // scaled to sum to `up`; stored as tab[p * 32 + i] = F(p - HL + i down) (zero past the end).
+// One CTA per row p: each CTA forms the normalising sum itself (a few FP64 Bessel series per
+// thread) and writes its 32 entries, so the rows are built side by side.
 __global__ void __launch_bounds__(256) mr_table(LaunchArgs a)
 {
     __shared__ double part[256];
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(256) mr_table(LaunchArgs a)
         __syncthreads();
     }
     const double scale = (double)up / part[0];
-    for (int e = threadIdx.x; e < down * kMrNJ; e += blockDim.x) {
+    for (int e = blockIdx.x * kMrNJ + threadIdx.x; e < (blockIdx.x + 1) * kMrNJ; e += blockDim.x) {
         const int p = e / kMrNJ, i = e % kMrNJ;
         const int m = p - HL + i * down;
         float v = 0.0f;
@@ -191,7 +191,7 @@ __device__ __forceinline__ MrChan mr_chan(const LaunchArgs& a, const RoomConst& 
 
 // Floats in each intermediate buffer (mr_y, mr_ye): the workspace layout's r_l * sum_b S M L_b
 // plus 8 floats of slack per channel and 4 at the end; the debug build's guards check against it.
-__device__ __forceinline__ int64_t mr_inter_floats(const LaunchArgs& a)
+[[maybe_unused]] __device__ __forceinline__ int64_t mr_inter_floats(const LaunchArgs& a)
 {
     return (int64_t)a.rl * a.rir_total + 8 * (int64_t)a.B * a.S * a.M + 4;
 }
@@ -388,10 +388,10 @@ __global__ void __launch_bounds__(kMrThreads) mr_stage_a(LaunchArgs a, bool want
     }
 }
 
-// ---- stage B: the high-pass, in pieces ---------------------------------------------------------
+// ---- stages B and C: the high-pass and the second resampler ----------------------------------
 // The 80 Hz Butterworth high-pass H(z) = b0 (1 - z^-1)^2 / ((1 - p z^-1)(1 - p* z^-1)) runs over
-// each channel's L_m intermediate samples, in place, as a cascade of two complex first-order
-// sections in FP32, each pairing one zero at z = 1 with one pole:
+// each channel's L_m intermediate samples as a cascade of two complex first-order sections in FP32,
+// each pairing one zero at z = 1 with one pole:
 //   u[n] = p  u[n-1] + (x[n] - x[n-1]),   v[n] = p* v[n-1] + (u[n] - u[n-1]),   y[n] = b0 Re v[n].
 // The poles lie close to z = 1 (|p| ~ 1 - 2.8e-3 at 112 kHz), where the direct form
 // y[n] = b0 (x[n] - 2 x[n-1] + x[n-2]) - a1 y[n-1] - a2 y[n-2] amplifies every rounding by its DC
@@ -419,27 +419,19 @@ __device__ __forceinline__ HpfCoef hpf_coef(double fsr)
     return c;
 }
 
-__device__ __forceinline__ void mr_channel_of(const LaunchArgs& a, int64_t chan, int& b, int& s, int& m)
-{
-    m = (int)(chan % a.M);
-    s = (int)((chan / a.M) % a.S);
-    b = (int)(chan / ((int64_t)a.M * a.S));
-}
-
 // Rooms whose rank needs the all-pairs count below; larger batches keep their own order.
 constexpr int kOrderMax = 65536;
 
-// Every channel of room b has L_m intermediate samples (mr_chan) and ceil(L_m / P) pieces; L_m
-// and the RIR length do not decrease with T60, so rooms are ranked by decreasing T60 (ties by
-// index; a room the prologue rejected last).  counts[p] = the number of rooms with more than p
-// pieces, so the rooms that have a piece p are ranks [0, counts[p]).  counts (pmax entries) must
-// be zero on entry.
-__global__ void __launch_bounds__(256) mr_room_order(LaunchArgs a, int P, int pmax, int* __restrict__ counts)
+// Every RIR of room b has L_b output samples and ceil(L_b / Pn) pieces; L_b does not decrease
+// with T60, so rooms are ranked by decreasing T60 (ties by index; a room the prologue rejected
+// last).  counts[p] = the number of rooms with more than p pieces, so the rooms that have a piece p
+// are ranks [0, counts[p]).  counts (pmax entries) must be zero on entry.
+__global__ void __launch_bounds__(256) mr_room_order(LaunchArgs a, int Pn, int pmax, int* __restrict__ counts)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= a.B) return;
     const RoomConst rb = a.room[b];
-    const int64_t Lb = rb.len >= 1 ? mr_chan(a, rb, b, 0, 0).Lm : 0;
+    const int Lb = rb.len >= 1 ? rb.len : 0;
     if (a.B <= kOrderMax) {
         const float tb = rb.len >= 1 ? a.rt60[b] : -1.0f;
         int rank = 0;
@@ -448,16 +440,68 @@ __global__ void __launch_bounds__(256) mr_room_order(LaunchArgs a, int P, int pm
             rank += (tc > tb) || (tc == tb && c < b);
         }
         a.mr_order[rank] = b;
-        const int np = (int)((Lb + P - 1) / P);
+        const int np = (Lb + Pn - 1) / Pn;
         for (int q = 0; q < np && q < pmax; ++q) atomicAdd(&counts[q], 1);
     } else if (b < pmax) {
         counts[b] = a.B;        // unsorted: every room is a candidate for every piece
     }
 }
 
+// The high-pass state of one channel: sections u, v and the last input.
+struct HpfState {
+    float ur, ui, vr, vi, x1;
+};
+
+// One sample through the two sections; returns y = b0 Re v.
+__device__ __forceinline__ float hpf_step(const HpfCoef& c, HpfState& h, float x0)
+{
+    const float dx = __fsub_rn(x0, h.x1);
+    h.x1 = x0;
+    const float nr = __fmaf_rn(c.pr, h.ur, __fmaf_rn(-c.pi, h.ui, dx));       // u <- p u + dx
+    const float ni = __fmaf_rn(c.pr, h.ui, __fmul_rn(c.pi, h.ur));
+    const float dr = __fsub_rn(nr, h.ur), di = __fsub_rn(ni, h.ui);
+    h.ur = nr;
+    h.ui = ni;
+    const float mr = __fmaf_rn(c.pr, h.vr, __fmaf_rn(c.pi, h.vi, dr));        // v <- p* v + du
+    const float mi = __fmaf_rn(c.pr, h.vi, __fmaf_rn(-c.pi, h.vr, di));
+    h.vr = mr;
+    h.vi = mi;
+    return __fmul_rn(c.b0, mr);
+}
+
+// A piece's start state, stored by the warm-up pass (one record per channel and piece).
+struct PieceState {
+    float ur, ui, vr, vi, x1, pad0, pad1, pad2;
+};
+
+// Unit t of the units (piece, room rank, channel) in that order, pieces from `first`: the rooms
+// with a piece p are ranks [0, counts[p]) (mr_room_order), so a warp's 32 units are pieces of
+// nearly equal length.  Returns the piece (-1: none) and sets the room, source, mic and channel
+// kind; CH = channels per room.
+__device__ __forceinline__ int mr_unit(const LaunchArgs& a, int64_t t, int first, int pmax, const int* counts, int CH,
+                                       int& b, int& s, int& m, bool& is_early)
+{
+    int p = -1;
+    for (int q = first; q < pmax; ++q) {
+        const int64_t nq = (int64_t)counts[q] * CH;
+        if (t < nq) { p = q; break; }
+        t -= nq;
+    }
+    if (p < 0) return -1;
+    const int SM = a.S * a.M;
+    const int k = (int)(t / CH), j = (int)(t - (int64_t)k * CH);
+    b = a.B <= kOrderMax ? a.mr_order[k] : k;
+    is_early = j >= SM;
+    const int jj = is_early ? j - SM : j;
+    s = jj / a.M;
+    m = jj - s * a.M;
+    return p;
+}
+
+// ---- the warm-up pass: each piece's start state --------------------------------------------
 constexpr int kSeqThreads = 128;
 constexpr int kSeqChunk = 32;              // samples per staged chunk and unit (16 lanes x 2 per row)
-constexpr int kSeqRow = kSeqChunk + 4;     // row stride (floats): 16-byte rows, float4 reads of a row conflict-free
+constexpr int kSeqRow = kSeqChunk + 4;     // row stride (floats): 16-byte rows
 
 // Asynchronous 8-byte global -> shared copy of n bytes (0, 4 or 8), the rest zero-filled.
 __device__ __forceinline__ void cp_async8(float* dst, const float* src, int n)
@@ -483,22 +527,12 @@ __device__ __forceinline__ void seq_stage_in(float* T, float* const* ptr, const 
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-// Pieces: a channel's L_m samples are cut into pieces of P; piece p starts at S = p P.  The
-// high-pass state forgets where it started: after W samples a start state contributes less than
-// rho^W <= 1e-9 of itself (rho = |p|, the pole radius), so piece p's start state is the state the
-// recursion reaches from a zero state over the W samples before S (exact when S <= W, where it
-// starts at sample 0).  warm = true: every piece p >= 1 runs that warm-up (reading only) and
-// stores its state; warm = false: every piece runs from its state (zero for piece 0) over its own
-// samples and writes the result in place.  Units are (piece, room rank, channel) in that order:
-// the rooms with a piece p are ranks [0, counts[p]) (mr_room_order), so a warp's 32 units are
-// pieces of nearly equal length.
-struct PieceState {
-    float ur, ui, vr, vi, x1, pad0, pad1, pad2;   // section states u, v and the last input
-};
-
-__global__ void __launch_bounds__(kSeqThreads) mr_hpf_piece(LaunchArgs a, bool with_early, bool warm, int P, int W,
-                                                            int pmax, const int* __restrict__ counts,
-                                                            PieceState* __restrict__ state)
+// Piece p >= 1 starts at k_s = r_l (p Pn - kMrHalo); its start state is the state the recursion
+// reaches from a zero state over the W samples before k_s (exact when k_s <= W: it starts at 0).
+// Each unit reads those samples (staged in 32-sample chunks) and stores the state.
+__global__ void __launch_bounds__(kSeqThreads) mr_hpf_warm(LaunchArgs a, bool with_early, int Pn, int W, int pmax,
+                                                           const int* __restrict__ counts,
+                                                           PieceState* __restrict__ state)
 {
     __shared__ __align__(16) float tile[kSeqThreads / 32][2][32 * kSeqRow];
     __shared__ float* wptr[kSeqThreads / 32][32];
@@ -506,36 +540,24 @@ __global__ void __launch_bounds__(kSeqThreads) mr_hpf_piece(LaunchArgs a, bool w
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int SM = a.S * a.M;
     const int CH = SM * (with_early ? 2 : 1);
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int len = 0, p = -1;
+    int b = 0, s = 0, m = 0;
+    bool is_early = false;
+    const int p = mr_unit(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, 1, pmax, counts, CH, b, s, m, is_early);
+    int len = 0;
     float* x = nullptr;
     PieceState* rec = nullptr;
-    for (int q = warm ? 1 : 0; q < pmax; ++q) {      // locate the unit: piece q holds counts[q] CH units
-        const int64_t nq = (int64_t)counts[q] * CH;
-        if (t < nq) { p = q; break; }
-        t -= nq;
-    }
-    if (p >= 0) {
-        const int k = (int)(t / CH), j = (int)(t - (int64_t)k * CH);
-        const int b = a.B <= kOrderMax ? a.mr_order[k] : k;
+    if (p >= 1) {
         const RoomConst rc = a.room[b];
         if (rc.len >= 1) {
-            const bool is_early = j >= SM;
-            const int jj = is_early ? j - SM : j;
-            const int s = jj / a.M, m = jj - s * a.M;
             const MrChan ch = mr_chan(a, rc, b, s, m);
-            const int64_t S = (int64_t)p * P;
-            if (S < ch.Lm && FRAM_GUARD(a.hdr, (ch.off & 3) == 0 && ch.off + ch.Lm <= mr_inter_floats(a))) {
+            const int64_t ks = (int64_t)a.rl * ((int64_t)p * Pn - kMrHalo);
+            if (ks > 0 && ks <= ch.Lm &&
+                FRAM_GUARD(a.hdr, (ch.off & 3) == 0 && ch.off + ch.Lm <= mr_inter_floats(a))) {
                 const int64_t gc = ((int64_t)b * a.S + s) * a.M + m + (is_early ? (int64_t)a.B * SM : 0);
                 rec = state + gc * pmax + p;
-                if (warm) {
-                    const int64_t b0 = S > W ? S - W : 0;
-                    x = (is_early ? a.mr_ye : a.mr_y) + ch.off + b0;
-                    len = (int)(S - b0);
-                } else {
-                    x = (is_early ? a.mr_ye : a.mr_y) + ch.off + S;
-                    len = (int)(ch.Lm - S < P ? ch.Lm - S : P);
-                }
+                const int64_t b0 = ks > W ? ks - W : 0;           // both multiples of 4
+                x = (is_early ? a.mr_ye : a.mr_y) + ch.off + b0;
+                len = (int)(ks - b0);
             }
         }
     }
@@ -549,30 +571,11 @@ __global__ void __launch_bounds__(kSeqThreads) mr_hpf_piece(LaunchArgs a, bool w
     __syncwarp();
     if (Lw == 0) return;                     // the whole warp has no unit (uniform)
     const HpfCoef c = hpf_coef((double)a.rl * a.fs);
-    float ur = 0.f, ui = 0.f, vr = 0.f, vi = 0.f, x1 = 0.f;
-    if (!warm && p > 0 && rec) {
-        const PieceState st = *rec;
-        ur = st.ur; ui = st.ui; vr = st.vr; vi = st.vi; x1 = st.x1;
-    }
-    auto step = [&](float x0) {
-        const float dx = __fsub_rn(x0, x1);
-        x1 = x0;
-        const float nr = __fmaf_rn(c.pr, ur, __fmaf_rn(-c.pi, ui, dx));       // u <- p u + dx
-        const float ni = __fmaf_rn(c.pr, ui, __fmul_rn(c.pi, ur));
-        const float dr = __fsub_rn(nr, ur), di = __fsub_rn(ni, ui);
-        ur = nr;
-        ui = ni;
-        const float mr = __fmaf_rn(c.pr, vr, __fmaf_rn(c.pi, vi, dr));        // v <- p* v + du
-        const float mi = __fmaf_rn(c.pr, vi, __fmaf_rn(-c.pi, vr, di));
-        vr = mr;
-        vi = mi;
-        return __fmul_rn(c.b0, mr);
-    };
+    HpfState h{0.f, 0.f, 0.f, 0.f, 0.f};
     const unsigned has = __ballot_sync(0xffffffffu, x != nullptr);
     const float* anyp = ptr[__ffs(has) - 1];
     seq_stage_in(tile[wid][0], ptr, lens, anyp, 0, lane);
     for (int k0 = 0, buf = 0; k0 < Lw; k0 += kSeqChunk, buf ^= 1) {
-        float* T = tile[wid][buf];
         // The next chunk flies while this one is filtered; its buffer was emptied by the previous chunk.
         if (k0 + kSeqChunk < Lw) {
             seq_stage_in(tile[wid][buf ^ 1], ptr, lens, anyp, k0 + kSeqChunk, lane);
@@ -581,146 +584,198 @@ __global__ void __launch_bounds__(kSeqThreads) mr_hpf_piece(LaunchArgs a, bool w
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         }
         __syncwarp();
-        float* row = T + lane * kSeqRow;
-        if (warm) {
-            // the state at the end of the warm-up: stop exactly at the unit's last sample
-            const int n = len - k0 < kSeqChunk ? (len - k0 > 0 ? len - k0 : 0) : kSeqChunk;
-            for (int i = 0; i < n; ++i) step(row[i]);
-        } else {
-#pragma unroll 4
-            for (int i = 0; i < kSeqChunk; i += 4) {
-                float4 v = *reinterpret_cast<const float4*>(row + i);
-                v.x = step(v.x); v.y = step(v.y); v.z = step(v.z); v.w = step(v.w);
-                *reinterpret_cast<float4*>(row + i) = v;
-            }
-            __syncwarp();
-            const int c2 = 2 * (lane & 15), kk = k0 + c2;
-#pragma unroll 8
-            for (int i = 0; i < 16; ++i) {
-                const int q = 2 * i + (lane >> 4);
-                float* xq = ptr[q];
-                const int Lq = lens[q];
-                const float2 v = *reinterpret_cast<const float2*>(T + q * kSeqRow + c2);
-                if (kk + 1 < Lq) __stcs(reinterpret_cast<float2*>(xq + kk), v);
-                else if (kk < Lq) xq[kk] = v.x;
-            }
-        }
+        const float* row = tile[wid][buf] + lane * kSeqRow;
+        // stop exactly at the unit's last sample
+        const int n = len - k0 < kSeqChunk ? (len - k0 > 0 ? len - k0 : 0) : kSeqChunk;
+        for (int i = 0; i < n; ++i) hpf_step(c, h, row[i]);
         __syncwarp();
     }
-    if (warm && rec) *rec = PieceState{ur, ui, vr, vi, x1, 0.f, 0.f, 0.f};
+    if (rec) *rec = PieceState{h.ur, h.ui, h.vr, h.vi, h.x1, 0.f, 0.f, 0.f};
 }
 
-// ---- stage C: the resampler 1/RL, one thread per output sample ------------------------------
-// y[n] = sum_k z[k] F_C(n RL - k), k in [0, L_m); a block stages z over its outputs' window.
-constexpr int kMrOutT = 256;           // threads per block
-constexpr int kMrPer = 4;              // consecutive outputs per thread: its window starts 16-byte aligned
-constexpr int kMrOut = kMrOutT * kMrPer;
+// ---- the high-pass fused with the second resampler (ratio 1/RL, compile-time taps) -----------
+// Output n of a channel is y[n] = sum_k z[k] F_C(n RL - k), |n RL - k| <= HLC = 10 RL, z the
+// high-passed intermediate signal (zero outside [0, L_m)).  One thread walks one piece: it runs the
+// recursion from k_s = RL (n_lo - kMrHalo) in groups of RL samples (group m = samples m RL + j,
+// j < RL) and keeps 21 accumulators, acc[t] for output m - 10 + t: sample j of group m adds
+// z F_C((t - 10) RL - j) = z c[t RL - j] to every t it reaches (t >= 1 when j > 0), and after its
+// first sample output m - 10 is complete.  Iterations take 4 groups = 4 RL samples of each of the
+// warp's 32 pieces (k_s is a multiple of 4, so these are RL whole 16-byte vectors per piece), staged
+// through shared memory by double-buffered asynchronous copies; every sample's register and
+// coefficient are then compile-time.
+constexpr int kFuseThreads = 128;
 
-// Window value w[M] (M = 0 .. (kMrPer - 1) RL + 2 HLC) read once and added to every output j whose
-// taps cover it: output j uses offsets j RL + i, i in [0, 2 HLC], with coefficient F_C(HLC - i).
-// The staged window starts PAD = (-10 RL) mod 4 samples before the first tap, on a 16-byte boundary.
-template <int RL>
-constexpr int kDownPad = (4 - (10 * RL) % 4) % 4;
+struct FuseRow {
+    const float* x;     // the channel's intermediate signal (sample 0)
+    int ks, lm;         // first sample of the piece's walk (may be negative), L_m
+};
 
-template <int RL, int M, int J>
-__device__ __forceinline__ void fir_tap(float x, float* acc)
+// Asynchronous 16-byte global -> shared copy of n bytes (0..16), the rest zero-filled.
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, int n)
 {
-    constexpr int HLC2 = 20 * RL;
-    constexpr int i = M - J * RL - kDownPad<RL>;
-    if constexpr (i >= 0 && i <= HLC2) {
-        constexpr float c = kFc<RL>.v[HLC2 - i];
-        acc[J] = __fmaf_rn(x, c, acc[J]);
-    }
-}
-
-template <int RL, int M, int... J>
-__device__ __forceinline__ void fir_step(float x, float* acc, std::integer_sequence<int, J...>)
-{
-    (fir_tap<RL, M, J>(x, acc), ...);
-}
-
-// Window values 4 C .. 4 C + 3, one 16-byte shared load.
-template <int RL, int C>
-__device__ __forceinline__ void fir_chunk(const float4* __restrict__ w4, float* acc)
-{
-    const float4 v = w4[C];
-    fir_step<RL, 4 * C + 0>(v.x, acc, std::make_integer_sequence<int, kMrPer>{});
-    fir_step<RL, 4 * C + 1>(v.y, acc, std::make_integer_sequence<int, kMrPer>{});
-    fir_step<RL, 4 * C + 2>(v.z, acc, std::make_integer_sequence<int, kMrPer>{});
-    fir_step<RL, 4 * C + 3>(v.w, acc, std::make_integer_sequence<int, kMrPer>{});
-}
-
-template <int RL, int... C>
-__device__ __forceinline__ void fir_dot(const float4* __restrict__ w4, float* acc, std::integer_sequence<int, C...>)
-{
-    (fir_chunk<RL, C>(w4, acc), ...);
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
 
 template <int RL>
-__global__ void __launch_bounds__(kMrOutT) mr_down(LaunchArgs a, float* __restrict__ rir, float* __restrict__ early)
-{
-    constexpr int HLC = 10 * RL;
-    constexpr int PAD = kDownPad<RL>;
-    constexpr int NW = (kMrPer - 1) * RL + 2 * HLC + 1 + PAD;    // window values one thread reads
-    constexpr int W = ((kMrOut * RL + 2 * HLC + 4 + PAD) + 3) & ~3;   // staged window, whole float4s
-    __shared__ __align__(16) float zw[W];
-    const int64_t nch = (int64_t)a.B * a.S * a.M;
-    const int64_t cidx = blockIdx.x;
-    const bool is_early = cidx >= nch;
-    const int64_t chan = is_early ? cidx - nch : cidx;
-    int b, s, m;
-    mr_channel_of(a, chan, b, s, m);
-    const RoomConst rc = a.room[b];
-    const int L = rc.len;
-    const int64_t n0 = (int64_t)blockIdx.y * kMrOut;
-    if (L < 1 || n0 >= L) return;
-    const MrChan ch = mr_chan(a, rc, b, s, m);
-    // block-uniform: the window reads stay in the channel, the outputs in the RIR buffer
-    if (!FRAM_GUARD(a.hdr, ch.off >= 0 && ch.off + ch.Lm <= mr_inter_floats(a) && rc.rir_off >= 0 &&
-                               rc.rir_off + ((int64_t)s * a.M + m + 1) * L <= a.rir_total))
-        return;
-    const float* z = (is_early ? a.mr_ye : a.mr_y) + ch.off;
-    const int64_t k0 = n0 * RL - HLC - PAD;           // window [k0, k0 + W), 16-byte aligned
-    // whole float4s inside [0, L_m) as one 16-byte load each, the vectors at the ends element-wise
-#pragma unroll 4
-    for (int v = threadIdx.x; v < W / 4; v += kMrOutT) {
-        const int64_t k = k0 + 4 * v;
-        float4 q;
-        if (k >= 0 && k + 3 < ch.Lm) {
-            q = __ldcs(reinterpret_cast<const float4*>(z + k));
-        } else {
-            q.x = (k >= 0 && k < ch.Lm) ? z[k] : 0.f;
-            q.y = (k + 1 >= 0 && k + 1 < ch.Lm) ? z[k + 1] : 0.f;
-            q.z = (k + 2 >= 0 && k + 2 < ch.Lm) ? z[k + 2] : 0.f;
-            q.w = (k + 3 >= 0 && k + 3 < ch.Lm) ? z[k + 3] : 0.f;
+struct FuseLane {
+    HpfCoef c;
+    HpfState h;
+    float acc[21];
+    int rb;             // L_m - k_s: z is zero from this walk position on
+    int n_lo, n_hi;     // the piece's outputs
+    float* y;           // the channel's output (sample 0)
+
+    template <int J, int T>
+    __device__ __forceinline__ void add1(float z)
+    {
+        constexpr int i = T * RL - J;
+        if constexpr (i >= 0) {
+            constexpr float cf = kFc<RL>.v[i];
+            acc[T] = __fmaf_rn(z, cf, acc[T]);
         }
-        reinterpret_cast<float4*>(zw)[v] = q;
     }
-    __syncthreads();
-    static_assert((kMrPer * RL) % 4 == 0, "each thread's window starts on a float4");
-    // outputs n = n0 + kMrPer t + j: taps k = n RL - HLC .. n RL + HLC, i.e. window offsets
-    // (kMrPer t + j) RL + PAD + i, i in [0, 2 HLC]
-    float acc[kMrPer];
+    template <int J, int... T>
+    __device__ __forceinline__ void add(float z, std::integer_sequence<int, T...>)
+    {
+        (add1<J, T>(z), ...);
+    }
+    // walk position r (a multiple of RL plus J)
+    template <int J>
+    __device__ __forceinline__ void sample(float x, int r)
+    {
+        const float z0 = hpf_step(c, h, x);
+        add<J>(r < rb ? z0 : 0.0f, std::make_integer_sequence<int, 21>{});
+    }
+    template <int J0, int... J>
+    __device__ __forceinline__ void rest(const float* xv, int r, std::integer_sequence<int, J...>)
+    {
+        (sample<J + 1>(xv[J0 + J + 1], r + J + 1), ...);
+    }
+    // group GG of the iteration starting at walk position r0; g = the group's walk index
+    template <int GG>
+    __device__ __forceinline__ void group(const float* xv, int r0, int g)
+    {
+        constexpr int J0 = GG * RL;
+        sample<0>(xv[J0], r0 + J0);
+        const int n = n_lo + g - (kMrHalo + 10);
+        if (g >= kMrHalo + 10 && n < n_hi) y[n] = acc[0];
+        rest<J0>(xv, r0 + J0, std::make_integer_sequence<int, RL - 1>{});
 #pragma unroll
-    for (int j = 0; j < kMrPer; ++j) acc[j] = 0.f;
-    fir_dot<RL>(reinterpret_cast<const float4*>(zw + threadIdx.x * kMrPer * RL), acc,
-                std::make_integer_sequence<int, (NW + 3) / 4>{});
-    float* y = (is_early ? early : rir) + rc.rir_off + ((int64_t)s * a.M + m) * L;
+        for (int t = 0; t < 20; ++t) acc[t] = acc[t + 1];
+        acc[20] = 0.0f;
+    }
+};
+
+template <int RL>
+__global__ void __launch_bounds__(kFuseThreads) mr_hpf_down(LaunchArgs a, bool with_early, int Pn, int pmax,
+                                                            const int* __restrict__ counts,
+                                                            const PieceState* __restrict__ state,
+                                                            float* __restrict__ rir, float* __restrict__ early)
+{
+    constexpr int CHK = 4 * RL;          // walk samples per iteration
+    constexpr int RS = 8 * RL + 4;       // row stride (floats): two slots; RS / 4 odd, so the
+                                         // 16-byte reads of 8 rows hit distinct banks
+    __shared__ __align__(16) float ring[kFuseThreads / 32][32 * RS];
+    __shared__ __align__(16) FuseRow rows[kFuseThreads / 32][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int SM = a.S * a.M;
+    const int CH = SM * (with_early ? 2 : 1);
+    int b = 0, s = 0, m = 0;
+    bool is_early = false;
+    const int p = mr_unit(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, 0, pmax, counts, CH, b, s, m, is_early);
+    FuseLane<RL> L;
+    L.c = hpf_coef((double)RL * a.fs);
+    L.h = HpfState{0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int j = 0; j < kMrPer; ++j) {
-        const int64_t n = n0 + (int64_t)threadIdx.x * kMrPer + j;
-        if (n < L) y[n] = acc[j];
+    for (int t = 0; t < 21; ++t) L.acc[t] = 0.0f;
+    L.rb = 0;
+    L.n_lo = 0;
+    L.n_hi = 0;
+    L.y = nullptr;
+    FuseRow row{nullptr, 0, 0};
+    int groups = 0;
+    if (p >= 0) {
+        const RoomConst rc = a.room[b];
+        const int n_lo = p * Pn;
+        if (rc.len >= 1 && n_lo < rc.len) {
+            const MrChan ch = mr_chan(a, rc, b, s, m);
+            if (FRAM_GUARD(a.hdr, (ch.off & 3) == 0 && ch.off + ch.Lm <= mr_inter_floats(a) && rc.rir_off >= 0 &&
+                                      rc.rir_off + ((int64_t)s * a.M + m + 1) * rc.len <= a.rir_total)) {
+                const int ks = RL * (n_lo - kMrHalo);
+                L.n_lo = n_lo;
+                L.n_hi = min(n_lo + Pn, rc.len);
+                L.rb = (int)(ch.Lm - ks);
+                L.y = (is_early ? early : rir) + rc.rir_off + ((int64_t)s * a.M + m) * rc.len;
+                row = FuseRow{(is_early ? a.mr_ye : a.mr_y) + ch.off, ks, (int)ch.Lm};
+                groups = L.n_hi - n_lo + kMrHalo + 10;
+                if (p > 0 && ks > 0) {
+                    const int64_t gc = ((int64_t)b * a.S + s) * a.M + m + (is_early ? (int64_t)a.B * SM : 0);
+                    const PieceState st = state[gc * pmax + p];
+                    L.h = HpfState{st.ur, st.ui, st.vr, st.vi, st.x1};
+                }
+            }
+        }
+    }
+    rows[wid][lane] = row;
+    int its = (groups + 3) / 4;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) its = max(its, __shfl_xor_sync(0xffffffffu, its, o));
+    __syncwarp();
+    if (its == 0) return;                    // the whole warp has no unit (uniform)
+    const unsigned has = __ballot_sync(0xffffffffu, row.x != nullptr);
+    const float* anyp = rows[wid][__ffs(has) - 1].x;
+    // iteration `it` of every row into slot it & 1: vector v = i 32 + lane is vector e of row q
+    auto stage = [&](int it) {
+        float* slot = ring[wid] + (it & 1) * CHK;
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+            const int v = i * 32 + lane;
+            const int q = v / RL, e = v - q * RL;
+            const FuseRow rq = rows[wid][q];
+            const int k = rq.ks + it * CHK + 4 * e;
+            int nb = k < 0 ? 0 : 4 * (rq.lm - k);
+            nb = nb < 0 ? 0 : (nb > 16 ? 16 : nb);
+            cp_async16(slot + q * RS + 4 * e, nb ? rq.x + k : anyp, nb);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    stage(0);
+    for (int it = 0; it < its; ++it) {
+        if (it + 1 < its) {
+            stage(it + 1);       // its slot was emptied by iteration it - 1
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        __syncwarp();
+        const float4* src = reinterpret_cast<const float4*>(ring[wid] + lane * RS + (it & 1) * CHK);
+        float xv[CHK];
+#pragma unroll
+        for (int e = 0; e < RL; ++e) {
+            const float4 q = src[e];
+            xv[4 * e] = q.x;
+            xv[4 * e + 1] = q.y;
+            xv[4 * e + 2] = q.z;
+            xv[4 * e + 3] = q.w;
+        }
+        const int r0 = it * CHK;
+        L.template group<0>(xv, r0, 4 * it);
+        L.template group<1>(xv, r0, 4 * it + 1);
+        L.template group<2>(xv, r0, 4 * it + 2);
+        L.template group<3>(xv, r0, 4 * it + 3);
+        __syncwarp();
     }
 }
 
 template <int RL>
-cudaError_t launch_down(const LaunchArgs& a, float* rir, float* early, cudaStream_t st)
+cudaError_t launch_hpf_down(const LaunchArgs& a, int Pn, int pmax, const int* counts, const PieceState* pstate,
+                            float* rir, float* early, cudaStream_t st)
 {
-    const int64_t nch = (int64_t)a.B * a.S * a.M * (early ? 2 : 1);
-    if (nch == 0) return cudaSuccess;
-    const int maxlen = a.max_len;
-    dim3 grid((unsigned)nch, (unsigned)((maxlen + kMrOut - 1) / kMrOut));   // channels on x (no 65535 cap)
-    mr_down<RL><<<grid, kMrOutT, 0, st>>>(a, rir, early);
+    const int64_t nthr = (int64_t)a.B * a.S * a.M * (early ? 2 : 1) * pmax;
+    if (nthr == 0) return cudaSuccess;
+    const unsigned nblk = (unsigned)((nthr + kFuseThreads - 1) / kFuseThreads);
+    mr_hpf_down<RL><<<nblk, kFuseThreads, 0, st>>>(a, early != nullptr, Pn, pmax, counts, pstate, rir, early);
     return cudaGetLastError();
 }
 
@@ -732,7 +787,7 @@ cudaError_t launch_synthesize_mr(const LaunchArgs& a, const float* pos_hi, const
     (void)pos_hi;
     (void)pos_lo;     // stage A reads the sorted copies the preparation made
     if (a.B == 0) return cudaSuccess;
-    mr_table<<<1, 256, 0, st>>>(a);
+    mr_table<<<a.down, 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int TA = kSubA * a.rl;
@@ -741,33 +796,30 @@ cudaError_t launch_synthesize_mr(const LaunchArgs& a, const float* pos_hi, const
     if ((e = kernel_residency((const void*)mr_stage_a, kMrThreads, smem, &per_sm)) != cudaSuccess) return e;
     mr_stage_a<<<device_sm_count() * per_sm, kMrThreads, smem, st>>>(a, early != nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // stage B: the high-pass in pieces (warm-up states, then every piece in place)
+    // stages B and C: the high-pass fused with the second resampler, in pieces (warm-up states first)
     const MrPieces pc = mr_pieces(a.fs, a.max_len);
     int* counts = a.mr_counts;
     if ((e = cudaMemsetAsync(counts, 0, sizeof(int) * pc.pmax, st)) != cudaSuccess) return e;
-    mr_room_order<<<(a.B + 255) / 256, 256, 0, st>>>(a, pc.P, pc.pmax, counts);
+    mr_room_order<<<(a.B + 255) / 256, 256, 0, st>>>(a, pc.Pn, pc.pmax, counts);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     PieceState* pstate = reinterpret_cast<PieceState*>(a.mr_pstate);
-    const int64_t nthr = (int64_t)a.B * a.S * a.M * (early ? 2 : 1) * pc.pmax;
-    const unsigned nblk = (unsigned)((nthr + kSeqThreads - 1) / kSeqThreads);
     if (pc.pmax > 1) {
-        mr_hpf_piece<<<nblk, kSeqThreads, 0, st>>>(a, early != nullptr, true, pc.P, pc.W, pc.pmax, counts, pstate);
+        const int64_t nthr = (int64_t)a.B * a.S * a.M * (early ? 2 : 1) * (pc.pmax - 1);
+        const unsigned nblk = (unsigned)((nthr + kSeqThreads - 1) / kSeqThreads);
+        mr_hpf_warm<<<nblk, kSeqThreads, 0, st>>>(a, early != nullptr, pc.Pn, pc.W, pc.pmax, counts, pstate);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    mr_hpf_piece<<<nblk, kSeqThreads, 0, st>>>(a, early != nullptr, false, pc.P, pc.W, pc.pmax, counts, pstate);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // stage C
     switch (a.rl) {
-    case 2: return launch_down<2>(a, rir, early, st);
-    case 3: return launch_down<3>(a, rir, early, st);
-    case 4: return launch_down<4>(a, rir, early, st);
-    case 5: return launch_down<5>(a, rir, early, st);
-    case 6: return launch_down<6>(a, rir, early, st);
-    case 7: return launch_down<7>(a, rir, early, st);
-    case 8: return launch_down<8>(a, rir, early, st);
-    case 9: return launch_down<9>(a, rir, early, st);
-    case 10: return launch_down<10>(a, rir, early, st);
-    case 11: return launch_down<11>(a, rir, early, st);
+    case 2: return launch_hpf_down<2>(a, pc.Pn, pc.pmax, counts, pstate, rir, early, st);
+    case 3: return launch_hpf_down<3>(a, pc.Pn, pc.pmax, counts, pstate, rir, early, st);
+    case 4: return launch_hpf_down<4>(a, pc.Pn, pc.pmax, counts, pstate, rir, early, st);
+    case 5: return launch_hpf_down<5>(a, pc.Pn, pc.pmax, counts, pstate, rir, early, st);
+    case 6: return launch_hpf_down<6>(a, pc.Pn, pc.pmax, counts, pstate, rir, early, st);
+    case 7: return launch_hpf_down<7>(a, pc.Pn, pc.pmax, counts, pstate, rir, early, st);
+    case 8: return launch_hpf_down<8>(a, pc.Pn, pc.pmax, counts, pstate, rir, early, st);
+    case 9: return launch_hpf_down<9>(a, pc.Pn, pc.pmax, counts, pstate, rir, early, st);
+    case 10: return launch_hpf_down<10>(a, pc.Pn, pc.pmax, counts, pstate, rir, early, st);
+    case 11: return launch_hpf_down<11>(a, pc.Pn, pc.pmax, counts, pstate, rir, early, st);
     default: return cudaErrorInvalidValue;
     }
 }
