@@ -300,9 +300,10 @@ inline MrRates mr_rates(double fs)
 // reaches over the W samples before k_s (the pole radius rho of the 80 Hz high-pass at r_l fs gives
 // rho^W <= 1e-9 of the state it forgets).  pmax pieces cover the longest RIR.  The recursion is
 // latency bound per thread (two dependent fused multiply-adds per sample), so the pieces are short
-// enough to give every SM enough independent channels (~32768 intermediate samples splits a
-// 16 kHz batch's 0.1-0.7 s channels into 1-3 pieces) and long enough to keep the warm-up reads (W
-// of every r_l Pn samples) small.
+// enough to give every SM enough independent channels (~16384 intermediate samples splits a
+// 16 kHz batch's 0.1-0.7 s channels into 1-5 pieces) and long enough to keep the warm-up reads (W
+// of every r_l Pn samples) modest; 8192 to 32768 measured within noise of each other on a
+// 1024-room batch, 16384 best on 256 rooms.
 constexpr int kMrHalo = 12;
 
 struct MrPieces {
@@ -317,7 +318,7 @@ inline MrPieces mr_pieces(double fs, int max_len)
     const double rho = std::sqrt(a2);
     MrPieces pc;
     pc.W = ((int)std::ceil(std::log(1e-9) / std::log(rho)) + 63) & ~63;
-    const int P = std::max(32768, 4 * pc.W);
+    const int P = std::max(16384, 2 * pc.W);
     pc.Pn = ((P + r.rl - 1) / r.rl + 3) & ~3;
     pc.pmax = (int)(((int64_t)(max_len > 0 ? max_len : 1) + pc.Pn - 1) / pc.Pn);
     return pc;
