@@ -77,13 +77,35 @@ __device__ __forceinline__ float2 c_rot(float2 a)
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
+// Complex add / subtract as one packed FP32 instruction each (add/sub.rn.f32x2: both halves
+// rounded exactly as the scalar operations).
+__device__ __forceinline__ float2 p_add(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
+// 4-point DFT: six of its eight complex additions go through packed FP32; the two that add the
+// +-i-rotated difference d stay scalar (a packed operation cannot apply the (+, -) signs).
 template <bool INV>
 __device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2& v3)
 {
-    const float2 t0 = c_add(v0, v2), t1 = c_sub(v0, v2), t2 = c_add(v1, v3), t3 = c_rot<INV>(c_sub(v1, v3));
-    v0 = c_add(t0, t2);
+    const float2 t0 = p_add(v0, v2), t1 = p_sub(v0, v2), t2 = p_add(v1, v3), d = p_sub(v1, v3);
+    const float2 t3 = c_rot<INV>(d);
+    v0 = p_add(t0, t2);
+    v2 = p_sub(t0, t2);
     v1 = c_add(t1, t3);
-    v2 = c_sub(t0, t2);
     v3 = c_sub(t1, t3);
 }
 
