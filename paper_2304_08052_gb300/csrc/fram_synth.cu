@@ -6,13 +6,16 @@
 //                      array centre, binning margin, log2 r, and the direct path of every
 //                      (source, mic) pair in FP64 (delay split into a float pair, amplitude
 //                      1/D, Eq. 9 window).
-//   2. item_scan       one CTA: prefix sum of S * ntiles_b -> work-item table (room, source, tile).
-//   3. bin_images      one warp per (room, source): each image's delay to the array centre
+//   2. item_scan       one CTA: prefix sum of S * ntiles_b over the rooms (each room's first
+//                      work item).
+//   3. bin_images      one CTA per (room, source): each image's delay to the array centre
 //                      (the binning key, in samples), a stable counting sort of the images by
 //                      32-sample key block and the first sorted position of every block.
 //                      Per-mic delays differ from the key by at most the array radius in
 //                      samples ("margin").  sort_positions copies the positions into that
-//                      order; item_ranges writes the per-item records.
+//                      order; item_ranges finds each work item's (room, source, tile) by binary
+//                      search over the rooms' first items and writes the item table and the
+//                      per-item records.
 //   4. synth_kernel    persistent warps pull (room, source, tile, mic) units from a counter.
 //                      Per unit the warp owns a private tile buffer in shared memory, computes
 //                      the arrival (delay t = D fs/c0 from a float-pair distance, amplitude,
@@ -172,14 +175,6 @@ __global__ void __launch_bounds__(1024) item_scan(LaunchArgs a)
         a.item_off[a.B] = carry;
         a.hdr->n_items = carry;
     }
-    __syncthreads();
-    // Fill the item table: item -> (room, source << 16 | tile).
-    for (int b = threadIdx.x; b < a.B; b += blockDim.x) {
-        const int nt = a.room[b].ntiles;
-        int q = a.item_off[b];
-        for (int s = 0; s < a.S; ++s)
-            for (int t = 0; t < nt; ++t) a.items[q++] = make_int2(b, (s << 16) | t);
-    }
 }
 
 // One warp per (room, source): binning keys and a stable counting sort of the images by 32-sample
@@ -330,13 +325,25 @@ __device__ __forceinline__ void image_delay(float phx, float phy, float phz, flo
 
 // Work-item records for the synthesis: room, source, tile, and the run of sorted images whose
 // binning key lies within K + margin of the tile (from the 32-sample block table).
+// Item qi belongs to the room b with item_off[b] <= qi < item_off[b + 1] (binary search; rooms
+// without items have empty ranges), as source s and tile tau of its S x ntiles items.  The item
+// table (room, source << 16 | tile) is written here, in parallel, for the adjoint (a serial fill
+// in item_scan's single CTA took ~0.1 ms per large_4096 step).
 __global__ void item_ranges(LaunchArgs a, int64_t max_items)
 {
     const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= max_items || qi >= a.hdr->n_items) return;
-    const int2 it = a.items[qi];
-    const int b = it.x, s = it.y >> 16, tau = it.y & 0xffff;
+    int lo = 0, hi = a.B;                  // item_off[lo] <= qi < item_off[hi] = n_items
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (a.item_off[mid] <= qi) lo = mid;
+        else hi = mid;
+    }
+    const int b = lo;
     const RoomConst rc = a.room[b];
+    const int r = (int)(qi - a.item_off[b]);
+    const int s = r / rc.ntiles, tau = r - s * rc.ntiles;
+    a.items[qi] = make_int2(b, (s << 16) | tau);
     ItemRec ir;
     ir.b = b;
     ir.s = s;
