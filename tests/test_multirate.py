@@ -162,3 +162,36 @@ def test_multirate_full_training_batch_on_sampled_rooms(oracle_mod):
             seg_r = slice(int(ro[i]) + s * sc.M * L, int(ro[i]) + (s + 1) * sc.M * L)
             for got, want in ((hg[seg_g], h_ref[seg_r]), (heg[seg_g], he_ref[seg_r])):
                 assert np.abs(got.astype(np.float64) - want).max() <= TOL * np.abs(want).max(), (b, s)
+
+
+def _piece_outputs(fs):
+    """Output samples per high-pass piece, as the library cuts them: pieces of
+    max(16384, 2 W) intermediate samples (W: the smallest multiple of 64 with rho^W <= 1e-9, rho
+    the pole radius of the 80 Hz high-pass at r_l fs), rounded up to a multiple of 4 outputs."""
+    rl = int(np.floor(np.sqrt(np.floor(1e6 / fs))))
+    k = np.tan(np.pi * 80.0 / (rl * fs))
+    rho = np.sqrt((1.0 - np.sqrt(2.0) * k + k * k) / (1.0 + np.sqrt(2.0) * k + k * k))
+    W = (int(np.ceil(np.log(1e-9) / np.log(rho))) + 63) & ~63
+    P = max(16384, 2 * W)
+    return ((P + rl - 1) // rl + 3) & ~3
+
+
+@pytest.mark.gpu
+def test_multirate_piece_boundaries(oracle_mod):
+    # RIR lengths on and next to multiples of the high-pass pieces: each piece starts its walk 12
+    # groups of r_l intermediate samples before its first output from the warm-up state, so the
+    # outputs on both sides of every boundary (and a last piece of one sample) must match.
+    import torch
+    fs = 16000.0
+    Pn = _piece_outputs(fs)
+    lens = [Pn - 1, Pn, Pn + 1, 2 * Pn, 2 * Pn + 1]
+    B = len(lens)
+    rt60 = np.array([(L - 0.5) / fs for L in lens], np.float32)
+    dims = np.tile(np.array([[6.0, 5.0, 3.0]], np.float32), (B, 1))
+    mic = np.tile(np.array([[[4.0, 2.5, 1.2], [4.05, 2.5, 1.2]]], np.float32), (B, 1, 1))
+    src = np.tile(np.array([[[2.0, 3.0, 1.5]]], np.float32), (B, 1, 1))
+    sc = scenes.Scene("pieces", B, 1, 2, fs, 40, dims, rt60, src, mic, np.full(B, 200, np.int32))
+    ds, h, h_ref, he, he_ref = _run(oracle_mod, sc, 71, early=True)
+    assert [int(x) for x in ds.rir_len] == lens
+    assert _errors(sc, ds, h, h_ref).max() <= TOL
+    assert _errors(sc, ds, he, he_ref).max() <= TOL
