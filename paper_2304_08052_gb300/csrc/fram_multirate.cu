@@ -166,6 +166,17 @@ __device__ __forceinline__ int64_t ceil_div(int64_t n, int64_t d)   // d > 0
     return n >= 0 ? (n + d - 1) / d : -((-n) / d);
 }
 
+// ceil(n / d) for |n| < 2^24 and d > 0 without an integer division: n inv_d (inv_d = 1/d rounded,
+// n exact in float) is within 2^-22 of n / d relative, less than one for every quotient below
+// 2^21, so its ceiling is off by at most one, which an exact integer comparison each way fixes.
+__device__ __forceinline__ int64_t ceil_div_small(int n, int d, float inv_d)
+{
+    int k = __float2int_ru(__fmul_rn((float)n, inv_d));
+    if ((int64_t)(k - 1) * d >= n) --k;
+    else if ((int64_t)k * d < n) ++k;
+    return k;
+}
+
 // Intermediate-signal geometry of room b: L_h, L_m and the offset of channel (s, m).
 struct MrChan {
     int64_t Lh, Lm, off;
@@ -272,6 +283,7 @@ __global__ void __launch_bounds__(kMrThreads) mr_stage_a(LaunchArgs a, bool want
     for (int e = threadIdx.x; e < down * kMrNJ; e += blockDim.x) tab[e] = a.mr_tab[e];
     __syncthreads();
     const double c0 = a.c0, fh = a.fh;
+    const float inv_down = 1.0f / (float)down;
     const int64_t n_units = (int64_t)a.hdr->n_items * M * nsub;
     int u = 0;
     if (lane == 0) u = atomicAdd(&a.hdr->queue, 1);
@@ -343,9 +355,11 @@ __global__ void __launch_bounds__(kMrThreads) mr_stage_a(LaunchArgs a, bool want
                         q = (qh > (double)(ch.Lh - 1)) ? ch.Lh - 1 : (int64_t)qh;
                         Df = (float)D;
                     }
-                    A = a.samp[ir.v0 + p] / Df;
+                    A = __fdividef(a.samp[ir.v0 + p], Df);       // ~2 ulp; no integer decision rests on A
                     const int64_t c = q * up;
-                    const int64_t kmin = ceil_div(c - HL, down);
+                    const int64_t nn = c - HL;
+                    const int64_t kmin = (nn > -(1 << 24) && nn < (1 << 24)) ? ceil_div_small((int)nn, down, inv_down)
+                                                                             : ceil_div(nn, down);
                     valid = Df > 0.0f && A == A && fabsf(A) < 3.0e38f && kmin + 31 >= K0 - 32 && kmin < K0 + TA + 32;
                     bi0 = (int)(kmin - K0 + 32);
                     const int m0 = (int)(kmin * down - c + HL);
