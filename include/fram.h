@@ -84,6 +84,7 @@ typedef struct fram_params {
                            /*    polyphase resamplers of half length 10 max(up, down), DC gain */
                            /*    up; 2nd-order Butterworth high-pass (bilinear, pre-warped).   */
                            /*    Forward only: fram_synthesize_backward returns FRAM_EINVAL.  */
+                           /*    Needs r_l * max_len < 2^30 (FRAM_EINVAL otherwise).           */
     int32_t reserved;      /* must be 0                                                     */
 } fram_params;
 

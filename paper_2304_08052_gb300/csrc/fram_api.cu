@@ -291,8 +291,19 @@ static int check_scene(const fram_scene* sc, bool need_arrays)
     return FRAM_OK;
 }
 
+// Multi-rate mode: the kernels index a channel's intermediate samples (r_l per output sample) in
+// 32-bit integers, so r_l max_len must stay below 2^30 (an RIR of ~97 million samples at r_l = 11).
+static int check_mr_len(const fram_scene* sc, const fram_params* p)
+{
+    if (p->delay_mode == 1 && (int64_t)mr_rates(p->fs).rl * sc->max_len >= ((int64_t)1 << 30))
+        return fail(FRAM_EINVAL, "delay_mode 1 needs r_l * max_len < 2^30 (r_l = %d, max_len = %d)",
+                    mr_rates(p->fs).rl, sc->max_len);
+    return FRAM_OK;
+}
+
 static int check_ws(const fram_scene* sc, const fram_params* p, void* ws, size_t bytes, WsLayout* out)
 {
+    if (check_mr_len(sc, p) != FRAM_OK) return FRAM_EINVAL;
     const WsLayout w = ws_layout(*sc, tile_for(sc, p), p->delay_mode, p->fs);
     if (w.max_tiles > 0xffff) return fail(FRAM_EINVAL, "too many tiles per RIR (raise the tile length)");
     if (!ws) return fail(FRAM_EWORKSPACE, "workspace is null");
@@ -308,6 +319,7 @@ int workspace_bytes_at_launch_tile(const fram_scene* sc, const fram_params* p, s
     if ((rc = check_params(p)) != FRAM_OK) return rc;
     if ((rc = check_scene(sc, false)) != FRAM_OK) return rc;
     if (!bytes) return fail(FRAM_EINVAL, "bytes is null");
+    if ((rc = check_mr_len(sc, p)) != FRAM_OK) return rc;
     const WsLayout w = ws_layout(*sc, tile_for(sc, p), p->delay_mode, p->fs);
     if (w.max_tiles > 0xffff) return fail(FRAM_EINVAL, "too many tiles per RIR (raise the tile length)");
     *bytes = w.total;
@@ -431,6 +443,7 @@ int fram_workspace_size(const fram_scene* scene, const fram_params* p, size_t* b
     if ((rc = check_params(p)) != FRAM_OK) return rc;
     if ((rc = check_scene(scene, false)) != FRAM_OK) return rc;
     if (!bytes) return fail(FRAM_EINVAL, "bytes is null");
+    if ((rc = check_mr_len(scene, p)) != FRAM_OK) return rc;
     const WsLayout w = ws_layout(*scene, tile_of(p), p->delay_mode, p->fs);
     if (w.max_tiles > 0xffff) return fail(FRAM_EINVAL, "too many tiles per RIR (raise the tile length)");
     *bytes = w.total;

@@ -32,6 +32,14 @@ def test_delay_mode_validation():
     for bad in (dict(delay_mode=2), dict(delay_mode=-1), dict(delay_mode=1, fs=6000.0)):
         assert L.fram_workspace_size(ctypes.byref(sc), ctypes.byref(api.Params(**bad).c()),
                                      ctypes.byref(n)) == _lib.FRAM_EINVAL
+    # r_l max_len must stay below 2^30 (32-bit intermediate-sample indices): r_l = 7 at 16 kHz
+    long_sc = _scene_struct(max_len=(1 << 30) // 7 + 1, rir_total=4 * 2 * 3 * ((1 << 30) // 7 + 1))
+    assert L.fram_workspace_size(ctypes.byref(long_sc), ctypes.byref(api.Params(delay_mode=1).c()),
+                                 ctypes.byref(n)) == _lib.FRAM_EINVAL
+    assert b"2^30" in L.fram_last_error()
+    # the continuous mode takes that length (at tile 4096: 37,450 tiles per RIR, below 65536)
+    assert L.fram_workspace_size(ctypes.byref(long_sc), ctypes.byref(api.Params(tile=4096).c()),
+                                 ctypes.byref(n)) == 0
 
 
 def test_backward_is_refused_in_the_multirate_mode():
