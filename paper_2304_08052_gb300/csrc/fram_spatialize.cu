@@ -595,6 +595,21 @@ __global__ void __launch_bounds__(NT, NC == 4096 ? 4 : (NC == 8192 ? 2 : 1)) sp_
         s1 = s0 + 1;
     }
     const int b = A.room0 + cb;
+    if (!tgt && m == 0) {
+        // Mixture at mic 0: sum_s g_s y_s0, the mic-0 images sp_image0 already transformed (the
+        // inverse transform is linear), summed in the time domain in source order.
+        float* out = A.mix + ((int64_t)b * A.M) * A.N;
+        const float* img = A.img0 + (int64_t)cb * A.S * A.N;
+        const int64_t base = (int64_t)j * NC;
+        for (int u = threadIdx.x; u < NC; u += NT) {
+            const int64_t n = base + u;
+            if (n >= A.N) break;
+            float acc = 0.0f;
+            for (int s2 = 0; s2 < A.S; ++s2) acc = __fmaf_rn(A.gains[(int64_t)b * A.S + s2], img[(int64_t)s2 * A.N + n], acc);
+            out[n] = acc;
+        }
+        return;
+    }
     const float2* Hb = tgt ? A.HT : A.HS;
     const int hs = (tgt && A.sep) ? A.ns : A.S;
     __shared__ SpTerm terms[kMaxTerms];
