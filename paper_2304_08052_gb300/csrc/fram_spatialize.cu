@@ -313,8 +313,11 @@ __device__ __forceinline__ Twiddles load_twiddles(const float2* __restrict__ tw_
 }
 
 // Spectra: one CTA per signal window, RIR partition or target-RIR partition of the chunk.
+// Residency at NC = 4096: six CTAs per SM here and five for the inverse transforms (sp_image0,
+// sp_mix), which spill a few bytes at that register budget; four (64 registers) took 13.33 ms per
+// batch_1024 against 12.82, six for all three 14.65.
 template <int NC, int NT>
-__global__ void __launch_bounds__(NT, NC == 4096 ? 4 : (NC == 8192 ? 2 : 1)) sp_forward(SpArgs A)
+__global__ void __launch_bounds__(NT, NC == 4096 ? 6 : (NC == 8192 ? 2 : 1)) sp_forward(SpArgs A)
 {
     extern __shared__ __align__(16) float2 sp_buf[];
     const int nsig = A.rooms * A.S * A.J;
@@ -492,7 +495,7 @@ __device__ __forceinline__ void store_zero_block(float* out, int64_t N, int j)
 
 // Mic-0 image of every (room, source), block by block.
 template <int NC, int NT>
-__global__ void __launch_bounds__(NT, NC == 4096 ? 4 : (NC == 8192 ? 2 : 1)) sp_image0(SpArgs A)
+__global__ void __launch_bounds__(NT, NC == 4096 ? 5 : (NC == 8192 ? 2 : 1)) sp_image0(SpArgs A)
 {
     extern __shared__ __align__(16) float2 sp_buf[];
     const int jid = blockIdx.x;
@@ -579,7 +582,7 @@ __global__ void __launch_bounds__(256) sp_gains(SpArgs A)
 
 // Mixture blocks (room, mic, block) and target blocks (room, speaker, mic, block).
 template <int NC, int NT>
-__global__ void __launch_bounds__(NT, NC == 4096 ? 4 : (NC == 8192 ? 2 : 1)) sp_mix(SpArgs A)
+__global__ void __launch_bounds__(NT, NC == 4096 ? 5 : (NC == 8192 ? 2 : 1)) sp_mix(SpArgs A)
 {
     extern __shared__ __align__(16) float2 sp_buf[];
     const int nmix = A.rooms * A.M * A.J;
