@@ -699,6 +699,9 @@ SpLayout sp_layout(const fram_scene& sc, const fram_spatial& sp, bool sep)
         // stream through HBM rather than staying in L2, which costs less than idle SMs.
         const size_t target = (size_t)4 << 30;
         chunk = (int)std::max<size_t>(1, target / std::max<size_t>(per_room, 1));
+        // equal chunks (e.g. 512 + 512 rooms rather than 690 + 334), so no launch runs half full
+        const int nchunks = (std::max(sc.B, 1) + chunk - 1) / chunk;
+        chunk = (std::max(sc.B, 1) + nchunks - 1) / nchunks;
     }
     w.chunk = std::max(1, std::min(chunk, std::max(sc.B, 1)));
     size_t off = 0;
