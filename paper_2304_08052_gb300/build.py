@@ -49,10 +49,23 @@ def _newest(paths):
 
 
 def build(force: bool = False, verbose: bool = False, extra=(), debug_bounds: bool = False) -> str:
+    out_dir = OUT_DEBUG if debug_bounds else OUT
+    os.makedirs(out_dir, exist_ok=True)
+    # Processes that build at the same time (one per GPU rank) take turns: the first compiles,
+    # the others then find everything up to date.
+    import fcntl
+    with open(os.path.join(out_dir, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose, extra, debug_bounds)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose: bool, extra, debug_bounds: bool) -> str:
     out_dir, lib_path = (OUT_DEBUG, LIB_DEBUG) if debug_bounds else (OUT, LIB)
     if debug_bounds:
         extra = tuple(extra) + ("-DFRAM_DEBUG_BOUNDS",)
-    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     srcs = sources()
     hdr_t = _newest(headers())
