@@ -314,8 +314,8 @@ __device__ __forceinline__ Twiddles load_twiddles(const float2* __restrict__ tw_
 
 // Spectra: one CTA per signal window, RIR partition or target-RIR partition of the chunk.
 // Residency at NC = 4096: six CTAs per SM here and five for the inverse transforms (sp_image0,
-// sp_mix), which spill a few bytes at that register budget; four (64 registers) took 13.33 ms per
-// batch_1024 against 12.82, six for all three 14.65.
+// sp_mix); four (64 registers) took 13.33 ms per batch_1024 against 12.82, six for all three 13.39
+// (14.65 while the spectral sums took four bin pairs per pass and spilled).
 template <int NC, int NT>
 __global__ void __launch_bounds__(NT, NC == 4096 ? 6 : (NC == 8192 ? 2 : 1)) sp_forward(SpArgs A)
 {
@@ -410,7 +410,7 @@ template <int NC, int NT>
 __device__ __forceinline__ void spectral_sum(float2* sp_buf, const SpTerm* terms, int nt)
 {
     constexpr int KP = NC / (2 * NT);          // bin pairs per thread
-    constexpr int KH = KP >= 4 ? 4 : KP;       // pairs per pass (register budget)
+    constexpr int KH = KP >= 2 ? 2 : KP;       // pairs per pass (four spilled at five CTAs per SM)
     static_assert(KP % KH == 0, "pairs per pass must divide the pairs per thread");
 #pragma unroll 1
     for (int h0 = 0; h0 < KP; h0 += KH) {
