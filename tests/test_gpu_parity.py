@@ -307,8 +307,8 @@ def test_nonfinite_image_sets_status_and_is_skipped(oracle_mod):
 # ------------------------------------------------------------------------------------------
 # Adjoint
 # ------------------------------------------------------------------------------------------
-def _grad_compare(oracle_mod, sc, seed, early, rooms=None):
-    ds = api.DeviceScene(sc, _params(sc))
+def _grad_compare(oracle_mod, sc, seed, early, rooms=None, tile=0):
+    ds = api.DeviceScene(sc, _params(sc, tile=tile))
     vs = api.sample(ds, seed=seed)
     # Seeded upstream gradients (the gradient of sum (h - y)^2 has this form for a Gaussian y);
     # the same float32 values go to both sides.
@@ -347,6 +347,15 @@ def test_gradients_tiny(oracle_mod):
 def test_gradients_grad_64(oracle_mod):
     sc = scenes.grad_64(0)
     e = _grad_compare(oracle_mod, sc, seed=1, early=False)
+    assert max(e.values()) < TOL, e
+
+
+@pytest.mark.parametrize("tile", [1024, 2048])
+def test_gradients_multi_tile_items(oracle_mod, tile):
+    # RIRs of 0.3-0.6 s spanning several tiles, at the default tile and at the one the benchmark's
+    # tuner picks on GB300: the adjoint's items and their halos against the oracle.
+    sc = scenes.tiny(seed=11, B=4, S=2, M=3, images=400, t60_lo=0.3, t60_hi=0.6)
+    e = _grad_compare(oracle_mod, sc, seed=9, early=True, tile=tile)
     assert max(e.values()) < TOL, e
 
 
