@@ -359,7 +359,10 @@ __global__ void __launch_bounds__(256) g_gather(LaunchArgs a, const float* __res
     const RoomConst rc = a.room[b];
     if (rc.ntiles < 1) return;
     const int64_t v0 = rc.vs_off + (int64_t)s * rc.n_vs;
-    for (int p = threadIdx.x; p < rc.n_vs; p += blockDim.x) a.samp[v0 + p] = g[v0 + a.perm[v0 + p]];
+    for (int p = threadIdx.x; p < rc.n_vs; p += blockDim.x) {
+        const int q = a.perm[v0 + p];
+        if (FRAM_GUARD(a.hdr, q >= 0 && q < rc.n_vs && v0 + rc.n_vs <= a.n_vs_total)) a.samp[v0 + p] = g[v0 + q];
+    }
 }
 
 // Asynchronous 4-byte global -> shared copy; a zero source size fills zeros and reads nothing.

@@ -277,7 +277,8 @@ __global__ void __launch_bounds__(256) bin_images(LaunchArgs a, const float* __r
         __syncwarp();
         if (lane == leader && act) hist[j] = basepos + __popc(peers);
         __syncwarp();
-        if (act) {
+        if (act && FRAM_GUARD(a.hdr, j >= 0 && j < NB && basepos + rank >= 0 && basepos + rank < n &&
+                              v0 + n <= a.n_vs_total)) {
             a.perm[v0 + basepos + rank] = i;
             a.skey[v0 + basepos + rank] = j << 5;
         }
@@ -294,7 +295,9 @@ __global__ void __launch_bounds__(256) sort_positions(LaunchArgs a, const float*
     if (rc.ntiles < 1) return;      // a room the prologue rejected has no sorted order
     const int64_t v0 = rc.vs_off + (int64_t)s * rc.n_vs;
     for (int p = threadIdx.x; p < rc.n_vs; p += blockDim.x) {
-        const int64_t i = v0 + a.perm[v0 + p];
+        const int q = a.perm[v0 + p];
+        if (!FRAM_GUARD(a.hdr, q >= 0 && q < rc.n_vs && v0 + rc.n_vs <= a.n_vs_total)) continue;
+        const int64_t i = v0 + q;
         const float* ph = pos_hi + 3 * i;
         float lx = 0.0f, ly = 0.0f, lz = 0.0f;
         if (pos_lo) { const float* pl = pos_lo + 3 * i; lx = pl[0]; ly = pl[1]; lz = pl[2]; }
@@ -342,6 +345,7 @@ __global__ void item_ranges(LaunchArgs a, int64_t max_items)
     const int b = lo;
     const RoomConst rc = a.room[b];
     const int r = (int)(qi - a.item_off[b]);
+    if (!FRAM_GUARD(a.hdr, rc.ntiles >= 1 && r >= 0 && r < a.S * rc.ntiles)) return;
     const int s = r / rc.ntiles, tau = r - s * rc.ntiles;
     a.items[qi] = make_int2(b, (s << 16) | tau);
     ItemRec ir;
@@ -368,8 +372,11 @@ __global__ void __launch_bounds__(256) amp_gather(LaunchArgs a, const float* __r
     const RoomConst rc = a.room[b];
     if (rc.ntiles < 1) return;      // a room the prologue rejected has no sorted order
     const int64_t v0 = rc.vs_off + (int64_t)s * rc.n_vs;
-    for (int p = threadIdx.x; p < rc.n_vs; p += blockDim.x)
-        a.samp[v0 + p] = exp2f(g[v0 + a.perm[v0 + p]] * rc.log2r);
+    for (int p = threadIdx.x; p < rc.n_vs; p += blockDim.x) {
+        const int q = a.perm[v0 + p];
+        if (FRAM_GUARD(a.hdr, q >= 0 && q < rc.n_vs && v0 + rc.n_vs <= a.n_vs_total))
+            a.samp[v0 + p] = exp2f(g[v0 + q] * rc.log2r);
+    }
 }
 
 // Arrival record (delta, P, a, b) of the tap identity for t = n_c + delta (|delta| <= 1/2),

@@ -1,6 +1,7 @@
 """Cases run against one build of libfram (the library FRAM_LIBRARY names, else the release
-build): sample, synthesise with the early RIR and run the adjoint with early-RIR upstream
-gradients over the half lengths, tile lengths and scene shapes the parity tests sweep, and the
+build): sample, synthesise with the early RIR, run the adjoint with early-RIR upstream
+gradients and carry its gradients back through the sampler, over the half lengths, tile lengths
+and scene shapes the parity tests sweep; spatialise ragged signals with targets; and run the
 multi-rate path (delay_mode 1) with the early RIR at every second-resampler rate, ragged tiles and
 a batch whose high-pass runs in several pieces; then print, per case, the device status bits and
 a SHA-256 of every output.  tests/test_gpu_debug_bounds.py
@@ -34,8 +35,24 @@ def run_case(sc, tile, seed):
     G = torch.empty(ds.rir_total, device="cuda").normal_(generator=gen)
     Ge = torch.empty(ds.rir_total, device="cuda").normal_(generator=gen)
     gv, gm, gs, gr = api.synthesize_backward_raw(ds, vs.pos_hi, vs.pos_lo, vs.g, vs.r, G, Ge)
+    # through the sampler (draws of `seed` held fixed), with a random gradient on the amplitudes
+    gg = torch.empty(ds.n_vs_total, device="cuda").normal_(generator=gen)
+    sb = api.sample_backward(ds, seed, gv, grad_g=gg, grad_r=gr, grad_src_in=gs, grad_mic_in=gm)
     torch.cuda.synchronize()
-    return {"status": ds.status(), "out": _digest(h, he, gv, gm, gs, gr)}
+    return {"status": ds.status(), "out": _digest(h, he, gv, gm, gs, gr, *sb)}
+
+
+def run_spatial(sc, tile, seed, n_speech, N, block):
+    ds = api.DeviceScene(sc, api.Params(fs=sc.fs, half_len=sc.half_len, tile=tile))
+    vs = api.sample(ds, seed=seed)
+    h = api.synthesize(ds, vs)
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    x = torch.empty((ds.B, ds.S, N), device="cuda").normal_(generator=gen)
+    x[:, :, N // 3:N // 3 + 700] = 0.0           # a silent stretch: zero-flagged windows
+    lev = torch.empty((ds.B, ds.S), device="cuda").uniform_(-5.0, 5.0, generator=gen)
+    mix, tg, gains = api.spatialize(ds, h, x, lev, n_speech, targets=True, block=block)
+    torch.cuda.synchronize()
+    return {"status": ds.status() | api.spatialize_status(ds), "out": _digest(mix, tg, gains)}
 
 
 def run_multirate(sc, tile, seed):
@@ -66,6 +83,10 @@ def cases():
         sc = scenes.tiny(seed=int(fs) % 89, B=3, S=2, M=2, images=120, fs=fs, t60_lo=t60[0], t60_hi=t60[1])
         for tile in (256, 2048):
             out[f"mr_{int(fs)}_tile{tile}"] = run_multirate(sc, tile, 40 + tile % 7)
+    # spatialisation: ragged signal lengths against the block, one and several speakers
+    for N, block, ns in ((5000, 0, 1), (12345, 4096, 2), (3000, 8192, 2)):
+        sc = scenes.tiny(seed=N % 97, B=3, S=3, M=2, images=200, t60_lo=0.1, t60_hi=0.3)
+        out[f"sp_N{N}_block{block}"] = run_spatial(sc, 0, 21, ns, N, block)
     # 48 rooms of the 1024-room training batch (T60 0.1-0.7 s): up to five high-pass pieces per channel
     out["mr_batch_1024_48rooms"] = run_multirate(scenes.batch_1024(0).subset(range(48)), 0, 9)
     return out

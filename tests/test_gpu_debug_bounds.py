@@ -2,8 +2,9 @@
 in for a memory checker, which this GPU pool does not offer: in it, the synthesis and adjoint
 kernels check every arrival's shared-buffer footprint, every gather window against its staged
 buffer, and every work unit's image rows and RIR range before the access, the multi-rate kernels
-every unit's intermediate-signal range, filter row and RIR range, and all of them record
-FRAM_DEV_BOUNDS instead of running outside a buffer.  Over the half lengths, tile lengths and
+every unit's intermediate-signal range, filter row and RIR range, the binning and gather kernels
+every slot and permutation value of the sorted order, and all of them record FRAM_DEV_BOUNDS
+instead of running outside a buffer.  Over the half lengths, tile lengths and
 scene shapes the parity tests sweep, no guard may fire, and the outputs must equal the release
 build's bit for bit (the guards change no arithmetic)."""
 import json
