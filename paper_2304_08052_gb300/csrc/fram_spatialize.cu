@@ -493,6 +493,34 @@ __device__ __forceinline__ void store_zero_block(float* out, int64_t N, int j)
         if (base + u < N) out[base + u] = 0.0f;
 }
 
+// Term list of one output block, built by all threads at once: thread i < ncand tests candidate
+// i (cand(i, term) loads its flags and gain and returns whether the term is nonzero), so the
+// flag loads of all candidates are in flight together instead of one after another in a single
+// thread; the nonzero terms are compacted in candidate order.  Returns the number of terms, in
+// every thread; synchronises.
+template <int NT, typename Cand>
+__device__ __forceinline__ int build_terms(SpTerm* terms, int ncand, Cand cand)
+{
+    static_assert(NT >= kMaxTerms, "one candidate per thread");
+    __shared__ int wcnt[NT / 32];
+    SpTerm t{};
+    const bool ok = (int)threadIdx.x < ncand && cand((int)threadIdx.x, t);
+    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) wcnt[w] = __popc(bal);
+    __syncthreads();
+    int base = 0, total = 0;
+#pragma unroll
+    for (int u = 0; u < NT / 32; ++u) {
+        const int c = wcnt[u];
+        base += u < w ? c : 0;
+        total += c;
+    }
+    if (ok) terms[base + __popc(bal & ((1u << lane) - 1u))] = t;
+    __syncthreads();
+    return total;
+}
+
 // Mic-0 image of every (room, source), block by block.
 template <int NC, int NT>
 __global__ void __launch_bounds__(NT, NC == 4096 ? 5 : (NC == 8192 ? 2 : 1)) sp_image0(SpArgs A)
@@ -501,18 +529,14 @@ __global__ void __launch_bounds__(NT, NC == 4096 ? 5 : (NC == 8192 ? 2 : 1)) sp_
     const int jid = blockIdx.x;
     const int cb = jid / (A.S * A.J), s = (jid / A.J) % A.S, j = jid % A.J;
     __shared__ SpTerm terms[kMaxTerms];
-    __shared__ int nt_s;
     const int64_t xi = ((int64_t)cb * A.S + s) * A.J, hi = (((int64_t)cb * A.S + s) * A.M) * A.Q;   // mic 0
     const Twiddles tw = load_twiddles<NC, NT>(A.tw_c);
-    if (threadIdx.x == 0) {       // nonzero terms only, in q order
-        int nt = 0;
-        for (int q = 0; q < A.Q && q <= j; ++q)
-            if (A.XF[xi + j - q] && A.HF[hi + q])
-                terms[nt++] = SpTerm{A.XS + (xi + j - q) * NC, A.HS + (hi + q) * NC, 1.0f};
-        nt_s = nt;
-    }
-    __syncthreads();
-    const int nt = nt_s;
+    // nonzero terms only, in q order
+    const int nt = build_terms<NT>(terms, min(A.Q, j + 1), [&](int q, SpTerm& t) {
+        const bool nz = (A.XF[xi + j - q] != 0) & (A.HF[hi + q] != 0);
+        t = SpTerm{A.XS + (xi + j - q) * NC, A.HS + (hi + q) * NC, 1.0f};
+        return nz;
+    });
     float* out = A.img0 + ((int64_t)cb * A.S + s) * A.N;
     if (nt == 0) {
         store_zero_block<NC, NT>(out, A.N, j);
@@ -616,23 +640,19 @@ __global__ void __launch_bounds__(NT, NC == 4096 ? 5 : (NC == 8192 ? 2 : 1)) sp_
     const float2* Hb = tgt ? A.HT : A.HS;
     const int hs = (tgt && A.sep) ? A.ns : A.S;
     __shared__ SpTerm terms[kMaxTerms];
-    __shared__ int nt_s;
     const int* Hf = tgt ? A.HTF : A.HF;
     const Twiddles tw = load_twiddles<NC, NT>(A.tw_c);
-    if (threadIdx.x == 0) {       // nonzero terms only, in (source, q) order
-        int nt = 0;
-        for (int s = s0; s < s1; ++s) {
-            const float g = A.gains[(int64_t)b * A.S + s];
-            for (int q = 0; q < A.Q && q <= j; ++q) {
-                const int64_t xi = ((int64_t)cb * A.S + s) * A.J + (j - q);
-                const int64_t hi = (((int64_t)cb * hs + s) * A.M + m) * A.Q + q;
-                if (g != 0.0f && A.XF[xi] && Hf[hi]) terms[nt++] = SpTerm{A.XS + xi * NC, Hb + hi * NC, g};
-            }
-        }
-        nt_s = nt;
-    }
-    __syncthreads();
-    const int nt = nt_s;
+    // nonzero terms only, in (source, q) order: candidate i is source s0 + i / nq, partition i % nq
+    const int nq = min(A.Q, j + 1);
+    const int nt = build_terms<NT>(terms, (s1 - s0) * nq, [&](int i, SpTerm& t) {
+        const int s = s0 + i / nq, q = i - (i / nq) * nq;
+        const float g = A.gains[(int64_t)b * A.S + s];
+        const int64_t xi = ((int64_t)cb * A.S + s) * A.J + (j - q);
+        const int64_t hi = (((int64_t)cb * hs + s) * A.M + m) * A.Q + q;
+        const bool nz = (g != 0.0f) & (A.XF[xi] != 0) & (Hf[hi] != 0);
+        t = SpTerm{A.XS + xi * NC, Hb + hi * NC, g};
+        return nz;
+    });
     float* out = tgt ? A.tg + (((int64_t)b * A.ns + s0) * A.M + m) * A.N : A.mix + ((int64_t)b * A.M + m) * A.N;
     if (nt == 0) {
         store_zero_block<NC, NT>(out, A.N, j);
