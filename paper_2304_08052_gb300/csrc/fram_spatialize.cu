@@ -185,11 +185,34 @@ struct Twiddles {
     __device__ __forceinline__ float2 operator()(int k) const { return c_mul(TA[k >> 7], TB[k & 127]); }
 };
 
+// Destination of an inverse transform's kept half: complex point n >= NC/2 of the window holds
+// real samples 2 (n - NC/2) and 2 (n - NC/2) + 1 of output block j, written times `scale` to
+// out[base + 2 (n - NC/2) + {0, 1}] while the index is below N; pair stores when out is 8-byte
+// aligned.
+struct BlockStore {
+    float* out;
+    int64_t N, base;
+    float scale;
+    bool v2;
+    __device__ __forceinline__ void put(int n, float2 z, int NC) const
+    {
+        const int64_t u = base + 2 * (int64_t)(n - NC / 2);
+        if (v2 && u + 1 < N) {
+            *reinterpret_cast<float2*>(out + u) = make_float2(z.x * scale, z.y * scale);
+        } else {
+            if (u < N) out[u] = z.x * scale;
+            if (u + 1 < N) out[u + 1] = z.y * scale;
+        }
+    }
+};
+
 // One Stockham stage of radix R over the NC-point buffer, stride Ns (the length already done).
 // Column j takes buf[j + r NC/R] (r < R), twiddles them by w^(r (j mod Ns) NC/(Ns R)), runs an
-// R-point DFT and writes buf[(j - j mod Ns) R + j mod Ns + r Ns].
+// R-point DFT and writes buf[(j - j mod Ns) R + j mod Ns + r Ns].  With `bs` (last stage only,
+// Ns R = NC) the outputs n = j + r Ns >= NC/2 go to the output block instead, and the stage ends
+// without a barrier.
 template <int NC, int NT, int R, bool INV, int Ns>
-__device__ __forceinline__ void fft_stage(float2* buf, const Twiddles& tw)
+__device__ __forceinline__ void fft_stage(float2* buf, const Twiddles& tw, const BlockStore* bs = nullptr)
 {
     constexpr int NJ = NC / R;
     static_assert(NJ % NT == 0, "threads must divide the columns");
@@ -249,13 +272,24 @@ __device__ __forceinline__ void fft_stage(float2* buf, const Twiddles& tw)
         }
         dft<R, INV>(v[p]);
     }
+    // output r of the DFT sits in v[p][r], or in v[p][4 (r % 4) + r / 4] after the 4 x 4 DFT16
+    if constexpr (Ns * R == NC) {
+        if (bs) {
+#pragma unroll
+            for (int p = 0; p < PER; ++p) {
+                const int j = tid + p * NT;          // j < Ns: the output base is j itself
+#pragma unroll
+                for (int r = R / 2; r < R; ++r) bs->put(j + r * Ns, R == 16 ? v[p][4 * (r & 3) + (r >> 2)] : v[p][r], NC);
+            }
+            return;
+        }
+    }
     __syncthreads();
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
         const int j = tid + p * NT;
         const int jm = j & (Ns - 1);
         const int base = (j - jm) * R + jm;
-        // output r of the DFT sits in v[p][r], or in v[p][4 (r % 4) + r / 4] after the 4 x 4 DFT16
         auto out = [&](int r) { return R == 16 ? v[p][4 * (r & 3) + (r >> 2)] : v[p][r]; };
         if constexpr (Ns % 256 == 0) {
             const int sb = sw(base);
@@ -271,19 +305,22 @@ __device__ __forceinline__ void fft_stage(float2* buf, const Twiddles& tw)
 
 // In-place complex FFT of NC points (a power of two >= 8) in shared memory; the buffer must be
 // complete (synchronised) on entry and is complete on exit.  Forward: X[k] = sum x[n] w^(nk),
-// w = e^(-2 pi i/NC); inverse: w = e^(+2 pi i/NC), unscaled.
+// w = e^(-2 pi i/NC); inverse: w = e^(+2 pi i/NC), unscaled.  With `bs` the last stage writes
+// the upper half of the result to the output block instead (the buffer is then left incomplete).
 template <int NC, int NT, bool INV, int Ns = 1>
-__device__ __forceinline__ void cfft(float2* buf, const Twiddles& tw)
+__device__ __forceinline__ void cfft(float2* buf, const Twiddles& tw, const BlockStore* bs = nullptr)
 {
-    if constexpr (Ns * 16 <= NC) {
+    if constexpr (Ns * 16 == NC) {
+        fft_stage<NC, NT, 16, INV, Ns>(buf, tw, bs);
+    } else if constexpr (Ns * 16 < NC) {
         fft_stage<NC, NT, 16, INV, Ns>(buf, tw);
-        cfft<NC, NT, INV, Ns * 16>(buf, tw);
+        cfft<NC, NT, INV, Ns * 16>(buf, tw, bs);
     } else if constexpr (Ns * 8 == NC) {
-        fft_stage<NC, NT, 8, INV, Ns>(buf, tw);
+        fft_stage<NC, NT, 8, INV, Ns>(buf, tw, bs);
     } else if constexpr (Ns * 4 == NC) {
-        fft_stage<NC, NT, 4, INV, Ns>(buf, tw);
+        fft_stage<NC, NT, 4, INV, Ns>(buf, tw, bs);
     } else if constexpr (Ns * 2 == NC) {
-        fft_stage<NC, NT, 2, INV, Ns>(buf, tw);
+        fft_stage<NC, NT, 2, INV, Ns>(buf, tw, bs);
     }
 }
 
@@ -375,20 +412,24 @@ __global__ void __launch_bounds__(NT, NC == 4096 ? 6 : (NC == 8192 ? 2 : 1)) sp_
     if (!nz) return;
     cfft<NC, NT, false>(sp_buf, tw);
     // Split: with Zc = conj(Z[NC-k]), E = (Z[k] + Zc)/2, O = -i (Z[k] - Zc)/2,
-    // X[k] = E + w_P^k O and X[NC-k] = conj(E - w_P^k O).
-    for (int k = threadIdx.x; k <= NC / 2; k += NT) {
-        if (k == 0) {
-            const float2 z = sp_buf[sw(0)];
-            dst[0] = make_float2(z.x + z.y, z.x - z.y);       // DC, Nyquist
-            continue;
-        }
-        const float2 zk = sp_buf[sw(k)], zc = c_conj(sp_buf[sw(NC - k)]);
+    // X[k] = E + w_P^k O and X[NC-k] = conj(E - w_P^k O).  Stored in the paired layout: slot
+    // p < NC/2 holds (X[p], X[NC-p]), slot 0 (X[0] packed as (DC, Nyquist), X[NC/2]).
+    float4* dst4 = reinterpret_cast<float4*>(dst);
+    for (int k = threadIdx.x; k < NC / 2; k += NT) {
+        const int kk = k == 0 ? NC / 2 : k;
+        const float2 zk = sp_buf[sw(kk)], zc = c_conj(sp_buf[sw(NC - kk)]);
         const float2 E = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y));
         const float2 D = c_sub(zk, zc);
         const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
-        const float2 WO = c_mul(__ldg(&A.tw_r[k]), O);
-        dst[k] = c_add(E, WO);
-        if (k != NC - k) dst[NC - k] = c_conj(c_sub(E, WO));
+        const float2 WO = c_mul(__ldg(&A.tw_r[kk]), O);
+        const float2 Xk = c_add(E, WO);
+        if (k == 0) {
+            const float2 z = sp_buf[sw(0)];
+            dst4[0] = make_float4(z.x + z.y, z.x - z.y, Xk.x, Xk.y);      // (DC, Nyquist), X[NC/2]
+        } else {
+            const float2 Xc = c_conj(c_sub(E, WO));
+            dst4[k] = make_float4(Xk.x, Xk.y, Xc.x, Xc.y);
+        }
     }
 }
 
@@ -397,21 +438,28 @@ __device__ __forceinline__ float2 packed_mul(float2 a, float2 b, bool dc)
     return dc ? make_float2(a.x * b.x, a.y * b.y) : c_mul(a, b);
 }
 
-// sp_buf[k] = sum_t g_t X_t[k] H_t[k] (packed products) over nt terms.  Each thread owns bin
-// pairs (2p, 2p+1), p = tid + i NT, loaded as float4 with all of a term's loads in flight before
-// the products; accumulators stay in registers, in term order (deterministic).
+// One term g X H of an output block's spectral sum.
 struct SpTerm {
     const float2* X;
     const float2* H;
     float g;
 };
 
+// sp_buf <- the packed spectrum Z of the real inverse transform of Y = sum_t g_t X_t H_t over nt
+// terms (spectra in the paired layout: slot p holds bins p and NC - p, slot 0 bins 0 (DC and
+// Nyquist packed) and NC/2).  Each thread owns slots p = tid + i NT, loaded as float4 with all of
+// a term's loads in flight before the products; accumulators stay in registers, in term order
+// (deterministic).  Both bins of a conjugate pair are then in one thread, so the pre-step of the
+// half-length real inverse runs in registers: with Yc = conj(Y[NC-k]), E = (Y[k] + Yc)/2,
+// O = (Y[k] - Yc)/2 conj(w_P^k), Z[k] = E + i O and Z[NC-k] = conj(E - i O); Z[0] from the
+// packed DC and Nyquist.  The real sample t of the window is afterwards the unscaled inverse
+// transform of Z at t/2 (.x even t, .y odd t), times 1/NC.
 template <int NC, int NT>
-__device__ __forceinline__ void spectral_sum(float2* sp_buf, const SpTerm* terms, int nt)
+__device__ __forceinline__ void spectral_sum(float2* sp_buf, const SpTerm* terms, int nt, const float2* __restrict__ tw_r)
 {
-    constexpr int KP = NC / (2 * NT);          // bin pairs per thread
-    constexpr int KH = KP >= 2 ? 2 : KP;       // pairs per pass (four spilled at five CTAs per SM)
-    static_assert(KP % KH == 0, "pairs per pass must divide the pairs per thread");
+    constexpr int KP = NC / (2 * NT);          // slots per thread
+    constexpr int KH = KP >= 2 ? 2 : KP;       // slots per pass (four spilled at five CTAs per SM)
+    static_assert(KP % KH == 0, "slots per pass must divide the slots per thread");
 #pragma unroll 1
     for (int h0 = 0; h0 < KP; h0 += KH) {
         float4 acc[KH];
@@ -443,44 +491,17 @@ __device__ __forceinline__ void spectral_sum(float2* sp_buf, const SpTerm* terms
 #pragma unroll
         for (int i = 0; i < KH; ++i) {
             const int p = threadIdx.x + (h0 + i) * NT;
-            sp_buf[sw(2 * p)] = make_float2(acc[i].x, acc[i].y);
-            sp_buf[sw(2 * p + 1)] = make_float2(acc[i].z, acc[i].w);
+            // pair (k, NC - k): k = p, or NC/2 (self-paired) in slot 0, whose first bin is DC / Nyquist
+            const int k = p == 0 ? NC / 2 : p;
+            const float2 xk = p == 0 ? make_float2(acc[i].z, acc[i].w) : make_float2(acc[i].x, acc[i].y);
+            const float2 xc = make_float2(acc[i].z, -acc[i].w);
+            const float2 E = make_float2(0.5f * (xk.x + xc.x), 0.5f * (xk.y + xc.y));
+            const float2 D = c_sub(xk, xc);
+            const float2 O = c_mul(make_float2(0.5f * D.x, 0.5f * D.y), c_conj(__ldg(&tw_r[k])));
+            sp_buf[sw(k)] = make_float2(E.x - O.y, E.y + O.x);                       // E + i O
+            if (p == 0) sp_buf[sw(0)] = make_float2(0.5f * (acc[i].x + acc[i].y), 0.5f * (acc[i].x - acc[i].y));
+            else sp_buf[sw(NC - k)] = make_float2(E.x + O.y, O.x - E.y);               // conj(E - i O)
         }
-    }
-}
-
-// sp_buf <- inverse real transform of the packed spectrum already in sp_buf (complete on entry);
-// real sample t of the window is then sp_buf[t/2].x or .y times 1/NC.
-template <int NC, int NT>
-__device__ void inverse_real(float2* sp_buf, const Twiddles& tw, const float2* __restrict__ tw_r)
-{
-    for (int k = threadIdx.x; k <= NC / 2; k += NT) {
-        if (k == 0) {
-            const float2 a = sp_buf[sw(0)];
-            sp_buf[sw(0)] = make_float2(0.5f * (a.x + a.y), 0.5f * (a.x - a.y));
-            continue;
-        }
-        const float2 xk = sp_buf[sw(k)], xc = c_conj(sp_buf[sw(NC - k)]);
-        const float2 E = make_float2(0.5f * (xk.x + xc.x), 0.5f * (xk.y + xc.y));
-        const float2 D = c_sub(xk, xc);
-        const float2 O = c_mul(make_float2(0.5f * D.x, 0.5f * D.y), c_conj(__ldg(&tw_r[k])));
-        sp_buf[sw(k)] = make_float2(E.x - O.y, E.y + O.x);                   // E + i O
-        if (k != NC - k) sp_buf[sw(NC - k)] = make_float2(E.x + O.y, O.x - E.y);   // conj(E - i O)
-    }
-    __syncthreads();
-    cfft<NC, NT, true>(sp_buf, tw);
-}
-
-// Writes the second half of the inverse window (output block j) to out[j Bk + u], u < Bk, < N.
-template <int NC, int NT>
-__device__ __forceinline__ void store_block(const float2* sp_buf, float* out, int64_t N, int j, float scale)
-{
-    const int64_t base = (int64_t)j * NC;
-    for (int n = NC / 2 + threadIdx.x; n < NC; n += NT) {
-        const float2 z = sp_buf[sw(n)];
-        const int64_t u = base + 2 * (int64_t)(n - NC / 2);
-        if (u < N) out[u] = z.x * scale;
-        if (u + 1 < N) out[u + 1] = z.y * scale;
     }
 }
 
@@ -542,10 +563,10 @@ __global__ void __launch_bounds__(NT, NC == 4096 ? 5 : (NC == 8192 ? 2 : 1)) sp_
         store_zero_block<NC, NT>(out, A.N, j);
         return;
     }
-    spectral_sum<NC, NT>(sp_buf, terms, nt);
+    spectral_sum<NC, NT>(sp_buf, terms, nt, A.tw_r);
     __syncthreads();
-    inverse_real<NC, NT>(sp_buf, tw, A.tw_r);
-    store_block<NC, NT>(sp_buf, out, A.N, j, 1.0f / NC);
+    const BlockStore bs{out, A.N, (int64_t)j * NC, 1.0f / NC, (reinterpret_cast<uintptr_t>(out) & 7) == 0};
+    cfft<NC, NT, true>(sp_buf, tw, &bs);
 }
 
 // Block-wide FP64 sum in a fixed tree; the result is valid in thread 0.
@@ -658,10 +679,10 @@ __global__ void __launch_bounds__(NT, NC == 4096 ? 5 : (NC == 8192 ? 2 : 1)) sp_
         store_zero_block<NC, NT>(out, A.N, j);
         return;
     }
-    spectral_sum<NC, NT>(sp_buf, terms, nt);
+    spectral_sum<NC, NT>(sp_buf, terms, nt, A.tw_r);
     __syncthreads();
-    inverse_real<NC, NT>(sp_buf, tw, A.tw_r);
-    store_block<NC, NT>(sp_buf, out, A.N, j, 1.0f / NC);
+    const BlockStore bs{out, A.N, (int64_t)j * NC, 1.0f / NC, (reinterpret_cast<uintptr_t>(out) & 7) == 0};
+    cfft<NC, NT, true>(sp_buf, tw, &bs);
 }
 
 template <int NC, int NT>
