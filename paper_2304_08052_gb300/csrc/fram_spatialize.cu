@@ -211,8 +211,11 @@ struct BlockStore {
 // R-point DFT and writes buf[(j - j mod Ns) R + j mod Ns + r Ns].  With `bs` (last stage only,
 // Ns R = NC) the outputs n = j + r Ns >= NC/2 go to the output block instead, and the stage ends
 // without a barrier.
+// With `vin` (first stage only, one column per thread) the column's inputs come from the
+// thread's registers instead of the buffer, and no barrier precedes the writes.
 template <int NC, int NT, int R, bool INV, int Ns>
-__device__ __forceinline__ void fft_stage(float2* buf, const Twiddles& tw, const BlockStore* bs = nullptr)
+__device__ __forceinline__ void fft_stage(float2* buf, const Twiddles& tw, const BlockStore* bs = nullptr,
+                                          const float2* vin = nullptr)
 {
     constexpr int NJ = NC / R;
     static_assert(NJ % NT == 0, "threads must divide the columns");
@@ -224,8 +227,13 @@ __device__ __forceinline__ void fft_stage(float2* buf, const Twiddles& tw, const
     for (int p = 0; p < PER; ++p) {
         const int j = tid + p * NT;
         const int sj = sw(j);                  // sw(j + r NJ) = sw(j) + r NJ: NJ is a multiple of 256
+        if (Ns == 1 && PER == 1 && vin) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[p][r] = buf[sj + r * NJ];
+            for (int r = 0; r < R; ++r) v[p][r] = vin[r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[p][r] = buf[sj + r * NJ];
+        }
         if constexpr (Ns > 1) {
             // w^r for r < R from two table entries (w and w^4 for radix 8), at most 2 products deep
             const int step = (j & (Ns - 1)) * (NC / (Ns * R));
@@ -284,7 +292,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, const Twiddles& tw, const
             return;
         }
     }
-    __syncthreads();
+    if (!(Ns == 1 && PER == 1 && vin)) __syncthreads();
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
         const int j = tid + p * NT;
@@ -307,13 +315,17 @@ __device__ __forceinline__ void fft_stage(float2* buf, const Twiddles& tw, const
 // complete (synchronised) on entry and is complete on exit.  Forward: X[k] = sum x[n] w^(nk),
 // w = e^(-2 pi i/NC); inverse: w = e^(+2 pi i/NC), unscaled.  With `bs` the last stage writes
 // the upper half of the result to the output block instead (the buffer is then left incomplete).
+// With `vin` the first stage (radix 16, one column j = thread per thread: NC = 16 NT) takes its
+// inputs x[j + r NT], r < 16, from the thread's registers; the buffer is then not read first.
 template <int NC, int NT, bool INV, int Ns = 1>
-__device__ __forceinline__ void cfft(float2* buf, const Twiddles& tw, const BlockStore* bs = nullptr)
+__device__ __forceinline__ void cfft(float2* buf, const Twiddles& tw, const BlockStore* bs = nullptr,
+                                     const float2* vin = nullptr)
 {
+    static_assert(Ns > 1 || NC == 16 * NT || NC < 256, "register inputs need one first-stage column per thread");
     if constexpr (Ns * 16 == NC) {
-        fft_stage<NC, NT, 16, INV, Ns>(buf, tw, bs);
+        fft_stage<NC, NT, 16, INV, Ns>(buf, tw, bs, vin);
     } else if constexpr (Ns * 16 < NC) {
-        fft_stage<NC, NT, 16, INV, Ns>(buf, tw);
+        fft_stage<NC, NT, 16, INV, Ns>(buf, tw, nullptr, vin);
         cfft<NC, NT, INV, Ns * 16>(buf, tw, bs);
     } else if constexpr (Ns * 8 == NC) {
         fft_stage<NC, NT, 8, INV, Ns>(buf, tw, bs);
@@ -350,11 +362,12 @@ __device__ __forceinline__ Twiddles load_twiddles(const float2* __restrict__ tw_
 }
 
 // Spectra: one CTA per signal window, RIR partition or target-RIR partition of the chunk.
-// Residency at NC = 4096: six CTAs per SM here and five for the inverse transforms (sp_image0,
-// sp_mix); four (64 registers) took 13.33 ms per batch_1024 against 12.82, six for all three 13.39
-// (14.65 while the spectral sums took four bin pairs per pass and spilled).
+// Residency at NC = 4096: five CTAs per SM (48 registers) for every transform kernel.  With the
+// first stage fed from registers, six here spilled the 16 inputs (10.84 against 10.76 ms per
+// batch_1024); before that six here beat five (12.82 ms), and four for all (64 registers) took
+// 13.33, six for all 13.39.
 template <int NC, int NT>
-__global__ void __launch_bounds__(NT, NC == 4096 ? 6 : (NC == 8192 ? 2 : 1)) sp_forward(SpArgs A)
+__global__ void __launch_bounds__(NT, NC == 4096 ? 5 : (NC == 8192 ? 2 : 1)) sp_forward(SpArgs A)
 {
     extern __shared__ __align__(16) float2 sp_buf[];
     const int nsig = A.rooms * A.S * A.J;
@@ -395,22 +408,29 @@ __global__ void __launch_bounds__(NT, NC == 4096 ? 6 : (NC == 8192 ? 2 : 1)) sp_
         dst = (tgt ? A.HT : A.HS) + (int64_t)jid * NC;
         flag = (tgt ? A.HTF : A.HF) + jid;
     }
+    // Thread j's points j + r NT (r < 16) are exactly the first radix-16 stage's column j, so
+    // they stay in registers.
+    static_assert(NC == 16 * NT, "one first-stage column per thread");
     bool nonzero = false;
-    for (int n = threadIdx.x; n < NC; n += NT) {
+    float2 vin[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int n = threadIdx.x + r * NT;
         const int t0 = 2 * n, t1 = 2 * n + 1;
         const int64_t i0 = start + t0, i1 = start + t1;
         const float a = (t0 < lim && i0 >= 0 && i0 < len) ? src[i0] : 0.f;
         const float b = (t1 < lim && i1 >= 0 && i1 < len) ? src[i1] : 0.f;
-        sp_buf[sw(n)] = make_float2(a, b);
+        vin[r] = make_float2(a, b);
         nonzero = nonzero || a != 0.0f || b != 0.0f;
     }
     const Twiddles tw = load_twiddles<NC, NT>(A.tw_c);
     // An all-zero window (a silent stretch of a source, an RIR partition past its end) has a zero
-    // spectrum: it is flagged and skipped by every sum that would read it.
+    // spectrum: it is flagged and skipped by every sum that would read it.  (The barrier also
+    // completes the twiddle tables.)
     const int nz = __syncthreads_or(nonzero ? 1 : 0);
     if (threadIdx.x == 0) *flag = nz;
     if (!nz) return;
-    cfft<NC, NT, false>(sp_buf, tw);
+    cfft<NC, NT, false>(sp_buf, tw, nullptr, vin);
     // Split: with Zc = conj(Z[NC-k]), E = (Z[k] + Zc)/2, O = -i (Z[k] - Zc)/2,
     // X[k] = E + w_P^k O and X[NC-k] = conj(E - w_P^k O).  Stored in the paired layout: slot
     // p < NC/2 holds (X[p], X[NC-p]), slot 0 (X[0] packed as (DC, Nyquist), X[NC/2]).
