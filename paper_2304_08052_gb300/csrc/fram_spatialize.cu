@@ -178,11 +178,15 @@ __device__ __forceinline__ void dft(float2* v)
 // two stages spread over all banks while unit-stride accesses stay conflict-free.
 __device__ __forceinline__ int sw(int e) { return e ^ ((e >> 4) & 15); }
 
-// exp(-2 pi i k / NC) as TA[k >> 7] * TB[k & 127] from two small tables in shared memory.
+// exp(-2 pi i k / NC) as TA[k >> 7] * TB[k & 127] from two small tables in shared memory.  TB
+// entry i sits at i + i / 16 (one pad entry per 16): the stages look TB up at strides 1 to 128
+// entries across a half-warp, which the plain layout folds onto 2 to 8 addresses of one bank
+// pair, and the padded one spreads over distinct bank pairs (or one broadcast address).
+__device__ __forceinline__ int tb_pos(int i) { return i + (i >> 4); }
 struct Twiddles {
     const float2* TA;
     const float2* TB;
-    __device__ __forceinline__ float2 operator()(int k) const { return c_mul(TA[k >> 7], TB[k & 127]); }
+    __device__ __forceinline__ float2 operator()(int k) const { return c_mul(TA[k >> 7], TB[tb_pos(k & 127)]); }
 };
 
 // Destination of an inverse transform's kept half: complex point n >= NC/2 of the window holds
@@ -353,9 +357,9 @@ template <int NC, int NT>
 __device__ __forceinline__ Twiddles load_twiddles(const float2* __restrict__ tw_c)
 {
     static_assert(NC >= 128 && NC / 128 <= 128, "two-level table covers 128 x 128 entries");
-    __shared__ float2 ta[NC / 128], tb[128];
+    __shared__ float2 ta[NC / 128], tb[128 + 8];
     for (int i = threadIdx.x; i < 128; i += NT) {
-        tb[i] = __ldg(&tw_c[i]);
+        tb[tb_pos(i)] = __ldg(&tw_c[i]);
         if (i < NC / 128) ta[i] = __ldg(&tw_c[i * 128]);
     }
     return Twiddles{ta, tb};
@@ -589,47 +593,93 @@ __global__ void __launch_bounds__(NT, NC == 4096 ? 5 : (NC == 8192 ? 2 : 1)) sp_
     cfft<NC, NT, true>(sp_buf, tw, &bs);
 }
 
-// Block-wide FP64 sum in a fixed tree; the result is valid in thread 0.
-__device__ double block_sum(double v, double* red)
+constexpr int kGainThreads = 512;
+
+// Sums over n < N of y_a[n] y_b[n] for nq <= NQ pairs (a[q], b[q]) at once (b ignored when SQ:
+// the energies y_a^2), into out[q] (shared, written by thread 0).  Each thread takes samples
+// n = tid + k kGainThreads in runs of 32, summed in FP32 per run and in FP64 across runs; the
+// warps' FP64 sums are then added in warp order.  Every pair's loads of one sample are
+// independent, so a pass keeps NQ (or 2 NQ) loads in flight per sample.
+template <int NQ, bool SQ>
+__device__ void pair_sums(const float* __restrict__ y, int64_t N, const int* a, const int* b, int nq, double* red,
+                          double* out)
 {
+    const float* ya[NQ];
+    const float* yb[NQ];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = 0; q < NQ; ++q) {
+        ya[q] = y + (int64_t)a[q] * N;
+        yb[q] = y + (int64_t)b[q] * N;
+    }
+    double acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+    for (int64_t n0 = threadIdx.x; n0 < N; n0 += 32 * (int64_t)kGainThreads) {
+        const int cnt = (int)min((int64_t)32, (N - n0 + kGainThreads - 1) / kGainThreads);
+        float part[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) part[q] = 0.f;
+#pragma unroll 4
+        for (int kk = 0; kk < cnt; ++kk) {
+            const int64_t n = n0 + (int64_t)kk * kGainThreads;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                if (q < nq) {
+                    const float u = __ldg(ya[q] + n);
+                    const float v = SQ ? u : __ldg(yb[q] + n);
+                    part[q] = __fmaf_rn(u, v, part[q]);
+                }
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] += part[q];
+    }
+    constexpr int NW = kGainThreads / 32;
+    const int w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double v = acc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[q * NW + w] = v;
+    }
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = v;
-    __syncthreads();
-    double t = 0.0;
     if (threadIdx.x == 0)
-        for (int i = 0; i < nw; ++i) t += red[i];
-    return t;
+        for (int q = 0; q < nq; ++q) {
+            double t = 0.0;
+            for (int i = 0; i < NW; ++i) t += red[q * NW + i];
+            out[q] = t;
+        }
+    __syncthreads();
 }
 
-// Per room: E_s = sum y_s0^2, speech cross terms, then the gains (FP64, as the levels define them).
-__global__ void __launch_bounds__(256) sp_gains(SpArgs A)
+// Per room: E_s = sum y_s0^2 (every source in one pass), the speech cross terms (pairs s < t <
+// n_speech, four per pass), then the gains (FP64, as the levels define them).
+__global__ void __launch_bounds__(kGainThreads) sp_gains(SpArgs A)
 {
-    __shared__ double red[8];
-    __shared__ double E[8], Cx[8][8];
+    __shared__ double red[8 * (kGainThreads / 32)];
+    __shared__ double E[8], Cx[8][8], tmp[4];
     const int cb = blockIdx.x;
     const float* y = A.img0 + (int64_t)cb * A.S * A.N;
-    // pairs (s, t): s == t energies for every source, s < t cross terms between speakers
-    for (int s = 0; s < A.S; ++s)
-        for (int t = s; t < (s < A.ns ? A.ns : s + 1); ++t) {
-            const float* ys = y + (int64_t)s * A.N;
-            const float* yt = y + (int64_t)t * A.N;
-            double acc = 0.0;
-            float part = 0.f;
-            int cnt = 0;
-            for (int64_t n = threadIdx.x; n < A.N; n += blockDim.x) {
-                part = __fmaf_rn(ys[n], yt[n], part);
-                if (++cnt == 32) { acc += part; part = 0.f; cnt = 0; }   // FP32 runs of 32, FP64 across
-            }
-            acc += part;
-            const double tot = block_sum(acc, red);
-            if (threadIdx.x == 0) {
-                if (s == t) E[s] = tot;
-                else Cx[s][t] = Cx[t][s] = tot;
-            }
+    {
+        int a[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] = min(q, A.S - 1);
+        pair_sums<8, true>(y, A.N, a, a, A.S, red, E);
+    }
+    const int npairs = A.ns * (A.ns - 1) / 2;
+    for (int p0 = 0; p0 < npairs; p0 += 4) {
+        int a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {       // pair p0 + i in (s, t) order, s < t < n_speech
+            int p = min(p0 + i, npairs - 1), s = 0;
+            while (p >= A.ns - 1 - s) { p -= A.ns - 1 - s; ++s; }
+            a[i] = s;
+            b[i] = s + 1 + p;
         }
+        pair_sums<4, false>(y, A.N, a, b, min(4, npairs - p0), red, tmp);
+        if (threadIdx.x == 0)
+            for (int i = 0; i < min(4, npairs - p0); ++i) Cx[a[i]][b[i]] = Cx[b[i]][a[i]] = tmp[i];
+    }
     if (threadIdx.x == 0) {
         const int b = A.room0 + cb;
         double g[8];
@@ -719,7 +769,7 @@ cudaError_t launch_chunk(const SpArgs& A, cudaStream_t st)
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     sp_image0<NC, NT><<<A.rooms * A.S * A.J, NT, smem, st>>>(A);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    sp_gains<<<A.rooms, 256, 0, st>>>(A);
+    sp_gains<<<A.rooms, kGainThreads, 0, st>>>(A);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int nmix = A.rooms * A.J * A.M * (1 + (A.tg ? A.ns : 0));
     sp_mix<NC, NT><<<nmix, NT, smem, st>>>(A);
