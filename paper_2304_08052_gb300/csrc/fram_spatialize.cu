@@ -60,6 +60,7 @@ struct SpArgs {
     int* HF;
     int* HTF;                      // (== HF when !sep)
     float* img0;                   // [rooms][S][N]
+    double* eparts;                // [rooms][S][J]: energy of each block of img0
     Header* hdr;
 };
 
@@ -192,21 +193,31 @@ struct Twiddles {
 // Destination of an inverse transform's kept half: complex point n >= NC/2 of the window holds
 // real samples 2 (n - NC/2) and 2 (n - NC/2) + 1 of output block j, written times `scale` to
 // out[base + 2 (n - NC/2) + {0, 1}] while the index is below N; pair stores when out is 8-byte
-// aligned.
+// aligned.  put() returns the sum of squares of the samples it wrote.
 struct BlockStore {
     float* out;
     int64_t N, base;
     float scale;
     bool v2;
-    __device__ __forceinline__ void put(int n, float2 z, int NC) const
+    __device__ __forceinline__ float put(int n, float2 z, int NC) const
     {
         const int64_t u = base + 2 * (int64_t)(n - NC / 2);
+        const float a = z.x * scale, b = z.y * scale;
+        float e = 0.f;
         if (v2 && u + 1 < N) {
-            *reinterpret_cast<float2*>(out + u) = make_float2(z.x * scale, z.y * scale);
+            *reinterpret_cast<float2*>(out + u) = make_float2(a, b);
+            e = __fmaf_rn(b, b, a * a);
         } else {
-            if (u < N) out[u] = z.x * scale;
-            if (u + 1 < N) out[u + 1] = z.y * scale;
+            if (u < N) {
+                out[u] = a;
+                e = a * a;
+            }
+            if (u + 1 < N) {
+                out[u + 1] = b;
+                e = __fmaf_rn(b, b, e);
+            }
         }
+        return e;
     }
 };
 
@@ -218,8 +229,8 @@ struct BlockStore {
 // With `vin` (first stage only, one column per thread) the column's inputs come from the
 // thread's registers instead of the buffer, and no barrier precedes the writes.
 template <int NC, int NT, int R, bool INV, int Ns>
-__device__ __forceinline__ void fft_stage(float2* buf, const Twiddles& tw, const BlockStore* bs = nullptr,
-                                          const float2* vin = nullptr)
+__device__ __forceinline__ float fft_stage(float2* buf, const Twiddles& tw, const BlockStore* bs = nullptr,
+                                           const float2* vin = nullptr)
 {
     constexpr int NJ = NC / R;
     static_assert(NJ % NT == 0, "threads must divide the columns");
@@ -287,13 +298,14 @@ __device__ __forceinline__ void fft_stage(float2* buf, const Twiddles& tw, const
     // output r of the DFT sits in v[p][r], or in v[p][4 (r % 4) + r / 4] after the 4 x 4 DFT16
     if constexpr (Ns * R == NC) {
         if (bs) {
+            float e = 0.f;                           // sum of squares of the samples stored
 #pragma unroll
             for (int p = 0; p < PER; ++p) {
                 const int j = tid + p * NT;          // j < Ns: the output base is j itself
 #pragma unroll
-                for (int r = R / 2; r < R; ++r) bs->put(j + r * Ns, R == 16 ? v[p][4 * (r & 3) + (r >> 2)] : v[p][r], NC);
+                for (int r = R / 2; r < R; ++r) e += bs->put(j + r * Ns, R == 16 ? v[p][4 * (r & 3) + (r >> 2)] : v[p][r], NC);
             }
-            return;
+            return e;
         }
     }
     if (!(Ns == 1 && PER == 1 && vin)) __syncthreads();
@@ -313,30 +325,33 @@ __device__ __forceinline__ void fft_stage(float2* buf, const Twiddles& tw, const
         }
     }
     __syncthreads();
+    return 0.f;
 }
 
 // In-place complex FFT of NC points (a power of two >= 8) in shared memory; the buffer must be
 // complete (synchronised) on entry and is complete on exit.  Forward: X[k] = sum x[n] w^(nk),
 // w = e^(-2 pi i/NC); inverse: w = e^(+2 pi i/NC), unscaled.  With `bs` the last stage writes
-// the upper half of the result to the output block instead (the buffer is then left incomplete).
+// the upper half of the result to the output block instead (the buffer is then left incomplete)
+// and returns the sum of squares of the samples this thread stored (0 without `bs`).
 // With `vin` the first stage (radix 16, one column j = thread per thread: NC = 16 NT) takes its
 // inputs x[j + r NT], r < 16, from the thread's registers; the buffer is then not read first.
 template <int NC, int NT, bool INV, int Ns = 1>
-__device__ __forceinline__ void cfft(float2* buf, const Twiddles& tw, const BlockStore* bs = nullptr,
+__device__ __forceinline__ float cfft(float2* buf, const Twiddles& tw, const BlockStore* bs = nullptr,
                                      const float2* vin = nullptr)
 {
     static_assert(Ns > 1 || NC == 16 * NT || NC < 256, "register inputs need one first-stage column per thread");
     if constexpr (Ns * 16 == NC) {
-        fft_stage<NC, NT, 16, INV, Ns>(buf, tw, bs, vin);
+        return fft_stage<NC, NT, 16, INV, Ns>(buf, tw, bs, vin);
     } else if constexpr (Ns * 16 < NC) {
         fft_stage<NC, NT, 16, INV, Ns>(buf, tw, nullptr, vin);
-        cfft<NC, NT, INV, Ns * 16>(buf, tw, bs);
+        return cfft<NC, NT, INV, Ns * 16>(buf, tw, bs);
     } else if constexpr (Ns * 8 == NC) {
-        fft_stage<NC, NT, 8, INV, Ns>(buf, tw, bs);
+        return fft_stage<NC, NT, 8, INV, Ns>(buf, tw, bs);
     } else if constexpr (Ns * 4 == NC) {
-        fft_stage<NC, NT, 4, INV, Ns>(buf, tw, bs);
-    } else if constexpr (Ns * 2 == NC) {
-        fft_stage<NC, NT, 2, INV, Ns>(buf, tw, bs);
+        return fft_stage<NC, NT, 4, INV, Ns>(buf, tw, bs);
+    } else {
+        static_assert(Ns * 2 == NC, "power-of-two length");
+        return fft_stage<NC, NT, 2, INV, Ns>(buf, tw, bs);
     }
 }
 
@@ -583,24 +598,38 @@ __global__ void __launch_bounds__(NT, NC == 4096 ? 5 : (NC == 8192 ? 2 : 1)) sp_
         return nz;
     });
     float* out = A.img0 + ((int64_t)cb * A.S + s) * A.N;
+    double* ep = A.eparts + ((int64_t)cb * A.S + s) * A.J + j;
     if (nt == 0) {
         store_zero_block<NC, NT>(out, A.N, j);
+        if (threadIdx.x == 0) *ep = 0.0;
         return;
     }
     spectral_sum<NC, NT>(sp_buf, terms, nt, A.tw_r);
     __syncthreads();
     const BlockStore bs{out, A.N, (int64_t)j * NC, 1.0f / NC, (reinterpret_cast<uintptr_t>(out) & 7) == 0};
-    cfft<NC, NT, true>(sp_buf, tw, &bs);
+    // the block's energy for the levels: each thread's FP32 sum of squares of the samples it
+    // stored, added in FP64 across the warp (fixed tree) and across warps in warp order
+    double e = cfft<NC, NT, true>(sp_buf, tw, &bs);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    __shared__ double ew[NT / 32];
+    if ((threadIdx.x & 31) == 0) ew[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < NT / 32; ++w) t += ew[w];
+        *ep = t;
+    }
 }
 
 constexpr int kGainThreads = 512;
 
-// Sums over n < N of y_a[n] y_b[n] for nq <= NQ pairs (a[q], b[q]) at once (b ignored when SQ:
-// the energies y_a^2), into out[q] (shared, written by thread 0).  Each thread takes samples
-// n = tid + k kGainThreads in runs of 32, summed in FP32 per run and in FP64 across runs; the
-// warps' FP64 sums are then added in warp order.  Every pair's loads of one sample are
-// independent, so a pass keeps NQ (or 2 NQ) loads in flight per sample.
-template <int NQ, bool SQ>
+// Sums over n < N of y_a[n] y_b[n] for nq <= NQ pairs (a[q], b[q]) at once, into out[q]
+// (shared, written by thread 0).  Each thread takes samples n = tid + k kGainThreads in runs of
+// 32, summed in FP32 per run and in FP64 across runs; the warps' FP64 sums are then added in warp
+// order.  Every pair's loads of one sample are independent, so a pass keeps 2 NQ loads in flight
+// per sample.
+template <int NQ>
 __device__ void pair_sums(const float* __restrict__ y, int64_t N, const int* a, const int* b, int nq, double* red,
                           double* out)
 {
@@ -626,7 +655,7 @@ __device__ void pair_sums(const float* __restrict__ y, int64_t N, const int* a, 
             for (int q = 0; q < NQ; ++q)
                 if (q < nq) {
                     const float u = __ldg(ya[q] + n);
-                    const float v = SQ ? u : __ldg(yb[q] + n);
+                    const float v = __ldg(yb[q] + n);
                     part[q] = __fmaf_rn(u, v, part[q]);
                 }
         }
@@ -652,20 +681,22 @@ __device__ void pair_sums(const float* __restrict__ y, int64_t N, const int* a, 
     __syncthreads();
 }
 
-// Per room: E_s = sum y_s0^2 (every source in one pass), the speech cross terms (pairs s < t <
-// n_speech, four per pass), then the gains (FP64, as the levels define them).
+// Per room: E_s = sum y_s0^2 from the block energies sp_image0 left (added in block order), the
+// speech cross terms (pairs s < t < n_speech, four per pass over the images), then the gains
+// (FP64, as the levels define them).
 __global__ void __launch_bounds__(kGainThreads) sp_gains(SpArgs A)
 {
-    __shared__ double red[8 * (kGainThreads / 32)];
+    __shared__ double red[4 * (kGainThreads / 32)];
     __shared__ double E[8], Cx[8][8], tmp[4];
     const int cb = blockIdx.x;
     const float* y = A.img0 + (int64_t)cb * A.S * A.N;
-    {
-        int a[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) a[q] = min(q, A.S - 1);
-        pair_sums<8, true>(y, A.N, a, a, A.S, red, E);
+    if (threadIdx.x < A.S) {
+        const double* ep = A.eparts + ((int64_t)cb * A.S + threadIdx.x) * A.J;
+        double t = 0.0;
+        for (int j = 0; j < A.J; ++j) t += ep[j];
+        E[threadIdx.x] = t;
     }
+    __syncthreads();
     const int npairs = A.ns * (A.ns - 1) / 2;
     for (int p0 = 0; p0 < npairs; p0 += 4) {
         int a[4], b[4];
@@ -676,7 +707,7 @@ __global__ void __launch_bounds__(kGainThreads) sp_gains(SpArgs A)
             a[i] = s;
             b[i] = s + 1 + p;
         }
-        pair_sums<4, false>(y, A.N, a, b, min(4, npairs - p0), red, tmp);
+        pair_sums<4>(y, A.N, a, b, min(4, npairs - p0), red, tmp);
         if (threadIdx.x == 0)
             for (int i = 0; i < min(4, npairs - p0); ++i) Cx[a[i]][b[i]] = Cx[b[i]][a[i]] = tmp[i];
     }
@@ -779,7 +810,7 @@ cudaError_t launch_chunk(const SpArgs& A, cudaStream_t st)
 struct SpLayout {
     int Bk, J, Q, chunk;
     bool sep;
-    size_t header, tw_c, tw_r, XS, HS, HT, XF, HF, HTF, img0, gains, total;
+    size_t header, tw_c, tw_r, XS, HS, HT, XF, HF, HTF, img0, eparts, gains, total;
 };
 
 // Default block: 4096 (the smallest transform: more CTAs per SM hide the stage barriers better
@@ -832,6 +863,7 @@ SpLayout sp_layout(const fram_scene& sc, const fram_spatial& sp, bool sep)
     w.HF = take(sizeof(int) * C * sc.S * sc.M * w.Q);
     w.HTF = sep ? take(sizeof(int) * C * sp.n_speech * sc.M * w.Q) : w.HF;
     w.img0 = take(sizeof(float) * C * sc.S * (size_t)sp.n_samples);
+    w.eparts = take(sizeof(double) * C * sc.S * w.J);
     w.gains = take(sizeof(float) * (size_t)std::max(sc.B, 1) * sc.S);
     w.total = off;
     return w;
@@ -907,6 +939,7 @@ extern "C" int fram_spatialize(const fram_scene* scene, const fram_spatial* sp, 
     A.HS = reinterpret_cast<float2*>(base + w.HS);
     A.HT = reinterpret_cast<float2*>(base + w.HT);
     A.img0 = reinterpret_cast<float*>(base + w.img0);
+    A.eparts = reinterpret_cast<double*>(base + w.eparts);
     A.XF = reinterpret_cast<int*>(base + w.XF);
     A.HF = reinterpret_cast<int*>(base + w.HF);
     A.HTF = reinterpret_cast<int*>(base + w.HTF);
