@@ -38,7 +38,7 @@ METRIC = "multi-ch RIRs/s and sinc-taps/s (fwd, fwd+bwd) at 1 GB300, % of roofli
 # DRAM bytes (read + write) of one synth_kernel launch per output sample, from one ncu capture
 # (large_4096, first 256 rooms, 283357184 output samples: 0.0641 GB read + 1.0731 GB written);
 # reported only while the synthesis source is the one that was measured (its SHA-256 prefix).
-SYNTH_TRAFFIC = {"source_sha256": "5c644faf470bbf2e", "bytes_per_sample": (64043776 + 1072916480) / 283357184}
+SYNTH_TRAFFIC = {"source_sha256": "96f1c3b045dc4cc7", "bytes_per_sample": (64156160 + 1072641792) / 283357184}
 
 # Kernels of libfram per fwd step: sample_prologue, sample_kernel; room_prologue, item_scan,
 # bin_images, sort_positions, item_ranges (preparation); amp_gather, synth_kernel (synthesis).
