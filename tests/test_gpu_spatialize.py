@@ -170,6 +170,7 @@ def test_single_sample_rirs_and_silent_sources(oracle_mod):
     (48000.0, 63, 2, 1, 3, 48000, (0.6, 1.0)),    # long RIRs: up to 12 partitions per output block
     (16000.0, 40, 1, 1, 1, 20000, (0.2, 0.4)),    # one speaker, one mic, no noise
     (16000.0, 40, 5, 3, 4, 30000, (0.1, 0.3)),    # three speakers and two noise sources
+    (16000.0, 40, 8, 6, 2, 9000, (0.1, 0.2)),     # the most sources, 15 speaker pairs (four passes)
 ])
 def test_spatialize_shapes(oracle_mod, fs, K, S, n_speech, M, N, t60):
     sc = scenes.tiny(seed=77 + S, B=2, S=S, M=M, images=100, fs=fs, K=K, t60_lo=t60[0], t60_hi=t60[1])
