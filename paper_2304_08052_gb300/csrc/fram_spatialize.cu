@@ -11,19 +11,26 @@
 // IFFT(sum_q X_{j-q} H_q) (the first half wraps around).  Real transforms of length P run as
 // complex transforms of length NC = P/2 = Bk on even/odd pairs, with the usual split
 // post-processing; the half spectrum is stored as NC complex bins with the Nyquist bin's real
-// part packed into the imaginary part of bin 0, so the bin-wise product is elementwise.
+// part packed into the imaginary part of bin 0, so the bin-wise product is elementwise.  Bins are
+// stored conjugate-paired (slot p: bins p and NC - p), so the inverse's pre-step, which combines
+// k with NC - k, runs in the registers of the thread that summed both.
 //
 // The complex transform is one CTA's Stockham autosort FFT in shared memory: radix-16 stages
 // (one 16-point DFT per thread and column, computed as 4 x 4 in registers), then one radix-8, -4
 // or -2 stage; each stage reads all its inputs into registers, synchronises and writes, so one
-// NC-element buffer suffices.
+// NC-element buffer suffices.  A forward transform's first stage starts from the registers the
+// inputs were loaded into; an inverse transform's last stage writes the kept half of the window
+// straight to the output.
 //
 // Pipeline per chunk of rooms (by default about 4 GiB of spectra, so every launch fills the GPU):
 //   sp_forward  spectra of every signal window and RIR partition (and target-RIR partition)
-//   sp_image0   mic-0 image of every source, block by block (for the levels)
-//   sp_gains    per room: energies and speech cross terms at mic 0 -> gains (FP64)
-//   sp_mix      per (room, mic, block): IFFT(sum_s g_s sum_q X H) -> mixture; per (room,
-//               speaker, mic, block): IFFT(g_s sum_q X H') -> targets
+//   sp_image0   mic-0 image of every source, block by block, with each block's energy (for the
+//               levels)
+//   sp_gains    per room: energies (from the blocks) and speech cross terms at mic 0 -> gains
+//               (FP64)
+//   sp_mix      per (room, mic, block): IFFT(sum_s g_s sum_q X H) -> mixture (mic 0 summed from
+//               the images instead); per (room, speaker, mic, block): IFFT(g_s sum_q X H') ->
+//               targets
 #include <algorithm>
 #include <cmath>
 
